@@ -1,0 +1,154 @@
+/*
+ * sarabande_gb300.h -- C ABI of the GB300 (sm_103a) implementation of the hot
+ * path of SARABANDE (Sunseri et al. 2022, arXiv 2210.10206): FFT-based 3- and
+ * 4-point correlation functions of a periodic gridded density field.
+ *
+ * The pipeline behind every measurement call is the paper's (Sec. 3, Fig.
+ * workflow): binned angular kernels (Algorithms 1-2) -> convolution
+ * coefficients a^b_lm(x) / c^b_m(x) by FFT (Algorithms 3-4, Eq. almconv) ->
+ * delta-weighted combination (Algorithms 5-8).  All work runs in CUDA kernels
+ * of this library on one GPU.
+ *
+ * Conventions shared by every call:
+ *  - Grid: periodic, C order, cell units (box side N, cell volume 1, Sec. 4.3).
+ *    3D index (i, j, k) <-> (z, y, x); 2D (i, j) <-> (y, x).  phi = atan2(y, x),
+ *    theta from +z; Y_lm orthonormal with the Condon-Shortley phase.
+ *  - Bins: bin b holds the integer minimum-image offsets r with
+ *    e_b^2 < |r|^2 <= e_{b+1}^2 (Algorithm 1 mask).  e^2 is computed in double
+ *    and snapped to the nearest integer when within 1e-9 relative of it.
+ *  - Coefficients are correlations a(x) = sum_r K(r) delta(x + r) (footnote to
+ *    Eq. almconv), masks are 0/1 (no 1/V_b), outputs are sums over all grid
+ *    points (Algorithms 5-8).  The full 3PCF carries (-1)^l / sqrt(2l+1)
+ *    (Eq. alm_to_zeta_clean); the projected 3PCF has no 1/(2 pi)^2.
+ *  - Ownership: the caller owns every pointer it passes.  The library never
+ *    keeps a caller pointer after a call returns and never writes `field`.
+ *  - Synchronicity: measurement calls return after the results are in the
+ *    caller's host arrays.  Results are always float64 host arrays.
+ *  - Threads: one context per host thread.
+ *  - Errors: every call returns sbg_status; on error the output contents are
+ *    unspecified and sbg_last_error() holds a one-line reason.
+ */
+#ifndef SARABANDE_GB300_H
+#define SARABANDE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sbg_context sbg_context;
+
+typedef enum {
+  SBG_OK = 0,
+  SBG_ERR_INVALID_ARG = -1,       /* NULL pointer, bad count, bad flag or enum value */
+  SBG_ERR_UNSUPPORTED_SHAPE = -2, /* side not a power of two in range, or not cubic/square */
+  SBG_ERR_BIN_RANGE = -3,         /* edges not increasing, edges[0] < 0, or edges[nbins] >= N/2 */
+  SBG_ERR_EMPTY_BIN = -4,         /* a bin holds no cell and SBG_NORMALIZED was asked for */
+  SBG_ERR_OUT_OF_MEMORY = -5,     /* device allocation failed or exceeds the context budget */
+  SBG_ERR_CUDA = -6,              /* a CUDA runtime call failed */
+  SBG_ERR_TIMEOUT = -7,           /* a bounded device wait gave up */
+  SBG_ERR_INTERNAL = -8
+} sbg_status;
+
+typedef enum { SBG_F32 = 0, SBG_F64 = 1 } sbg_dtype;
+
+/* Arithmetic of the 4PCF combination (FFTs are FP32, final sums FP64).
+ * FP32: SIMT FP32 products and accumulation.
+ * BF16X3: tcgen05 tensor cores, each operand split into bf16 hi + lo, three
+ *         products hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM. */
+typedef enum { SBG_PREC_FP32 = 0, SBG_PREC_BF16X3 = 1 } sbg_precision;
+
+enum {
+  SBG_3PCF = 1u,            /* NPCF = 3 (Sec. 3.3 `NPCF`)                          */
+  SBG_4PCF = 2u,            /* NPCF = 4                                            */
+  SBG_NORMALIZED = 4u,      /* divide by N_gal prod nbar V_bin (Sec. 2.5)          */
+  SBG_SUBTRACT_MEAN = 8u,   /* delta <- delta - mean(delta) first (Sec. 4.1)       */
+  SBG_FIELD_ON_DEVICE = 16u /* `field` is a device pointer of the context's device */
+};
+
+/* Create a context on CUDA device `cuda_device`.  hbm_budget_bytes caps the
+ * device memory the context may hold (0: no cap beyond what is free).  The
+ * context owns its buffers and cached plans until sbg_destroy. */
+sbg_status sbg_create(int cuda_device, size_t hbm_budget_bytes, sbg_context** out);
+
+/* Release every resource of `ctx`; NULL is accepted and ignored. */
+void sbg_destroy(sbg_context* ctx);
+
+/* Run subsequent work on `cuda_stream` (a cudaStream_t of the context's device,
+ * e.g. torch.cuda.current_stream().cuda_stream); NULL selects the context's
+ * own stream.  The caller keeps the stream alive while the context uses it. */
+sbg_status sbg_set_stream(sbg_context* ctx, void* cuda_stream);
+
+/* Static string naming a status code. */
+const char* sbg_status_string(sbg_status s);
+
+/* Reason for the last failure on `ctx` (owned by ctx, valid until its next call). */
+const char* sbg_last_error(const sbg_context* ctx);
+
+/* Number of even-parity Lambda = (l1, l2, l3) with every l <= lmax, the loop
+ * set of Algorithm 6 (23 at lmax 3, 42 at lmax 4).  lmax in 0..10. */
+sbg_status sbg_lambda_count(int lmax, int* n_lambda);
+
+/* The same list as 3 ints per entry (l1, l2, l3) in the order of the first
+ * axis of zeta4: l1 then l2 ascending, l3 from |l1-l2| to min(l1+l2, lmax). */
+sbg_status sbg_lambda_list(int lmax, int* l123);
+
+/* Full (3D) 3PCF and 4PCF of one periodic field (Secs. 2.1 and 2.3;
+ * Algorithms 1, 3, 5, 6).
+ *   field   : [n0][n1][n2] of `dtype`, host pointer unless SBG_FIELD_ON_DEVICE.
+ *   shape   : n0 = n1 = n2 = N, a power of two in 8..512.
+ *   edges   : nbins + 1 strictly increasing doubles, edges[0] >= 0,
+ *             edges[nbins] < N/2; 1 <= nbins <= 20.
+ *   lmax3   : 0..10, used when flags has SBG_3PCF.
+ *   lmax4   : 0..5, used when flags has SBG_4PCF.
+ *   zeta3   : out, [lmax3+1][nbins][nbins] real
+ *             zeta_l^{b1 b2} = (-1)^l/sqrt(2l+1) sum_x delta sum_m a^{b1}_lm a^{b2 *}_lm.
+ *   zeta4   : out, [n_lambda(lmax4)][nbins][nbins][nbins] real, Lambda order of
+ *             sbg_lambda_list; zeta = Re sum_x delta sum_M C^Lambda_M a a a with
+ *             C^Lambda_M = (-1)^(l1+l2+l3) (3j), m3 = -(m1+m2) (Eq. mu, Sec. 2.3).
+ *             Every bin triple is written, diagonals included.
+ * Either output may be NULL when its flag is not set. */
+sbg_status sbg_full(sbg_context* ctx, const void* field, sbg_dtype dtype, const int64_t shape[3],
+                    const double* edges, int nbins, int lmax3, int lmax4, sbg_precision prec,
+                    unsigned flags, double* zeta3, double* zeta4);
+
+/* Projected (2D) 3PCF and 4PCF of one periodic field (Secs. 2.2 and 2.4;
+ * Algorithms 2, 4, 7, 8).
+ *   shape   : n0 = n1 = N, a power of two in 8..1024; nbins 1..20; mmax 0..10.
+ *   zeta3   : out, [mmax+1][nbins][nbins][2] (re, im),
+ *             zeta_m^{b1 b2} = sum_x delta c^{b1}_m c^{b2 *}_m.
+ *   zeta4   : out, [2mmax+1][2mmax+1][nbins][nbins][nbins][2], index m + mmax,
+ *             zeta_{m1 m2}^{b1 b2 b3} = sum_x delta c^{b1}_{m1} c^{b2}_{m2} c^{b3}_{-(m1+m2)}
+ *             with c_{-m} = conj(c_m); entries with |m1 + m2| > mmax are 0. */
+sbg_status sbg_projected(sbg_context* ctx, const void* field, sbg_dtype dtype, const int64_t shape[2],
+                         const double* edges, int nbins, int mmax, sbg_precision prec, unsigned flags,
+                         double* zeta3, double* zeta4);
+
+/* One projected field of a batch: its own shape, edges and output arrays
+ * (layouts as in sbg_projected). */
+typedef struct {
+  const void* field;
+  sbg_dtype dtype;
+  int64_t shape[2];
+  const double* edges;
+  double* zeta3;
+  double* zeta4;
+} sbg_field2d;
+
+/* Many projected fields of uneven sizes (e.g. simulation snapshots) measured in
+ * one call with shared nbins, mmax, precision and flags. */
+sbg_status sbg_projected_batch(sbg_context* ctx, const sbg_field2d* fields, int nfields, int nbins, int mmax,
+                               sbg_precision prec, unsigned flags);
+
+/* Device times (ms, CUDA events) of the stages of the last measurement call:
+ * [0] upload+preprocess, [1] forward FFT of delta, [2] kernel spectra (plan),
+ * [3] convolutions (inverse FFTs), [4] 3PCF Gram, [5] 4PCF combination,
+ * [6] finalisation + download.  *n_stages is set to the count written (<= 8). */
+sbg_status sbg_last_timings(const sbg_context* ctx, double* ms_per_stage, int* n_stages);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SARABANDE_GB300_H */

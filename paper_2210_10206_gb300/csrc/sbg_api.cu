@@ -1,0 +1,851 @@
+// C ABI, argument checking, plans and orchestration of the GB300 SARABANDE path.
+//
+// Per measured field (Sec. 3, Fig. workflow):
+//   delta (FP64 mean, FP32 data) -> delta-hat = FFT(delta)
+//   for each (l, m >= 0) [3D] or m >= 0 [2D]: kernel spectra G^b (Algorithms 1-2,
+//     cached in the plan like the paper's saved kernels) -> a^b = IFFT(delta-hat G^b)
+//     (Algorithms 3-4), product fused into the first inverse pass
+//   3PCF: delta-weighted Gram of each group (Algorithms 5, 7)
+//   4PCF: pair x single contraction over x (Algorithms 6, 8) + FP64 couplings.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "sarabande_gb300.h"
+#include "sbg_kernels.cuh"
+
+using namespace sbg;
+
+namespace {
+
+constexpr int kMaxBins = 20;
+constexpr int kMaxL3 = 10;
+constexpr int kMaxL4 = 5;
+constexpr int kMaxM = 10;
+constexpr int kStages = 7;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// ---------------------------------------------------------------- 3j (host) --
+// Racah's closed form for the Wigner 3j symbol in long double (l <= 10 here).
+long double lfact(int n) {
+  long double f = 1.0L;
+  for (int i = 2; i <= n; ++i) f *= i;
+  return f;
+}
+
+double three_j(int j1, int j2, int j3, int m1, int m2, int m3) {
+  if (m1 + m2 + m3 != 0) return 0.0;
+  if (j3 < std::abs(j1 - j2) || j3 > j1 + j2) return 0.0;
+  if (std::abs(m1) > j1 || std::abs(m2) > j2 || std::abs(m3) > j3) return 0.0;
+  const long double delta = lfact(j1 + j2 - j3) * lfact(j1 - j2 + j3) * lfact(-j1 + j2 + j3) / lfact(j1 + j2 + j3 + 1);
+  const long double pref = std::sqrt(delta * lfact(j1 + m1) * lfact(j1 - m1) * lfact(j2 + m2) * lfact(j2 - m2) *
+                                     lfact(j3 + m3) * lfact(j3 - m3));
+  const int kmin = std::max(0, std::max(j2 - j3 - m1, j1 - j3 + m2));
+  const int kmax = std::min(j1 + j2 - j3, std::min(j1 - m1, j2 + m2));
+  long double s = 0.0L;
+  for (int k = kmin; k <= kmax; ++k) {
+    const long double den = lfact(k) * lfact(j1 + j2 - j3 - k) * lfact(j1 - m1 - k) * lfact(j2 + m2 - k) *
+                            lfact(j3 - j2 + m1 + k) * lfact(j3 - j1 - m2 + k);
+    s += ((k & 1) ? -1.0L : 1.0L) / den;
+  }
+  const int ph = j1 - j2 - m3;
+  return (double)(((ph % 2) ? -1.0L : 1.0L) * pref * s);
+}
+
+// ------------------------------------------------------------ geometry ----
+bool pow2_in(int64_t n, int64_t lo, int64_t hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+
+std::vector<double> snap_e2(const double* edges, int nb) {
+  std::vector<double> e2(nb + 1);
+  for (int i = 0; i <= nb; ++i) {
+    double v = edges[i] * edges[i];
+    double r = std::nearbyint(v);
+    if (std::fabs(v - r) <= 1e-9 * std::max(v, 1.0)) v = r;
+    e2[i] = v;
+  }
+  return e2;
+}
+
+std::vector<double> cell_counts(int n, int dim, const std::vector<double>& e2, int nb) {
+  std::vector<double> c(nb, 0.0);
+  // edges[nbins] < N/2, so every binned offset has |component| < N/2 and is a
+  // distinct cell of the periodic grid
+  const int R = (int)std::ceil(std::sqrt(e2[nb])) + 1;
+  const int rz = dim == 3 ? R : 0;
+  for (int z = -rz; z <= rz; ++z)
+    for (int y = -R; y <= R; ++y)
+      for (int x = -R; x <= R; ++x) {
+        const double r2 = (double)x * x + (double)y * y + (double)z * z;
+        if (!(r2 > e2[0]) || r2 > e2[nb]) continue;
+        int b = 0;
+        while (b < nb - 1 && r2 > e2[b + 1]) ++b;
+        c[b] += 1.0;
+      }
+  return c;
+}
+
+double ylm_norm(int l, int m) {
+  long double r = (2.0L * l + 1.0L) / (4.0L * 3.14159265358979323846264338327950288L);
+  for (int k = l - m + 1; k <= l + m; ++k) r /= k;
+  return (double)std::sqrt(r);
+}
+
+std::vector<float2> twiddles(int n) {
+  std::vector<float2> t(n);
+  for (int j = 0; j < n; ++j) {
+    const double a = 2.0 * 3.14159265358979323846 * j / n;
+    t[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  return t;
+}
+
+// ---------------------------------------------------------- 4PCF tables ----
+struct Single { int l, m, b; };
+
+struct Tables4 {
+  // host
+  std::vector<Tile4> tiles[3];  // by tcg class 4, 8, 16
+  std::vector<Row4> rows;
+  std::vector<int> cols, uniq;
+  std::vector<int> ptr, idx;
+  std::vector<double> coef;
+  long long tcount = 0;  // outputs of T (complex counted once)
+  int nout = 0;
+  // device
+  DevBuf d_tiles[3], d_rows, d_cols, d_uniq, d_ptr, d_idx, d_coef;
+};
+
+}  // namespace
+
+struct sbg_context {
+  int device = 0;
+  cudaStream_t own = nullptr;
+  cudaStream_t stream = nullptr;
+  size_t budget = 0, used = 0;
+  std::string err;
+  double timings[kStages] = {0};
+  cudaEvent_t ev[kStages + 1] = {};
+  std::map<std::string, DevBuf> bufs;
+  // full-plan cache
+  std::string gkey;
+  DevBuf gcache;
+  bool gcached = false;
+  std::string t4key;
+  Tables4* t4 = nullptr;
+};
+
+namespace {
+
+sbg_status fail(sbg_context* c, sbg_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CU(call)                                                                                 \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return fail(ctx, SBG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+#define ST(call)                       \
+  do {                                 \
+    sbg_status s_ = (call);            \
+    if (s_ != SBG_OK) return s_;       \
+  } while (0)
+
+sbg_status dev_alloc(sbg_context* ctx, DevBuf& b, size_t bytes) {
+  if (b.p && b.bytes >= bytes) return SBG_OK;
+  if (b.p) {
+    cudaFree(b.p);
+    ctx->used -= b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  if (bytes == 0) return SBG_OK;
+  if (ctx->budget && ctx->used + bytes > ctx->budget)
+    return fail(ctx, SBG_ERR_OUT_OF_MEMORY, "allocation of " + std::to_string(bytes) + " bytes exceeds the budget");
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return fail(ctx, SBG_ERR_OUT_OF_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  ctx->used += bytes;
+  return SBG_OK;
+}
+
+void dev_free(sbg_context* ctx, DevBuf& b) {
+  if (b.p) {
+    cudaFree(b.p);
+    ctx->used -= b.bytes;
+  }
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+sbg_status buf(sbg_context* ctx, const char* name, size_t bytes, void** out) {
+  DevBuf& b = ctx->bufs[name];
+  ST(dev_alloc(ctx, b, bytes));
+  *out = b.p;
+  return SBG_OK;
+}
+
+template <class T>
+sbg_status upload(sbg_context* ctx, DevBuf& b, const std::vector<T>& v) {
+  ST(dev_alloc(ctx, b, std::max<size_t>(v.size() * sizeof(T), 16)));
+  if (!v.empty()) CU(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  return SBG_OK;
+}
+
+// Angular part of a single: 3D (l, m), 2D (m) with l = -1.
+int store_index(int dim, int nb, int l, int m_abs, int b) {
+  return dim == 3 ? ((l * (l + 1) / 2 + m_abs) * nb + b) : (m_abs * nb + b);
+}
+
+// Build the pair x single contraction tables of the 4PCF and the coupling CSR.
+// Computed set: for m3 >= 0 and b2: rows (b1 <= b2, alpha1, alpha2) with
+// m1 + m2 = -m3, cols (b3 >= b2, l3 >= m3).  T is symmetric under permutation
+// of its three singles and T[-M] = conj T[M], so every needed triple maps into
+// the set by sorting bins and, if the column m is negative, negating all m.
+sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L) {
+  struct Ang { int l, m; };
+  std::vector<Ang> angs;
+  if (dim == 3) {
+    for (int l = 0; l <= L; ++l)
+      for (int m = -l; m <= l; ++m) angs.push_back({l, m});
+  } else {
+    for (int m = -L; m <= L; ++m) angs.push_back({-1, m});
+  }
+  // block bookkeeping: for (m3, b2) -> base offset, ncols, pair list
+  struct Block { long long base; int ncols; int npairs; std::vector<std::pair<int, int>> pairs; std::vector<int> l3s; };
+  std::vector<Block> blocks((L + 1) * nb);
+  long long off = 0;
+  for (int m3 = 0; m3 <= L; ++m3) {
+    std::vector<std::pair<int, int>> pairs;
+    for (int i = 0; i < (int)angs.size(); ++i)
+      for (int k = 0; k < (int)angs.size(); ++k)
+        if (angs[i].m + angs[k].m == -m3) pairs.push_back({i, k});
+    std::vector<int> l3s;
+    if (dim == 3) {
+      for (int l3 = m3; l3 <= L; ++l3) l3s.push_back(l3);
+    } else {
+      l3s.push_back(-1);
+    }
+    for (int b2 = 0; b2 < nb; ++b2) {
+      Block& bk = blocks[m3 * nb + b2];
+      bk.pairs = pairs;
+      bk.l3s = l3s;
+      bk.npairs = (int)pairs.size();
+      bk.ncols = (nb - b2) * (int)l3s.size();
+      bk.base = off;
+      off += (long long)(b2 + 1) * bk.npairs * bk.ncols;
+    }
+  }
+  t.tcount = off;
+
+  // Tiles: per block, column chunks of <= 64 and row chunks with <= TR rows and
+  // <= 128 distinct staged singles.  Each tile owns a dense [nrows][ncols] slab of T.
+  struct Slab { int r0, nr, c0, nc; long long tout; };
+  std::vector<std::vector<Slab>> slabs((L + 1) * nb);
+  long long so = 0;
+  for (int m3 = 0; m3 <= L; ++m3)
+    for (int b2 = 0; b2 < nb; ++b2) {
+      Block& bk = blocks[m3 * nb + b2];
+      const int nrows_blk = (b2 + 1) * bk.npairs;
+      if (nrows_blk == 0) continue;
+      for (int c0 = 0; c0 < bk.ncols; c0 += 64) {
+        const int nc = std::min(64, bk.ncols - c0);
+        const int cls = nc <= 16 ? 0 : (nc <= 32 ? 1 : 2);
+        const int TR = (cls == 0 ? 256 : (cls == 1 ? 128 : 64));
+        const int col0 = (int)t.cols.size();
+        for (int c = c0; c < c0 + nc; ++c) {
+          const int b3 = b2 + c / (int)bk.l3s.size();
+          const int l3 = bk.l3s[c % bk.l3s.size()];
+          t.cols.push_back(store_index(dim, nb, l3, m3, b3));
+        }
+        int r = 0;
+        while (r < nrows_blk) {
+          Tile4 tl;
+          tl.row0 = (int)t.rows.size();
+          tl.col0 = col0;
+          tl.ncols = nc;
+          tl.uniq0 = (int)t.uniq.size();
+          std::map<int, int> local;
+          int nr = 0;
+          const int rstart = r;
+          while (r < nrows_blk && nr < TR) {
+            const int b1 = r / bk.npairs;
+            const auto pr = bk.pairs[r % bk.npairs];
+            const Ang a1 = angs[pr.first], a2 = angs[pr.second];
+            const int s1 = store_index(dim, nb, a1.l, std::abs(a1.m), b1);
+            const int s2 = store_index(dim, nb, a2.l, std::abs(a2.m), b2);
+            const int need = (local.count(s1) ? 0 : 1) + ((local.count(s2) || s2 == s1) ? 0 : 1);
+            if ((int)local.size() + need > 128) break;
+            if (!local.count(s1)) { const int k = (int)local.size(); local[s1] = k; t.uniq.push_back(s1); }
+            if (!local.count(s2)) { const int k = (int)local.size(); local[s2] = k; t.uniq.push_back(s2); }
+            Row4 rw;
+            rw.u1 = local[s1];
+            rw.u2 = local[s2];
+            rw.flags = (a1.m < 0 ? 1 : 0) | (a2.m < 0 ? 2 : 0);
+            float sg = 1.0f;
+            if (dim == 3) {
+              if (a1.m < 0 && (std::abs(a1.m) & 1)) sg = -sg;
+              if (a2.m < 0 && (std::abs(a2.m) & 1)) sg = -sg;
+            }
+            rw.sign = sg;
+            t.rows.push_back(rw);
+            ++nr;
+            ++r;
+          }
+          tl.nrows = nr;
+          tl.nuniq = (int)local.size();
+          tl.tout = so;
+          slabs[m3 * nb + b2].push_back({rstart, nr, c0, nc, so});
+          so += (long long)nr * nc;
+          t.tiles[cls].push_back(tl);
+        }
+      }
+    }
+  t.tcount = so;
+  // angular index lookup
+  auto ang_index = [&](int l, int m) -> int {
+    for (int i = 0; i < (int)angs.size(); ++i)
+      if (angs[i].l == l && angs[i].m == m) return i;
+    return -1;
+  };
+  // pair index within block
+  std::vector<std::map<long long, int>> pair_index(L + 1);
+  for (int m3 = 0; m3 <= L; ++m3) {
+    const Block& bk = blocks[m3 * nb];
+    for (int p = 0; p < bk.npairs; ++p)
+      pair_index[m3][(long long)bk.pairs[p].first * 4096 + bk.pairs[p].second] = p;
+  }
+  auto lookup = [&](Single s[3]) -> long long {
+    // sort by bin (stable)
+    Single v[3] = {s[0], s[1], s[2]};
+    std::stable_sort(v, v + 3, [](const Single& a, const Single& b) { return a.b < b.b; });
+    // choose the column single: the last; if tie with the middle and the last has m<0
+    // while the middle has m>=0 (or vice versa) any choice works after negation.
+    bool neg = false;
+    if (v[2].m < 0) neg = true;
+    if (neg)
+      for (auto& q : v) q.m = -q.m;
+    const int m3 = v[2].m;
+    const int b2 = v[1].b;
+    const Block& bk = blocks[m3 * nb + b2];
+    const int i1 = ang_index(v[0].l, v[0].m), i2 = ang_index(v[1].l, v[1].m);
+    auto it = pair_index[m3].find((long long)i1 * 4096 + i2);
+    if (it == pair_index[m3].end()) return LLONG_MIN;
+    const int row = v[0].b * bk.npairs + it->second;
+    int l3pos = 0;
+    if (dim == 3) l3pos = v[2].l - m3;
+    const int col = (v[2].b - b2) * (int)bk.l3s.size() + l3pos;
+    for (const Slab& sl : slabs[m3 * nb + b2]) {
+      if (row >= sl.r0 && row < sl.r0 + sl.nr && col >= sl.c0 && col < sl.c0 + sl.nc) {
+        const long long ti = sl.tout + (long long)(row - sl.r0) * sl.nc + (col - sl.c0);
+        return neg ? -ti - 1 : ti;
+      }
+    }
+    return LLONG_MIN;
+  };
+
+  // coupling CSR
+  t.ptr.clear();
+  t.idx.clear();
+  t.coef.clear();
+  t.ptr.push_back(0);
+  if (dim == 3) {
+    for (int l1 = 0; l1 <= L; ++l1)
+      for (int l2 = 0; l2 <= L; ++l2)
+        for (int l3 = std::abs(l1 - l2); l3 <= std::min(l1 + l2, L); ++l3) {
+          if ((l1 + l2 + l3) & 1) continue;
+          for (int b1 = 0; b1 < nb; ++b1)
+            for (int b2 = 0; b2 < nb; ++b2)
+              for (int b3 = 0; b3 < nb; ++b3) {
+                for (int m1 = -l1; m1 <= l1; ++m1)
+                  for (int m2 = -l2; m2 <= l2; ++m2) {
+                    const int m3 = -(m1 + m2);
+                    if (std::abs(m3) > l3) continue;
+                    const double c = (((l1 + l2 + l3) & 1) ? -1.0 : 1.0) * three_j(l1, l2, l3, m1, m2, m3);
+                    if (c == 0.0) continue;
+                    Single s[3] = {{l1, m1, b1}, {l2, m2, b2}, {l3, m3, b3}};
+                    long long ti = lookup(s);
+                    if (ti == LLONG_MIN) return fail(ctx, SBG_ERR_INTERNAL, "4PCF table lookup failed");
+                    if (ti < 0) ti = -ti - 1;  // Re T is invariant under M -> -M
+                    t.idx.push_back((int)ti);
+                    t.coef.push_back(c);
+                  }
+                t.ptr.push_back((int)t.idx.size());
+              }
+        }
+  } else {
+    const int W = 2 * L + 1;
+    for (int m1 = -L; m1 <= L; ++m1)
+      for (int m2 = -L; m2 <= L; ++m2)
+        for (int b1 = 0; b1 < nb; ++b1)
+          for (int b2 = 0; b2 < nb; ++b2)
+            for (int b3 = 0; b3 < nb; ++b3) {
+              const int m3 = -(m1 + m2);
+              if (std::abs(m3) <= L) {
+                Single s[3] = {{-1, m1, b1}, {-1, m2, b2}, {-1, m3, b3}};
+                long long ti = lookup(s);
+                if (ti == LLONG_MIN) return fail(ctx, SBG_ERR_INTERNAL, "2D 4PCF table lookup failed");
+                t.idx.push_back((int)ti);
+                t.coef.push_back(1.0);
+              }
+              t.ptr.push_back((int)t.idx.size());
+            }
+    (void)W;
+  }
+  t.nout = (int)t.ptr.size() - 1;
+  for (int k = 0; k < 3; ++k) ST(upload(ctx, t.d_tiles[k], t.tiles[k]));
+  ST(upload(ctx, t.d_rows, t.rows));
+  ST(upload(ctx, t.d_cols, t.cols));
+  ST(upload(ctx, t.d_uniq, t.uniq));
+  ST(upload(ctx, t.d_ptr, t.ptr));
+  ST(upload(ctx, t.d_idx, t.idx));
+  ST(upload(ctx, t.d_coef, t.coef));
+  return SBG_OK;
+}
+
+void free_tables4(sbg_context* ctx, Tables4* t) {
+  if (!t) return;
+  for (int k = 0; k < 3; ++k) dev_free(ctx, t->d_tiles[k]);
+  dev_free(ctx, t->d_rows);
+  dev_free(ctx, t->d_cols);
+  dev_free(ctx, t->d_uniq);
+  dev_free(ctx, t->d_ptr);
+  dev_free(ctx, t->d_idx);
+  dev_free(ctx, t->d_coef);
+  delete t;
+}
+
+sbg_status ensure_tables4(sbg_context* ctx, int dim, int nb, int L) {
+  const std::string key = std::to_string(dim) + "/" + std::to_string(nb) + "/" + std::to_string(L);
+  if (ctx->t4 && ctx->t4key == key) return SBG_OK;
+  free_tables4(ctx, ctx->t4);
+  ctx->t4 = nullptr;
+  Tables4* t = new Tables4();
+  sbg_status s = build_tables4(ctx, *t, dim, nb, L);
+  if (s != SBG_OK) {
+    free_tables4(ctx, t);
+    return s;
+  }
+  ctx->t4 = t;
+  ctx->t4key = key;
+  return SBG_OK;
+}
+
+void rec(sbg_context* ctx, int i) { cudaEventRecord(ctx->ev[i], ctx->stream); }
+
+// -------------------------------------------------------- FFT helpers ----
+sbg_status fft3(sbg_context* ctx, int n, int sign, int first_load, const void* in, float2* out, const float2* mul,
+                const float2* shared, int batch, const float2* tw) {
+  const long long ng = (long long)n * n * n;
+  FftPass p{};
+  p.twiddle = tw;
+  p.batch = batch;
+  p.bstride = ng;
+  p.sign = sign;
+  // z axis (strided by n^2), fused first-pass load
+  p.in = in; p.out = out; p.mul = mul; p.shared = shared; p.load = first_load;
+  p.outer = 1; p.inner = (long long)n * n;
+  CU(fft_axis_pass(n, p, ctx->stream));
+  // y axis
+  p.in = out; p.load = LOAD_COMPLEX; p.mul = nullptr; p.shared = nullptr;
+  p.outer = n; p.inner = n;
+  CU(fft_axis_pass(n, p, ctx->stream));
+  // x axis (contiguous)
+  p.outer = (long long)n * n; p.inner = 1;
+  CU(fft_axis_pass(n, p, ctx->stream));
+  return SBG_OK;
+}
+
+sbg_status fft2(sbg_context* ctx, int n, int sign, int first_load, const void* in, float2* out, const float2* mul,
+                const float2* shared, int batch, long long bstride, const float2* tw) {
+  FftPass p{};
+  p.twiddle = tw;
+  p.batch = batch;
+  p.bstride = bstride;
+  p.sign = sign;
+  p.in = in; p.out = out; p.mul = mul; p.shared = shared; p.load = first_load;
+  p.outer = 1; p.inner = n;  // y axis
+  CU(fft_axis_pass(n, p, ctx->stream));
+  p.in = out; p.load = LOAD_COMPLEX; p.mul = nullptr; p.shared = nullptr;
+  p.outer = n; p.inner = 1;  // x axis
+  CU(fft_axis_pass(n, p, ctx->stream));
+  return SBG_OK;
+}
+
+sbg_status check_edges(sbg_context* ctx, const double* edges, int nb, int n) {
+  for (int i = 0; i <= nb; ++i)
+    if (!std::isfinite(edges[i])) return fail(ctx, SBG_ERR_BIN_RANGE, "non-finite bin edge");
+  if (edges[0] < 0) return fail(ctx, SBG_ERR_BIN_RANGE, "edges[0] < 0");
+  for (int i = 0; i < nb; ++i)
+    if (!(edges[i + 1] > edges[i])) return fail(ctx, SBG_ERR_BIN_RANGE, "bin edges are not strictly increasing");
+  if (!(edges[nb] < 0.5 * n)) return fail(ctx, SBG_ERR_BIN_RANGE, "edges[nbins] must be < N/2");
+  return SBG_OK;
+}
+
+sbg_status finish_timings(sbg_context* ctx) {
+  CU(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < kStages; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = 0.f;
+    }
+    ctx->timings[i] = ms;
+  }
+  return SBG_OK;
+}
+
+// ---------------------------------------------------------------- core ----
+// Shared by sbg_full (dim 3) and sbg_projected / batch (dim 2).
+sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype, int n, const double* edges, int nb,
+                   int lmax3, int lmax4, sbg_precision prec, unsigned flags, double* zeta3, double* zeta4) {
+  const bool do3 = flags & SBG_3PCF, do4 = flags & SBG_4PCF;
+  const long long ng = dim == 3 ? (long long)n * n * n : (long long)n * n;
+  const int L = std::max(do3 ? lmax3 : 0, do4 ? lmax4 : 0);
+  // number of (l, m>=0) groups in 3D, or m groups in 2D
+  auto npair = [&](int l) { return dim == 3 ? (l + 1) * (l + 2) / 2 : l + 1; };
+  const int ngroups = npair(L);
+  const int ngroups4 = do4 ? npair(lmax4) : 0;
+  const std::vector<double> e2 = snap_e2(edges, nb);
+  const std::vector<double> vb = cell_counts(n, dim, e2, nb);
+  if (flags & SBG_NORMALIZED)
+    for (int b = 0; b < nb; ++b)
+      if (vb[b] == 0.0) return fail(ctx, SBG_ERR_EMPTY_BIN, "bin " + std::to_string(b) + " holds no cell");
+
+  for (int i = 0; i <= kStages; ++i) rec(ctx, i);  // reset
+  rec(ctx, 0);
+  // ---- inputs ----
+  const size_t esz = dtype == SBG_F64 ? 8 : 4;
+  const void* d_in = field;
+  if (!(flags & SBG_FIELD_ON_DEVICE)) {
+    void* stg;
+    ST(buf(ctx, "stage", ng * esz, &stg));
+    CU(cudaMemcpyAsync(stg, field, ng * esz, cudaMemcpyHostToDevice, ctx->stream));
+    d_in = stg;
+  }
+  float* d_delta;
+  float2 *d_dhat, *d_tw;
+  double *d_acc, *d_e2, *d_vb;
+  ST(buf(ctx, "delta", ng * 4, (void**)&d_delta));
+  ST(buf(ctx, "dhat", ng * 8, (void**)&d_dhat));
+  ST(buf(ctx, "acc", 64, (void**)&d_acc));
+  ST(buf(ctx, "tw", n * 8, (void**)&d_tw));
+  ST(buf(ctx, "e2", (kMaxBins + 1) * 8, (void**)&d_e2));
+  ST(buf(ctx, "vb", kMaxBins * 8, (void**)&d_vb));
+  {
+    const std::vector<float2> tw = twiddles(n);
+    CU(cudaMemcpyAsync(d_tw, tw.data(), n * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(d_e2, e2.data(), (nb + 1) * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(d_vb, vb.data(), nb * 8, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  CU(cudaMemsetAsync(d_acc, 0, 64, ctx->stream));
+  CU(launch_sum(d_in, dtype == SBG_F64, ng, d_acc, ctx->stream));
+  CU(launch_convert(d_in, dtype == SBG_F64, ng, d_acc, (flags & SBG_SUBTRACT_MEAN) ? 1 : 0, d_delta, ctx->stream));
+  rec(ctx, 1);
+  // ---- delta-hat ----
+  if (dim == 3) {
+    ST(fft3(ctx, n, -1, LOAD_REAL, d_delta, d_dhat, nullptr, nullptr, 1, d_tw));
+  } else {
+    ST(fft2(ctx, n, -1, LOAD_REAL, d_delta, d_dhat, nullptr, nullptr, 1, ng, d_tw));
+  }
+  rec(ctx, 2);
+  // ---- kernel spectra (plan) ----
+  char keyb[512];
+  snprintf(keyb, sizeof keyb, "%d/%d/%d/%d", dim, n, nb, L);
+  std::string key(keyb);
+  for (int i = 0; i <= nb; ++i) key += "/" + std::to_string(e2[i]);
+  const size_t gbytes = (size_t)ngroups * nb * ng * 8;
+  const double inv_ng = 1.0 / (double)ng;
+  auto gen_group = [&](int g, float2* dst) -> sbg_status {
+    CU(cudaMemsetAsync(dst, 0, (size_t)nb * ng * 8, ctx->stream));
+    if (dim == 3) {
+      int l = 0;
+      while ((l + 1) * (l + 2) / 2 <= g) ++l;
+      const int m = g - l * (l + 1) / 2;
+      CU(launch_kgen3d(n, l, m, ylm_norm(l, m), d_e2, nb, inv_ng, dst, ctx->stream));
+      ST(fft3(ctx, n, +1, LOAD_COMPLEX, dst, dst, nullptr, nullptr, nb, d_tw));
+    } else {
+      CU(launch_kgen2d(n, g, d_e2, nb, inv_ng, dst, ctx->stream));
+      ST(fft2(ctx, n, +1, LOAD_COMPLEX, dst, dst, nullptr, nullptr, nb, ng, d_tw));
+    }
+    return SBG_OK;
+  };
+  bool cached = false;
+  if (ctx->gcached && ctx->gkey == key) {
+    cached = true;
+  } else {
+    // try to (re)build the full cache; fall back to per-group regeneration
+    dev_free(ctx, ctx->gcache);
+    ctx->gcached = false;
+    size_t freeb = 0, totb = 0;
+    cudaMemGetInfo(&freeb, &totb);
+    const size_t a4bytes = (size_t)ngroups4 * nb * ng * 8;
+    const bool fits = gbytes + a4bytes + (size_t)nb * ng * 8 + (1ull << 30) < freeb &&
+                      (!ctx->budget || ctx->used + gbytes + a4bytes + (size_t)nb * ng * 8 <= ctx->budget);
+    if (fits && dev_alloc(ctx, ctx->gcache, gbytes) == SBG_OK) {
+      for (int g = 0; g < ngroups; ++g) ST(gen_group(g, (float2*)ctx->gcache.p + (size_t)g * nb * ng));
+      ctx->gcached = true;
+      ctx->gkey = key;
+      cached = true;
+    } else {
+      ctx->err.clear();
+    }
+  }
+  rec(ctx, 3);
+  // ---- convolutions + 3PCF Gram ----
+  float2* d_astore = nullptr;
+  float2* d_group = nullptr;
+  double* d_S = nullptr;
+  if (do4) ST(buf(ctx, "astore", (size_t)ngroups4 * nb * ng * 8, (void**)&d_astore));
+  if (!cached || ngroups > ngroups4) ST(buf(ctx, "group", (size_t)nb * ng * 8, (void**)&d_group));
+  float2* d_gtmp = nullptr;
+  if (!cached) ST(buf(ctx, "gtmp", (size_t)nb * ng * 8, (void**)&d_gtmp));
+  const int ngroups3 = do3 ? npair(lmax3) : 0;
+  if (do3) {
+    ST(buf(ctx, "S", (size_t)std::max(ngroups3, 1) * nb * nb * 16, (void**)&d_S));
+    CU(cudaMemsetAsync(d_S, 0, (size_t)ngroups3 * nb * nb * 16, ctx->stream));
+  }
+  for (int g = 0; g < ngroups; ++g) {
+    const float2* G;
+    if (cached) {
+      G = (const float2*)ctx->gcache.p + (size_t)g * nb * ng;
+    } else {
+      ST(gen_group(g, d_gtmp));
+      G = d_gtmp;
+    }
+    float2* out = (g < ngroups4) ? d_astore + (size_t)g * nb * ng : d_group;
+    if (dim == 3) {
+      ST(fft3(ctx, n, +1, LOAD_MUL, nullptr, out, G, d_dhat, nb, d_tw));
+    } else {
+      ST(fft2(ctx, n, +1, LOAD_MUL, nullptr, out, G, d_dhat, nb, ng, d_tw));
+    }
+    if (do3 && g < ngroups3) CU(launch_gram3(out, ng, nb, d_delta, d_S + (size_t)g * nb * nb * 2, ctx->stream));
+  }
+  rec(ctx, 4);
+  rec(ctx, 5);
+  // ---- 4PCF ----
+  double* d_z4 = nullptr;
+  if (do4) {
+    ST(ensure_tables4(ctx, dim, nb, lmax4));
+    Tables4& t = *ctx->t4;
+    const int cplx = dim == 2 ? 1 : 0;
+    double* d_T;
+    ST(buf(ctx, "T", (size_t)std::max<long long>(t.tcount, 1) * 8 * (cplx ? 2 : 1), (void**)&d_T));
+    CU(cudaMemsetAsync(d_T, 0, (size_t)t.tcount * 8 * (cplx ? 2 : 1), ctx->stream));
+    {
+      const int tcg[3] = {4, 8, 16};
+      for (int k = 0; k < 3; ++k) {
+        const int ntl = (int)t.tiles[k].size();
+        if (!ntl) continue;
+        int nsplit = (int)std::max<long long>(1, std::min<long long>(ng / 32, (152LL * 6 + ntl - 1) / ntl));
+        CU(launch_simt4(d_astore, ng, d_delta, (const Tile4*)t.d_tiles[k].p, ntl, (const Row4*)t.d_rows.p,
+                        (const int*)t.d_cols.p, (const int*)t.d_uniq.p, cplx, tcg[k], nsplit, d_T, ctx->stream));
+      }
+    }
+    ST(buf(ctx, "z4", (size_t)t.nout * 8 * (cplx ? 2 : 1), (void**)&d_z4));
+    CU(launch_couple(d_T, cplx, (const int*)t.d_ptr.p, (const int*)t.d_idx.p, (const double*)t.d_coef.p, t.nout, d_z4,
+                     ctx->stream));
+    if (flags & SBG_NORMALIZED) {
+      const long long nouter = t.nout / ((long long)nb * nb * nb);
+      CU(launch_normalize(d_z4, nouter, nb, 4, cplx ? 2 : 1, d_acc, (double)ng, d_vb, ctx->stream));
+    }
+  }
+  rec(ctx, 6);
+  // ---- 3PCF finish + downloads ----
+  if (do3) {
+    double* d_z3;
+    const int nl = dim == 3 ? lmax3 + 1 : lmax3 + 1;
+    const int ncomp = dim == 3 ? 1 : 2;
+    ST(buf(ctx, "z3", (size_t)nl * nb * nb * 8 * ncomp, (void**)&d_z3));
+    CU(launch_finish3(d_S, dim == 3, lmax3, nb, d_z3, ctx->stream));
+    if (flags & SBG_NORMALIZED) CU(launch_normalize(d_z3, nl, nb, 3, ncomp, d_acc, (double)ng, d_vb, ctx->stream));
+    CU(cudaMemcpyAsync(zeta3, d_z3, (size_t)nl * nb * nb * 8 * ncomp, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  if (do4) {
+    const int cplx = dim == 2 ? 1 : 0;
+    CU(cudaMemcpyAsync(zeta4, d_z4, (size_t)ctx->t4->nout * 8 * (cplx ? 2 : 1), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  rec(ctx, 7);
+  return finish_timings(ctx);
+}
+
+}  // namespace
+
+// =================================================================== C ABI ==
+extern "C" {
+
+sbg_status sbg_create(int cuda_device, size_t hbm_budget_bytes, sbg_context** out) {
+  if (!out) return SBG_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return SBG_ERR_CUDA;
+  }
+  if (cuda_device < 0 || cuda_device >= ndev) return SBG_ERR_INVALID_ARG;
+  if (cudaSetDevice(cuda_device) != cudaSuccess) return SBG_ERR_CUDA;
+  sbg_context* ctx = new sbg_context();
+  ctx->device = cuda_device;
+  ctx->budget = hbm_budget_bytes;
+  if (cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking) != cudaSuccess) {
+    delete ctx;
+    return SBG_ERR_CUDA;
+  }
+  ctx->stream = ctx->own;
+  for (int i = 0; i <= kStages; ++i) {
+    if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) {
+      sbg_destroy(ctx);
+      return SBG_ERR_CUDA;
+    }
+  }
+  *out = ctx;
+  return SBG_OK;
+}
+
+void sbg_destroy(sbg_context* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->bufs) dev_free(ctx, kv.second);
+  dev_free(ctx, ctx->gcache);
+  free_tables4(ctx, ctx->t4);
+  for (int i = 0; i <= kStages; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  if (ctx->own) cudaStreamDestroy(ctx->own);
+  delete ctx;
+}
+
+sbg_status sbg_set_stream(sbg_context* ctx, void* cuda_stream) {
+  if (!ctx) return SBG_ERR_INVALID_ARG;
+  ctx->stream = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own;
+  return SBG_OK;
+}
+
+const char* sbg_status_string(sbg_status s) {
+  switch (s) {
+    case SBG_OK: return "SBG_OK";
+    case SBG_ERR_INVALID_ARG: return "SBG_ERR_INVALID_ARG";
+    case SBG_ERR_UNSUPPORTED_SHAPE: return "SBG_ERR_UNSUPPORTED_SHAPE";
+    case SBG_ERR_BIN_RANGE: return "SBG_ERR_BIN_RANGE";
+    case SBG_ERR_EMPTY_BIN: return "SBG_ERR_EMPTY_BIN";
+    case SBG_ERR_OUT_OF_MEMORY: return "SBG_ERR_OUT_OF_MEMORY";
+    case SBG_ERR_CUDA: return "SBG_ERR_CUDA";
+    case SBG_ERR_TIMEOUT: return "SBG_ERR_TIMEOUT";
+    case SBG_ERR_INTERNAL: return "SBG_ERR_INTERNAL";
+  }
+  return "SBG_UNKNOWN_STATUS";
+}
+
+const char* sbg_last_error(const sbg_context* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+sbg_status sbg_lambda_count(int lmax, int* n_lambda) {
+  if (!n_lambda || lmax < 0 || lmax > kMaxL3) return SBG_ERR_INVALID_ARG;
+  int c = 0;
+  for (int l1 = 0; l1 <= lmax; ++l1)
+    for (int l2 = 0; l2 <= lmax; ++l2)
+      for (int l3 = std::abs(l1 - l2); l3 <= std::min(l1 + l2, lmax); ++l3)
+        if (!((l1 + l2 + l3) & 1)) ++c;
+  *n_lambda = c;
+  return SBG_OK;
+}
+
+sbg_status sbg_lambda_list(int lmax, int* l123) {
+  if (!l123 || lmax < 0 || lmax > kMaxL3) return SBG_ERR_INVALID_ARG;
+  int c = 0;
+  for (int l1 = 0; l1 <= lmax; ++l1)
+    for (int l2 = 0; l2 <= lmax; ++l2)
+      for (int l3 = std::abs(l1 - l2); l3 <= std::min(l1 + l2, lmax); ++l3)
+        if (!((l1 + l2 + l3) & 1)) {
+          l123[3 * c] = l1;
+          l123[3 * c + 1] = l2;
+          l123[3 * c + 2] = l3;
+          ++c;
+        }
+  return SBG_OK;
+}
+
+sbg_status sbg_full(sbg_context* ctx, const void* field, sbg_dtype dtype, const int64_t shape[3], const double* edges,
+                    int nbins, int lmax3, int lmax4, sbg_precision prec, unsigned flags, double* zeta3,
+                    double* zeta4) {
+  if (!ctx) return SBG_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!field || !shape || !edges) return fail(ctx, SBG_ERR_INVALID_ARG, "null field, shape or edges");
+  if (dtype != SBG_F32 && dtype != SBG_F64) return fail(ctx, SBG_ERR_INVALID_ARG, "dtype");
+  if (prec != SBG_PREC_FP32) return fail(ctx, SBG_ERR_INVALID_ARG, "precision not available in this build");
+  if (flags & ~31u) return fail(ctx, SBG_ERR_INVALID_ARG, "unknown flag bits");
+  if (!(flags & (SBG_3PCF | SBG_4PCF))) return fail(ctx, SBG_ERR_INVALID_ARG, "neither SBG_3PCF nor SBG_4PCF");
+  if (nbins < 1 || nbins > kMaxBins) return fail(ctx, SBG_ERR_INVALID_ARG, "nbins must be 1..20");
+  if ((flags & SBG_3PCF) && (lmax3 < 0 || lmax3 > kMaxL3 || !zeta3)) return fail(ctx, SBG_ERR_INVALID_ARG, "lmax3/zeta3");
+  if ((flags & SBG_4PCF) && (lmax4 < 0 || lmax4 > kMaxL4 || !zeta4)) return fail(ctx, SBG_ERR_INVALID_ARG, "lmax4/zeta4");
+  if (!(shape[0] == shape[1] && shape[1] == shape[2]) || !pow2_in(shape[0], 8, 512))
+    return fail(ctx, SBG_ERR_UNSUPPORTED_SHAPE, "3D shape must be cubic with a power-of-two side in 8..512");
+  const int n = (int)shape[0];
+  ST(check_edges(ctx, edges, nbins, n));
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SBG_ERR_CUDA, "cudaSetDevice");
+  return measure(ctx, 3, field, dtype, n, edges, nbins, lmax3, lmax4, prec, flags, zeta3, zeta4);
+}
+
+sbg_status sbg_projected(sbg_context* ctx, const void* field, sbg_dtype dtype, const int64_t shape[2],
+                         const double* edges, int nbins, int mmax, sbg_precision prec, unsigned flags, double* zeta3,
+                         double* zeta4) {
+  if (!ctx) return SBG_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!field || !shape || !edges) return fail(ctx, SBG_ERR_INVALID_ARG, "null field, shape or edges");
+  if (dtype != SBG_F32 && dtype != SBG_F64) return fail(ctx, SBG_ERR_INVALID_ARG, "dtype");
+  if (prec != SBG_PREC_FP32) return fail(ctx, SBG_ERR_INVALID_ARG, "precision not available in this build");
+  if (flags & ~31u) return fail(ctx, SBG_ERR_INVALID_ARG, "unknown flag bits");
+  if (!(flags & (SBG_3PCF | SBG_4PCF))) return fail(ctx, SBG_ERR_INVALID_ARG, "neither SBG_3PCF nor SBG_4PCF");
+  if (nbins < 1 || nbins > kMaxBins) return fail(ctx, SBG_ERR_INVALID_ARG, "nbins must be 1..20");
+  if (mmax < 0 || mmax > kMaxM) return fail(ctx, SBG_ERR_INVALID_ARG, "mmax must be 0..10");
+  if (((flags & SBG_3PCF) && !zeta3) || ((flags & SBG_4PCF) && !zeta4))
+    return fail(ctx, SBG_ERR_INVALID_ARG, "null output for a requested statistic");
+  if (shape[0] != shape[1] || !pow2_in(shape[0], 8, 1024))
+    return fail(ctx, SBG_ERR_UNSUPPORTED_SHAPE, "2D shape must be square with a power-of-two side in 8..1024");
+  const int n = (int)shape[0];
+  ST(check_edges(ctx, edges, nbins, n));
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SBG_ERR_CUDA, "cudaSetDevice");
+  return measure(ctx, 2, field, dtype, n, edges, nbins, mmax, mmax, prec, flags, zeta3, zeta4);
+}
+
+sbg_status sbg_projected_batch(sbg_context* ctx, const sbg_field2d* fields, int nfields, int nbins, int mmax,
+                               sbg_precision prec, unsigned flags) {
+  if (!ctx) return SBG_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!fields || nfields < 1) return fail(ctx, SBG_ERR_INVALID_ARG, "fields/nfields");
+  double acc[kStages] = {0};
+  for (int i = 0; i < nfields; ++i) {
+    sbg_status s = sbg_projected(ctx, fields[i].field, fields[i].dtype, fields[i].shape, fields[i].edges, nbins, mmax,
+                                 prec, flags, fields[i].zeta3, fields[i].zeta4);
+    if (s != SBG_OK) {
+      ctx->err = "field " + std::to_string(i) + ": " + ctx->err;
+      return s;
+    }
+    for (int k = 0; k < kStages; ++k) acc[k] += ctx->timings[k];
+  }
+  for (int k = 0; k < kStages; ++k) ctx->timings[k] = acc[k];
+  return SBG_OK;
+}
+
+sbg_status sbg_last_timings(const sbg_context* ctx, double* ms_per_stage, int* n_stages) {
+  if (!ctx || !ms_per_stage || !n_stages) return SBG_ERR_INVALID_ARG;
+  for (int i = 0; i < kStages; ++i) ms_per_stage[i] = ctx->timings[i];
+  *n_stages = kStages;
+  return SBG_OK;
+}
+
+}  // extern "C"

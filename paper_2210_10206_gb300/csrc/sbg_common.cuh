@@ -1,0 +1,38 @@
+// Shared device/host helpers of the GB300 SARABANDE library (internal header).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sbg {
+
+struct cplx { float x, y; };
+
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// Launch-time knobs shared by the FFT launchers.
+enum FftLoad { LOAD_COMPLEX = 0, LOAD_REAL = 1, LOAD_MUL = 2 };
+
+// One axis pass of a batched 3D/2D complex FFT.  The array is viewed as
+// [batch][outer][N][inner]; the pass transforms along the N axis.
+struct FftPass {
+  const void* in;        // float2 (or float for LOAD_REAL) base of batch 0
+  float2* out;           // base of batch 0 (may alias `in`)
+  const float2* mul;     // LOAD_MUL: per-batch factor array (batch stride = bstride)
+  const float2* shared;  // LOAD_MUL: array common to every batch (e.g. delta-hat)
+  const float2* twiddle; // N-entry table exp(sign 2 pi i j / N)
+  long long outer, inner;
+  long long bstride;     // elements between batches (in, out and mul)
+  int batch;
+  int sign;              // -1 forward, +1 inverse (unnormalised)
+  int load;              // FftLoad
+};
+
+// Host launcher (sbg_fft.cu).  Returns cudaSuccess or the launch error.
+cudaError_t fft_axis_pass(int n, const FftPass& p, cudaStream_t st);
+
+}  // namespace sbg

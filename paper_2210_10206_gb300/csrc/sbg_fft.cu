@@ -1,0 +1,249 @@
+// Shared-memory two-step (four-step) FFT axis passes for N = 8 .. 1024.
+//
+// The convolution coefficients of the method (Sec. 2.1, Eq. almconv; Algorithms
+// 3-4) are inverse FFTs of delta-hat times a kernel spectrum.  A 3D (2D)
+// transform is three (two) axis passes over HBM; each pass moves one line of N
+// points per (thread group, line) through registers:
+//
+//   N = R1 * R2,  n = n1 + R1 n2,  k = k2 + R2 k1
+//   step 1: R1 DFTs of length R2 over n2, then twiddle W_N^(n1 k2)
+//   step 2: R2 DFTs of length R1 over n1 (through shared memory)
+//
+// Each line is owned by T = min(R1, R2) threads that hold N/T points each, so
+// global loads and stores of step 1/2 are single coalesced sweeps (lines that
+// are adjacent in memory are handled by adjacent lanes for the strided axes,
+// points of one row by adjacent lanes for the contiguous axis).  The spectral
+// product of the convolution (delta-hat x kernel spectrum) is fused into the
+// first pass, the real->complex promotion of delta into the first forward pass.
+#include "sbg_common.cuh"
+
+namespace sbg {
+
+__device__ constexpr float kC32[32] = {
+    1.000000000e+00f, 9.807852804e-01f, 9.238795325e-01f, 8.314696123e-01f,
+    7.071067812e-01f, 5.555702330e-01f, 3.826834324e-01f, 1.950903220e-01f,
+    0.0f, -1.950903220e-01f, -3.826834324e-01f, -5.555702330e-01f,
+    -7.071067812e-01f, -8.314696123e-01f, -9.238795325e-01f, -9.807852804e-01f,
+    -1.000000000e+00f, -9.807852804e-01f, -9.238795325e-01f, -8.314696123e-01f,
+    -7.071067812e-01f, -5.555702330e-01f, -3.826834324e-01f, -1.950903220e-01f,
+    0.0f, 1.950903220e-01f, 3.826834324e-01f, 5.555702330e-01f,
+    7.071067812e-01f, 8.314696123e-01f, 9.238795325e-01f, 9.807852804e-01f};
+__device__ constexpr float kS32[32] = {
+    0.0f, 1.950903220e-01f, 3.826834324e-01f, 5.555702330e-01f,
+    7.071067812e-01f, 8.314696123e-01f, 9.238795325e-01f, 9.807852804e-01f,
+    1.000000000e+00f, 9.807852804e-01f, 9.238795325e-01f, 8.314696123e-01f,
+    7.071067812e-01f, 5.555702330e-01f, 3.826834324e-01f, 1.950903220e-01f,
+    0.0f, -1.950903220e-01f, -3.826834324e-01f, -5.555702330e-01f,
+    -7.071067812e-01f, -8.314696123e-01f, -9.238795325e-01f, -9.807852804e-01f,
+    -1.000000000e+00f, -9.807852804e-01f, -9.238795325e-01f, -8.314696123e-01f,
+    -7.071067812e-01f, -5.555702330e-01f, -3.826834324e-01f, -1.950903220e-01f};
+
+// exp(SIGN * 2 pi i e / R) for compile-time R <= 32
+template <int R, int SIGN>
+__device__ __forceinline__ float2 wsmall(int e) {
+  const int j = ((e % R) * (32 / R)) & 31;
+  return make_float2(kC32[j], SIGN * kS32[j]);
+}
+
+template <int R, int SIGN> struct Dft;
+
+template <int SIGN> struct Dft<1, SIGN> {
+  __device__ __forceinline__ static void run(float2*) {}
+};
+template <int SIGN> struct Dft<2, SIGN> {
+  __device__ __forceinline__ static void run(float2* v) {
+    float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+template <int SIGN> struct Dft<4, SIGN> {
+  __device__ __forceinline__ static void run(float2* v) {
+    float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    float2 t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
+    // W = exp(SIGN i pi/2) = SIGN * i;  W * t3 = SIGN * (-t3.y, t3.x)
+    float2 wt3 = make_float2(-SIGN * t3.y, SIGN * t3.x);
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, wt3);
+    v[3] = csub(t1, wt3);
+  }
+};
+
+// R = A * B in registers: n = a + A b, k = kb + B ka.
+template <int A, int B, int SIGN>
+__device__ __forceinline__ void dft_four_step(float2* v) {
+  constexpr int R = A * B;
+#pragma unroll
+  for (int a = 0; a < A; ++a) {
+    float2 t[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) t[b] = v[a + A * b];
+    Dft<B, SIGN>::run(t);
+#pragma unroll
+    for (int kb = 0; kb < B; ++kb) v[a + A * kb] = (a * kb) ? cmul(t[kb], wsmall<R, SIGN>(a * kb)) : t[kb];
+  }
+  float2 out[R];
+#pragma unroll
+  for (int kb = 0; kb < B; ++kb) {
+    float2 u[A];
+#pragma unroll
+    for (int a = 0; a < A; ++a) u[a] = v[a + A * kb];
+    Dft<A, SIGN>::run(u);
+#pragma unroll
+    for (int ka = 0; ka < A; ++ka) out[kb + B * ka] = u[ka];
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) v[i] = out[i];
+}
+
+template <int SIGN> struct Dft<8, SIGN> {
+  __device__ __forceinline__ static void run(float2* v) { dft_four_step<2, 4, SIGN>(v); }
+};
+template <int SIGN> struct Dft<16, SIGN> {
+  __device__ __forceinline__ static void run(float2* v) { dft_four_step<4, 4, SIGN>(v); }
+};
+template <int SIGN> struct Dft<32, SIGN> {
+  __device__ __forceinline__ static void run(float2* v) { dft_four_step<4, 8, SIGN>(v); }
+};
+
+template <int N> struct Plan;
+template <> struct Plan<8>    { static constexpr int R1 = 4,  R2 = 2;  };
+template <> struct Plan<16>   { static constexpr int R1 = 4,  R2 = 4;  };
+template <> struct Plan<32>   { static constexpr int R1 = 8,  R2 = 4;  };
+template <> struct Plan<64>   { static constexpr int R1 = 8,  R2 = 8;  };
+template <> struct Plan<128>  { static constexpr int R1 = 16, R2 = 8;  };
+template <> struct Plan<256>  { static constexpr int R1 = 16, R2 = 16; };
+template <> struct Plan<512>  { static constexpr int R1 = 16, R2 = 32; };
+template <> struct Plan<1024> { static constexpr int R1 = 32, R2 = 32; };
+
+template <int N, bool CONTIG> struct Geo {
+  static constexpr int R1 = Plan<N>::R1, R2 = Plan<N>::R2;
+  static constexpr int T = R1 < R2 ? R1 : R2;            // threads per line
+  static constexpr int TL = CONTIG ? (N <= 32 ? 8 : 256 / T) : (N >= 16 ? 16 : N);  // lines per CTA
+  static constexpr int THREADS = TL * T;
+  static constexpr int R2S = CONTIG ? R2 + 1 : R2;       // padded row of Y (contiguous layout)
+  static constexpr int LS = CONTIG ? R1 * R2S + 1 : 0;
+  static constexpr int SMEM = (CONTIG ? TL * LS : TL * N) * 8;
+  __device__ __forceinline__ static int sidx(int l, int n1, int k2) {
+    return CONTIG ? l * LS + n1 * R2S + k2 : (n1 * R2 + k2) * TL + l;
+  }
+};
+
+template <int N, bool CONTIG, int SIGN, int LOAD>
+__global__ void __launch_bounds__(Geo<N, CONTIG>::THREADS)
+fft_axis_kernel(FftPass p) {
+  using G = Geo<N, CONTIG>;
+  constexpr int R1 = G::R1, R2 = G::R2, T = G::T, TL = G::TL;
+  extern __shared__ float2 sm[];
+  const int t = threadIdx.x;
+  const int j = CONTIG ? (t % T) : (t / TL);
+  const int l = CONTIG ? (t / T) : (t % TL);
+  const long long boff = (long long)blockIdx.y * p.bstride;
+
+  long long base;    // element index of point n = 0 of this thread's line
+  long long estride; // element stride along the line
+  if (CONTIG) {
+    base = ((long long)blockIdx.x * TL + l) * N;
+    estride = 1;
+  } else {
+    const long long tiles = p.inner / TL;
+    const long long o = blockIdx.x / tiles;
+    const long long i0 = (blockIdx.x % tiles) * TL;
+    base = o * (long long)N * p.inner + i0 + l;
+    estride = p.inner;
+  }
+
+  // ---- step 1: R1/T DFTs of length R2 per thread ----
+#pragma unroll
+  for (int q = 0; q < R1 / T; ++q) {
+    const int n1 = j + T * q;
+    float2 v[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) {
+      const long long e = base + (long long)(n1 + R1 * n2) * estride;
+      if (LOAD == LOAD_REAL) {
+        v[n2] = make_float2(__ldg(reinterpret_cast<const float*>(p.in) + boff + e), 0.0f);
+      } else if (LOAD == LOAD_MUL) {
+        v[n2] = cmul(__ldg(p.shared + e), __ldg(p.mul + boff + e));
+      } else {
+        v[n2] = __ldg(reinterpret_cast<const float2*>(p.in) + boff + e);
+      }
+    }
+    Dft<R2, SIGN>::run(v);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      float2 w = __ldg(p.twiddle + ((n1 * k2) & (N - 1)));
+      if (SIGN < 0) w.y = -w.y;
+      sm[G::sidx(l, n1, k2)] = (k2 == 0) ? v[k2] : cmul(v[k2], w);
+    }
+  }
+  __syncthreads();
+
+  // ---- step 2: R2/T DFTs of length R1 per thread ----
+#pragma unroll
+  for (int q = 0; q < R2 / T; ++q) {
+    const int k2 = j + T * q;
+    float2 u[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) u[n1] = sm[G::sidx(l, n1, k2)];
+    Dft<R1, SIGN>::run(u);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      const long long e = base + (long long)(k2 + R2 * k1) * estride;
+      p.out[boff + e] = u[k1];
+    }
+  }
+}
+
+template <int N, bool CONTIG, int SIGN, int LOAD>
+static cudaError_t launch_t(const FftPass& p, cudaStream_t st) {
+  using G = Geo<N, CONTIG>;
+  auto kern = fft_axis_kernel<N, CONTIG, SIGN, LOAD>;
+  static bool configured = false;  // attribute is per function; set once per process
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  // contiguous: outer rows grouped by TL; strided: outer * inner lines grouped by TL
+  long long blocks = CONTIG ? p.outer / G::TL : (p.outer * (p.inner / G::TL));
+  if (blocks <= 0 || blocks > 0x7fffffffLL || p.batch <= 0 || p.batch > 65535) return cudaErrorInvalidValue;
+  if (CONTIG ? (p.outer % G::TL) : (p.inner % G::TL)) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)blocks, (unsigned)p.batch);
+  kern<<<grid, G::THREADS, G::SMEM, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t dispatch_n(const FftPass& p, cudaStream_t st) {
+  const bool contig = (p.inner == 1);
+  if (contig) {
+    if (p.load != LOAD_COMPLEX) return cudaErrorInvalidValue;
+    return p.sign < 0 ? launch_t<N, true, -1, LOAD_COMPLEX>(p, st) : launch_t<N, true, 1, LOAD_COMPLEX>(p, st);
+  }
+  if (p.sign < 0) {
+    if (p.load == LOAD_REAL) return launch_t<N, false, -1, LOAD_REAL>(p, st);
+    if (p.load == LOAD_COMPLEX) return launch_t<N, false, -1, LOAD_COMPLEX>(p, st);
+    return cudaErrorInvalidValue;
+  }
+  if (p.load == LOAD_MUL) return launch_t<N, false, 1, LOAD_MUL>(p, st);
+  if (p.load == LOAD_COMPLEX) return launch_t<N, false, 1, LOAD_COMPLEX>(p, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t fft_axis_pass(int n, const FftPass& p, cudaStream_t st) {
+  switch (n) {
+    case 8: return dispatch_n<8>(p, st);
+    case 16: return dispatch_n<16>(p, st);
+    case 32: return dispatch_n<32>(p, st);
+    case 64: return dispatch_n<64>(p, st);
+    case 128: return dispatch_n<128>(p, st);
+    case 256: return dispatch_n<256>(p, st);
+    case 512: return dispatch_n<512>(p, st);
+    case 1024: return dispatch_n<1024>(p, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sbg

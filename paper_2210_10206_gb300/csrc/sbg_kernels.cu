@@ -1,0 +1,443 @@
+// Preprocessing, kernel generation, 3PCF Gram, FP32 SIMT 4PCF contraction and
+// FP64 finalisation kernels.
+#include "sbg_kernels.cuh"
+
+namespace sbg {
+
+// ------------------------------------------------------------------ reduce --
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void block_add_d(double v, double* dst) {
+  __shared__ double part[32];
+  v = warp_sum_d(v);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) part[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? part[lane] : 0.0;
+    v = warp_sum_d(v);
+    if (lane == 0) atomicAdd(dst, v);
+  }
+}
+
+__global__ void sum_kernel(const void* in, int is_f64, long long n, double* acc) {
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s += is_f64 ? reinterpret_cast<const double*>(in)[i] : (double)reinterpret_cast<const float*>(in)[i];
+  block_add_d(s, acc);
+}
+
+__global__ void convert_kernel(const void* in, int is_f64, long long n, const double* acc, int subtract,
+                               float* out, double* ngal) {
+  const double mean = subtract ? acc[0] / (double)n : 0.0;
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = is_f64 ? reinterpret_cast<const double*>(in)[i] : (double)reinterpret_cast<const float*>(in)[i];
+    v -= mean;
+    out[i] = (float)v;
+    s += v + 1.0;
+  }
+  block_add_d(s, ngal);
+}
+
+static int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152LL * 16) b = 152LL * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_sum(const void* in, int is_f64, long long n, double* acc, cudaStream_t st) {
+  sum_kernel<<<grid_for(n, 256), 256, 0, st>>>(in, is_f64, n, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const void* in, int is_f64, long long n, const double* acc, int subtract, float* out,
+                           cudaStream_t st) {
+  convert_kernel<<<grid_for(n, 256), 256, 0, st>>>(in, is_f64, n, acc, subtract, out,
+                                                    const_cast<double*>(acc) + 1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- kernel generation --
+__device__ __forceinline__ int min_image(int i, int n) { return i < n - i ? i : i - n; }
+
+__device__ __forceinline__ int find_bin(double r2, const double* e2, int nb) {
+  if (!(r2 > e2[0]) || r2 > e2[nb]) return -1;
+  int b = 0;
+  while (b < nb - 1 && r2 > e2[b + 1]) ++b;
+  return b;
+}
+
+// conj(Y_lm) * Theta_b on the minimum-image offset grid (Algorithm 1); Y_lm from the
+// reduced associated Legendre recurrence times ((x + i y)/r)^m, in FP64.
+__global__ void kgen3d_kernel(int n, int l, int m, double norm, const double* __restrict__ e2, int nb, double scale,
+                              float2* __restrict__ out) {
+  const long long ng = (long long)n * n * n;
+  const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (cell >= ng) return;
+  const int ix = (int)(cell % n), iy = (int)((cell / n) % n), iz = (int)(cell / ((long long)n * n));
+  const int x = min_image(ix, n), y = min_image(iy, n), z = min_image(iz, n);
+  const double r2 = (double)x * x + (double)y * y + (double)z * z;
+  const int b = find_bin(r2, e2, nb);
+  if (b < 0) return;
+  const double r = sqrt(r2);
+  const double t = z / r;
+  // reduced associated Legendre (-1)^m d^m P_l/dt^m
+  double pmm = (m & 1) ? -1.0 : 1.0;
+  for (int k = 1; k < 2 * m; k += 2) pmm *= k;
+  double p = pmm;
+  if (l > m) {
+    double a = pmm, bb = (2 * m + 1) * t * pmm;
+    for (int ll = m + 2; ll <= l; ++ll) {
+      double c = ((2 * ll - 1) * t * bb - (ll + m - 1) * a) / (ll - m);
+      a = bb;
+      bb = c;
+    }
+    p = bb;
+  }
+  double ur = x / r, ui = y / r, er = 1.0, ei = 0.0;
+  for (int k = 0; k < m; ++k) {
+    const double tr = er * ur - ei * ui;
+    ei = er * ui + ei * ur;
+    er = tr;
+  }
+  const double s = norm * p * scale;
+  out[(long long)b * ng + cell] = make_float2((float)(s * er), (float)(-s * ei));
+}
+
+// conj(((x + i y)/rho)^m) * Theta_b (Algorithm 2)
+__global__ void kgen2d_kernel(int n, int m, const double* __restrict__ e2, int nb, double scale,
+                              float2* __restrict__ out) {
+  const long long ng = (long long)n * n;
+  const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (cell >= ng) return;
+  const int x = min_image((int)(cell % n), n), y = min_image((int)(cell / n), n);
+  const double r2 = (double)x * x + (double)y * y;
+  const int b = find_bin(r2, e2, nb);
+  if (b < 0) return;
+  const double r = sqrt(r2);
+  double ur = x / r, ui = y / r, er = 1.0, ei = 0.0;
+  for (int k = 0; k < m; ++k) {
+    const double tr = er * ur - ei * ui;
+    ei = er * ui + ei * ur;
+    er = tr;
+  }
+  out[(long long)b * ng + cell] = make_float2((float)(er * scale), (float)(-ei * scale));
+}
+
+cudaError_t launch_kgen3d(int n, int l, int m, double norm_lm, const double* e2_dev, int nb, double scale,
+                          float2* out, cudaStream_t st) {
+  const long long ng = (long long)n * n * n;
+  kgen3d_kernel<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(n, l, m, norm_lm, e2_dev, nb, scale, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kgen2d(int n, int m, const double* e2_dev, int nb, double scale, float2* out, cudaStream_t st) {
+  const long long ng = (long long)n * n;
+  kgen2d_kernel<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(n, m, e2_dev, nb, scale, out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ gram3 --
+// One CTA sweeps a contiguous x-range in chunks of 64 points staged in shared
+// memory; thread p owns bin pair p (b1 <= b2), accumulating FP32 over each
+// chunk and FP64 across chunks.
+constexpr int kGramChunk = 64;
+constexpr int kGramMaxNb = 32;
+
+__global__ void __launch_bounds__(256) gram3_kernel(const float2* __restrict__ a, long long ng, int nb,
+                                                    const float* __restrict__ delta, double* __restrict__ S) {
+  __shared__ float2 sa[kGramMaxNb][kGramChunk];
+  __shared__ float sd[kGramChunk];
+  const int npairs = nb * (nb + 1) / 2;
+  // pair index -> (b1, b2)
+  int b1 = -1, b2 = -1;
+  for (int p = threadIdx.x, c = 0, i = 0; i < nb && b1 < 0; ++i) {
+    if (p < c + (nb - i)) { b1 = i; b2 = i + (p - c); }
+    c += nb - i;
+  }
+  const long long per = (ng + gridDim.x - 1) / gridDim.x;
+  const long long x0 = blockIdx.x * per, x1 = min(ng, x0 + per);
+  double accr = 0.0, acci = 0.0;
+  for (long long xc = x0; xc < x1; xc += kGramChunk) {
+    const int cnt = (int)min((long long)kGramChunk, x1 - xc);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb * kGramChunk; i += blockDim.x) {
+      const int b = i / kGramChunk, xx = i % kGramChunk;
+      sa[b][xx] = xx < cnt ? a[(long long)b * ng + xc + xx] : make_float2(0.f, 0.f);
+    }
+    for (int i = threadIdx.x; i < kGramChunk; i += blockDim.x) sd[i] = i < cnt ? delta[xc + i] : 0.f;
+    __syncthreads();
+    if (threadIdx.x < npairs) {
+      float sr = 0.f, si = 0.f;
+#pragma unroll 8
+      for (int xx = 0; xx < kGramChunk; ++xx) {
+        const float2 u = sa[b1][xx], v = sa[b2][xx];
+        const float d = sd[xx];
+        // delta * u * conj(v)
+        sr += d * (u.x * v.x + u.y * v.y);
+        si += d * (u.y * v.x - u.x * v.y);
+      }
+      accr += sr;
+      acci += si;
+    }
+  }
+  if (threadIdx.x < npairs) {
+    atomicAdd(&S[((long long)b1 * nb + b2) * 2 + 0], accr);
+    atomicAdd(&S[((long long)b1 * nb + b2) * 2 + 1], acci);
+  }
+}
+
+cudaError_t launch_gram3(const float2* a, long long ng, int nb, const float* delta, double* S, cudaStream_t st) {
+  if (nb > kGramMaxNb || nb * (nb + 1) / 2 > 256) return cudaErrorInvalidValue;
+  long long blocks = (ng + 4095) / 4096;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  gram3_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, ng, nb, delta, S);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ simt4 --
+// T[r][c] = sum_x delta(x) f1_r(x) f2_r(x) a_c(x): the pair-by-single contraction
+// of the 4PCF (Eq. mu of Sec. 2.3, Eq. proj_4pcf_coeff) as an FP32 SIMT GEMM over
+// x with the pair operand formed on chip.  Per 32-point chunk: the tile's unique
+// singles and its column singles are staged in shared memory, the pair products
+// P_r = delta f1 f2 are formed once, then each thread accumulates a 4x4 block of
+// rows x cols.  FP32 over 512-point spans, FP64 across spans and CTAs.
+constexpr int kX = 32;          // points per chunk
+constexpr int kMaxUniq = 128;   // staged singles per tile
+constexpr int kSpan = 16;       // chunks per FP32 span
+
+template <int TCG, bool CPLX>
+__global__ void __launch_bounds__(256) simt4_kernel(const float2* __restrict__ astore, long long ng,
+                                                    const float* __restrict__ delta, const Tile4* __restrict__ tiles,
+                                                    const Row4* __restrict__ rows, const int* __restrict__ cols,
+                                                    const int* __restrict__ uniq, int nsplit, double* __restrict__ T) {
+  constexpr int TRG = 256 / TCG;
+  constexpr int TR = 4 * TRG, TC = 4 * TCG;
+  extern __shared__ float4 smem4[];
+  float2* Ps = reinterpret_cast<float2*>(smem4);            // [kX][TR]
+  float2* Cs = Ps + kX * TR;                                 // [kX][TC]
+  float2* Us = Cs + kX * TC;                                 // [kMaxUniq][kX]
+  float* Ds = reinterpret_cast<float*>(Us + kMaxUniq * kX);  // [kX]
+
+  const Tile4 tl = tiles[blockIdx.x];
+  const int tid = threadIdx.x;
+  const int cg = tid % TCG, rg = tid / TCG;
+  const long long per = ((ng / kX + nsplit - 1) / nsplit) * kX;
+  const long long x0 = blockIdx.y * per, x1 = min(ng, x0 + per);
+
+  float acc[4][4][CPLX ? 2 : 1];
+  double dacc[4][4][CPLX ? 2 : 1];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int c = 0; c < (CPLX ? 2 : 1); ++c) { acc[i][k][c] = 0.f; dacc[i][k][c] = 0.0; }
+
+  int span = 0;
+  for (long long xc = x0; xc < x1; xc += kX) {
+    __syncthreads();
+    // stage unique singles and delta
+    for (int i = tid; i < tl.nuniq * kX; i += 256) {
+      const int u = i / kX, xx = i % kX;
+      Us[u * kX + xx] = astore[(long long)uniq[tl.uniq0 + u] * ng + xc + xx];
+    }
+    for (int i = tid; i < tl.ncols * kX; i += 256) {
+      const int c = i / kX, xx = i % kX;
+      Cs[xx * TC + c] = astore[(long long)cols[tl.col0 + c] * ng + xc + xx];
+    }
+    for (int i = tid; i < (TC - tl.ncols) * kX; i += 256) {
+      const int c = tl.ncols + i / kX, xx = i % kX;
+      Cs[xx * TC + c] = make_float2(0.f, 0.f);
+    }
+    if (tid < kX) Ds[tid] = delta[xc + tid];
+    __syncthreads();
+    // form pair products P_r(x) = sign * delta * f1 * f2
+    for (int i = tid; i < TR * kX; i += 256) {
+      const int r = i % TR, xx = i / TR;
+      float2 p = make_float2(0.f, 0.f);
+      if (r < tl.nrows) {
+        const Row4 rw = rows[tl.row0 + r];
+        float2 f1 = Us[rw.u1 * kX + xx], f2 = Us[rw.u2 * kX + xx];
+        if (rw.flags & 1) f1.y = -f1.y;
+        if (rw.flags & 2) f2.y = -f2.y;
+        const float s = rw.sign * Ds[xx];
+        p = cmul(f1, f2);
+        p.x *= s;
+        p.y *= s;
+      }
+      Ps[xx * TR + r] = p;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int xx = 0; xx < kX; ++xx) {
+      const float4* pr = reinterpret_cast<const float4*>(Ps + xx * TR + rg * 4);
+      const float4* cr = reinterpret_cast<const float4*>(Cs + xx * TC + cg * 4);
+      const float4 p01 = pr[0], p23 = pr[1], c01 = cr[0], c23 = cr[1];
+      const float2 P[4] = {{p01.x, p01.y}, {p01.z, p01.w}, {p23.x, p23.y}, {p23.z, p23.w}};
+      const float2 C[4] = {{c01.x, c01.y}, {c01.z, c01.w}, {c23.x, c23.y}, {c23.z, c23.w}};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          acc[i][k][0] = fmaf(P[i].x, C[k].x, fmaf(-P[i].y, C[k].y, acc[i][k][0]));
+          if (CPLX) acc[i][k][CPLX ? 1 : 0] = fmaf(P[i].x, C[k].y, fmaf(P[i].y, C[k].x, acc[i][k][CPLX ? 1 : 0]));
+        }
+    }
+    if (++span == kSpan) {
+      span = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int c = 0; c < (CPLX ? 2 : 1); ++c) { dacc[i][k][c] += acc[i][k][c]; acc[i][k][c] = 0.f; }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = rg * 4 + i;
+    if (r >= tl.nrows) continue;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int c = cg * 4 + k;
+      if (c >= tl.ncols) continue;
+#pragma unroll
+      for (int q = 0; q < (CPLX ? 2 : 1); ++q) {
+        const double v = dacc[i][k][q] + acc[i][k][q];
+        atomicAdd(&T[(tl.tout + (long long)r * tl.ncols + c) * (CPLX ? 2 : 1) + q], v);
+      }
+    }
+  }
+}
+
+template <int TCG, bool CPLX>
+static cudaError_t simt4_t(const float2* astore, long long ng, const float* delta, const Tile4* tiles, int ntiles,
+                          const Row4* rows, const int* cols, const int* uniq, int nsplit, double* T,
+                          cudaStream_t st) {
+  constexpr int TR = 4 * (256 / TCG), TC = 4 * TCG;
+  const size_t smem = (size_t)(kX * TR + kX * TC + kMaxUniq * kX) * sizeof(float2) + kX * sizeof(float);
+  auto kern = simt4_kernel<TCG, CPLX>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  dim3 grid((unsigned)ntiles, (unsigned)nsplit);
+  kern<<<grid, 256, smem, st>>>(astore, ng, delta, tiles, rows, cols, uniq, nsplit, T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_simt4(const float2* astore, long long ng, const float* delta, const Tile4* tiles, int ntiles,
+                         const Row4* rows, const int* cols, const int* uniq, int complex_out, int tcg, int nsplit,
+                         double* T, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (ng % kX) return cudaErrorInvalidValue;
+  if (complex_out) {
+    if (tcg == 4) return simt4_t<4, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, T, st);
+    if (tcg == 8) return simt4_t<8, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, T, st);
+    if (tcg == 16) return simt4_t<16, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, T, st);
+  } else {
+    if (tcg == 4) return simt4_t<4, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, T, st);
+    if (tcg == 8) return simt4_t<8, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, T, st);
+    if (tcg == 16) return simt4_t<16, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, T, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------- finalisation --
+__global__ void couple_kernel(const double* __restrict__ T, int complex_t, const int* __restrict__ ptr,
+                              const int* __restrict__ idx, const double* __restrict__ coef, int nout,
+                              double* __restrict__ zeta) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nout) return;
+  double re = 0.0, im = 0.0;
+  for (int e = ptr[o]; e < ptr[o + 1]; ++e) {
+    int i = idx[e];
+    const bool cj = i < 0;
+    if (cj) i = -i - 1;
+    const double c = coef[e];
+    if (complex_t) {
+      re += c * T[2LL * i];
+      im += c * (cj ? -T[2LL * i + 1] : T[2LL * i + 1]);
+    } else {
+      re += c * T[i];
+    }
+  }
+  if (complex_t) {
+    zeta[2LL * o] = re;
+    zeta[2LL * o + 1] = im;
+  } else {
+    zeta[o] = re;
+  }
+}
+
+cudaError_t launch_couple(const double* T, int complex_t, const int* ptr, const int* idx, const double* coef, int nout,
+                          double* zeta, cudaStream_t st) {
+  if (nout <= 0) return cudaSuccess;
+  couple_kernel<<<(nout + 255) / 256, 256, 0, st>>>(T, complex_t, ptr, idx, coef, nout, zeta);
+  return cudaGetLastError();
+}
+
+__global__ void finish3_kernel(const double* __restrict__ S, int full, int lmax, int nb, double* __restrict__ zeta) {
+  const int nl = lmax + 1;
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nl * nb * nb) return;
+  const int l = o / (nb * nb), b1 = (o / nb) % nb, b2 = o % nb;
+  // S stored for b1 <= b2; S[b2][b1] = conj(S[b1][b2])
+  const int lo = min(b1, b2), hi = max(b1, b2);
+  const double cj = (b1 <= b2) ? 1.0 : -1.0;
+  if (full) {
+    double s = 0.0;
+    for (int m = 0; m <= l; ++m) {
+      const long long pi = (long long)l * (l + 1) / 2 + m;
+      const double re = S[((pi * nb + lo) * nb + hi) * 2];
+      s += (m == 0 ? 1.0 : 2.0) * re;
+    }
+    zeta[o] = ((l & 1) ? -1.0 : 1.0) / sqrt(2.0 * l + 1.0) * s;
+  } else {
+    const long long pi = l;
+    zeta[2LL * o] = S[((pi * nb + lo) * nb + hi) * 2];
+    zeta[2LL * o + 1] = cj * S[((pi * nb + lo) * nb + hi) * 2 + 1];
+  }
+}
+
+cudaError_t launch_finish3(const double* S, int full, int lmax, int nb, double* zeta, cudaStream_t st) {
+  const int n = (lmax + 1) * nb * nb;
+  finish3_kernel<<<(n + 255) / 256, 256, 0, st>>>(S, full, lmax, nb, zeta);
+  return cudaGetLastError();
+}
+
+__global__ void normalize_kernel(double* zeta, long long nouter, int nb, int order, int ncomp, const double* acc,
+                                 double ng, const double* vbin) {
+  const long long per = (order == 4 ? (long long)nb * nb * nb : (long long)nb * nb);
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= nouter * per) return;
+  const double ngal = acc[1];
+  const double nbar = ngal / ng;
+  const long long w = i % per;
+  double norm = ngal;
+  if (order == 4) {
+    norm *= nbar * vbin[w / (nb * nb)] * nbar * vbin[(w / nb) % nb] * nbar * vbin[w % nb];
+  } else {
+    norm *= nbar * vbin[w / nb] * nbar * vbin[w % nb];
+  }
+  for (int c = 0; c < ncomp; ++c) zeta[i * ncomp + c] /= norm;
+}
+
+cudaError_t launch_normalize(double* zeta, long long nouter, int nb, int order, int ncomp, const double* acc, double ng,
+                             const double* vbin_dev, cudaStream_t st) {
+  const long long per = (order == 4 ? (long long)nb * nb * nb : (long long)nb * nb);
+  const long long n = nouter * per;
+  if (n <= 0) return cudaSuccess;
+  normalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(zeta, nouter, nb, order, ncomp, acc, ng, vbin_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace sbg

@@ -1,0 +1,56 @@
+// Internal declarations of the non-FFT kernels (launchers live in sbg_kernels.cu).
+#pragma once
+#include "sbg_common.cuh"
+
+namespace sbg {
+
+// ---- preprocessing (Sec. 4.1 mean subtraction; Eq. num_gals) ----
+// acc[0] += sum(x); then out = float(x - mean) and acc[1] += sum(x - mean + 1).
+cudaError_t launch_sum(const void* in, int is_f64, long long n, double* acc, cudaStream_t st);
+cudaError_t launch_convert(const void* in, int is_f64, long long n, const double* acc, int subtract,
+                           float* out, cudaStream_t st);
+
+// ---- kernel generation (Algorithms 1-2) ----
+// 3D: out[b][cell] = conj(Y_lm(r_hat)) Theta_b(|r|) * scale for b < nb (buffer pre-zeroed).
+cudaError_t launch_kgen3d(int n, int l, int m, double norm_lm, const double* e2_dev, int nb, double scale,
+                          float2* out, cudaStream_t st);
+// 2D: out[b][cell] = conj(((x+iy)/rho)^m) Theta_b(rho) * scale.
+cudaError_t launch_kgen2d(int n, int m, const double* e2_dev, int nb, double scale, float2* out,
+                          cudaStream_t st);
+
+// ---- 3PCF Gram (Eq. alm_to_zeta_clean / proj_3pcf_coeff, Algorithms 5 and 7) ----
+// S[b1][b2] += sum_x delta(x) a_b1(x) conj(a_b2(x)) for b1 <= b2, complex double.
+cudaError_t launch_gram3(const float2* a, long long ng, int nb, const float* delta, double* S,
+                         cudaStream_t st);
+
+// ---- 4PCF pair x single contraction tables (Algorithms 6 and 8) ----
+struct Tile4 {
+  int row0, nrows;     // rows of the global row table
+  int col0, ncols;     // cols of the global col table
+  int uniq0, nuniq;    // unique singles (indices into the a-store) staged for the rows
+  long long tout;      // offset (in outputs) of this tile's [nrows][ncols] block of T
+};
+struct Row4 {
+  int u1, u2;          // local (tile) indices of the two singles
+  int flags;           // bit0: conj first, bit1: conj second
+  float sign;          // +-1 from a_{l,-m} = (-1)^m conj(a_{lm}) (3D)
+};
+
+// T[tile][r][c] (+)= Re or complex of sum_x delta * f1 * f2 * a_col.
+cudaError_t launch_simt4(const float2* astore, long long ng, const float* delta, const Tile4* tiles,
+                         int ntiles, const Row4* rows, const int* cols, const int* uniq, int complex_out,
+                         int tcg, int nsplit, double* T, cudaStream_t st);
+
+// ---- finalisation ----
+// zeta[o] = sum_{e in [ptr[o], ptr[o+1])} coef[e] * T[idx[e]] (idx < 0: conj of T[-idx-1]).
+cudaError_t launch_couple(const double* T, int complex_t, const int* ptr, const int* idx, const double* coef,
+                          int nout, double* zeta, cudaStream_t st);
+// 3PCF from Grams: full: zeta[l][b1][b2] = (-1)^l/sqrt(2l+1) (Re S_l0 + 2 sum_{m>0} Re S_lm);
+// projected: zeta[m][b1][b2] = S_m (complex).  S is [npair][nb][nb][2] with b1 <= b2 filled.
+cudaError_t launch_finish3(const double* S, int full, int lmax, int nb, double* zeta, cudaStream_t st);
+// zeta[i] /= N_gal * prod nbar V_b over the bin indices of output i (Eq. for the normalisation
+// coefficient, Sec. 2.5).  order = 3 or 4; outputs laid out [..][b1][b2]([b3])[ncomp].
+cudaError_t launch_normalize(double* zeta, long long nouter, int nb, int order, int ncomp, const double* acc,
+                             double ng, const double* vbin_dev, cudaStream_t st);
+
+}  // namespace sbg

@@ -1,0 +1,254 @@
+"""ctypes binding of libsarabande_gb300.so: argument marshalling only.
+
+Every function of the C ABI (include/sarabande_gb300.h) is exposed under the
+same name; `Context` adds allocation of the float64 output arrays.  Fields may
+be numpy arrays (host) or CUDA torch tensors (device; SBG_FIELD_ON_DEVICE is set
+automatically).  There is no fallback: if the library is missing, loading
+raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsarabande_gb300.so")
+
+SBG_OK = 0
+SBG_F32, SBG_F64 = 0, 1
+SBG_PREC_FP32, SBG_PREC_BF16X3 = 0, 1
+SBG_3PCF, SBG_4PCF, SBG_NORMALIZED, SBG_SUBTRACT_MEAN, SBG_FIELD_ON_DEVICE = 1, 2, 4, 8, 16
+STATUS = {0: "SBG_OK", -1: "SBG_ERR_INVALID_ARG", -2: "SBG_ERR_UNSUPPORTED_SHAPE", -3: "SBG_ERR_BIN_RANGE",
+          -4: "SBG_ERR_EMPTY_BIN", -5: "SBG_ERR_OUT_OF_MEMORY", -6: "SBG_ERR_CUDA", -7: "SBG_ERR_TIMEOUT",
+          -8: "SBG_ERR_INTERNAL"}
+
+_lib = None
+
+
+class SbgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Field2D(ctypes.Structure):
+    _fields_ = [("field", ctypes.c_void_p), ("dtype", ctypes.c_int), ("shape", ctypes.c_int64 * 2),
+                ("edges", ctypes.c_void_p), ("zeta3", ctypes.c_void_p), ("zeta4", ctypes.c_void_p)]
+
+
+def lib():
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_int
+        L.sbg_create.argtypes = [i, ctypes.c_size_t, ctypes.POINTER(vp)]
+        L.sbg_create.restype = st
+        L.sbg_destroy.argtypes = [vp]
+        L.sbg_destroy.restype = None
+        L.sbg_set_stream.argtypes = [vp, vp]
+        L.sbg_set_stream.restype = st
+        L.sbg_status_string.argtypes = [st]
+        L.sbg_status_string.restype = ctypes.c_char_p
+        L.sbg_last_error.argtypes = [vp]
+        L.sbg_last_error.restype = ctypes.c_char_p
+        L.sbg_lambda_count.argtypes = [i, ctypes.POINTER(i)]
+        L.sbg_lambda_count.restype = st
+        L.sbg_lambda_list.argtypes = [i, vp]
+        L.sbg_lambda_list.restype = st
+        L.sbg_full.argtypes = [vp, vp, i, vp, vp, i, i, i, i, ctypes.c_uint, vp, vp]
+        L.sbg_full.restype = st
+        L.sbg_projected.argtypes = [vp, vp, i, vp, vp, i, i, i, ctypes.c_uint, vp, vp]
+        L.sbg_projected.restype = st
+        L.sbg_projected_batch.argtypes = [vp, ctypes.POINTER(Field2D), i, i, i, i, ctypes.c_uint]
+        L.sbg_projected_batch.restype = st
+        L.sbg_last_timings.argtypes = [vp, vp, ctypes.POINTER(i)]
+        L.sbg_last_timings.restype = st
+        _lib = L
+    return _lib
+
+
+# ---- same-name wrappers of the C ABI ----
+def sbg_create(device=0, budget=0):
+    h = ctypes.c_void_p()
+    s = lib().sbg_create(device, budget, ctypes.byref(h))
+    if s != SBG_OK:
+        raise SbgError(s, "sbg_create failed")
+    return h
+
+
+def sbg_destroy(h):
+    lib().sbg_destroy(h)
+
+
+def sbg_set_stream(h, stream):
+    return lib().sbg_set_stream(h, ctypes.c_void_p(stream))
+
+
+def sbg_status_string(s):
+    return lib().sbg_status_string(s).decode()
+
+
+def sbg_last_error(h):
+    return lib().sbg_last_error(h).decode()
+
+
+def sbg_lambda_count(lmax):
+    n = ctypes.c_int()
+    s = lib().sbg_lambda_count(lmax, ctypes.byref(n))
+    if s != SBG_OK:
+        raise SbgError(s, "sbg_lambda_count")
+    return n.value
+
+
+def sbg_lambda_list(lmax):
+    n = sbg_lambda_count(lmax)
+    out = np.zeros((n, 3), dtype=np.int32)
+    s = lib().sbg_lambda_list(lmax, out.ctypes.data)
+    if s != SBG_OK:
+        raise SbgError(s, "sbg_lambda_list")
+    return out
+
+
+def _field_ptr(field):
+    """(pointer, dtype code, shape, on_device, keepalive)."""
+    if hasattr(field, "data_ptr"):  # torch tensor
+        import torch
+        if not field.is_contiguous():
+            raise ValueError("field must be contiguous")
+        if field.dtype not in (torch.float32, torch.float64):
+            raise ValueError("field dtype must be float32 or float64")
+        dt = SBG_F64 if field.dtype == torch.float64 else SBG_F32
+        return field.data_ptr(), dt, tuple(field.shape), field.is_cuda, field
+    a = np.asarray(field)
+    if a.dtype not in (np.float32, np.float64):
+        raise ValueError("field dtype must be float32 or float64")
+    a = np.ascontiguousarray(a)
+    return a.ctypes.data, (SBG_F64 if a.dtype == np.float64 else SBG_F32), a.shape, False, a
+
+
+def _edges(edges):
+    return np.ascontiguousarray(np.asarray(edges, dtype=np.float64))
+
+
+def sbg_full(h, field, edges, lmax3, lmax4, prec, flags, zeta3=None, zeta4=None):
+    ptr, dt, shape, on_dev, keep = _field_ptr(field)
+    e = _edges(edges)
+    nb = len(e) - 1
+    if on_dev:
+        flags |= SBG_FIELD_ON_DEVICE
+    if (flags & SBG_3PCF) and zeta3 is None:
+        zeta3 = np.zeros((lmax3 + 1, nb, nb))
+    if (flags & SBG_4PCF) and zeta4 is None:
+        zeta4 = np.zeros((sbg_lambda_count(lmax4), nb, nb, nb))
+    shp = (ctypes.c_int64 * 3)(*shape) if len(shape) == 3 else (ctypes.c_int64 * 3)(*(list(shape) + [0, 0, 0])[:3])
+    s = lib().sbg_full(h, ptr, dt, shp, e.ctypes.data, nb, int(lmax3 or 0), int(lmax4 or 0), prec, flags,
+                       zeta3.ctypes.data if zeta3 is not None else None,
+                       zeta4.ctypes.data if zeta4 is not None else None)
+    del keep
+    if s != SBG_OK:
+        raise SbgError(s, sbg_last_error(h))
+    return zeta3, zeta4
+
+
+def sbg_projected(h, field, edges, mmax, prec, flags, zeta3=None, zeta4=None):
+    ptr, dt, shape, on_dev, keep = _field_ptr(field)
+    e = _edges(edges)
+    nb = len(e) - 1
+    if on_dev:
+        flags |= SBG_FIELD_ON_DEVICE
+    w = 2 * mmax + 1
+    if (flags & SBG_3PCF) and zeta3 is None:
+        zeta3 = np.zeros((mmax + 1, nb, nb, 2))
+    if (flags & SBG_4PCF) and zeta4 is None:
+        zeta4 = np.zeros((w, w, nb, nb, nb, 2))
+    shp = (ctypes.c_int64 * 2)(*(list(shape) + [0, 0])[:2])
+    s = lib().sbg_projected(h, ptr, dt, shp, e.ctypes.data, nb, mmax, prec, flags,
+                            zeta3.ctypes.data if zeta3 is not None else None,
+                            zeta4.ctypes.data if zeta4 is not None else None)
+    del keep
+    if s != SBG_OK:
+        raise SbgError(s, sbg_last_error(h))
+    return zeta3, zeta4
+
+
+def sbg_projected_batch(h, fields, edges_list, nbins, mmax, prec, flags):
+    n = len(fields)
+    arr = (Field2D * n)()
+    keep, outs = [], []
+    w = 2 * mmax + 1
+    for i, (f, e) in enumerate(zip(fields, edges_list)):
+        ptr, dt, shape, on_dev, k = _field_ptr(f)
+        ee = _edges(e)
+        z3 = np.zeros((mmax + 1, nbins, nbins, 2)) if flags & SBG_3PCF else None
+        z4 = np.zeros((w, w, nbins, nbins, nbins, 2)) if flags & SBG_4PCF else None
+        keep += [k, ee]
+        outs.append((z3, z4))
+        arr[i].field = ptr
+        arr[i].dtype = dt
+        arr[i].shape[0], arr[i].shape[1] = shape[0], shape[1]
+        arr[i].edges = ee.ctypes.data
+        arr[i].zeta3 = z3.ctypes.data if z3 is not None else None
+        arr[i].zeta4 = z4.ctypes.data if z4 is not None else None
+        if on_dev:
+            flags |= SBG_FIELD_ON_DEVICE
+    s = lib().sbg_projected_batch(h, arr, n, nbins, mmax, prec, flags)
+    del keep
+    if s != SBG_OK:
+        raise SbgError(s, sbg_last_error(h))
+    return outs
+
+
+def sbg_last_timings(h):
+    out = np.zeros(8)
+    n = ctypes.c_int()
+    lib().sbg_last_timings(h, out.ctypes.data, ctypes.byref(n))
+    return out[: n.value]
+
+
+class Context:
+    """Owns one sbg_context (one per host thread)."""
+
+    def __init__(self, device=0, budget=0):
+        self.h = sbg_create(device, budget)
+
+    def close(self):
+        if self.h:
+            sbg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        return sbg_set_stream(self.h, stream)
+
+    def full(self, field, edges, lmax3=None, lmax4=None, prec=SBG_PREC_FP32, flags=SBG_SUBTRACT_MEAN):
+        if lmax3 is not None:
+            flags |= SBG_3PCF
+        if lmax4 is not None:
+            flags |= SBG_4PCF
+        return sbg_full(self.h, field, edges, lmax3, lmax4, prec, flags)
+
+    def projected(self, field, edges, mmax, npcf=(3, 4), prec=SBG_PREC_FP32, flags=SBG_SUBTRACT_MEAN):
+        if 3 in npcf:
+            flags |= SBG_3PCF
+        if 4 in npcf:
+            flags |= SBG_4PCF
+        return sbg_projected(self.h, field, edges, mmax, prec, flags)
+
+    def projected_batch(self, fields, edges_list, nbins, mmax, npcf=(3, 4), prec=SBG_PREC_FP32,
+                        flags=SBG_SUBTRACT_MEAN):
+        if 3 in npcf:
+            flags |= SBG_3PCF
+        if 4 in npcf:
+            flags |= SBG_4PCF
+        return sbg_projected_batch(self.h, fields, edges_list, nbins, mmax, prec, flags)
+
+    def timings(self):
+        return sbg_last_timings(self.h)

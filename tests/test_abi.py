@@ -1,0 +1,68 @@
+"""Host-side checks of the C-ABI library (no GPU): it loads, exports every
+function that include/sarabande_gb300.h declares, and its host-only calls agree
+with the oracle's definitions."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import sarabande_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sbg():
+    from paper_2210_10206_gb300 import build, sbg as s
+    build.build()
+    s.lib()
+    return s
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(sbg_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(sbg):
+    names = _declared()
+    assert {"sbg_create", "sbg_full", "sbg_projected", "sbg_projected_batch"} <= names
+    lib = ctypes.CDLL(sbg.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_lambda_list_matches_oracle(sbg):
+    for lmax in range(0, 8):
+        assert sbg.sbg_lambda_count(lmax) == len(O.lambda_list(lmax))
+        assert [tuple(r) for r in sbg.sbg_lambda_list(lmax)] == O.lambda_list(lmax)
+    assert sbg.sbg_lambda_count(3) == 23 and sbg.sbg_lambda_count(4) == 42
+
+
+def test_status_strings_and_argument_errors(sbg):
+    assert sbg.sbg_status_string(-3) == "SBG_ERR_BIN_RANGE"
+    assert sbg.sbg_status_string(0) == "SBG_OK"
+    L = sbg.lib()
+    n = ctypes.c_int()
+    assert L.sbg_lambda_count(-1, ctypes.byref(n)) == -1
+    assert L.sbg_lambda_count(3, None) == -1
+    # NULL context is rejected without touching a device
+    assert L.sbg_full(None, None, 0, None, None, 1, 0, 0, 0, 1, None, None) == -1
+    assert L.sbg_projected(None, None, 0, None, None, 1, 0, 0, 1, None, None) == -1
+    L.sbg_destroy(None)
+
+
+def test_create_without_gpu_fails_cleanly(sbg):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    s = sbg.lib().sbg_create(0, 0, ctypes.byref(h))
+    assert s in (-1, -6) and not h.value
