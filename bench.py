@@ -1,0 +1,314 @@
+"""Benchmark: 4PCF fields/s on a 256^3 float32 lognormal field (lmax 4, 10 linear
+bins 2..32), the full 3D path (delta -> delta-hat -> 150 convolution
+coefficient arrays -> pair x single contraction -> couplings) through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x3|fp32] [--impl gpu|reference]
+
+One JSON line on rank 0.  `value` is device-timed throughput with the field
+already in HBM; `e2e` is the same call with a pinned host field (host->device
+copy of the field and device->host copy of zeta inside the timed region).
+Under torchrun each rank measures its own fields (weak scaling, no data-path
+collective); the timing is the max over ranks.
+`--impl reference` times the FP64 CPU oracle on a bounded sample instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "4PCF fields/s at 256³ (ℓmax 4, 10 bins): split-BF16 vs FP32 GPU, % roofline"
+WORKLOAD = "full256"
+LMAX4 = 4
+NB = 10
+# Algorithmic work of the 4PCF combination per field: the (Lambda, M) terms of
+# Algorithm 6 with m3 >= 0 (490 at lmax 4) x the bin triples b1 <= b2 <= b3
+# (220 at 10 bins) x N_g grid points x 4 flops (the real part of a complex
+# product with a complex pair product).
+ALG_TERMS_LM = 490
+ALG_BIN_TRIPLES = 220
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "bf16x3", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=256, help="grid side (256 is the benchmark workload; "
+                    "smaller sides are for profiling captures only)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) > 8:
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------- oracle leg --
+def oracle_sample(field, edges):
+    """Time the FP64 oracle, as it stands, on a bounded sample of one 256^3
+    4PCF field and scale to fields/s.  Per field the oracle runs
+    O.kernel_full for each (l, m in -l..l) (25 at lmax 4), O.a_coefficient for
+    each of those kernels' 10 bins (250), and O.triple_sum for each of the 804
+    (Lambda, M) terms over all grid points.  The sample times one call of
+    each, the last on a 1/32 slab of the grid, and scales by those counts."""
+    from oracle import sarabande_oracle as O
+    t0 = time.perf_counter()
+    d, _ = O.preprocess(field)
+    tk0 = time.perf_counter()
+    ks = O.kernel_full(d.shape, edges, 1, 1)
+    tk = time.perf_counter() - tk0
+    ta0 = time.perf_counter()
+    a0 = O.a_coefficient(d, ks[3])
+    ta = time.perf_counter() - ta0
+    ng = d.size
+    slab = ng // 32
+    dd = d.reshape(1, -1)[:, :slab]
+    A = np.stack([a0.ravel()[:slab]] * NB)
+    tb0 = time.perf_counter()
+    O.triple_sum(dd, A, A, A)
+    tb = (time.perf_counter() - tb0) * 32
+    n_k = (LMAX4 + 1) ** 2
+    n_a = n_k * NB
+    n_terms = sum(1 for (l1, l2, l3) in O.lambda_list(LMAX4) for m1 in range(-l1, l1 + 1)
+                  for m2 in range(-l2, l2 + 1) if abs(m1 + m2) <= l3)
+    per_field = n_k * tk + n_a * ta + n_terms * tb
+    return {"value": 1.0 / per_field, "unit": "fields/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"one 256^3 lognormal field, lmax 4, 10 bins: {n_k} x O.kernel_full, {n_a} x "
+                       f"O.a_coefficient and {n_terms} x O.triple_sum, each timed once (triple_sum on a "
+                       f"1/32 slab); per field {per_field:.0f} s extrapolated from "
+                       f"{time.perf_counter() - t0:.1f} s of oracle work"),
+            "seconds_per_field": per_field}
+
+
+def field_for(rank, grid=256):
+    from paper_2210_10206_gb300 import synth
+    w = dict(synth.WORKLOADS[WORKLOAD])
+    shape = (grid, grid, grid)
+    return synth.lognormal_field(w["seed"] + 100 * rank, shape, w["sigma"], w["slope"], w["cutoff"],
+                                 w["dtype"]), w["edges"]
+
+
+# ---------------------------------------------------------------- runners --
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "gpu" else "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def reduce_max(v, ws, device=None):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    field, edges = field_for(0)
+    times = []
+    for _ in range(args.warmup):
+        oracle_sample(field, edges)
+    for _ in range(args.steps):
+        times.append(oracle_sample(field, edges))
+    per = statistics.mean(t["seconds_per_field"] for t in times)
+    v = 1.0 / per
+    cb = dict(times[-1])
+    cb["value"] = v
+    cb.pop("seconds_per_field", None)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "fields/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "full 3D 4PCF, 256^3 float32 lognormal (sigma_G 1.5, P~k^-11/3), "
+                                  "lmax 4, 10 linear bins 2..32", "grid": 256, "nbins": NB, "lmax4": LMAX4},
+           "cpu_baseline": cb, "e2e": {"value": v, "unit": "fields/s", "h2d_bytes_per_step": 0,
+                                       "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_gpu(args):
+    import torch
+    from paper_2210_10206_gb300 import build, sbg
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ws, rank, local = dist_setup(args)
+    build.build()
+    field, edges = field_for(rank, args.grid)
+    ng = field.size
+    prec_name = args.prec
+    if prec_name == "auto":
+        prec_name = "bf16x3" if getattr(sbg, "HAS_BF16X3", False) else "fp32"
+    prec = sbg.SBG_PREC_BF16X3 if prec_name == "bf16x3" else sbg.SBG_PREC_FP32
+    ctx = sbg.Context(local)
+    dfield = torch.from_numpy(field).cuda()
+    flags = sbg.SBG_SUBTRACT_MEAN | sbg.SBG_4PCF
+    z4 = np.zeros((sbg.sbg_lambda_count(LMAX4), NB, NB, NB))
+    # plan (kernel spectra, tables) outside the timed region, then warm-up
+    t_plan0 = time.perf_counter()
+    sbg.sbg_full(ctx.h, dfield, edges, 0, LMAX4, prec, flags, None, z4)
+    t_plan = time.perf_counter() - t_plan0
+    cold_stages = sbg.sbg_last_timings(ctx.h)
+    for _ in range(max(args.warmup, 3) - 1):
+        sbg.sbg_full(ctx.h, dfield, edges, 0, LMAX4, prec, flags, None, z4)
+    # ---- device-timed region ----
+    clocks = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    stages = []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        sbg.sbg_full(ctx.h, dfield, edges, 0, LMAX4, prec, flags, None, z4)
+        stages.append(sbg.sbg_last_timings(ctx.h))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier(ws)
+    clk = clocks.stop()
+    stages = np.array(stages)
+    dev_ms = float(stages[:, :7].sum(1).mean())  # device time per step from the library's events
+    step_ms = reduce_max(dev_ms, ws, "cuda")
+    value = ws * 1000.0 / step_ms
+    launches = int(stages[:, 7].sum())
+    # ---- end-to-end through the C ABI with a pinned host field ----
+    host = torch.empty(field.shape, dtype=torch.float32, pin_memory=True)
+    host.numpy()[...] = field
+    hf = host.numpy()
+    sbg.sbg_full(ctx.h, hf, edges, 0, LMAX4, prec, flags, None, z4)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        sbg.sbg_full(ctx.h, hf, edges, 0, LMAX4, prec, flags, None, z4)
+    e_ms = (time.perf_counter() - e0) * 1000.0 / args.steps
+    e_ms = reduce_max(e_ms, ws, "cuda")
+    # ---- roofline of the dominant kernel: the 4PCF combination (stage 5) ----
+    comb_ms = float(stages[:, 5].mean())
+    conv_ms = float(stages[:, 3].mean())
+    alg_flops = ALG_TERMS_LM * ALG_BIN_TRIPLES * ng * 4.0
+    props = torch.cuda.get_device_properties(local)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    if prec_name == "bf16x3":
+        bound, unit = "tensor", "TFLOP/s"
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        peak_src = "of measured" if "bf16_tflops_sustained" in peaks else "of fallback"
+    else:
+        # FP32 SIMT: SMs x 128 FP32 lanes x 2 flops x the SM clock sampled under load
+        bound, unit = "alu", "TFLOP/s"
+        mhz = clk["sm_mhz"] or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1447.0)
+        peak = props.multi_processor_count * 128 * 2 * mhz * 1e6 / 1e12
+        peak_src = f"derived: {props.multi_processor_count} SMs x 128 lanes x 2 x {mhz:.0f} MHz"
+    achieved = alg_flops / (comb_ms * 1e-3) / 1e12
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+            "traffic": None, "kernel": "4PCF combination (sbg simt4/tc4)", "peak_source": peak_src,
+            "alg_flops_per_launch": alg_flops, "avg_ms": comb_ms}
+    hbm = peaks.get("hbm_gbs", 6787.9)
+    out = {"metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "bf16x3" if prec_name == "bf16x3" else "f32", "data": "synthetic",
+           "config": {"workload": "full 3D 4PCF, 256^3 float32 lognormal (sigma_G 1.5, P~k^-11/3), lmax 4, "
+                                  "10 linear bins 2..32", "grid": 256, "nbins": NB, "lmax4": LMAX4,
+                      "precision": prec_name, "l2": "inputs larger than L2 (20 GB of coefficients per step)",
+                      "kernel_spectra": "cached in the plan (Algorithm 1 run once per geometry)"},
+           "roofline": roof,
+           "stages_ms": {"preprocess": float(stages[:, 0].mean()), "fft_delta": float(stages[:, 1].mean()),
+                         "plan": float(stages[:, 2].mean()), "convolutions": conv_ms,
+                         "combination": comb_ms, "finalise": float(stages[:, 6].mean())},
+           # convolution stage: 150 coefficient arrays x 3 axis passes x (8 B read + 8 B write) per point
+           # plus the kernel spectrum read (8 B) of the first pass
+           "conv_gbs": 150 * 56 * ng / (conv_ms * 1e-3) / 1e9 if conv_ms else None,
+           "conv_hbm_frac": (150 * 56 * ng / (conv_ms * 1e-3) / 1e9) / hbm if conv_ms else None,
+           "cold_first_call_s": t_plan, "cold_plan_ms": float(cold_stages[2]),
+           "e2e": {"value": ws * 1000.0 / e_ms, "unit": "fields/s", "h2d_bytes_per_step": int(field.nbytes),
+                   "d2h_bytes_per_step": int(z4.nbytes)},
+           "gpu_launches": launches, "clocks": clk, "wall_s_timed": wall}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_sample(field, edges)
+        out["cpu_baseline"].pop("seconds_per_field", None)
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

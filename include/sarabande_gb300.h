@@ -145,7 +145,8 @@ sbg_status sbg_projected_batch(sbg_context* ctx, const sbg_field2d* fields, int 
 /* Device times (ms, CUDA events) of the stages of the last measurement call:
  * [0] upload+preprocess, [1] forward FFT of delta, [2] kernel spectra (plan),
  * [3] convolutions (inverse FFTs), [4] 3PCF Gram, [5] 4PCF combination,
- * [6] finalisation + download.  *n_stages is set to the count written (<= 8). */
+ * [6] finalisation + download; [7] (not a time) the number of kernels the call
+ * launched.  *n_stages is set to the count written (8); ms_per_stage must hold 8. */
 sbg_status sbg_last_timings(const sbg_context* ctx, double* ms_per_stage, int* n_stages);
 
 #ifdef __cplusplus

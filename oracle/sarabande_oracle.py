@@ -125,22 +125,24 @@ def kernel_full(shape, edges, l, m):
     Algorithm 1), shape [nbins, *shape], complex128."""
     z, y, x = offset_grids(shape)
     masks = bin_masks(shape, edges)
-    with np.errstate(invalid="ignore", divide="ignore"):
-        ystar = np.conj(sph_harm(l, m, z, y, x))
-    ystar = np.where(sum(c * c for c in (z, y, x)) > 0, ystar, 0.0)
-    return np.stack([np.where(mk, ystar, 0.0) for mk in masks])
+    out = np.zeros((len(masks),) + tuple(shape), dtype=np.complex128)
+    for b, mk in enumerate(masks):
+        # Y is evaluated only on the cells of the bin (r > 0 there)
+        out[b][mk] = np.conj(sph_harm(l, m, z[mk], y[mk], x[mk]))
+    return out
 
 
 def kernel_projected(shape, edges, m):
     """K^b_m(rho) = e^{-i m phi} Theta^b(rho) (Eq. c_m def kernel), with
     e^{i m phi} = ((x + i y)/rho)^m (Algorithm 2 notes); negative m allowed."""
     y, x = offset_grids(shape)
-    rho = np.sqrt((x * x + y * y).astype(np.float64))
-    with np.errstate(invalid="ignore", divide="ignore"):
-        u = (x + 1j * y) / rho
-    u = np.where(rho > 0, u, 0.0)
-    e = np.conj(u) ** m if m >= 0 else u ** (-m)
-    return np.stack([np.where(mk, e, 0.0) for mk in bin_masks(shape, edges)])
+    masks = bin_masks(shape, edges)
+    out = np.zeros((len(masks),) + tuple(shape), dtype=np.complex128)
+    for b, mk in enumerate(masks):
+        xb, yb = x[mk].astype(np.float64), y[mk].astype(np.float64)
+        u = (xb + 1j * yb) / np.sqrt(xb * xb + yb * yb)   # rho > 0 inside a bin
+        out[b][mk] = np.conj(u) ** m if m >= 0 else u ** (-m)
+    return out
 
 
 # ------------------------------------------------------------- convolution --
@@ -288,9 +290,17 @@ def zeta4_full(delta, edges, lmax, return_imag=False):
                 c = coupling(l1, l2, l3, m1, m2, m3)
                 if c == 0.0:
                     continue
-                p = (d * a[(l1, m1)])[:, None, :] * a[(l2, m2)][None, :, :]
-                z[i] += c * (p.reshape(nb * nb, -1) @ a[(l3, m3)].T).reshape(nb, nb, nb)
+                z[i] += c * triple_sum(d, a[(l1, m1)], a[(l2, m2)], a[(l3, m3)])
     return (z.real, z.imag) if return_imag else z.real
+
+
+def triple_sum(d, a1, a2, a3):
+    """sum_x d(x) a1[b1](x) a2[b2](x) a3[b3](x) for all bin triples: the
+    summand of Eq. mu (Sec. 2.3) / Eq. proj_4pcf_coeff at one (M) term.
+    a_i: [nb, X]; d: [1, X].  Returns [nb, nb, nb]."""
+    nb = a1.shape[0]
+    p = (d * a1)[:, None, :] * a2[None, :, :]
+    return (p.reshape(nb * nb, -1) @ a3.T).reshape(nb, nb, nb)
 
 
 def zeta4_full_entries(delta, edges, entries):
@@ -340,8 +350,7 @@ def zeta4_projected(delta, edges, mmax):
             m3 = -(m1 + m2)
             if abs(m3) > mmax:
                 continue
-            p = (d * c[m1])[:, None, :] * c[m2][None, :, :]
-            z[m1 + mmax, m2 + mmax] = (p.reshape(nb * nb, -1) @ c[m3].T).reshape(nb, nb, nb)
+            z[m1 + mmax, m2 + mmax] = triple_sum(d, c[m1], c[m2], c[m3])
     return z
 
 

@@ -118,6 +118,7 @@ struct Tables4 {
   std::vector<int> ptr, idx;
   std::vector<double> coef;
   long long tcount = 0;  // outputs of T (complex counted once)
+  bool tc = false;       // tiles built for the tensor-core kernel
   int nout = 0;
   // device
   DevBuf d_tiles[3], d_rows, d_cols, d_uniq, d_ptr, d_idx, d_coef;
@@ -127,11 +128,14 @@ struct Tables4 {
 
 struct sbg_context {
   int device = 0;
+  int nsm = 148;
   cudaStream_t own = nullptr;
   cudaStream_t stream = nullptr;
   size_t budget = 0, used = 0;
   std::string err;
   double timings[kStages] = {0};
+  long long nlaunch = 0;   // kernels launched by the current/last measurement call
+  long long last_launches = 0;
   cudaEvent_t ev[kStages + 1] = {};
   std::map<std::string, DevBuf> bufs;
   // full-plan cache
@@ -154,6 +158,12 @@ sbg_status fail(sbg_context* c, sbg_status s, const std::string& msg) {
     cudaError_t e_ = (call);                                                                     \
     if (e_ != cudaSuccess)                                                                       \
       return fail(ctx, SBG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+#define KL(call)        \
+  do {                  \
+    ++ctx->nlaunch;     \
+    CU(call);           \
   } while (0)
 
 #define ST(call)                       \
@@ -213,11 +223,17 @@ int store_index(int dim, int nb, int l, int m_abs, int b) {
 }
 
 // Build the pair x single contraction tables of the 4PCF and the coupling CSR.
-// Computed set: for m3 >= 0 and b2: rows (b1 <= b2, alpha1, alpha2) with
-// m1 + m2 = -m3, cols (b3 >= b2, l3 >= m3).  T is symmetric under permutation
-// of its three singles and T[-M] = conj T[M], so every needed triple maps into
-// the set by sorting bins and, if the column m is negative, negating all m.
-sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L) {
+// T[s1, s2, s3] = sum_x delta a_s1 a_s2 a_s3 is symmetric under permutations of
+// its singles s = (l, m, b) and T[-M] = conj T[M] (real delta), so the computed
+// set is: for each m3 >= 0 and bin b2, rows (alpha1, b1 <= b2, alpha2) with
+// m1 + m2 = -m3 and cols (b3 >= b2, l3 >= m3).  Every needed triple maps into
+// it by sorting the singles by bin and, if the last single's m is negative,
+// negating every m (Re T unchanged; conj for the complex 2D T).
+//   tc = false: FP32 SIMT tiles, rows per tile 256/128/64 by column class,
+//               <= 128 staged singles per tile.
+//   tc = true : tensor-core tiles of 128 rows (M of the MMA), <= kTcMaxU staged
+//               singles, <= 64 B-operand rows (2D: 2 per column single).
+sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, bool tc) {
   struct Ang { int l, m; };
   std::vector<Ang> angs;
   if (dim == 3) {
@@ -226,47 +242,49 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L) {
   } else {
     for (int m = -L; m <= L; ++m) angs.push_back({-1, m});
   }
-  // block bookkeeping: for (m3, b2) -> base offset, ncols, pair list
-  struct Block { long long base; int ncols; int npairs; std::vector<std::pair<int, int>> pairs; std::vector<int> l3s; };
-  std::vector<Block> blocks((L + 1) * nb);
-  long long off = 0;
-  for (int m3 = 0; m3 <= L; ++m3) {
-    std::vector<std::pair<int, int>> pairs;
-    for (int i = 0; i < (int)angs.size(); ++i)
-      for (int k = 0; k < (int)angs.size(); ++k)
-        if (angs[i].m + angs[k].m == -m3) pairs.push_back({i, k});
-    std::vector<int> l3s;
-    if (dim == 3) {
-      for (int l3 = m3; l3 <= L; ++l3) l3s.push_back(l3);
-    } else {
-      l3s.push_back(-1);
-    }
-    for (int b2 = 0; b2 < nb; ++b2) {
-      Block& bk = blocks[m3 * nb + b2];
-      bk.pairs = pairs;
-      bk.l3s = l3s;
-      bk.npairs = (int)pairs.size();
-      bk.ncols = (nb - b2) * (int)l3s.size();
-      bk.base = off;
-      off += (long long)(b2 + 1) * bk.npairs * bk.ncols;
-    }
-  }
-  t.tcount = off;
-
-  // Tiles: per block, column chunks of <= 64 and row chunks with <= TR rows and
-  // <= 128 distinct staged singles.  Each tile owns a dense [nrows][ncols] slab of T.
+  const int na = (int)angs.size();
+  auto ang_index = [&](int l, int m) -> int {
+    for (int i = 0; i < na; ++i)
+      if (angs[i].l == l && angs[i].m == m) return i;
+    return -1;
+  };
+  struct RowKey { int a1, a2, b1; };
   struct Slab { int r0, nr, c0, nc; long long tout; };
-  std::vector<std::vector<Slab>> slabs((L + 1) * nb);
+  struct Block {
+    std::vector<RowKey> rows;
+    std::map<long long, int> row_of;
+    std::vector<int> l3s;
+    int ncols = 0;
+    std::vector<Slab> slabs;
+  };
+  std::vector<Block> blocks((L + 1) * nb);
   long long so = 0;
+  const int col_chunk = tc ? (dim == 2 ? 32 : 64) : 64;
+  const int max_u = tc ? kTcMaxU : 128;
+  t.tc = tc;
   for (int m3 = 0; m3 <= L; ++m3)
     for (int b2 = 0; b2 < nb; ++b2) {
       Block& bk = blocks[m3 * nb + b2];
-      const int nrows_blk = (b2 + 1) * bk.npairs;
+      if (dim == 3) {
+        for (int l3 = m3; l3 <= L; ++l3) bk.l3s.push_back(l3);
+      } else {
+        bk.l3s.push_back(-1);
+      }
+      bk.ncols = (nb - b2) * (int)bk.l3s.size();
+      // rows ordered (alpha1, b1, alpha2): rows sharing alpha1 share their staged singles
+      for (int a1 = 0; a1 < na; ++a1)
+        for (int b1 = 0; b1 <= b2; ++b1)
+          for (int a2 = 0; a2 < na; ++a2)
+            if (angs[a1].m + angs[a2].m == -m3) {
+              bk.row_of[((long long)a1 * 4096 + a2) * 64 + b1] = (int)bk.rows.size();
+              bk.rows.push_back({a1, a2, b1});
+            }
+      const int nrows_blk = (int)bk.rows.size();
       if (nrows_blk == 0) continue;
-      for (int c0 = 0; c0 < bk.ncols; c0 += 64) {
-        const int nc = std::min(64, bk.ncols - c0);
-        const int cls = nc <= 16 ? 0 : (nc <= 32 ? 1 : 2);
-        const int TR = (cls == 0 ? 256 : (cls == 1 ? 128 : 64));
+      for (int c0 = 0; c0 < bk.ncols; c0 += col_chunk) {
+        const int nc = std::min(col_chunk, bk.ncols - c0);
+        const int cls = tc ? 0 : (nc <= 16 ? 0 : (nc <= 32 ? 1 : 2));
+        const int TR = tc ? 128 : (cls == 0 ? 256 : (cls == 1 ? 128 : 64));
         const int col0 = (int)t.cols.size();
         for (int c = c0; c < c0 + nc; ++c) {
           const int b3 = b2 + c / (int)bk.l3s.size();
@@ -284,13 +302,12 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L) {
           int nr = 0;
           const int rstart = r;
           while (r < nrows_blk && nr < TR) {
-            const int b1 = r / bk.npairs;
-            const auto pr = bk.pairs[r % bk.npairs];
-            const Ang a1 = angs[pr.first], a2 = angs[pr.second];
-            const int s1 = store_index(dim, nb, a1.l, std::abs(a1.m), b1);
+            const RowKey rk = bk.rows[r];
+            const Ang a1 = angs[rk.a1], a2 = angs[rk.a2];
+            const int s1 = store_index(dim, nb, a1.l, std::abs(a1.m), rk.b1);
             const int s2 = store_index(dim, nb, a2.l, std::abs(a2.m), b2);
             const int need = (local.count(s1) ? 0 : 1) + ((local.count(s2) || s2 == s1) ? 0 : 1);
-            if ((int)local.size() + need > 128) break;
+            if ((int)local.size() + need > max_u) break;
             if (!local.count(s1)) { const int k = (int)local.size(); local[s1] = k; t.uniq.push_back(s1); }
             if (!local.count(s2)) { const int k = (int)local.size(); local[s2] = k; t.uniq.push_back(s2); }
             Row4 rw;
@@ -307,50 +324,34 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L) {
             ++nr;
             ++r;
           }
+          if (nr == 0) return fail(ctx, SBG_ERR_INTERNAL, "4PCF tiling: a row needs more staged singles than allowed");
           tl.nrows = nr;
           tl.nuniq = (int)local.size();
           tl.tout = so;
-          slabs[m3 * nb + b2].push_back({rstart, nr, c0, nc, so});
+          bk.slabs.push_back({rstart, nr, c0, nc, so});
           so += (long long)nr * nc;
           t.tiles[cls].push_back(tl);
         }
       }
     }
   t.tcount = so;
-  // angular index lookup
-  auto ang_index = [&](int l, int m) -> int {
-    for (int i = 0; i < (int)angs.size(); ++i)
-      if (angs[i].l == l && angs[i].m == m) return i;
-    return -1;
-  };
-  // pair index within block
-  std::vector<std::map<long long, int>> pair_index(L + 1);
-  for (int m3 = 0; m3 <= L; ++m3) {
-    const Block& bk = blocks[m3 * nb];
-    for (int p = 0; p < bk.npairs; ++p)
-      pair_index[m3][(long long)bk.pairs[p].first * 4096 + bk.pairs[p].second] = p;
-  }
+
   auto lookup = [&](Single s[3]) -> long long {
-    // sort by bin (stable)
     Single v[3] = {s[0], s[1], s[2]};
     std::stable_sort(v, v + 3, [](const Single& a, const Single& b) { return a.b < b.b; });
-    // choose the column single: the last; if tie with the middle and the last has m<0
-    // while the middle has m>=0 (or vice versa) any choice works after negation.
-    bool neg = false;
-    if (v[2].m < 0) neg = true;
+    const bool neg = v[2].m < 0;
     if (neg)
       for (auto& q : v) q.m = -q.m;
     const int m3 = v[2].m;
     const int b2 = v[1].b;
     const Block& bk = blocks[m3 * nb + b2];
     const int i1 = ang_index(v[0].l, v[0].m), i2 = ang_index(v[1].l, v[1].m);
-    auto it = pair_index[m3].find((long long)i1 * 4096 + i2);
-    if (it == pair_index[m3].end()) return LLONG_MIN;
-    const int row = v[0].b * bk.npairs + it->second;
-    int l3pos = 0;
-    if (dim == 3) l3pos = v[2].l - m3;
+    auto it = bk.row_of.find(((long long)i1 * 4096 + i2) * 64 + v[0].b);
+    if (it == bk.row_of.end()) return LLONG_MIN;
+    const int row = it->second;
+    const int l3pos = dim == 3 ? v[2].l - m3 : 0;
     const int col = (v[2].b - b2) * (int)bk.l3s.size() + l3pos;
-    for (const Slab& sl : slabs[m3 * nb + b2]) {
+    for (const Slab& sl : bk.slabs) {
       if (row >= sl.r0 && row < sl.r0 + sl.nr && col >= sl.c0 && col < sl.c0 + sl.nc) {
         const long long ti = sl.tout + (long long)(row - sl.r0) * sl.nc + (col - sl.c0);
         return neg ? -ti - 1 : ti;
@@ -359,7 +360,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L) {
     return LLONG_MIN;
   };
 
-  // coupling CSR
+  // coupling CSR: one output per (Lambda, b1, b2, b3) [3D] or (m1, m2, b1, b2, b3) [2D]
   t.ptr.clear();
   t.idx.clear();
   t.coef.clear();
@@ -378,8 +379,8 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L) {
                     if (std::abs(m3) > l3) continue;
                     const double c = (((l1 + l2 + l3) & 1) ? -1.0 : 1.0) * three_j(l1, l2, l3, m1, m2, m3);
                     if (c == 0.0) continue;
-                    Single s[3] = {{l1, m1, b1}, {l2, m2, b2}, {l3, m3, b3}};
-                    long long ti = lookup(s);
+                    Single sg[3] = {{l1, m1, b1}, {l2, m2, b2}, {l3, m3, b3}};
+                    long long ti = lookup(sg);
                     if (ti == LLONG_MIN) return fail(ctx, SBG_ERR_INTERNAL, "4PCF table lookup failed");
                     if (ti < 0) ti = -ti - 1;  // Re T is invariant under M -> -M
                     t.idx.push_back((int)ti);
@@ -389,7 +390,6 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L) {
               }
         }
   } else {
-    const int W = 2 * L + 1;
     for (int m1 = -L; m1 <= L; ++m1)
       for (int m2 = -L; m2 <= L; ++m2)
         for (int b1 = 0; b1 < nb; ++b1)
@@ -397,15 +397,14 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L) {
             for (int b3 = 0; b3 < nb; ++b3) {
               const int m3 = -(m1 + m2);
               if (std::abs(m3) <= L) {
-                Single s[3] = {{-1, m1, b1}, {-1, m2, b2}, {-1, m3, b3}};
-                long long ti = lookup(s);
+                Single sg[3] = {{-1, m1, b1}, {-1, m2, b2}, {-1, m3, b3}};
+                long long ti = lookup(sg);
                 if (ti == LLONG_MIN) return fail(ctx, SBG_ERR_INTERNAL, "2D 4PCF table lookup failed");
                 t.idx.push_back((int)ti);
                 t.coef.push_back(1.0);
               }
               t.ptr.push_back((int)t.idx.size());
             }
-    (void)W;
   }
   t.nout = (int)t.ptr.size() - 1;
   for (int k = 0; k < 3; ++k) ST(upload(ctx, t.d_tiles[k], t.tiles[k]));
@@ -430,13 +429,13 @@ void free_tables4(sbg_context* ctx, Tables4* t) {
   delete t;
 }
 
-sbg_status ensure_tables4(sbg_context* ctx, int dim, int nb, int L) {
-  const std::string key = std::to_string(dim) + "/" + std::to_string(nb) + "/" + std::to_string(L);
+sbg_status ensure_tables4(sbg_context* ctx, int dim, int nb, int L, bool tc) {
+  const std::string key = std::to_string(dim) + "/" + std::to_string(nb) + "/" + std::to_string(L) + (tc ? "/tc" : "/simt");
   if (ctx->t4 && ctx->t4key == key) return SBG_OK;
   free_tables4(ctx, ctx->t4);
   ctx->t4 = nullptr;
   Tables4* t = new Tables4();
-  sbg_status s = build_tables4(ctx, *t, dim, nb, L);
+  sbg_status s = build_tables4(ctx, *t, dim, nb, L, tc);
   if (s != SBG_OK) {
     free_tables4(ctx, t);
     return s;
@@ -460,14 +459,14 @@ sbg_status fft3(sbg_context* ctx, int n, int sign, int first_load, const void* i
   // z axis (strided by n^2), fused first-pass load
   p.in = in; p.out = out; p.mul = mul; p.shared = shared; p.load = first_load;
   p.outer = 1; p.inner = (long long)n * n;
-  CU(fft_axis_pass(n, p, ctx->stream));
+  KL(fft_axis_pass(n, p, ctx->stream));
   // y axis
   p.in = out; p.load = LOAD_COMPLEX; p.mul = nullptr; p.shared = nullptr;
   p.outer = n; p.inner = n;
-  CU(fft_axis_pass(n, p, ctx->stream));
+  KL(fft_axis_pass(n, p, ctx->stream));
   // x axis (contiguous)
   p.outer = (long long)n * n; p.inner = 1;
-  CU(fft_axis_pass(n, p, ctx->stream));
+  KL(fft_axis_pass(n, p, ctx->stream));
   return SBG_OK;
 }
 
@@ -480,10 +479,10 @@ sbg_status fft2(sbg_context* ctx, int n, int sign, int first_load, const void* i
   p.sign = sign;
   p.in = in; p.out = out; p.mul = mul; p.shared = shared; p.load = first_load;
   p.outer = 1; p.inner = n;  // y axis
-  CU(fft_axis_pass(n, p, ctx->stream));
+  KL(fft_axis_pass(n, p, ctx->stream));
   p.in = out; p.load = LOAD_COMPLEX; p.mul = nullptr; p.shared = nullptr;
   p.outer = n; p.inner = 1;  // x axis
-  CU(fft_axis_pass(n, p, ctx->stream));
+  KL(fft_axis_pass(n, p, ctx->stream));
   return SBG_OK;
 }
 
@@ -499,6 +498,7 @@ sbg_status check_edges(sbg_context* ctx, const double* edges, int nb, int n) {
 
 sbg_status finish_timings(sbg_context* ctx) {
   CU(cudaStreamSynchronize(ctx->stream));
+  ctx->last_launches = ctx->nlaunch;
   for (int i = 0; i < kStages; ++i) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) {
@@ -528,6 +528,7 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
       if (vb[b] == 0.0) return fail(ctx, SBG_ERR_EMPTY_BIN, "bin " + std::to_string(b) + " holds no cell");
 
   for (int i = 0; i <= kStages; ++i) rec(ctx, i);  // reset
+  ctx->nlaunch = 0;
   rec(ctx, 0);
   // ---- inputs ----
   const size_t esz = dtype == SBG_F64 ? 8 : 4;
@@ -554,8 +555,8 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
     CU(cudaMemcpyAsync(d_vb, vb.data(), nb * 8, cudaMemcpyHostToDevice, ctx->stream));
   }
   CU(cudaMemsetAsync(d_acc, 0, 64, ctx->stream));
-  CU(launch_sum(d_in, dtype == SBG_F64, ng, d_acc, ctx->stream));
-  CU(launch_convert(d_in, dtype == SBG_F64, ng, d_acc, (flags & SBG_SUBTRACT_MEAN) ? 1 : 0, d_delta, ctx->stream));
+  KL(launch_sum(d_in, dtype == SBG_F64, ng, d_acc, ctx->stream));
+  KL(launch_convert(d_in, dtype == SBG_F64, ng, d_acc, (flags & SBG_SUBTRACT_MEAN) ? 1 : 0, d_delta, ctx->stream));
   rec(ctx, 1);
   // ---- delta-hat ----
   if (dim == 3) {
@@ -577,10 +578,10 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
       int l = 0;
       while ((l + 1) * (l + 2) / 2 <= g) ++l;
       const int m = g - l * (l + 1) / 2;
-      CU(launch_kgen3d(n, l, m, ylm_norm(l, m), d_e2, nb, inv_ng, dst, ctx->stream));
+      KL(launch_kgen3d(n, l, m, ylm_norm(l, m), d_e2, nb, inv_ng, dst, ctx->stream));
       ST(fft3(ctx, n, +1, LOAD_COMPLEX, dst, dst, nullptr, nullptr, nb, d_tw));
     } else {
-      CU(launch_kgen2d(n, g, d_e2, nb, inv_ng, dst, ctx->stream));
+      KL(launch_kgen2d(n, g, d_e2, nb, inv_ng, dst, ctx->stream));
       ST(fft2(ctx, n, +1, LOAD_COMPLEX, dst, dst, nullptr, nullptr, nb, ng, d_tw));
     }
     return SBG_OK;
@@ -634,35 +635,49 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
     } else {
       ST(fft2(ctx, n, +1, LOAD_MUL, nullptr, out, G, d_dhat, nb, ng, d_tw));
     }
-    if (do3 && g < ngroups3) CU(launch_gram3(out, ng, nb, d_delta, d_S + (size_t)g * nb * nb * 2, ctx->stream));
+    if (do3 && g < ngroups3) KL(launch_gram3(out, ng, nb, d_delta, d_S + (size_t)g * nb * nb * 2, ctx->stream));
   }
   rec(ctx, 4);
   rec(ctx, 5);
   // ---- 4PCF ----
   double* d_z4 = nullptr;
   if (do4) {
-    ST(ensure_tables4(ctx, dim, nb, lmax4));
+    const bool tc = prec == SBG_PREC_BF16X3;
+    ST(ensure_tables4(ctx, dim, nb, lmax4, tc));
     Tables4& t = *ctx->t4;
     const int cplx = dim == 2 ? 1 : 0;
     double* d_T;
     ST(buf(ctx, "T", (size_t)std::max<long long>(t.tcount, 1) * 8 * (cplx ? 2 : 1), (void**)&d_T));
     CU(cudaMemsetAsync(d_T, 0, (size_t)t.tcount * 8 * (cplx ? 2 : 1), ctx->stream));
-    {
+    if (tc) {
+      int* d_err;
+      ST(buf(ctx, "err", 16, (void**)&d_err));
+      CU(cudaMemsetAsync(d_err, 0, 16, ctx->stream));
+      const int ntl = (int)t.tiles[0].size();
+      const long long kblocks = ng / 32;
+      int nsplit = (int)std::max<long long>(1, std::min<long long>(kblocks / 64, (4LL * ctx->nsm + ntl - 1) / ntl));
+      KL(launch_tc4(d_astore, ng, d_delta, (const Tile4*)t.d_tiles[0].p, ntl, (const Row4*)t.d_rows.p,
+                    (const int*)t.d_cols.p, (const int*)t.d_uniq.p, cplx, nsplit, d_T, d_err, ctx->nsm, ctx->stream));
+      int herr = 0;
+      CU(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      CU(cudaStreamSynchronize(ctx->stream));
+      if (herr) return fail(ctx, SBG_ERR_TIMEOUT, "tensor-core 4PCF kernel gave up waiting (code " + std::to_string(herr) + ")");
+    } else {
       const int tcg[3] = {4, 8, 16};
       for (int k = 0; k < 3; ++k) {
         const int ntl = (int)t.tiles[k].size();
         if (!ntl) continue;
         int nsplit = (int)std::max<long long>(1, std::min<long long>(ng / 32, (152LL * 6 + ntl - 1) / ntl));
-        CU(launch_simt4(d_astore, ng, d_delta, (const Tile4*)t.d_tiles[k].p, ntl, (const Row4*)t.d_rows.p,
+        KL(launch_simt4(d_astore, ng, d_delta, (const Tile4*)t.d_tiles[k].p, ntl, (const Row4*)t.d_rows.p,
                         (const int*)t.d_cols.p, (const int*)t.d_uniq.p, cplx, tcg[k], nsplit, d_T, ctx->stream));
       }
     }
     ST(buf(ctx, "z4", (size_t)t.nout * 8 * (cplx ? 2 : 1), (void**)&d_z4));
-    CU(launch_couple(d_T, cplx, (const int*)t.d_ptr.p, (const int*)t.d_idx.p, (const double*)t.d_coef.p, t.nout, d_z4,
+    KL(launch_couple(d_T, cplx, (const int*)t.d_ptr.p, (const int*)t.d_idx.p, (const double*)t.d_coef.p, t.nout, d_z4,
                      ctx->stream));
     if (flags & SBG_NORMALIZED) {
       const long long nouter = t.nout / ((long long)nb * nb * nb);
-      CU(launch_normalize(d_z4, nouter, nb, 4, cplx ? 2 : 1, d_acc, (double)ng, d_vb, ctx->stream));
+      KL(launch_normalize(d_z4, nouter, nb, 4, cplx ? 2 : 1, d_acc, (double)ng, d_vb, ctx->stream));
     }
   }
   rec(ctx, 6);
@@ -672,8 +687,8 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
     const int nl = dim == 3 ? lmax3 + 1 : lmax3 + 1;
     const int ncomp = dim == 3 ? 1 : 2;
     ST(buf(ctx, "z3", (size_t)nl * nb * nb * 8 * ncomp, (void**)&d_z3));
-    CU(launch_finish3(d_S, dim == 3, lmax3, nb, d_z3, ctx->stream));
-    if (flags & SBG_NORMALIZED) CU(launch_normalize(d_z3, nl, nb, 3, ncomp, d_acc, (double)ng, d_vb, ctx->stream));
+    KL(launch_finish3(d_S, dim == 3, lmax3, nb, d_z3, ctx->stream));
+    if (flags & SBG_NORMALIZED) KL(launch_normalize(d_z3, nl, nb, 3, ncomp, d_acc, (double)ng, d_vb, ctx->stream));
     CU(cudaMemcpyAsync(zeta3, d_z3, (size_t)nl * nb * nb * 8 * ncomp, cudaMemcpyDeviceToHost, ctx->stream));
   }
   if (do4) {
@@ -702,6 +717,7 @@ sbg_status sbg_create(int cuda_device, size_t hbm_budget_bytes, sbg_context** ou
   sbg_context* ctx = new sbg_context();
   ctx->device = cuda_device;
   ctx->budget = hbm_budget_bytes;
+  cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, cuda_device);
   if (cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking) != cudaSuccess) {
     delete ctx;
     return SBG_ERR_CUDA;
@@ -786,7 +802,7 @@ sbg_status sbg_full(sbg_context* ctx, const void* field, sbg_dtype dtype, const 
   ctx->err.clear();
   if (!field || !shape || !edges) return fail(ctx, SBG_ERR_INVALID_ARG, "null field, shape or edges");
   if (dtype != SBG_F32 && dtype != SBG_F64) return fail(ctx, SBG_ERR_INVALID_ARG, "dtype");
-  if (prec != SBG_PREC_FP32) return fail(ctx, SBG_ERR_INVALID_ARG, "precision not available in this build");
+  if (prec != SBG_PREC_FP32 && prec != SBG_PREC_BF16X3) return fail(ctx, SBG_ERR_INVALID_ARG, "precision");
   if (flags & ~31u) return fail(ctx, SBG_ERR_INVALID_ARG, "unknown flag bits");
   if (!(flags & (SBG_3PCF | SBG_4PCF))) return fail(ctx, SBG_ERR_INVALID_ARG, "neither SBG_3PCF nor SBG_4PCF");
   if (nbins < 1 || nbins > kMaxBins) return fail(ctx, SBG_ERR_INVALID_ARG, "nbins must be 1..20");
@@ -807,7 +823,7 @@ sbg_status sbg_projected(sbg_context* ctx, const void* field, sbg_dtype dtype, c
   ctx->err.clear();
   if (!field || !shape || !edges) return fail(ctx, SBG_ERR_INVALID_ARG, "null field, shape or edges");
   if (dtype != SBG_F32 && dtype != SBG_F64) return fail(ctx, SBG_ERR_INVALID_ARG, "dtype");
-  if (prec != SBG_PREC_FP32) return fail(ctx, SBG_ERR_INVALID_ARG, "precision not available in this build");
+  if (prec != SBG_PREC_FP32 && prec != SBG_PREC_BF16X3) return fail(ctx, SBG_ERR_INVALID_ARG, "precision");
   if (flags & ~31u) return fail(ctx, SBG_ERR_INVALID_ARG, "unknown flag bits");
   if (!(flags & (SBG_3PCF | SBG_4PCF))) return fail(ctx, SBG_ERR_INVALID_ARG, "neither SBG_3PCF nor SBG_4PCF");
   if (nbins < 1 || nbins > kMaxBins) return fail(ctx, SBG_ERR_INVALID_ARG, "nbins must be 1..20");
@@ -828,6 +844,7 @@ sbg_status sbg_projected_batch(sbg_context* ctx, const sbg_field2d* fields, int 
   ctx->err.clear();
   if (!fields || nfields < 1) return fail(ctx, SBG_ERR_INVALID_ARG, "fields/nfields");
   double acc[kStages] = {0};
+  long long nl = 0;
   for (int i = 0; i < nfields; ++i) {
     sbg_status s = sbg_projected(ctx, fields[i].field, fields[i].dtype, fields[i].shape, fields[i].edges, nbins, mmax,
                                  prec, flags, fields[i].zeta3, fields[i].zeta4);
@@ -836,15 +853,18 @@ sbg_status sbg_projected_batch(sbg_context* ctx, const sbg_field2d* fields, int 
       return s;
     }
     for (int k = 0; k < kStages; ++k) acc[k] += ctx->timings[k];
+    nl += ctx->last_launches;
   }
   for (int k = 0; k < kStages; ++k) ctx->timings[k] = acc[k];
+  ctx->last_launches = nl;
   return SBG_OK;
 }
 
 sbg_status sbg_last_timings(const sbg_context* ctx, double* ms_per_stage, int* n_stages) {
   if (!ctx || !ms_per_stage || !n_stages) return SBG_ERR_INVALID_ARG;
   for (int i = 0; i < kStages; ++i) ms_per_stage[i] = ctx->timings[i];
-  *n_stages = kStages;
+  ms_per_stage[kStages] = (double)ctx->last_launches;
+  *n_stages = kStages + 1;
   return SBG_OK;
 }
 

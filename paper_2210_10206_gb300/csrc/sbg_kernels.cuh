@@ -41,6 +41,15 @@ cudaError_t launch_simt4(const float2* astore, long long ng, const float* delta,
                          int ntiles, const Row4* rows, const int* cols, const int* uniq, int complex_out,
                          int tcg, int nsplit, double* T, cudaStream_t st);
 
+// Tensor-core (tcgen05) split-BF16 version of the same contraction (sbg_tc.cu).
+// Tiles of exactly <= 128 rows, <= kTcMaxU staged singles and <= 64 B rows
+// (3D: columns; 2D: two per column).  *err is set (never cleared) if a bounded
+// wait inside the kernel expired.
+constexpr int kTcMaxU = 48;
+cudaError_t launch_tc4(const float2* astore, long long ng, const float* delta, const Tile4* tiles, int ntiles,
+                       const Row4* rows, const int* cols, const int* uniq, int complex_out, int nsplit, double* T,
+                       int* err, int nsm, cudaStream_t st);
+
 // ---- finalisation ----
 // zeta[o] = sum_{e in [ptr[o], ptr[o+1])} coef[e] * T[idx[e]] (idx < 0: conj of T[-idx-1]).
 cudaError_t launch_couple(const double* T, int complex_t, const int* ptr, const int* idx, const double* coef,

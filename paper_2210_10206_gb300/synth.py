@@ -58,7 +58,7 @@ def gaussian_field(seed, shape, slope, cutoff=None):
         p = np.where(k > 0, k ** float(slope), 0.0)
     if cutoff is not None:
         p = p * np.exp(-0.5 * (k / cutoff) ** 2)
-    g = np.fft.irfftn(np.fft.rfftn(w) * np.sqrt(p), s=shape)
+    g = np.fft.irfftn(np.fft.rfftn(w) * np.sqrt(p), s=shape, axes=tuple(range(len(shape))))
     g -= g.mean()
     return g / g.std()
 
