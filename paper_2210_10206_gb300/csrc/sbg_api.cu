@@ -114,14 +114,14 @@ struct Tables4 {
   // host
   std::vector<Tile4> tiles[3];  // by tcg class 4, 8, 16
   std::vector<Row4> rows;
-  std::vector<int> cols, uniq;
+  std::vector<int> cols, uniq, colslot;
   std::vector<int> ptr, idx;
   std::vector<double> coef;
   long long tcount = 0;  // outputs of T (complex counted once)
   bool tc = false;       // tiles built for the tensor-core kernel
   int nout = 0;
   // device
-  DevBuf d_tiles[3], d_rows, d_cols, d_uniq, d_ptr, d_idx, d_coef;
+  DevBuf d_tiles[3], d_rows, d_cols, d_uniq, d_colslot, d_ptr, d_idx, d_coef;
 };
 
 }  // namespace
@@ -260,7 +260,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
   std::vector<Block> blocks((L + 1) * nb);
   long long so = 0;
   const int col_chunk = tc ? (dim == 2 ? 32 : 64) : 64;
-  const int max_u = tc ? kTcMaxU : 128;
+  const int max_u = tc ? kTcMaxSlots : 128;
   t.tc = tc;
   for (int m3 = 0; m3 <= L; ++m3)
     for (int b2 = 0; b2 < nb; ++b2) {
@@ -293,12 +293,16 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
         }
         int r = 0;
         while (r < nrows_blk) {
-          Tile4 tl;
+          Tile4 tl{};
           tl.row0 = (int)t.rows.size();
           tl.col0 = col0;
           tl.ncols = nc;
           tl.uniq0 = (int)t.uniq.size();
           std::map<int, int> local;
+          // tensor-core tiles stage one slot list covering rows and columns
+          if (tc)
+            for (int c = 0; c < nc; ++c)
+              if (!local.count(t.cols[col0 + c])) { const int k = (int)local.size(); local[t.cols[col0 + c]] = k; }
           int nr = 0;
           const int rstart = r;
           while (r < nrows_blk && nr < TR) {
@@ -308,8 +312,8 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
             const int s2 = store_index(dim, nb, a2.l, std::abs(a2.m), b2);
             const int need = (local.count(s1) ? 0 : 1) + ((local.count(s2) || s2 == s1) ? 0 : 1);
             if ((int)local.size() + need > max_u) break;
-            if (!local.count(s1)) { const int k = (int)local.size(); local[s1] = k; t.uniq.push_back(s1); }
-            if (!local.count(s2)) { const int k = (int)local.size(); local[s2] = k; t.uniq.push_back(s2); }
+            if (!local.count(s1)) { const int k = (int)local.size(); local[s1] = k; if (!tc) t.uniq.push_back(s1); }
+            if (!local.count(s2)) { const int k = (int)local.size(); local[s2] = k; if (!tc) t.uniq.push_back(s2); }
             Row4 rw;
             rw.u1 = local[s1];
             rw.u2 = local[s2];
@@ -327,6 +331,22 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
           if (nr == 0) return fail(ctx, SBG_ERR_INTERNAL, "4PCF tiling: a row needs more staged singles than allowed");
           tl.nrows = nr;
           tl.nuniq = (int)local.size();
+          if (tc) {
+            // slots sorted by store index so that consecutive singles form one copy
+            std::vector<int> order;
+            for (auto& kv : local) order.push_back(kv.first);  // std::map iterates in key order
+            std::map<int, int> pos;
+            for (int k = 0; k < (int)order.size(); ++k) pos[order[k]] = k;
+            std::vector<int> remap(local.size());
+            for (auto& kv : local) remap[kv.second] = pos[kv.first];
+            for (int k = tl.row0; k < tl.row0 + nr; ++k) {
+              t.rows[k].u1 = remap[t.rows[k].u1];
+              t.rows[k].u2 = remap[t.rows[k].u2];
+            }
+            for (int v : order) t.uniq.push_back(v);
+            tl.colslot0 = (int)t.colslot.size();
+            for (int c = 0; c < nc; ++c) t.colslot.push_back(pos[t.cols[col0 + c]]);
+          }
           tl.tout = so;
           bk.slabs.push_back({rstart, nr, c0, nc, so});
           so += (long long)nr * nc;
@@ -411,6 +431,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
   ST(upload(ctx, t.d_rows, t.rows));
   ST(upload(ctx, t.d_cols, t.cols));
   ST(upload(ctx, t.d_uniq, t.uniq));
+  ST(upload(ctx, t.d_colslot, t.colslot));
   ST(upload(ctx, t.d_ptr, t.ptr));
   ST(upload(ctx, t.d_idx, t.idx));
   ST(upload(ctx, t.d_coef, t.coef));
@@ -423,6 +444,7 @@ void free_tables4(sbg_context* ctx, Tables4* t) {
   dev_free(ctx, t->d_rows);
   dev_free(ctx, t->d_cols);
   dev_free(ctx, t->d_uniq);
+  dev_free(ctx, t->d_colslot);
   dev_free(ctx, t->d_ptr);
   dev_free(ctx, t->d_idx);
   dev_free(ctx, t->d_coef);
@@ -448,8 +470,11 @@ sbg_status ensure_tables4(sbg_context* ctx, int dim, int nb, int L, bool tc) {
 void rec(sbg_context* ctx, int i) { cudaEventRecord(ctx->ev[i], ctx->stream); }
 
 // -------------------------------------------------------- FFT helpers ----
+// 3D transform in three axis passes; with final_out the last pass writes the
+// blocked coefficient store (singles single0 .. single0 + batch - 1 of nsingle).
 sbg_status fft3(sbg_context* ctx, int n, int sign, int first_load, const void* in, float2* out, const float2* mul,
-                const float2* shared, int batch, const float2* tw) {
+                const float2* shared, int batch, const float2* tw, float2* final_out = nullptr, int nsingle = 0,
+                int single0 = 0) {
   const long long ng = (long long)n * n * n;
   FftPass p{};
   p.twiddle = tw;
@@ -466,12 +491,16 @@ sbg_status fft3(sbg_context* ctx, int n, int sign, int first_load, const void* i
   KL(fft_axis_pass(n, p, ctx->stream));
   // x axis (contiguous)
   p.outer = (long long)n * n; p.inner = 1;
+  if (final_out) {
+    p.out = final_out; p.out_blocked = 1; p.nsingle = nsingle; p.single0 = single0;
+  }
   KL(fft_axis_pass(n, p, ctx->stream));
   return SBG_OK;
 }
 
 sbg_status fft2(sbg_context* ctx, int n, int sign, int first_load, const void* in, float2* out, const float2* mul,
-                const float2* shared, int batch, long long bstride, const float2* tw) {
+                const float2* shared, int batch, long long bstride, const float2* tw, float2* final_out = nullptr,
+                int nsingle = 0, int single0 = 0) {
   FftPass p{};
   p.twiddle = tw;
   p.batch = batch;
@@ -482,6 +511,9 @@ sbg_status fft2(sbg_context* ctx, int n, int sign, int first_load, const void* i
   KL(fft_axis_pass(n, p, ctx->stream));
   p.in = out; p.load = LOAD_COMPLEX; p.mul = nullptr; p.shared = nullptr;
   p.outer = n; p.inner = 1;  // x axis
+  if (final_out) {
+    p.out = final_out; p.out_blocked = 1; p.nsingle = nsingle; p.single0 = single0;
+  }
   KL(fft_axis_pass(n, p, ctx->stream));
   return SBG_OK;
 }
@@ -612,8 +644,9 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
   float2* d_astore = nullptr;
   float2* d_group = nullptr;
   double* d_S = nullptr;
-  if (do4) ST(buf(ctx, "astore", (size_t)ngroups4 * nb * ng * 8, (void**)&d_astore));
-  if (!cached || ngroups > ngroups4) ST(buf(ctx, "group", (size_t)nb * ng * 8, (void**)&d_group));
+  const int nsingle = ngroups4 * nb;  // singles in the blocked coefficient store
+  if (do4) ST(buf(ctx, "astore", (size_t)nsingle * ng * 8, (void**)&d_astore));
+  ST(buf(ctx, "group", (size_t)nb * ng * 8, (void**)&d_group));
   float2* d_gtmp = nullptr;
   if (!cached) ST(buf(ctx, "gtmp", (size_t)nb * ng * 8, (void**)&d_gtmp));
   const int ngroups3 = do3 ? npair(lmax3) : 0;
@@ -629,13 +662,18 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
       ST(gen_group(g, d_gtmp));
       G = d_gtmp;
     }
-    float2* out = (g < ngroups4) ? d_astore + (size_t)g * nb * ng : d_group;
+    const bool stored = g < ngroups4;
+    float2* fin = stored ? d_astore : nullptr;
     if (dim == 3) {
-      ST(fft3(ctx, n, +1, LOAD_MUL, nullptr, out, G, d_dhat, nb, d_tw));
+      ST(fft3(ctx, n, +1, LOAD_MUL, nullptr, d_group, G, d_dhat, nb, d_tw, fin, nsingle, g * nb));
     } else {
-      ST(fft2(ctx, n, +1, LOAD_MUL, nullptr, out, G, d_dhat, nb, ng, d_tw));
+      ST(fft2(ctx, n, +1, LOAD_MUL, nullptr, d_group, G, d_dhat, nb, ng, d_tw, fin, nsingle, g * nb));
     }
-    if (do3 && g < ngroups3) KL(launch_gram3(out, ng, nb, d_delta, d_S + (size_t)g * nb * nb * 2, ctx->stream));
+    if (do3 && g < ngroups3) {
+      double* Sg = d_S + (size_t)g * nb * nb * 2;
+      if (stored) KL(launch_gram3(d_astore, ng, nb, d_delta, Sg, nsingle, g * nb, ctx->stream));
+      else KL(launch_gram3(d_group, ng, nb, d_delta, Sg, 0, 0, ctx->stream));
+    }
   }
   rec(ctx, 4);
   rec(ctx, 5);
@@ -655,9 +693,25 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
       CU(cudaMemsetAsync(d_err, 0, 16, ctx->stream));
       const int ntl = (int)t.tiles[0].size();
       const long long kblocks = ng / 32;
-      int nsplit = (int)std::max<long long>(1, std::min<long long>(kblocks / 64, (4LL * ctx->nsm + ntl - 1) / ntl));
+      // x-splits per tile: units = ntl * nsplit spread evenly over the CTAs
+      int best = 1;
+      double best_eff = 0.0;
+      for (int k = 1; k <= 16 && k <= kblocks; ++k) {
+        const long long units = (long long)ntl * k;
+        const long long rounds = (units + ctx->nsm - 1) / ctx->nsm;
+        const double eff = (double)units / (double)(rounds * ctx->nsm);
+        if (eff > best_eff + 0.02) { best_eff = eff; best = k; }
+      }
+      int* d_cnt;
+      const long long units = (long long)ntl * best;
+      const long long rounds = (units + ctx->nsm - 1) / ctx->nsm;
+      const long long nk_unit = (kblocks + best - 1) / best;
+      const long long epochs = rounds * ((nk_unit + kTcEpoch - 1) / kTcEpoch) + 4;
+      ST(buf(ctx, "tccnt", (size_t)epochs * 4, (void**)&d_cnt));
+      CU(cudaMemsetAsync(d_cnt, 0, (size_t)epochs * 4, ctx->stream));
       KL(launch_tc4(d_astore, ng, d_delta, (const Tile4*)t.d_tiles[0].p, ntl, (const Row4*)t.d_rows.p,
-                    (const int*)t.d_cols.p, (const int*)t.d_uniq.p, cplx, nsplit, d_T, d_err, ctx->nsm, ctx->stream));
+                    (const int*)t.d_colslot.p, (const int*)t.d_uniq.p, nsingle, cplx, best, d_T, d_cnt, d_err,
+                    ctx->nsm, ctx->stream));
       int herr = 0;
       CU(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
       CU(cudaStreamSynchronize(ctx->stream));
@@ -669,7 +723,8 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
         if (!ntl) continue;
         int nsplit = (int)std::max<long long>(1, std::min<long long>(ng / 32, (152LL * 6 + ntl - 1) / ntl));
         KL(launch_simt4(d_astore, ng, d_delta, (const Tile4*)t.d_tiles[k].p, ntl, (const Row4*)t.d_rows.p,
-                        (const int*)t.d_cols.p, (const int*)t.d_uniq.p, cplx, tcg[k], nsplit, d_T, ctx->stream));
+                        (const int*)t.d_cols.p, (const int*)t.d_uniq.p, cplx, tcg[k], nsplit, nsingle, d_T,
+                        ctx->stream));
       }
     }
     ST(buf(ctx, "z4", (size_t)t.nout * 8 * (cplx ? 2 : 1), (void**)&d_z4));

@@ -130,7 +130,7 @@ template <int N, bool CONTIG> struct Geo {
   }
 };
 
-template <int N, bool CONTIG, int SIGN, int LOAD>
+template <int N, bool CONTIG, int SIGN, int LOAD, bool OUTB>
 __global__ void __launch_bounds__(Geo<N, CONTIG>::THREADS)
 fft_axis_kernel(FftPass p) {
   using G = Geo<N, CONTIG>;
@@ -191,15 +191,16 @@ fft_axis_kernel(FftPass p) {
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       const long long e = base + (long long)(k2 + R2 * k1) * estride;
-      p.out[boff + e] = u[k1];
+      if (OUTB) p.out[blocked_index(e, p.single0 + (int)blockIdx.y, p.nsingle)] = u[k1];
+      else p.out[boff + e] = u[k1];
     }
   }
 }
 
-template <int N, bool CONTIG, int SIGN, int LOAD>
+template <int N, bool CONTIG, int SIGN, int LOAD, bool OUTB = false>
 static cudaError_t launch_t(const FftPass& p, cudaStream_t st) {
   using G = Geo<N, CONTIG>;
-  auto kern = fft_axis_kernel<N, CONTIG, SIGN, LOAD>;
+  auto kern = fft_axis_kernel<N, CONTIG, SIGN, LOAD, OUTB>;
   static bool configured = false;  // attribute is per function; set once per process
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
@@ -220,8 +221,13 @@ static cudaError_t dispatch_n(const FftPass& p, cudaStream_t st) {
   const bool contig = (p.inner == 1);
   if (contig) {
     if (p.load != LOAD_COMPLEX) return cudaErrorInvalidValue;
+    if (p.out_blocked) {
+      if (p.sign < 0) return cudaErrorInvalidValue;
+      return launch_t<N, true, 1, LOAD_COMPLEX, true>(p, st);
+    }
     return p.sign < 0 ? launch_t<N, true, -1, LOAD_COMPLEX>(p, st) : launch_t<N, true, 1, LOAD_COMPLEX>(p, st);
   }
+  if (p.out_blocked) return cudaErrorInvalidValue;
   if (p.sign < 0) {
     if (p.load == LOAD_REAL) return launch_t<N, false, -1, LOAD_REAL>(p, st);
     if (p.load == LOAD_COMPLEX) return launch_t<N, false, -1, LOAD_COMPLEX>(p, st);

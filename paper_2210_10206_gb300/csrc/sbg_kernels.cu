@@ -150,7 +150,8 @@ constexpr int kGramChunk = 64;
 constexpr int kGramMaxNb = 32;
 
 __global__ void __launch_bounds__(256) gram3_kernel(const float2* __restrict__ a, long long ng, int nb,
-                                                    const float* __restrict__ delta, double* __restrict__ S) {
+                                                    const float* __restrict__ delta, double* __restrict__ S,
+                                                    int nsingle, int single0) {
   __shared__ float2 sa[kGramMaxNb][kGramChunk];
   __shared__ float sd[kGramChunk];
   const int npairs = nb * (nb + 1) / 2;
@@ -168,7 +169,9 @@ __global__ void __launch_bounds__(256) gram3_kernel(const float2* __restrict__ a
     __syncthreads();
     for (int i = threadIdx.x; i < nb * kGramChunk; i += blockDim.x) {
       const int b = i / kGramChunk, xx = i % kGramChunk;
-      sa[b][xx] = xx < cnt ? a[(long long)b * ng + xc + xx] : make_float2(0.f, 0.f);
+      const long long x = xc + xx;
+      sa[b][xx] = xx < cnt ? a[nsingle ? blocked_index(x, single0 + b, nsingle) : (long long)b * ng + x]
+                           : make_float2(0.f, 0.f);
     }
     for (int i = threadIdx.x; i < kGramChunk; i += blockDim.x) sd[i] = i < cnt ? delta[xc + i] : 0.f;
     __syncthreads();
@@ -192,11 +195,12 @@ __global__ void __launch_bounds__(256) gram3_kernel(const float2* __restrict__ a
   }
 }
 
-cudaError_t launch_gram3(const float2* a, long long ng, int nb, const float* delta, double* S, cudaStream_t st) {
+cudaError_t launch_gram3(const float2* a, long long ng, int nb, const float* delta, double* S, int nsingle,
+                         int single0, cudaStream_t st) {
   if (nb > kGramMaxNb || nb * (nb + 1) / 2 > 256) return cudaErrorInvalidValue;
   long long blocks = (ng + 4095) / 4096;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  gram3_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, ng, nb, delta, S);
+  gram3_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, ng, nb, delta, S, nsingle, single0);
   return cudaGetLastError();
 }
 
@@ -210,19 +214,21 @@ cudaError_t launch_gram3(const float2* a, long long ng, int nb, const float* del
 constexpr int kX = 32;          // points per chunk
 constexpr int kMaxUniq = 128;   // staged singles per tile
 constexpr int kSpan = 16;       // chunks per FP32 span
+constexpr int kUS = kX + 1;     // padded row of a staged single (bank spread)
 
 template <int TCG, bool CPLX>
 __global__ void __launch_bounds__(256) simt4_kernel(const float2* __restrict__ astore, long long ng,
                                                     const float* __restrict__ delta, const Tile4* __restrict__ tiles,
                                                     const Row4* __restrict__ rows, const int* __restrict__ cols,
-                                                    const int* __restrict__ uniq, int nsplit, double* __restrict__ T) {
+                                                    const int* __restrict__ uniq, int nsplit, int nsingle,
+                                                    double* __restrict__ T) {
   constexpr int TRG = 256 / TCG;
   constexpr int TR = 4 * TRG, TC = 4 * TCG;
   extern __shared__ float4 smem4[];
   float2* Ps = reinterpret_cast<float2*>(smem4);            // [kX][TR]
   float2* Cs = Ps + kX * TR;                                 // [kX][TC]
-  float2* Us = Cs + kX * TC;                                 // [kMaxUniq][kX]
-  float* Ds = reinterpret_cast<float*>(Us + kMaxUniq * kX);  // [kX]
+  float2* Us = Cs + kX * TC;                                 // [kMaxUniq][kUS]
+  float* Ds = reinterpret_cast<float*>(Us + kMaxUniq * kUS);  // [kX]
 
   const Tile4 tl = tiles[blockIdx.x];
   const int tid = threadIdx.x;
@@ -245,11 +251,11 @@ __global__ void __launch_bounds__(256) simt4_kernel(const float2* __restrict__ a
     // stage unique singles and delta
     for (int i = tid; i < tl.nuniq * kX; i += 256) {
       const int u = i / kX, xx = i % kX;
-      Us[u * kX + xx] = astore[(long long)uniq[tl.uniq0 + u] * ng + xc + xx];
+      Us[u * kUS + xx] = astore[blocked_index(xc + xx, uniq[tl.uniq0 + u], nsingle)];
     }
     for (int i = tid; i < tl.ncols * kX; i += 256) {
       const int c = i / kX, xx = i % kX;
-      Cs[xx * TC + c] = astore[(long long)cols[tl.col0 + c] * ng + xc + xx];
+      Cs[xx * TC + c] = astore[blocked_index(xc + xx, cols[tl.col0 + c], nsingle)];
     }
     for (int i = tid; i < (TC - tl.ncols) * kX; i += 256) {
       const int c = tl.ncols + i / kX, xx = i % kX;
@@ -263,7 +269,7 @@ __global__ void __launch_bounds__(256) simt4_kernel(const float2* __restrict__ a
       float2 p = make_float2(0.f, 0.f);
       if (r < tl.nrows) {
         const Row4 rw = rows[tl.row0 + r];
-        float2 f1 = Us[rw.u1 * kX + xx], f2 = Us[rw.u2 * kX + xx];
+        float2 f1 = Us[rw.u1 * kUS + xx], f2 = Us[rw.u2 * kUS + xx];
         if (rw.flags & 1) f1.y = -f1.y;
         if (rw.flags & 2) f2.y = -f2.y;
         const float s = rw.sign * Ds[xx];
@@ -318,10 +324,10 @@ __global__ void __launch_bounds__(256) simt4_kernel(const float2* __restrict__ a
 
 template <int TCG, bool CPLX>
 static cudaError_t simt4_t(const float2* astore, long long ng, const float* delta, const Tile4* tiles, int ntiles,
-                          const Row4* rows, const int* cols, const int* uniq, int nsplit, double* T,
+                          const Row4* rows, const int* cols, const int* uniq, int nsplit, int nsingle, double* T,
                           cudaStream_t st) {
   constexpr int TR = 4 * (256 / TCG), TC = 4 * TCG;
-  const size_t smem = (size_t)(kX * TR + kX * TC + kMaxUniq * kX) * sizeof(float2) + kX * sizeof(float);
+  const size_t smem = (size_t)(kX * TR + kX * TC + kMaxUniq * kUS) * sizeof(float2) + kX * sizeof(float);
   auto kern = simt4_kernel<TCG, CPLX>;
   static bool configured = false;
   if (!configured) {
@@ -330,23 +336,23 @@ static cudaError_t simt4_t(const float2* astore, long long ng, const float* delt
     configured = true;
   }
   dim3 grid((unsigned)ntiles, (unsigned)nsplit);
-  kern<<<grid, 256, smem, st>>>(astore, ng, delta, tiles, rows, cols, uniq, nsplit, T);
+  kern<<<grid, 256, smem, st>>>(astore, ng, delta, tiles, rows, cols, uniq, nsplit, nsingle, T);
   return cudaGetLastError();
 }
 
 cudaError_t launch_simt4(const float2* astore, long long ng, const float* delta, const Tile4* tiles, int ntiles,
                          const Row4* rows, const int* cols, const int* uniq, int complex_out, int tcg, int nsplit,
-                         double* T, cudaStream_t st) {
+                         int nsingle, double* T, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   if (ng % kX) return cudaErrorInvalidValue;
   if (complex_out) {
-    if (tcg == 4) return simt4_t<4, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, T, st);
-    if (tcg == 8) return simt4_t<8, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, T, st);
-    if (tcg == 16) return simt4_t<16, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, T, st);
+    if (tcg == 4) return simt4_t<4, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, st);
+    if (tcg == 8) return simt4_t<8, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, st);
+    if (tcg == 16) return simt4_t<16, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, st);
   } else {
-    if (tcg == 4) return simt4_t<4, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, T, st);
-    if (tcg == 8) return simt4_t<8, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, T, st);
-    if (tcg == 16) return simt4_t<16, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, T, st);
+    if (tcg == 4) return simt4_t<4, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, st);
+    if (tcg == 8) return simt4_t<8, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, st);
+    if (tcg == 16) return simt4_t<16, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -20,14 +20,18 @@ cudaError_t launch_kgen2d(int n, int m, const double* e2_dev, int nb, double sca
 
 // ---- 3PCF Gram (Eq. alm_to_zeta_clean / proj_3pcf_coeff, Algorithms 5 and 7) ----
 // S[b1][b2] += sum_x delta(x) a_b1(x) conj(a_b2(x)) for b1 <= b2, complex double.
-cudaError_t launch_gram3(const float2* a, long long ng, int nb, const float* delta, double* S,
-                         cudaStream_t st);
+// nsingle > 0: `a` is the blocked coefficient store and bin b is single single0 + b;
+// nsingle = 0: `a` is [nb][ng].
+cudaError_t launch_gram3(const float2* a, long long ng, int nb, const float* delta, double* S, int nsingle,
+                         int single0, cudaStream_t st);
 
 // ---- 4PCF pair x single contraction tables (Algorithms 6 and 8) ----
 struct Tile4 {
   int row0, nrows;     // rows of the global row table
   int col0, ncols;     // cols of the global col table
-  int uniq0, nuniq;    // unique singles (indices into the a-store) staged for the rows
+  int uniq0, nuniq;    // staged singles (store indices); tensor-core tiles: sorted slot list
+  int colslot0;        // tensor-core tiles: slot of each column (colslot table)
+  int pad;
   long long tout;      // offset (in outputs) of this tile's [nrows][ncols] block of T
 };
 struct Row4 {
@@ -39,16 +43,19 @@ struct Row4 {
 // T[tile][r][c] (+)= Re or complex of sum_x delta * f1 * f2 * a_col.
 cudaError_t launch_simt4(const float2* astore, long long ng, const float* delta, const Tile4* tiles,
                          int ntiles, const Row4* rows, const int* cols, const int* uniq, int complex_out,
-                         int tcg, int nsplit, double* T, cudaStream_t st);
+                         int tcg, int nsplit, int nsingle, double* T, cudaStream_t st);
 
 // Tensor-core (tcgen05) split-BF16 version of the same contraction (sbg_tc.cu).
 // Tiles of exactly <= 128 rows, <= kTcMaxU staged singles and <= 64 B rows
 // (3D: columns; 2D: two per column).  *err is set (never cleared) if a bounded
 // wait inside the kernel expired.
-constexpr int kTcMaxU = 48;
+constexpr int kTcMaxSlots = 112;  // singles staged per K-block (rows and columns together)
+constexpr int kTcEpoch = 256;     // K-blocks between progress checkpoints of the lag limiter
+// Units (tile, x-split) are spread over a cooperative grid of one CTA per SM;
+// cnt holds one progress counter per (round, epoch), zeroed by the caller.
 cudaError_t launch_tc4(const float2* astore, long long ng, const float* delta, const Tile4* tiles, int ntiles,
-                       const Row4* rows, const int* cols, const int* uniq, int complex_out, int nsplit, double* T,
-                       int* err, int nsm, cudaStream_t st);
+                       const Row4* rows, const int* colslot, const int* slots, int nsingle, int complex_out,
+                       int nsplit, double* T, int* cnt, int* err, int nsm, cudaStream_t st);
 
 // ---- finalisation ----
 // zeta[o] = sum_{e in [ptr[o], ptr[o+1])} coef[e] * T[idx[e]] (idx < 0: conj of T[-idx-1]).

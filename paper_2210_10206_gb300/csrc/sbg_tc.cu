@@ -10,8 +10,9 @@
 //
 // Roles of a persistent CTA (one per SM):
 //   warp 9     loader: cp.async.bulk of the raw FP32 inputs of each 32-point
-//              K-block (delta, the tile's staged singles, its column singles)
-//              into a 4-deep ring, completion on mbarriers (expect_tx);
+//              K-block (delta and the tile's staged singles, which lie in a few
+//              contiguous runs of the blocked coefficient store) into a 4-deep
+//              ring, completion on mbarriers (expect_tx);
 //   warps 0-7  producers: form the swizzled (SW128, K-major) bf16 hi/lo A and B
 //              tiles of a K-block in a 2-deep ring; every 64 K-blocks they also
 //              fold the TMEM accumulator into a second TMEM accumulator
@@ -20,6 +21,10 @@
 //   warp 8     MMA issuer: one thread issues 12 tcgen05.mma (M=128, K=16) per
 //              K-block and commits to the mbarriers that free the operand stage
 //              and publish the accumulator.
+// Work units (tile, x-split) are dealt round-robin to a cooperative grid of one
+// CTA per SM; the loaders of all CTAs advance through x together (a CTA may run
+// at most two 256-K-block epochs ahead of the slowest), so that the singles of
+// the current x-window are read from HBM once and then served from L2.
 // Every wait is bounded (1 s of %globaltimer); on expiry the CTA records an
 // error code, drains its own copies, frees TMEM and returns.
 #include <algorithm>
@@ -32,7 +37,6 @@ namespace {
 
 constexpr int kRS = 4;                 // raw stages
 constexpr int kOS = 2;                 // operand stages
-constexpr int kMaxC = 64;              // staged column singles (3D); 2D uses <= 32
 constexpr int kFlush = 64;             // K-blocks per inner accumulation range
 constexpr int kKX = 32;                // grid points per K-block (64 bf16 = one 128-B row)
 constexpr int kProd = 256;             // producer threads (warps 0..7)
@@ -41,8 +45,10 @@ constexpr int kATile = 128 * 128;      // bytes of one 128-row bf16 K-block tile
 constexpr int kBTile = 64 * 128;       // bytes of one <=64-row tile
 constexpr int kOpStage = 2 * kATile + 2 * kBTile;
 constexpr int kRawD = kKX * 4;
-constexpr int kRawStage = kRawD + (kTcMaxU + kMaxC) * kKX * 8;
-constexpr int kSmem = kOS * kOpStage + kRS * kRawStage + 256 + 1024;
+constexpr int kRawStage = kRawD + kTcMaxSlots * kKX * 8;
+constexpr int kLag = 2;                // epochs a loader may run ahead of the slowest CTA
+constexpr int kMeta = 256 + 3 * kTcMaxSlots * 4;  // barriers + run table
+constexpr int kSmem = kOS * kOpStage + kRS * kRawStage + kMeta + 1024;
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -149,16 +155,17 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-struct Item {
+struct Unit {
   int tile;
   long long x0;
   int nk;
 };
 
-__device__ __forceinline__ Item item_of(int i, int ntiles, int nsplit, long long ng) {
-  Item it;
-  const int split = i / ntiles;
-  it.tile = i % ntiles;
+// Unit u covers x-split u / ntiles of tile u % ntiles.
+__device__ __forceinline__ Unit unit_of(long long u, int ntiles, int nsplit, long long ng) {
+  Unit it;
+  const int split = (int)(u / ntiles);
+  it.tile = (int)(u % ntiles);
   const long long per = ((ng / kKX + nsplit - 1) / nsplit) * kKX;
   it.x0 = split * per;
   const long long x1 = min(ng, it.x0 + per);
@@ -171,12 +178,28 @@ __device__ __forceinline__ int n_mma(const Tile4& t, int cplx) {
   return (nb + 15) & ~15;
 }
 
+// Bounded wait for a global progress counter written by other CTAs.
+__device__ __forceinline__ bool wait_count(const int* c, int target, volatile int* err, int code) {
+  if (*(volatile const int*)c >= target) return true;
+  const unsigned long long t0 = gtime();
+  while (*(volatile const int*)c < target) {
+    if (*err) return false;
+    if (gtime() - t0 > kWaitNs) {
+      atomicCAS((int*)err, 0, code);
+      return false;
+    }
+    __nanosleep(256);
+  }
+  return true;
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads, 1)
 tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restrict__ delta,
-           const Tile4* __restrict__ tiles, int ntiles, const Row4* __restrict__ rows, const int* __restrict__ cols,
-           const int* __restrict__ uniq, int cplx, int nsplit, double* __restrict__ T, int* err_flag) {
+           const Tile4* __restrict__ tiles, int ntiles, const Row4* __restrict__ rows,
+           const int* __restrict__ colslot, const int* __restrict__ slots, int nsingle, int cplx, int nsplit,
+           double* __restrict__ T, int* cnt, int* err_flag) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* op_base = sm;
@@ -188,11 +211,17 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
   uint64_t* op_empty = bars + 2 * kRS + kOS;
   uint64_t* acc_full = bars + 2 * kRS + 2 * kOS;
   uint32_t* tmem_slot = (uint32_t*)(acc_full + 1);
+  int* run_start = (int*)(bars + 32);            // loader-private run table
+  int* run_len = run_start + kTcMaxSlots;
+  int* run_slot = run_len + kTcMaxSlots;
   volatile int* err = err_flag;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int nitems = ntiles * nsplit;
+  const long long nunits = (long long)ntiles * nsplit;
+  const long long nrounds = (nunits + gridDim.x - 1) / gridDim.x;
+  const long long nk_unit = ((ng / kKX) + nsplit - 1) / nsplit;
+  const int epochs = (int)((nk_unit + kTcEpoch - 1) / kTcEpoch);
 
   if (tid == 0) {
     for (int i = 0; i < kRS; ++i) {
@@ -220,38 +249,68 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
     // ------------------------------------------------------------- loader --
     uint32_t g = 0;
     bool ok = true;
-    for (int i = blockIdx.x; i < nitems && ok; i += gridDim.x) {
-      const Item it = item_of(i, ntiles, nsplit, ng);
-      const Tile4 tl = tiles[it.tile];
-      const uint32_t bytes = kRawD + (uint32_t)(tl.nuniq + tl.ncols) * kKX * 8;
-      for (int kb = 0; kb < it.nk; ++kb, ++g) {
-        const int rs = g % kRS;
-        const uint32_t ph = (g / kRS) & 1;
-        int good = 1;
-        if (lane == 0) good = mbar_wait(&raw_empty[rs], ph ^ 1, err, 11);
-        good = __shfl_sync(0xffffffffu, good, 0);
-        if (!good) {
-          ok = false;
-          break;
-        }
-        uint8_t* st = raw_base + rs * kRawStage;
-        if (lane == 0) mbar_expect_tx(&raw_full[rs], bytes);
-        __syncwarp();
-        const long long x = it.x0 + (long long)kb * kKX;
-        const int ncopy = 1 + tl.nuniq + tl.ncols;
-        for (int c = lane; c < ncopy; c += 32) {
-          if (c == 0) {
-            bulk_g2s(st, delta + x, kRawD, &raw_full[rs]);
-          } else if (c <= tl.nuniq) {
-            const int u = c - 1;
-            bulk_g2s(st + kRawD + u * kKX * 8, astore + (long long)uniq[tl.uniq0 + u] * ng + x, kKX * 8,
-                     &raw_full[rs]);
-          } else {
-            const int cc = c - 1 - tl.nuniq;
-            bulk_g2s(st + kRawD + (kTcMaxU + cc) * kKX * 8, astore + (long long)cols[tl.col0 + cc] * ng + x,
-                     kKX * 8, &raw_full[rs]);
+    for (long long rd = 0; rd < nrounds && ok; ++rd) {
+      const long long u = rd * gridDim.x + blockIdx.x;
+      Unit it{0, 0, 0};
+      Tile4 tl{};
+      int nruns = 0;
+      if (u < nunits) {
+        it = unit_of(u, ntiles, nsplit, ng);
+        tl = tiles[it.tile];
+        if (lane == 0) {
+          // runs of consecutive store indices in the tile's (sorted) slot list
+          for (int k = 0; k < tl.nuniq; ++k) {
+            const int v = slots[tl.uniq0 + k];
+            if (nruns > 0 && v == run_start[nruns - 1] + run_len[nruns - 1]) {
+              ++run_len[nruns - 1];
+            } else {
+              run_start[nruns] = v;
+              run_len[nruns] = 1;
+              run_slot[nruns] = k;
+              ++nruns;
+            }
           }
         }
+        nruns = __shfl_sync(0xffffffffu, nruns, 0);
+        __syncwarp();
+      }
+      const uint32_t bytes = kRawD + (uint32_t)tl.nuniq * kKX * 8;
+      for (int e = 0; e < epochs && ok; ++e) {
+        const long long ce = rd * epochs + e;  // global epoch index
+        if (ce >= kLag) {
+          int good = 1;
+          if (lane == 0) good = wait_count(&cnt[ce - kLag], (int)gridDim.x, err, 13);
+          if (!__shfl_sync(0xffffffffu, good, 0)) {
+            ok = false;
+            break;
+          }
+        }
+        const int kb1 = min(it.nk, (e + 1) * kTcEpoch);
+        for (int kb = e * kTcEpoch; kb < kb1; ++kb, ++g) {
+          const int rs = g % kRS;
+          const uint32_t ph = (g / kRS) & 1;
+          int good = 1;
+          if (lane == 0) good = mbar_wait(&raw_empty[rs], ph ^ 1, err, 11);
+          if (!__shfl_sync(0xffffffffu, good, 0)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = raw_base + rs * kRawStage;
+          if (lane == 0) mbar_expect_tx(&raw_full[rs], bytes);
+          __syncwarp();
+          const long long x = it.x0 + (long long)kb * kKX;
+          const long long slab = (x >> 5) * (long long)nsingle;  // start of this K-block in the blocked store
+          for (int r = lane; r <= nruns; r += 32) {
+            if (r == nruns) {
+              bulk_g2s(st, delta + x, kRawD, &raw_full[rs]);
+            } else {
+              bulk_g2s(st + kRawD + run_slot[r] * kKX * 8, astore + (slab + run_start[r]) * kKX,
+                       (uint32_t)run_len[r] * kKX * 8, &raw_full[rs]);
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) atomicAdd(&cnt[ce], 1);
       }
     }
     // drain: wait (bounded) for every issued stage's copies to land
@@ -264,8 +323,8 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
     if (lane == 0) {
       uint32_t q = 0;
       bool ok = true;
-      for (int i = blockIdx.x; i < nitems && ok; i += gridDim.x) {
-        const Item it = item_of(i, ntiles, nsplit, ng);
+      for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        const Unit it = unit_of(u, ntiles, nsplit, ng);
         const Tile4 tl = tiles[it.tile];
         const int N = n_mma(tl, cplx);
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
@@ -300,10 +359,17 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
     const int quarter = warp & 3, half = warp >> 2;
     uint32_t g = 0, q = 0, f = 0;
     bool ok = true;
-    for (int i = blockIdx.x; i < nitems && ok; i += gridDim.x) {
-      const Item it = item_of(i, ntiles, nsplit, ng);
+    for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+      const Unit it = unit_of(u, ntiles, nsplit, ng);
       const Tile4 tl = tiles[it.tile];
       const int N = n_mma(tl, cplx);
+      int cslot[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int c = rb + 32 * k;
+        const int cs = cplx ? (c >> 1) : c;
+        cslot[k] = (c < N && cs < tl.ncols) ? colslot[tl.colslot0 + cs] : 0;
+      }
       Row4 rw[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -321,7 +387,6 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
         const uint8_t* raw = raw_base + rs * kRawStage;
         const float* D = (const float*)raw;
         const float4* U4 = (const float4*)(raw + kRawD);
-        const float4* C4 = (const float4*)(raw + kRawD + kTcMaxU * kKX * 8);
         uint8_t* op = op_base + os * kOpStage;
         // ---- A: 4 rows x 4 points per thread ----
 #pragma unroll
@@ -360,7 +425,7 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
             const int part = cplx ? (c & 1) : 0;
             uint4 hv = make_uint4(0, 0, 0, 0), lv = make_uint4(0, 0, 0, 0);
             if (cs < tl.ncols) {
-              const float4 c0 = C4[cs * 16 + 2 * j], c1 = C4[cs * 16 + 2 * j + 1];
+              const float4 c0 = U4[cslot[k] * 16 + 2 * j], c1 = U4[cslot[k] * 16 + 2 * j + 1];
               const float2 av[4] = {{c0.x, c0.y}, {c0.z, c0.w}, {c1.x, c1.y}, {c1.z, c1.w}};
               uint32_t h[4], l[4];
 #pragma unroll
@@ -431,8 +496,8 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
 }
 
 cudaError_t launch_tc4(const float2* astore, long long ng, const float* delta, const Tile4* tiles, int ntiles,
-                       const Row4* rows, const int* cols, const int* uniq, int complex_out, int nsplit, double* T,
-                       int* err, int nsm, cudaStream_t st) {
+                       const Row4* rows, const int* colslot, const int* slots, int nsingle, int complex_out,
+                       int nsplit, double* T, int* cnt, int* err, int nsm, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   if (ng % kKX) return cudaErrorInvalidValue;
   static bool configured = false;
@@ -441,10 +506,17 @@ cudaError_t launch_tc4(const float2* astore, long long ng, const float* delta, c
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const long long nitems = (long long)ntiles * nsplit;
-  const int grid = (int)std::min<long long>(nitems, nsm);
-  tc4_kernel<<<grid, kThreads, kSmem, st>>>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, complex_out, nsplit,
-                                            T, err);
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc4_kernel, kThreads, kSmem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  // every CTA takes part in every round so that the progress counters fill up
+  const int grid = nsm;
+  void* args[] = {(void*)&astore, (void*)&ng,     (void*)&delta, (void*)&tiles, (void*)&ntiles,
+                  (void*)&rows,   (void*)&colslot, (void*)&slots, (void*)&nsingle, (void*)&complex_out,
+                  (void*)&nsplit, (void*)&T,      (void*)&cnt,   (void*)&err};
+  e = cudaLaunchCooperativeKernel((const void*)tc4_kernel, dim3(grid), dim3(kThreads), args, kSmem, st);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
