@@ -149,6 +149,29 @@ sbg_status sbg_projected_batch(sbg_context* ctx, const sbg_field2d* fields, int 
  * launched.  *n_stages is set to the count written (8); ms_per_stage must hold 8. */
 sbg_status sbg_last_timings(const sbg_context* ctx, double* ms_per_stage, int* n_stages);
 
+/* Projected 3PCF that allocates no device memory (the paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc
+ * during a measurement, e.g. code running inside a pre-sized memory pool or an
+ * allocator that must not be re-entered).  It computes exactly the zeta3 of
+ * sbg_projected (SBG_3PCF) with the same kernels, but every intermediate buffer
+ * lives in one static device array of the library (about 11 MB, held on every
+ * device that loads the library until the process exits).
+ *   field  : device pointer, [n][n] of `dtype` (n a power of two, 8..256).
+ *   edges  : host pointer, nbins + 1 increasing doubles, edges[nbins] < n/2,
+ *            nbins 1..10; mmax 0..10.
+ *   flags  : 0 or SBG_SUBTRACT_MEAN.
+ *   zeta3  : device pointer, [mmax+1][nbins][nbins][2] (re, im).
+ *   stream : cudaStream_t to run on (NULL: legacy default stream).
+ * Work is queued on `stream`; zeta3 is valid once the stream has completed.
+ * Sizes beyond the maxima return SBG_ERR_UNSUPPORTED_SHAPE (n) or
+ * SBG_ERR_INVALID_ARG (nbins, mmax, flags).  The first call made with a device
+ * current looks up the array's device address for that device; make that
+ * first call before any stream capture.  All calls share the one array: calls
+ * whose work overlaps on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller. */
+sbg_status sbg_projected3_noalloc(const void* field, sbg_dtype dtype, int64_t n, const double* edges, int nbins,
+                                  int mmax, unsigned flags, double* zeta3, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,8 @@ def lib():
         L.sbg_projected_batch.restype = st
         L.sbg_last_timings.argtypes = [vp, vp, ctypes.POINTER(i)]
         L.sbg_last_timings.restype = st
+        L.sbg_projected3_noalloc.argtypes = [vp, i, ctypes.c_int64, vp, i, i, ctypes.c_uint, vp, vp]
+        L.sbg_projected3_noalloc.restype = st
         _lib = L
     return _lib
 
@@ -206,6 +208,22 @@ def sbg_last_timings(h):
     n = ctypes.c_int()
     lib().sbg_last_timings(h, out.ctypes.data, ctypes.byref(n))
     return out[: n.value]
+
+
+def sbg_projected3_noalloc(field, edges, mmax, flags, zeta3, stream=0):
+    """Projected 3PCF with no device allocation: `field` and `zeta3` are CUDA
+    torch tensors ([n][n] float32/float64 and [mmax+1][nb][nb][2] float64);
+    work is queued on `stream` (a cudaStream_t as int)."""
+    ptr, dt, shape, on_dev, keep = _field_ptr(field)
+    if not on_dev or not hasattr(zeta3, "data_ptr") or not zeta3.is_cuda:
+        raise ValueError("field and zeta3 must be device tensors")
+    e = _edges(edges)
+    s = lib().sbg_projected3_noalloc(ptr, dt, shape[0], e.ctypes.data, len(e) - 1, mmax, flags,
+                                     zeta3.data_ptr(), ctypes.c_void_p(stream))
+    del keep
+    if s != SBG_OK:
+        raise SbgError(s, "sbg_projected3_noalloc")
+    return zeta3
 
 
 class Context:
