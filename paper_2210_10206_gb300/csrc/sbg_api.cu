@@ -248,135 +248,188 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
       if (angs[i].l == l && angs[i].m == m) return i;
     return -1;
   };
-  struct RowKey { int a1, a2, b1; };
-  struct Slab { int r0, nr, c0, nc; long long tout; };
+  // Two ways of choosing the formed pairs (rows) so that every canonical triple
+  // has one of its pairs among the rows and its third single among the columns:
+  //  tc = false (SIMT): bins sorted b1 <= b2 <= b3; rows (alpha1, b1 <= b2, alpha2),
+  //                     columns (b3 >= b2, l3) -> one block per (m3, b2);
+  //  tc = true (tensor): bins split in two halves; rows are pairs within one half
+  //                     (any triple has two bins in the same half), columns are
+  //                     every (b3, l3) -> one block per m3 with uniform columns.
+  auto half = [&](int b) { return b < (nb + 1) / 2 ? 0 : 1; };
+  struct RowKey { int a1, b1, a2, b2; };
+  struct Slab { int r0, nr, c0, nc; long long tout; int row0; };
   struct Block {
+    int m3 = 0, b2 = 0;
     std::vector<RowKey> rows;
     std::map<long long, int> row_of;
     std::vector<int> l3s;
-    int ncols = 0;
+    int ncols = 0, bcol0 = 0;  // columns: b3 in [bcol0, nb) x l3s, b3-major
     std::vector<Slab> slabs;
   };
-  std::vector<Block> blocks((L + 1) * nb);
-  long long so = 0;
-  const int col_chunk = tc ? (dim == 2 ? 32 : 64) : 64;
-  const int max_u = tc ? kTcMaxSlots : 128;
-  t.tc = tc;
+  auto rkey = [](int a1, int b1, int a2, int b2) -> long long {
+    return (((long long)a1 * 64 + b1) * 4096 + a2) * 64 + b2;
+  };
+  std::vector<Block> blocks;
+  auto block_of = [&](int m3, int b2) -> int { return tc ? m3 : m3 * nb + b2; };
   for (int m3 = 0; m3 <= L; ++m3)
-    for (int b2 = 0; b2 < nb; ++b2) {
-      Block& bk = blocks[m3 * nb + b2];
+    for (int b2 = 0; b2 < (tc ? 1 : nb); ++b2) {
+      Block bk;
+      bk.m3 = m3;
+      bk.b2 = b2;
       if (dim == 3) {
         for (int l3 = m3; l3 <= L; ++l3) bk.l3s.push_back(l3);
       } else {
         bk.l3s.push_back(-1);
       }
-      bk.ncols = (nb - b2) * (int)bk.l3s.size();
-      // rows ordered (alpha1, b1, alpha2): rows sharing alpha1 share their staged singles
-      for (int a1 = 0; a1 < na; ++a1)
-        for (int b1 = 0; b1 <= b2; ++b1)
-          for (int a2 = 0; a2 < na; ++a2)
-            if (angs[a1].m + angs[a2].m == -m3) {
-              bk.row_of[((long long)a1 * 4096 + a2) * 64 + b1] = (int)bk.rows.size();
-              bk.rows.push_back({a1, a2, b1});
-            }
-      const int nrows_blk = (int)bk.rows.size();
-      if (nrows_blk == 0) continue;
-      for (int c0 = 0; c0 < bk.ncols; c0 += col_chunk) {
-        const int nc = std::min(col_chunk, bk.ncols - c0);
-        const int cls = tc ? 0 : (nc <= 16 ? 0 : (nc <= 32 ? 1 : 2));
-        const int TR = tc ? 128 : (cls == 0 ? 256 : (cls == 1 ? 128 : 64));
-        const int col0 = (int)t.cols.size();
-        for (int c = c0; c < c0 + nc; ++c) {
-          const int b3 = b2 + c / (int)bk.l3s.size();
-          const int l3 = bk.l3s[c % bk.l3s.size()];
-          t.cols.push_back(store_index(dim, nb, l3, m3, b3));
-        }
-        int r = 0;
-        while (r < nrows_blk) {
-          Tile4 tl{};
-          tl.row0 = (int)t.rows.size();
-          tl.col0 = col0;
-          tl.ncols = nc;
-          tl.uniq0 = (int)t.uniq.size();
-          std::map<int, int> local;
-          // tensor-core tiles stage one slot list covering rows and columns
-          if (tc)
-            for (int c = 0; c < nc; ++c)
-              if (!local.count(t.cols[col0 + c])) { const int k = (int)local.size(); local[t.cols[col0 + c]] = k; }
-          int nr = 0;
-          const int rstart = r;
-          while (r < nrows_blk && nr < TR) {
-            const RowKey rk = bk.rows[r];
-            const Ang a1 = angs[rk.a1], a2 = angs[rk.a2];
-            const int s1 = store_index(dim, nb, a1.l, std::abs(a1.m), rk.b1);
-            const int s2 = store_index(dim, nb, a2.l, std::abs(a2.m), b2);
-            const int need = (local.count(s1) ? 0 : 1) + ((local.count(s2) || s2 == s1) ? 0 : 1);
-            if ((int)local.size() + need > max_u) break;
-            if (!local.count(s1)) { const int k = (int)local.size(); local[s1] = k; if (!tc) t.uniq.push_back(s1); }
-            if (!local.count(s2)) { const int k = (int)local.size(); local[s2] = k; if (!tc) t.uniq.push_back(s2); }
-            Row4 rw;
-            rw.u1 = local[s1];
-            rw.u2 = local[s2];
-            rw.flags = (a1.m < 0 ? 1 : 0) | (a2.m < 0 ? 2 : 0);
-            float sg = 1.0f;
-            if (dim == 3) {
-              if (a1.m < 0 && (std::abs(a1.m) & 1)) sg = -sg;
-              if (a2.m < 0 && (std::abs(a2.m) & 1)) sg = -sg;
-            }
-            rw.sign = sg;
-            t.rows.push_back(rw);
-            ++nr;
-            ++r;
+      if (!tc) {
+        bk.bcol0 = b2;
+        // rows ordered (alpha1, b1, alpha2): rows sharing alpha1 share their staged singles
+        for (int a1 = 0; a1 < na; ++a1)
+          for (int b1 = 0; b1 <= b2; ++b1)
+            for (int a2 = 0; a2 < na; ++a2)
+              if (angs[a1].m + angs[a2].m == -m3) bk.rows.push_back({a1, b1, a2, b2});
+      } else {
+        bk.bcol0 = 0;
+        for (int b1 = 0; b1 < nb; ++b1)
+          for (int bb = b1; bb < nb; ++bb) {
+            if (half(b1) != half(bb)) continue;
+            for (int a1 = 0; a1 < na; ++a1)
+              for (int a2 = (bb == b1 ? a1 : 0); a2 < na; ++a2)
+                if (angs[a1].m + angs[a2].m == -m3) bk.rows.push_back({a1, b1, a2, bb});
           }
-          if (nr == 0) return fail(ctx, SBG_ERR_INTERNAL, "4PCF tiling: a row needs more staged singles than allowed");
-          tl.nrows = nr;
-          tl.nuniq = (int)local.size();
-          if (tc) {
-            // slots sorted by store index so that consecutive singles form one copy
-            std::vector<int> order;
-            for (auto& kv : local) order.push_back(kv.first);  // std::map iterates in key order
-            std::map<int, int> pos;
-            for (int k = 0; k < (int)order.size(); ++k) pos[order[k]] = k;
-            std::vector<int> remap(local.size());
-            for (auto& kv : local) remap[kv.second] = pos[kv.first];
-            for (int k = tl.row0; k < tl.row0 + nr; ++k) {
-              t.rows[k].u1 = remap[t.rows[k].u1];
-              t.rows[k].u2 = remap[t.rows[k].u2];
-            }
-            for (int v : order) t.uniq.push_back(v);
-            tl.colslot0 = (int)t.colslot.size();
-            for (int c = 0; c < nc; ++c) t.colslot.push_back(pos[t.cols[col0 + c]]);
+      }
+      bk.ncols = (nb - bk.bcol0) * (int)bk.l3s.size();
+      for (int r = 0; r < (int)bk.rows.size(); ++r) {
+        const RowKey& k = bk.rows[r];
+        bk.row_of[rkey(k.a1, k.b1, k.a2, k.b2)] = r;
+      }
+      blocks.push_back(std::move(bk));
+    }
+  long long so = 0;
+  const int col_chunk = tc ? (dim == 2 ? 32 : 64) : 64;
+  const int max_u = tc ? kTcMaxSlots : 128;
+  t.tc = tc;
+  for (Block& bk : blocks) {
+    const int nrows_blk = (int)bk.rows.size();
+    if (nrows_blk == 0) continue;
+    for (int c0 = 0; c0 < bk.ncols; c0 += col_chunk) {
+      const int nc = std::min(col_chunk, bk.ncols - c0);
+      const int cls = tc ? 0 : (nc <= 16 ? 0 : (nc <= 32 ? 1 : 2));
+      const int TR = tc ? 128 : (cls == 0 ? 256 : (cls == 1 ? 128 : 64));
+      const int col0 = (int)t.cols.size();
+      for (int c = c0; c < c0 + nc; ++c) {
+        const int b3 = bk.bcol0 + c / (int)bk.l3s.size();
+        const int l3 = bk.l3s[c % bk.l3s.size()];
+        t.cols.push_back(store_index(dim, nb, l3, bk.m3, b3));
+      }
+      int r = 0;
+      while (r < nrows_blk) {
+        Tile4 tl{};
+        tl.row0 = (int)t.rows.size();
+        tl.col0 = col0;
+        tl.ncols = nc;
+        tl.uniq0 = (int)t.uniq.size();
+        std::map<int, int> local;
+        // tensor-core tiles stage one slot list covering rows and columns
+        if (tc)
+          for (int c = 0; c < nc; ++c)
+            if (!local.count(t.cols[col0 + c])) { const int k = (int)local.size(); local[t.cols[col0 + c]] = k; }
+        int nr = 0;
+        const int rstart = r;
+        while (r < nrows_blk && nr < TR) {
+          const RowKey rk = bk.rows[r];
+          const Ang a1 = angs[rk.a1], a2 = angs[rk.a2];
+          const int s1 = store_index(dim, nb, a1.l, std::abs(a1.m), rk.b1);
+          const int s2 = store_index(dim, nb, a2.l, std::abs(a2.m), rk.b2);
+          const int need = (local.count(s1) ? 0 : 1) + ((local.count(s2) || s2 == s1) ? 0 : 1);
+          if ((int)local.size() + need > max_u) break;
+          if (!local.count(s1)) { const int k = (int)local.size(); local[s1] = k; if (!tc) t.uniq.push_back(s1); }
+          if (!local.count(s2)) { const int k = (int)local.size(); local[s2] = k; if (!tc) t.uniq.push_back(s2); }
+          Row4 rw;
+          rw.u1 = local[s1];
+          rw.u2 = local[s2];
+          rw.flags = (a1.m < 0 ? 1 : 0) | (a2.m < 0 ? 2 : 0);
+          float sg = 1.0f;
+          if (dim == 3) {
+            if (a1.m < 0 && (std::abs(a1.m) & 1)) sg = -sg;
+            if (a2.m < 0 && (std::abs(a2.m) & 1)) sg = -sg;
           }
-          tl.tout = so;
-          bk.slabs.push_back({rstart, nr, c0, nc, so});
-          so += (long long)nr * nc;
-          t.tiles[cls].push_back(tl);
+          rw.sign = sg;
+          t.rows.push_back(rw);
+          ++nr;
+          ++r;
         }
+        if (nr == 0) return fail(ctx, SBG_ERR_INTERNAL, "4PCF tiling: a row needs more staged singles than allowed");
+        tl.nrows = nr;
+        tl.nuniq = (int)local.size();
+        if (tc) {
+          // slots sorted by store index so that consecutive singles form one copy
+          std::vector<int> order;
+          for (auto& kv : local) order.push_back(kv.first);  // std::map iterates in key order
+          std::map<int, int> pos;
+          for (int k = 0; k < (int)order.size(); ++k) pos[order[k]] = k;
+          std::vector<int> remap(local.size());
+          for (auto& kv : local) remap[kv.second] = pos[kv.first];
+          for (int k = tl.row0; k < tl.row0 + nr; ++k) {
+            t.rows[k].u1 = remap[t.rows[k].u1];
+            t.rows[k].u2 = remap[t.rows[k].u2];
+          }
+          for (int v : order) t.uniq.push_back(v);
+          tl.colslot0 = (int)t.colslot.size();
+          for (int c = 0; c < nc; ++c) t.colslot.push_back(pos[t.cols[col0 + c]]);
+        }
+        tl.tout = so;
+        bk.slabs.push_back({rstart, nr, c0, nc, so, tl.row0});
+        so += (long long)nr * nc;
+        t.tiles[cls].push_back(tl);
       }
     }
+  }
   t.tcount = so;
 
-  auto lookup = [&](Single s[3]) -> long long {
-    Single v[3] = {s[0], s[1], s[2]};
-    std::stable_sort(v, v + 3, [](const Single& a, const Single& b) { return a.b < b.b; });
-    const bool neg = v[2].m < 0;
-    if (neg)
-      for (auto& q : v) q.m = -q.m;
-    const int m3 = v[2].m;
-    const int b2 = v[1].b;
-    const Block& bk = blocks[m3 * nb + b2];
-    const int i1 = ang_index(v[0].l, v[0].m), i2 = ang_index(v[1].l, v[1].m);
-    auto it = bk.row_of.find(((long long)i1 * 4096 + i2) * 64 + v[0].b);
+  // T index of a triple of singles (any order, any sign of M); negative when the
+  // entry found is the conjugate (all m negated).  rowsign receives the sign the
+  // tensor-core kernel leaves out of that entry's row.
+  auto find_entry = [&](const Single& x, const Single& y, const Single& z, bool neg, float* rowsign) -> long long {
+    const int m3 = z.m;
+    if (m3 < 0 || m3 > L) return LLONG_MIN;
+    if (x.m + y.m != -m3) return LLONG_MIN;
+    const int bi = block_of(m3, tc ? 0 : y.b);
+    if (bi < 0 || bi >= (int)blocks.size()) return LLONG_MIN;
+    const Block& bk = blocks[bi];
+    int i1 = ang_index(x.l, x.m), i2 = ang_index(y.l, y.m);
+    int b1 = x.b, b2 = y.b;
+    if (tc && b1 == b2 && i2 < i1) std::swap(i1, i2);
+    auto it = bk.row_of.find(rkey(i1, b1, i2, b2));
     if (it == bk.row_of.end()) return LLONG_MIN;
     const int row = it->second;
-    const int l3pos = dim == 3 ? v[2].l - m3 : 0;
-    const int col = (v[2].b - b2) * (int)bk.l3s.size() + l3pos;
+    if (z.b < bk.bcol0) return LLONG_MIN;
+    const int l3pos = dim == 3 ? z.l - m3 : 0;
+    const int col = (z.b - bk.bcol0) * (int)bk.l3s.size() + l3pos;
     for (const Slab& sl : bk.slabs) {
       if (row >= sl.r0 && row < sl.r0 + sl.nr && col >= sl.c0 && col < sl.c0 + sl.nc) {
         const long long ti = sl.tout + (long long)(row - sl.r0) * sl.nc + (col - sl.c0);
+        if (rowsign) *rowsign = t.rows[sl.row0 + (row - sl.r0)].sign;
         return neg ? -ti - 1 : ti;
       }
     }
+    return LLONG_MIN;
+  };
+  auto lookup = [&](Single s[3], float* rowsign) -> long long {
+    static const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    for (int neg = 0; neg < 2; ++neg)
+      for (const auto& p : perms) {
+        Single x = s[p[0]], y = s[p[1]], z = s[p[2]];
+        if (neg) { x.m = -x.m; y.m = -y.m; z.m = -z.m; }
+        if (x.b > y.b) continue;
+        if (tc) {
+          if (half(x.b) != half(y.b)) continue;
+        } else {
+          if (z.b < y.b) continue;
+        }
+        const long long ti = find_entry(x, y, z, neg != 0, rowsign);
+        if (ti != LLONG_MIN) return ti;
+      }
     return LLONG_MIN;
   };
 
@@ -400,11 +453,12 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
                     const double c = (((l1 + l2 + l3) & 1) ? -1.0 : 1.0) * three_j(l1, l2, l3, m1, m2, m3);
                     if (c == 0.0) continue;
                     Single sg[3] = {{l1, m1, b1}, {l2, m2, b2}, {l3, m3, b3}};
-                    long long ti = lookup(sg);
+                    float rs = 1.0f;
+                    long long ti = lookup(sg, &rs);
                     if (ti == LLONG_MIN) return fail(ctx, SBG_ERR_INTERNAL, "4PCF table lookup failed");
                     if (ti < 0) ti = -ti - 1;  // Re T is invariant under M -> -M
                     t.idx.push_back((int)ti);
-                    t.coef.push_back(c);
+                    t.coef.push_back(tc ? c * rs : c);
                   }
                 t.ptr.push_back((int)t.idx.size());
               }
@@ -418,7 +472,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
               const int m3 = -(m1 + m2);
               if (std::abs(m3) <= L) {
                 Single sg[3] = {{-1, m1, b1}, {-1, m2, b2}, {-1, m3, b3}};
-                long long ti = lookup(sg);
+                long long ti = lookup(sg, nullptr);
                 if (ti == LLONG_MIN) return fail(ctx, SBG_ERR_INTERNAL, "2D 4PCF table lookup failed");
                 t.idx.push_back((int)ti);
                 t.coef.push_back(1.0);

@@ -31,17 +31,19 @@ struct FftPass {
   int sign;              // -1 forward, +1 inverse (unnormalised)
   int load;              // FftLoad
   // Contiguous (last) pass only: when out_blocked is set, batch b of the output
-  // goes to the blocked coefficient store, element x of single s = single0 + b
-  // at ((x / 32) * nsingle + s) * 32 + x % 32 (32-point blocks of every single
-  // are adjacent, so one 32-point K-block of all singles is one contiguous slab).
+  // goes to the blocked coefficient store as single s = single0 + b (see
+  // blocked_re).
   int out_blocked;
   int nsingle;
   int single0;
 };
 
-// Index of grid point x of single s in the blocked coefficient store.
-__host__ __device__ __forceinline__ long long blocked_index(long long x, int s, int nsingle) {
-  return ((x >> 5) * nsingle + s) * 32 + (x & 31);
+// Blocked coefficient store (float view): for each 32-point K-block xb and
+// single s, 64 floats [Re x0..x31][Im x0..x31] at ((xb * nsingle + s) * 64).
+// One K-block of every single is one contiguous slab, and real and imaginary
+// parts of neighbouring points are adjacent (packed f32x2 arithmetic).
+__host__ __device__ __forceinline__ long long blocked_re(long long x, int s, int nsingle) {
+  return ((x >> 5) * nsingle + s) * 64 + (x & 31);
 }
 
 // Host launcher (sbg_fft.cu).  Returns cudaSuccess or the launch error.

@@ -191,8 +191,13 @@ fft_axis_kernel(FftPass p) {
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       const long long e = base + (long long)(k2 + R2 * k1) * estride;
-      if (OUTB) p.out[blocked_index(e, p.single0 + (int)blockIdx.y, p.nsingle)] = u[k1];
-      else p.out[boff + e] = u[k1];
+      if (OUTB) {
+        float* o = reinterpret_cast<float*>(p.out) + blocked_re(e, p.single0 + (int)blockIdx.y, p.nsingle);
+        o[0] = u[k1].x;
+        o[32] = u[k1].y;
+      } else {
+        p.out[boff + e] = u[k1];
+      }
     }
   }
 }

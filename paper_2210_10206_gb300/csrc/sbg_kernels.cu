@@ -170,8 +170,16 @@ __global__ void __launch_bounds__(256) gram3_kernel(const float2* __restrict__ a
     for (int i = threadIdx.x; i < nb * kGramChunk; i += blockDim.x) {
       const int b = i / kGramChunk, xx = i % kGramChunk;
       const long long x = xc + xx;
-      sa[b][xx] = xx < cnt ? a[nsingle ? blocked_index(x, single0 + b, nsingle) : (long long)b * ng + x]
-                           : make_float2(0.f, 0.f);
+      float2 v = make_float2(0.f, 0.f);
+      if (xx < cnt) {
+        if (nsingle) {
+          const float* f = reinterpret_cast<const float*>(a) + blocked_re(x, single0 + b, nsingle);
+          v = make_float2(f[0], f[32]);
+        } else {
+          v = a[(long long)b * ng + x];
+        }
+      }
+      sa[b][xx] = v;
     }
     for (int i = threadIdx.x; i < kGramChunk; i += blockDim.x) sd[i] = i < cnt ? delta[xc + i] : 0.f;
     __syncthreads();
@@ -251,11 +259,13 @@ __global__ void __launch_bounds__(256) simt4_kernel(const float2* __restrict__ a
     // stage unique singles and delta
     for (int i = tid; i < tl.nuniq * kX; i += 256) {
       const int u = i / kX, xx = i % kX;
-      Us[u * kUS + xx] = astore[blocked_index(xc + xx, uniq[tl.uniq0 + u], nsingle)];
+      const float* f = reinterpret_cast<const float*>(astore) + blocked_re(xc + xx, uniq[tl.uniq0 + u], nsingle);
+      Us[u * kUS + xx] = make_float2(f[0], f[32]);
     }
     for (int i = tid; i < tl.ncols * kX; i += 256) {
       const int c = i / kX, xx = i % kX;
-      Cs[xx * TC + c] = astore[blocked_index(xc + xx, cols[tl.col0 + c], nsingle)];
+      const float* f = reinterpret_cast<const float*>(astore) + blocked_re(xc + xx, cols[tl.col0 + c], nsingle);
+      Cs[xx * TC + c] = make_float2(f[0], f[32]);
     }
     for (int i = tid; i < (TC - tl.ncols) * kX; i += 256) {
       const int c = tl.ncols + i / kX, xx = i % kX;

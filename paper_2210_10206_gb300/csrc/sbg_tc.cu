@@ -3,10 +3,12 @@
 // For one tile of 128 rows r (pairs of singles) and N columns c (singles):
 //     D[r][c] = sum_x Re( P_r(x) * delta(x) a_c(x) ),   P_r = sign f1 f2
 // (Eq. mu of Sec. 2.3 / Eq. proj_4pcf_coeff of Sec. 2.4 before the coupling
-// contraction).  As a real GEMM over K = 2 x-points: A[r][2x, 2x+1] = (Re P, Im P)
-// and B[c][2x, 2x+1] = (Re(delta a), -Im(delta a)); 2D adds the column
-// (Im(delta a), Re(delta a)) for Im.  Each operand is split into bf16 hi + lo
-// and D += Ahi Bhi + Ahi Blo + Alo Bhi (three MMAs into one TMEM accumulator).
+// contraction).  As a real GEMM over K = 64 per 32-point K-block:
+// A[r] = (Re P(x0..x31), Im P(x0..x31)), B[c] = (Re(delta a), -Im(delta a)); 2D adds
+// the column (Im(delta a), Re(delta a)) for Im.  Each operand is split into
+// bf16 hi + lo and D += Ahi Bhi + Ahi Blo + Alo Bhi (three MMAs into one TMEM
+// accumulator).  The row signs (-1)^m of a_{l,-m} are applied in the FP64
+// coupling step, not here.
 //
 // Roles of a persistent CTA (one per SM):
 //   warp 9     loader: cp.async.bulk of the raw FP32 inputs of each 32-point
@@ -111,6 +113,50 @@ __device__ __forceinline__ void split2(float re, float im, uint32_t& hi, uint32_
   hi = bf16x2_rn(re, im);
   const float hr = __uint_as_float(hi << 16), hi_ = __uint_as_float(hi & 0xffff0000u);
   lo = bf16x2_rn(re - hr, im - hi_);
+}
+
+// packed f32x2 arithmetic (two FP32 lanes per instruction)
+__device__ __forceinline__ uint64_t pk(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk(uint64_t v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// split a pair (v0, v1) into bf16x2 hi and lo words (v0 in the low half)
+__device__ __forceinline__ void split_pair(uint64_t v, uint32_t& hi, uint32_t& lo) {
+  float v0, v1;
+  upk(v, v0, v1);
+  hi = bf16x2_rn(v0, v1);
+  const uint64_t hf = pk(__uint_as_float(hi << 16), __uint_as_float(hi & 0xffff0000u));
+  float l0, l1;
+  upk(sub2(v, hf), l0, l1);
+  lo = bf16x2_rn(l0, l1);
+}
+
+// Row (A) or column (B) handled by producer thread group g in pass k: each warp's
+// four rows are two with (row & 7) < 4 and two with (row & 7) >= 4, so that the
+// real-part chunks of a 128-byte swizzled row land in disjoint bank halves.
+__device__ __forceinline__ int pass_row(int g, int k) {
+  const int perm = (k & 1) ? ((g & 3) == 0 ? 2 : (g & 3) == 1 ? 6 : (g & 3) == 2 ? 3 : 7)
+                           : ((g & 3) == 0 ? 0 : (g & 3) == 1 ? 4 : (g & 3) == 2 ? 1 : 5);
+  return ((g >> 2) + 8 * (k >> 1)) * 8 + perm;
 }
 
 __device__ __forceinline__ uint32_t swz(int row, int chunk) {
@@ -354,91 +400,141 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
     }
   } else {
     // ---------------------------------------------------------- producers --
-    const int j = tid & 7;       // 16-byte chunk = 4 grid points
-    const int rb = tid >> 3;     // 0..31
+    const int h = tid & 7;       // points 4h .. 4h+3 of the K-block
+    const int g = tid >> 3;      // 0..31
     const int quarter = warp & 3, half = warp >> 2;
-    uint32_t g = 0, q = 0, f = 0;
+    uint32_t gr = 0, q = 0, f = 0;
     bool ok = true;
     for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
       const Unit it = unit_of(u, ntiles, nsplit, ng);
       const Tile4 tl = tiles[it.tile];
       const int N = n_mma(tl, cplx);
-      int cslot[2];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int c = rb + 32 * k;
-        const int cs = cplx ? (c >> 1) : c;
-        cslot[k] = (c < N && cs < tl.ncols) ? colslot[tl.colslot0 + cs] : 0;
-      }
-      Row4 rw[4];
+      // A rows of this thread (4 passes) and their staged slots / conjugation
+      int au1[4], au2[4];
+      uint64_t as1[4], as2[4], ans2[4];
+      uint32_t aoffr[4], aoffi[4];
+      bool aval[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const int r = rb + 32 * k;
-        if (r < tl.nrows) rw[k] = rows[tl.row0 + r];
-        else rw[k] = Row4{0, 0, 0, 0.f};
+        const int r = pass_row(g, k);
+        aval[k] = r < tl.nrows;
+        const Row4 rw = aval[k] ? rows[tl.row0 + r] : Row4{0, 0, 0, 1.f};
+        au1[k] = rw.u1;
+        au2[k] = rw.u2;
+        const float s1 = (rw.flags & 1) ? -1.f : 1.f, s2 = (rw.flags & 2) ? -1.f : 1.f;
+        as1[k] = pk(s1, s1);
+        as2[k] = pk(s2, s2);
+        ans2[k] = pk(-s2, -s2);
+        aoffr[k] = swz(r, h >> 1) + 8 * (h & 1);
+        aoffi[k] = swz(r, 4 + (h >> 1)) + 8 * (h & 1);
+      }
+      // B rows of this thread: 3D columns c = pass_row(g, 0/1); 2D column single g -> rows 2g, 2g+1
+      int bslot[2];
+      bool bval[2], bact[2];
+      uint32_t boffr[2], boffi[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int c = cplx ? (2 * g + k) : pass_row(g, k);
+        const int cs = cplx ? g : c;
+        bact[k] = c < N;
+        bval[k] = bact[k] && cs < tl.ncols;
+        bslot[k] = bval[k] ? colslot[tl.colslot0 + cs] : 0;
+        boffr[k] = swz(c, h >> 1) + 8 * (h & 1);
+        boffi[k] = swz(c, 4 + (h >> 1)) + 8 * (h & 1);
       }
       bool first_flush = true;
-      for (int kb = 0; kb < it.nk; ++kb, ++g, ++q) {
-        const int rs = g % kRS, os = q % kOS;
-        if (!mbar_wait(&raw_full[rs], (g / kRS) & 1, err, 31) || !mbar_wait(&op_empty[os], ((q / kOS) & 1) ^ 1, err, 32)) {
+      for (int kb = 0; kb < it.nk; ++kb, ++gr, ++q) {
+        const int rs = gr % kRS, os = q % kOS;
+        if (!mbar_wait(&raw_full[rs], (gr / kRS) & 1, err, 31) ||
+            !mbar_wait(&op_empty[os], ((q / kOS) & 1) ^ 1, err, 32)) {
           ok = false;
           break;
         }
         const uint8_t* raw = raw_base + rs * kRawStage;
-        const float* D = (const float*)raw;
+        const float4* D4 = (const float4*)raw;
         const float4* U4 = (const float4*)(raw + kRawD);
         uint8_t* op = op_base + os * kOpStage;
-        // ---- A: 4 rows x 4 points per thread ----
+        // ---- A: pair products, all loads first ----
+        float4 r1[4], i1[4], r2[4], i2[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const int r = rb + 32 * k;
-          uint4 hv = make_uint4(0, 0, 0, 0), lv = make_uint4(0, 0, 0, 0);
-          if (r < tl.nrows) {
-            const float4 p0 = U4[rw[k].u1 * 16 + 2 * j], p1 = U4[rw[k].u1 * 16 + 2 * j + 1];
-            const float4 q0 = U4[rw[k].u2 * 16 + 2 * j], q1 = U4[rw[k].u2 * 16 + 2 * j + 1];
-            float2 f1[4] = {{p0.x, p0.y}, {p0.z, p0.w}, {p1.x, p1.y}, {p1.z, p1.w}};
-            float2 f2[4] = {{q0.x, q0.y}, {q0.z, q0.w}, {q1.x, q1.y}, {q1.z, q1.w}};
-            const float s1 = (rw[k].flags & 1) ? -1.f : 1.f, s2 = (rw[k].flags & 2) ? -1.f : 1.f;
-            uint32_t h[4], l[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float ar = f1[e].x, ai = s1 * f1[e].y, br = f2[e].x, bi = s2 * f2[e].y;
-              const float pr = rw[k].sign * (ar * br - ai * bi);
-              const float pi = rw[k].sign * (ar * bi + ai * br);
-              split2(pr, pi, h[e], l[e]);
-            }
-            hv = make_uint4(h[0], h[1], h[2], h[3]);
-            lv = make_uint4(l[0], l[1], l[2], l[3]);
-          }
-          *(uint4*)(op + swz(r, j)) = hv;
-          *(uint4*)(op + kATile + swz(r, j)) = lv;
+          r1[k] = U4[au1[k] * 16 + h];
+          i1[k] = U4[au1[k] * 16 + 8 + h];
+          r2[k] = U4[au2[k] * 16 + h];
+          i2[k] = U4[au2[k] * 16 + 8 + h];
         }
-        // ---- B: rows c of delta * a_col, 4 points per thread ----
-        {
-          const float4 d4 = ((const float4*)D)[j];
-          const float dd[4] = {d4.x, d4.y, d4.z, d4.w};
 #pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            const int c = rb + 32 * k;
-            if (c >= N) continue;
-            const int cs = cplx ? (c >> 1) : c;
-            const int part = cplx ? (c & 1) : 0;
-            uint4 hv = make_uint4(0, 0, 0, 0), lv = make_uint4(0, 0, 0, 0);
-            if (cs < tl.ncols) {
-              const float4 c0 = U4[cslot[k] * 16 + 2 * j], c1 = U4[cslot[k] * 16 + 2 * j + 1];
-              const float2 av[4] = {{c0.x, c0.y}, {c0.z, c0.w}, {c1.x, c1.y}, {c1.z, c1.w}};
-              uint32_t h[4], l[4];
+        for (int k = 0; k < 4; ++k) {
+          uint32_t hr[2] = {0, 0}, lr[2] = {0, 0}, hi[2] = {0, 0}, li[2] = {0, 0};
+          if (aval[k]) {
 #pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const float vr = dd[e] * av[e].x, vi = dd[e] * av[e].y;
-                if (part == 0) split2(vr, -vi, h[e], l[e]);
-                else split2(vi, vr, h[e], l[e]);
-              }
-              hv = make_uint4(h[0], h[1], h[2], h[3]);
-              lv = make_uint4(l[0], l[1], l[2], l[3]);
+            for (int p = 0; p < 2; ++p) {
+              const uint64_t ar = p ? pk(r1[k].z, r1[k].w) : pk(r1[k].x, r1[k].y);
+              const uint64_t ai = mul2(p ? pk(i1[k].z, i1[k].w) : pk(i1[k].x, i1[k].y), as1[k]);
+              const uint64_t br = p ? pk(r2[k].z, r2[k].w) : pk(r2[k].x, r2[k].y);
+              const uint64_t bi0 = p ? pk(i2[k].z, i2[k].w) : pk(i2[k].x, i2[k].y);
+              const uint64_t bi = mul2(bi0, as2[k]), nbi = mul2(bi0, ans2[k]);
+              const uint64_t pr = fma2(ar, br, mul2(ai, nbi));   // ar br - ai bi
+              const uint64_t pi = fma2(ar, bi, mul2(ai, br));    // ar bi + ai br
+              split_pair(pr, hr[p], lr[p]);
+              split_pair(pi, hi[p], li[p]);
             }
-            *(uint4*)(op + 2 * kATile + swz(c, j)) = hv;
-            *(uint4*)(op + 2 * kATile + kBTile + swz(c, j)) = lv;
+          }
+          *(uint2*)(op + aoffr[k]) = make_uint2(hr[0], hr[1]);
+          *(uint2*)(op + kATile + aoffr[k]) = make_uint2(lr[0], lr[1]);
+          *(uint2*)(op + aoffi[k]) = make_uint2(hi[0], hi[1]);
+          *(uint2*)(op + kATile + aoffi[k]) = make_uint2(li[0], li[1]);
+        }
+        // ---- B: delta * a of the column singles ----
+        {
+          const float4 d4 = D4[h];
+          const uint64_t d01 = pk(d4.x, d4.y), d23 = pk(d4.z, d4.w);
+          if (cplx) {
+            if (bact[0]) {
+              uint32_t vr_h[2] = {0, 0}, vr_l[2] = {0, 0}, vi_h[2] = {0, 0}, vi_l[2] = {0, 0};
+              if (bval[0]) {
+                const float4 ra = U4[bslot[0] * 16 + h], ia = U4[bslot[0] * 16 + 8 + h];
+                split_pair(mul2(d01, pk(ra.x, ra.y)), vr_h[0], vr_l[0]);
+                split_pair(mul2(d23, pk(ra.z, ra.w)), vr_h[1], vr_l[1]);
+                split_pair(mul2(d01, pk(ia.x, ia.y)), vi_h[0], vi_l[0]);
+                split_pair(mul2(d23, pk(ia.z, ia.w)), vi_h[1], vi_l[1]);
+              }
+              const uint32_t sg = 0x80008000u;  // negate both bf16 halves
+              uint8_t* bh = op + 2 * kATile;
+              uint8_t* bl = bh + kBTile;
+              // row 2g: (Re v, -Im v) -> real part of the output
+              *(uint2*)(bh + boffr[0]) = make_uint2(vr_h[0], vr_h[1]);
+              *(uint2*)(bl + boffr[0]) = make_uint2(vr_l[0], vr_l[1]);
+              *(uint2*)(bh + boffi[0]) = make_uint2(vi_h[0] ^ sg, vi_h[1] ^ sg);
+              *(uint2*)(bl + boffi[0]) = make_uint2(vi_l[0] ^ sg, vi_l[1] ^ sg);
+              // row 2g+1: (Im v, Re v) -> imaginary part of the output
+              if (bact[1]) {
+                *(uint2*)(bh + boffr[1]) = make_uint2(vi_h[0], vi_h[1]);
+                *(uint2*)(bl + boffr[1]) = make_uint2(vi_l[0], vi_l[1]);
+                *(uint2*)(bh + boffi[1]) = make_uint2(vr_h[0], vr_h[1]);
+                *(uint2*)(bl + boffi[1]) = make_uint2(vr_l[0], vr_l[1]);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+              if (!bact[k]) continue;
+              uint32_t vr_h[2] = {0, 0}, vr_l[2] = {0, 0}, vi_h[2] = {0, 0}, vi_l[2] = {0, 0};
+              if (bval[k]) {
+                const float4 ra = U4[bslot[k] * 16 + h], ia = U4[bslot[k] * 16 + 8 + h];
+                split_pair(mul2(d01, pk(ra.x, ra.y)), vr_h[0], vr_l[0]);
+                split_pair(mul2(d23, pk(ra.z, ra.w)), vr_h[1], vr_l[1]);
+                split_pair(mul2(d01, pk(ia.x, ia.y)), vi_h[0], vi_l[0]);
+                split_pair(mul2(d23, pk(ia.z, ia.w)), vi_h[1], vi_l[1]);
+              }
+              const uint32_t sg = 0x80008000u;
+              uint8_t* bh = op + 2 * kATile;
+              uint8_t* bl = bh + kBTile;
+              *(uint2*)(bh + boffr[k]) = make_uint2(vr_h[0], vr_h[1]);
+              *(uint2*)(bl + boffr[k]) = make_uint2(vr_l[0], vr_l[1]);
+              *(uint2*)(bh + boffi[k]) = make_uint2(vi_h[0] ^ sg, vi_h[1] ^ sg);
+              *(uint2*)(bl + boffi[k]) = make_uint2(vi_l[0] ^ sg, vi_l[1] ^ sg);
+            }
           }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
