@@ -11,21 +11,21 @@
 // coupling step, not here.
 //
 // Roles of a persistent CTA (one per SM):
-//   warp 9     loader: cp.async.bulk of the raw FP32 inputs of each 32-point
+//   warp 17    loader: cp.async.bulk of the raw FP32 inputs of each 32-point
 //              K-block (delta and the tile's staged singles, which lie in a few
 //              contiguous runs of the blocked coefficient store) into a 4-deep
 //              ring, completion on mbarriers (expect_tx);
-//   warps 0-7  producers: form the swizzled (SW128, K-major) bf16 hi/lo A and B
+//   warps 0-15 producers: form the swizzled (SW128, K-major) bf16 hi/lo A and B
 //              tiles of a K-block in a 2-deep ring; every 64 K-blocks they also
 //              fold the TMEM accumulator into a second TMEM accumulator
 //              (FP32 partial sums over at most 2048 points), and at the end of a
 //              work item add it to T in FP64;
-//   warp 8     MMA issuer: one thread issues 12 tcgen05.mma (M=128, K=16) per
+//   warp 16    MMA issuer: one thread issues 12 tcgen05.mma (M=128, K=16) per
 //              K-block and commits to the mbarriers that free the operand stage
 //              and publish the accumulator.
 // Work units (tile, x-split) are dealt round-robin to a cooperative grid of one
 // CTA per SM; the loaders of all CTAs advance through x together (a CTA may run
-// at most two 256-K-block epochs ahead of the slowest), so that the singles of
+// at most four 256-K-block epochs ahead of the slowest), so that the singles of
 // the current x-window are read from HBM once and then served from L2.
 // Every wait is bounded (1 s of %globaltimer); on expiry the CTA records an
 // error code, drains its own copies, frees TMEM and returns.
@@ -41,14 +41,15 @@ constexpr int kRS = 4;                 // raw stages
 constexpr int kOS = 2;                 // operand stages
 constexpr int kFlush = 64;             // K-blocks per inner accumulation range
 constexpr int kKX = 32;                // grid points per K-block (64 bf16 = one 128-B row)
-constexpr int kProd = 256;             // producer threads (warps 0..7)
+constexpr int kProd = 512;             // producer threads (warps 0..15)
+constexpr int kMmaWarp = kProd / 32, kLoadWarp = kMmaWarp + 1;
 constexpr int kThreads = kProd + 64;   // + MMA warp + loader warp
 constexpr int kATile = 128 * 128;      // bytes of one 128-row bf16 K-block tile
 constexpr int kBTile = 64 * 128;       // bytes of one <=64-row tile
 constexpr int kOpStage = 2 * kATile + 2 * kBTile;
 constexpr int kRawD = kKX * 4;
 constexpr int kRawStage = kRawD + kTcMaxSlots * kKX * 8;
-constexpr int kLag = 2;                // epochs a loader may run ahead of the slowest CTA
+constexpr int kLag = 4;                // epochs a loader may run ahead of the slowest CTA
 constexpr int kMeta = 256 + 3 * kTcMaxSlots * 4;  // barriers + run table
 constexpr int kSmem = kOS * kOpStage + kRS * kRawStage + kMeta + 1024;
 constexpr unsigned long long kWaitNs = 1000000000ull;
@@ -183,6 +184,22 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const float (&v)[4]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+               "r"(__float_as_uint(v[3]))
+               : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   uint32_t r[8];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
@@ -281,7 +298,7 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
     mbar_init(acc_full, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 8) {
+  if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
                  "r"(128));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -291,7 +308,7 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;  // inner accumulator at column 0, outer at column 64
 
-  if (warp == 9) {
+  if (warp == kLoadWarp) {
     // ------------------------------------------------------------- loader --
     uint32_t g = 0;
     bool ok = true;
@@ -364,7 +381,7 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
       const uint32_t first = g > kRS ? g - kRS : 0;
       for (uint32_t h = first; h < g; ++h) mbar_wait(&raw_full[h % kRS], (h / kRS) & 1, err, 12);
     }
-  } else if (warp == 8) {
+  } else if (warp == kMmaWarp) {
     // ---------------------------------------------------------------- MMA --
     if (lane == 0) {
       uint32_t q = 0;
@@ -401,8 +418,9 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
   } else {
     // ---------------------------------------------------------- producers --
     const int h = tid & 7;       // points 4h .. 4h+3 of the K-block
-    const int g = tid >> 3;      // 0..31
-    const int quarter = warp & 3, half = warp >> 2;
+    const int g = (tid >> 3) & 31;
+    const int kk = tid >> 8;     // 0: rows 0..63, 1: rows 64..127
+    const int quarter = warp & 3, part = warp >> 2;  // TMEM lane quarter, column quarter
     uint32_t gr = 0, q = 0, f = 0;
     bool ok = true;
     for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
@@ -410,13 +428,13 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
       const Tile4 tl = tiles[it.tile];
       const int N = n_mma(tl, cplx);
       // A rows of this thread (4 passes) and their staged slots / conjugation
-      int au1[4], au2[4];
-      uint64_t as1[4], as2[4], ans2[4];
-      uint32_t aoffr[4], aoffi[4];
-      bool aval[4];
+      int au1[2], au2[2];
+      uint64_t as1[2], as2[2], ans2[2];
+      uint32_t aoffr[2], aoffi[2];
+      bool aval[2];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int r = pass_row(g, k);
+      for (int k = 0; k < 2; ++k) {
+        const int r = pass_row(g, 2 * kk + k);
         aval[k] = r < tl.nrows;
         const Row4 rw = aval[k] ? rows[tl.row0 + r] : Row4{0, 0, 0, 1.f};
         au1[k] = rw.u1;
@@ -428,15 +446,16 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
         aoffr[k] = swz(r, h >> 1) + 8 * (h & 1);
         aoffi[k] = swz(r, 4 + (h >> 1)) + 8 * (h & 1);
       }
-      // B rows of this thread: 3D columns c = pass_row(g, 0/1); 2D column single g -> rows 2g, 2g+1
+      // B rows of this thread: 3D column c = pass_row(g, kk) (0..63); 2D column single g
+      // (threads of kk = 0 only) -> rows 2g and 2g+1
       int bslot[2];
       bool bval[2], bact[2];
       uint32_t boffr[2], boffi[2];
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        const int c = cplx ? (2 * g + k) : pass_row(g, k);
+        const int c = cplx ? (2 * g + k) : pass_row(g, kk);
         const int cs = cplx ? g : c;
-        bact[k] = c < N;
+        bact[k] = (cplx ? kk == 0 : k == 0) && c < N;
         bval[k] = bact[k] && cs < tl.ncols;
         bslot[k] = bval[k] ? colslot[tl.colslot0 + cs] : 0;
         boffr[k] = swz(c, h >> 1) + 8 * (h & 1);
@@ -455,16 +474,16 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
         const float4* U4 = (const float4*)(raw + kRawD);
         uint8_t* op = op_base + os * kOpStage;
         // ---- A: pair products, all loads first ----
-        float4 r1[4], i1[4], r2[4], i2[4];
+        float4 r1[2], i1[2], r2[2], i2[2];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 2; ++k) {
           r1[k] = U4[au1[k] * 16 + h];
           i1[k] = U4[au1[k] * 16 + 8 + h];
           r2[k] = U4[au2[k] * 16 + h];
           i2[k] = U4[au2[k] * 16 + 8 + h];
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 2; ++k) {
           uint32_t hr[2] = {0, 0}, lr[2] = {0, 0}, hi[2] = {0, 0}, li[2] = {0, 0};
           if (aval[k]) {
 #pragma unroll
@@ -549,26 +568,26 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
           }
           ++f;
           tc_fence_after();
-          const int hc = N >> 1;  // columns of this thread's half
+          const int qc = N >> 2;  // columns of this thread's quarter (N is a multiple of 16)
           const int row = quarter * 32 + lane;
           const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-          for (int c0 = 0; c0 < hc; c0 += 8) {
-            const int col = half * hc + c0;
-            float in[8], out[8];
-            tmem_ld8(tmem + lane_addr + col, in);
+          for (int c0 = 0; c0 < qc; c0 += 4) {
+            const int col = part * qc + c0;
+            float in[4], out[4];
+            tmem_ld4(tmem + lane_addr + col, in);
             if (first_flush) {
 #pragma unroll
-              for (int e = 0; e < 8; ++e) out[e] = in[e];
+              for (int e = 0; e < 4; ++e) out[e] = in[e];
             } else {
-              tmem_ld8(tmem + lane_addr + 64 + col, out);
+              tmem_ld4(tmem + lane_addr + 64 + col, out);
 #pragma unroll
-              for (int e = 0; e < 8; ++e) out[e] += in[e];
+              for (int e = 0; e < 4; ++e) out[e] += in[e];
             }
             if (!last) {
-              tmem_st8(tmem + lane_addr + 64 + col, out);
+              tmem_st4(tmem + lane_addr + 64 + col, out);
             } else if (row < tl.nrows) {
 #pragma unroll
-              for (int e = 0; e < 8; ++e) {
+              for (int e = 0; e < 4; ++e) {
                 const int c = col + e;
                 if (cplx) {
                   if ((c >> 1) < tl.ncols)
@@ -588,7 +607,7 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 8) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+  if (warp == kMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
 }
 
 cudaError_t launch_tc4(const float2* astore, long long ng, const float* delta, const Tile4* tiles, int ntiles,
