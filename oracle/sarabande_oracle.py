@@ -42,7 +42,7 @@ __all__ = [
     "sph_harm", "kernel_full", "kernel_projected", "a_coefficient",
     "a_full", "c_projected", "zeta3_full", "zeta4_full", "zeta3_projected",
     "zeta4_projected", "lambda_list", "wigner3j", "coupling",
-    "normalization", "preprocess", "brute_a", "zeta4_full_entries",
+    "normalization", "preprocess", "brute_a", "zeta4_full_entries", "kernel_full_bin",
 ]
 
 
@@ -132,6 +132,15 @@ def kernel_full(shape, edges, l, m):
     return out
 
 
+def kernel_full_bin(shape, edges, l, m, b):
+    """K^b_lm of kernel_full for the single bin b."""
+    z, y, x = offset_grids(shape)
+    mk = bin_masks(shape, edges)[b]
+    out = np.zeros(tuple(shape), dtype=np.complex128)
+    out[mk] = np.conj(sph_harm(l, m, z[mk], y[mk], x[mk]))
+    return out
+
+
 def kernel_projected(shape, edges, m):
     """K^b_m(rho) = e^{-i m phi} Theta^b(rho) (Eq. c_m def kernel), with
     e^{i m phi} = ((x + i y)/rho)^m (Algorithm 2 notes); negative m allowed."""
@@ -147,12 +156,14 @@ def kernel_projected(shape, edges, m):
 
 # ------------------------------------------------------------- convolution --
 
-def a_coefficient(delta, kernel):
+def a_coefficient(delta, kernel, delta_hat=None):
     """a(x) = sum_r K(r) delta(x + r) on the periodic grid (Eq. almconv, a
     correlation per its footnote), evaluated as IFFT(FFT(delta) * G) with
-    G(k) = sum_r K(r) e^{+2 pi i k.r/N} = N_g * IFFT(K)(k) (Algorithms 3-4)."""
+    G(k) = sum_r K(r) e^{+2 pi i k.r/N} = N_g * IFFT(K)(k) (Algorithms 3-4).
+    `delta_hat` may pass FFT(delta) when it is already at hand."""
     ng = delta.size
-    return np.fft.ifftn(np.fft.fftn(delta) * (np.fft.ifftn(kernel) * ng))
+    dh = np.fft.fftn(delta) if delta_hat is None else delta_hat
+    return np.fft.ifftn(dh * (np.fft.ifftn(kernel) * ng))
 
 
 def brute_a(delta, kernel):
@@ -309,14 +320,13 @@ def zeta4_full_entries(delta, edges, entries):
     a-arrays it needs (for spot checks at sizes where the full tensor is out
     of reach)."""
     cache = {}
+    dh = np.fft.fftn(delta)
 
     def a_of(l, m, b):
-        if (l, m) not in cache:
-            cache[(l, m)] = {}
-        if b not in cache[(l, m)]:
-            k = kernel_full(delta.shape, edges, l, m)[b]
-            cache[(l, m)][b] = a_coefficient(delta, k).ravel()
-        return cache[(l, m)][b]
+        if (l, m, b) not in cache:
+            k = kernel_full_bin(delta.shape, edges, l, m, b)
+            cache[(l, m, b)] = a_coefficient(delta, k, dh).ravel()
+        return cache[(l, m, b)]
 
     d = delta.ravel()
     out = []

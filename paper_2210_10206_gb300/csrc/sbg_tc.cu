@@ -83,18 +83,25 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait; false if this or another thread of the grid gave up.
+// Bounded wait; false if this or another thread of the grid gave up.  The
+// clock and the grid's error word (an L2 round trip) are consulted only every
+// 256 polls so that a wait that succeeds soon costs no more than the polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* err, int code) {
   if (mbar_try(b, parity)) return true;
-  const unsigned long long t0 = gtime();
-  while (!mbar_try(b, parity)) {
-    if (*err) return false;
-    if (gtime() - t0 > kWaitNs) {
-      atomicCAS((int*)err, 0, code);
-      return false;
+  unsigned long long t0 = 0;
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(b, parity)) return true;
+    if ((it & 255u) == 0) {
+      const unsigned long long now = gtime();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > kWaitNs) {
+        atomicCAS((int*)err, 0, code);
+        return false;
+      }
+      if (*err) return false;
     }
   }
-  return true;
 }
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -287,12 +294,13 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
   const int epochs = (int)((nk_unit + kTcEpoch - 1) / kTcEpoch);
 
   if (tid == 0) {
+    // producer-side barriers count one arrival per producer warp
     for (int i = 0; i < kRS; ++i) {
       mbar_init(&raw_full[i], 1);
-      mbar_init(&raw_empty[i], kProd);
+      mbar_init(&raw_empty[i], kProd / 32);
     }
     for (int i = 0; i < kOS; ++i) {
-      mbar_init(&op_full[i], kProd);
+      mbar_init(&op_full[i], kProd / 32);
       mbar_init(&op_empty[i], 1);
     }
     mbar_init(acc_full, 1);
@@ -556,9 +564,14 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
             }
           }
         }
+        // publish this warp's operand writes to the tensor core (async proxy)
+        // and release the raw stage: one arrival per warp
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&op_full[os]);
-        mbar_arrive(&raw_empty[rs]);
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&op_full[os]);
+          mbar_arrive(&raw_empty[rs]);
+        }
         // ---- fold the inner accumulator every kFlush K-blocks ----
         const bool last = kb + 1 == it.nk;
         if ((kb + 1) % kFlush == 0 || last) {

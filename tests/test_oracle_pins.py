@@ -477,3 +477,17 @@ def test_normalization_matches_explicit_product():
     assert O.normalization(shape, edges, ngal, 3, [0, 2]) == pytest.approx(ngal * nbar * counts[0] * nbar * counts[2])
     assert O.normalization(shape, edges, ngal, 4, [0, 1, 2]) == pytest.approx(
         ngal * nbar ** 3 * counts[0] * counts[1] * counts[2])
+
+
+def test_single_entry_oracle_matches_full_tensor():
+    # the one-entry path used for spot checks at full size equals the full tensor
+    d = RNG.normal(size=(16, 16, 16))
+    edges = [0.5, 1.5, 2.5, 3.5, 5.0]
+    z4 = O.zeta4_full(d, edges, 2)
+    lams = O.lambda_list(2)
+    entries = [((0, 0, 0), 0, 1, 2), ((1, 1, 2), 3, 0, 1), ((2, 2, 2), 2, 2, 3), ((2, 1, 1), 1, 3, 3)]
+    got = O.zeta4_full_entries(d, edges, entries)
+    for (lam, b1, b2, b3), g in zip(entries, got):
+        assert abs(g - z4[lams.index(lam), b1, b2, b3]) < 1e-12 * np.abs(z4).max()
+    k = O.kernel_full(d.shape, edges, 2, -1)
+    assert np.array_equal(O.kernel_full_bin(d.shape, edges, 2, -1, 2), k[2])
