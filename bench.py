@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--prec", default="auto", choices=["auto", "bf16x3", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compare", type=int, default=1, help="also time the other precision (default on)")
     ap.add_argument("--grid", type=int, default=256, help="grid side (256 is the benchmark workload; "
                     "smaller sides are for profiling captures only)")
     return ap.parse_args()
@@ -294,6 +295,22 @@ def run_gpu(args):
            "e2e": {"value": ws * 1000.0 / e_ms, "unit": "fields/s", "h2d_bytes_per_step": int(field.nbytes),
                    "d2h_bytes_per_step": int(z4.nbytes)},
            "gpu_launches": launches, "clocks": clk, "wall_s_timed": wall}
+    # ---- the other precision of the same path, same workload (split-BF16 vs FP32) ----
+    if args.compare:
+        other = "fp32" if prec_name == "bf16x3" else "bf16x3"
+        oprec = sbg.SBG_PREC_FP32 if other == "fp32" else sbg.SBG_PREC_BF16X3
+        for _ in range(2):
+            sbg.sbg_full(ctx.h, dfield, edges, 0, LMAX4, oprec, flags, None, z4)
+        ost = []
+        for _ in range(max(1, min(args.steps, 3))):
+            sbg.sbg_full(ctx.h, dfield, edges, 0, LMAX4, oprec, flags, None, z4)
+            ost.append(sbg.sbg_last_timings(ctx.h))
+        ost = np.array(ost)
+        oms = float(ost[:, :7].sum(1).mean())
+        ocomb = float(ost[:, 5].mean())
+        out["compare"] = {"precision": other, "value": 1000.0 / oms, "ms_per_step": oms, "combination_ms": ocomb,
+                          "combination_achieved_tflops": alg_flops / (ocomb * 1e-3) / 1e12,
+                          "speedup_of_headline": oms / step_ms}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = oracle_sample(field, edges)
         out["cpu_baseline"].pop("seconds_per_field", None)
