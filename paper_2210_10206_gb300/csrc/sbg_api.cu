@@ -307,7 +307,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
     }
   long long so = 0;
   const int col_chunk = tc ? (dim == 2 ? 32 : 64) : 64;
-  const int max_u = tc ? kTcMaxSlots : 128;
+  const int max_u = tc ? kTcMaxRowSlots : 128;
   t.tc = tc;
   for (Block& bk : blocks) {
     const int nrows_blk = (int)bk.rows.size();
@@ -330,10 +330,6 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
         tl.ncols = nc;
         tl.uniq0 = (int)t.uniq.size();
         std::map<int, int> local;
-        // tensor-core tiles stage one slot list covering rows and columns
-        if (tc)
-          for (int c = 0; c < nc; ++c)
-            if (!local.count(t.cols[col0 + c])) { const int k = (int)local.size(); local[t.cols[col0 + c]] = k; }
         int nr = 0;
         const int rstart = r;
         while (r < nrows_blk && nr < TR) {
@@ -375,8 +371,6 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
             t.rows[k].u2 = remap[t.rows[k].u2];
           }
           for (int v : order) t.uniq.push_back(v);
-          tl.colslot0 = (int)t.colslot.size();
-          for (int c = 0; c < nc; ++c) t.colslot.push_back(pos[t.cols[col0 + c]]);
         }
         tl.tout = so;
         bk.slabs.push_back({rstart, nr, c0, nc, so, tl.row0});
@@ -763,8 +757,11 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
       const long long epochs = rounds * ((nk_unit + kTcEpoch - 1) / kTcEpoch) + 4;
       ST(buf(ctx, "tccnt", (size_t)epochs * 4, (void**)&d_cnt));
       CU(cudaMemsetAsync(d_cnt, 0, (size_t)epochs * 4, ctx->stream));
-      KL(launch_tc4(d_astore, ng, d_delta, (const Tile4*)t.d_tiles[0].p, ntl, (const Row4*)t.d_rows.p,
-                    (const int*)t.d_colslot.p, (const int*)t.d_uniq.p, nsingle, cplx, best, d_T, d_cnt, d_err,
+      void* d_bstore;
+      ST(buf(ctx, "bstore", (size_t)nsingle * ng * 8 * (cplx ? 2 : 1), &d_bstore));
+      ctx->nlaunch += 1;  // bsplit_kernel
+      KL(launch_tc4(d_astore, d_bstore, d_delta, ng, (const Tile4*)t.d_tiles[0].p, ntl, (const Row4*)t.d_rows.p,
+                    (const int*)t.d_cols.p, (const int*)t.d_uniq.p, nsingle, cplx, best, d_T, d_cnt, d_err,
                     ctx->nsm, ctx->stream));
       int herr = 0;
       CU(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

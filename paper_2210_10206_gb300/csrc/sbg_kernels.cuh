@@ -46,16 +46,19 @@ cudaError_t launch_simt4(const float2* astore, long long ng, const float* delta,
                          int tcg, int nsplit, int nsingle, double* T, cudaStream_t st);
 
 // Tensor-core (tcgen05) split-BF16 version of the same contraction (sbg_tc.cu).
-// Tiles of exactly <= 128 rows, <= kTcMaxU staged singles and <= 64 B rows
-// (3D: columns; 2D: two per column).  *err is set (never cleared) if a bounded
+// Tiles of <= 128 rows whose row singles (<= kTcMaxRowSlots, sorted store
+// indices in `slots`) are staged per K-block, and <= 64 B rows (3D: columns;
+// 2D: two per column).  bstore (nsingle * ng * 8 bytes, x2 for 2D) receives the
+// bf16 B operand of every single.  *err is set (never cleared) if a bounded
 // wait inside the kernel expired.
-constexpr int kTcMaxSlots = 112;  // singles staged per K-block (rows and columns together)
-constexpr int kTcEpoch = 256;     // K-blocks between progress checkpoints of the lag limiter
+constexpr int kTcMaxRowSlots = 56;  // row singles staged per K-block
+constexpr int kTcEpoch = 256;       // K-blocks between progress checkpoints of the lag limiter
 // Units (tile, x-split) are spread over a cooperative grid of one CTA per SM;
 // cnt holds one progress counter per (round, epoch), zeroed by the caller.
-cudaError_t launch_tc4(const float2* astore, long long ng, const float* delta, const Tile4* tiles, int ntiles,
-                       const Row4* rows, const int* colslot, const int* slots, int nsingle, int complex_out,
-                       int nsplit, double* T, int* cnt, int* err, int nsm, cudaStream_t st);
+cudaError_t launch_tc4(const float2* astore, const void* bstore, const float* delta, long long ng,
+                       const Tile4* tiles, int ntiles, const Row4* rows, const int* cols, const int* slots,
+                       int nsingle, int complex_out, int nsplit, double* T, int* cnt, int* err, int nsm,
+                       cudaStream_t st);
 
 // ---- finalisation ----
 // zeta[o] = sum_{e in [ptr[o], ptr[o+1])} coef[e] * T[idx[e]] (idx < 0: conj of T[-idx-1]).

@@ -1,7 +1,7 @@
 // Tensor-core (tcgen05, sm_103a) split-BF16 contraction of the 4PCF.
 //
 // For one tile of 128 rows r (pairs of singles) and N columns c (singles):
-//     D[r][c] = sum_x Re( P_r(x) * delta(x) a_c(x) ),   P_r = sign f1 f2
+//     D[r][c] = sum_x Re( P_r(x) * delta(x) a_c(x) ),   P_r = f1 f2
 // (Eq. mu of Sec. 2.3 / Eq. proj_4pcf_coeff of Sec. 2.4 before the coupling
 // contraction).  As a real GEMM over K = 64 per 32-point K-block:
 // A[r] = (Re P(x0..x31), Im P(x0..x31)), B[c] = (Re(delta a), -Im(delta a)); 2D adds
@@ -10,17 +10,18 @@
 // accumulator).  The row signs (-1)^m of a_{l,-m} are applied in the FP64
 // coupling step, not here.
 //
-// Roles of a persistent CTA (one per SM):
-//   warp 17    loader: cp.async.bulk of the raw FP32 inputs of each 32-point
-//              K-block (delta and the tile's staged singles, which lie in a few
-//              contiguous runs of the blocked coefficient store) into a 4-deep
-//              ring, completion on mbarriers (expect_tx);
-//   warps 0-15 producers: form the swizzled (SW128, K-major) bf16 hi/lo A and B
-//              tiles of a K-block in a 2-deep ring; every 64 K-blocks they also
-//              fold the TMEM accumulator into a second TMEM accumulator
-//              (FP32 partial sums over at most 2048 points), and at the end of a
-//              work item add it to T in FP64;
-//   warp 16    MMA issuer: one thread issues 12 tcgen05.mma (M=128, K=16) per
+// B depends only on the column single and the K-block, so bsplit_kernel writes
+// it once per field (bf16 hi/lo rows in the blocked order); A depends on the
+// row pair and is formed on chip.  Roles of a persistent CTA (one per SM):
+//   warps 9-12 loaders: per-thread 16-byte cp.async of each K-block's raw FP32
+//              row singles and precomputed B rows into a 4-deep ring; each
+//              thread's copies complete onto the stage's mbarrier (noinc);
+//   warps 0-7  producers: copy the B rows into the 128-byte-swizzled K-major
+//              operand tiles, form the bf16 hi/lo A tile (packed f32x2
+//              arithmetic) in a 2-deep ring; every 64 K-blocks they fold the
+//              TMEM accumulator into a second TMEM accumulator, and at the end
+//              of a work unit add it to T in FP64;
+//   warp 8     MMA issuer: one thread issues 12 tcgen05.mma (M=128, K=16) per
 //              K-block and commits to the mbarriers that free the operand stage
 //              and publish the accumulator.
 // Work units (tile, x-split) are dealt round-robin to a cooperative grid of one
@@ -41,16 +42,21 @@ constexpr int kRS = 4;                 // raw stages
 constexpr int kOS = 2;                 // operand stages
 constexpr int kFlush = 64;             // K-blocks per inner accumulation range
 constexpr int kKX = 32;                // grid points per K-block (64 bf16 = one 128-B row)
-constexpr int kProd = 512;             // producer threads (warps 0..15)
-constexpr int kMmaWarp = kProd / 32, kLoadWarp = kMmaWarp + 1;
-constexpr int kThreads = kProd + 64;   // + MMA warp + loader warp
+constexpr int kProdWarps = 8;          // producer warps 0..7
+constexpr int kProd = kProdWarps * 32;
+constexpr int kMmaWarp = kProdWarps;   // warp 8
+constexpr int kLoadWarps = 4;          // warps 9..12
+constexpr int kLoad0 = kMmaWarp + 1;
+constexpr int kLoaders = kLoadWarps * 32;
+constexpr int kThreads = (kProdWarps + 1 + kLoadWarps) * 32;
 constexpr int kATile = 128 * 128;      // bytes of one 128-row bf16 K-block tile
 constexpr int kBTile = 64 * 128;       // bytes of one <=64-row tile
 constexpr int kOpStage = 2 * kATile + 2 * kBTile;
-constexpr int kRawD = kKX * 4;
-constexpr int kRawStage = kRawD + kTcMaxSlots * kKX * 8;
+constexpr int kRawA = kTcMaxRowSlots * kKX * 8;  // FP32 (re, im) row singles
+constexpr int kRawB = 64 * 256;                  // bf16 hi/lo B rows (unswizzled)
+constexpr int kRawStage = kRawA + kRawB;
 constexpr int kLag = 4;                // epochs a loader may run ahead of the slowest CTA
-constexpr int kMeta = 256 + 3 * kTcMaxSlots * 4;  // barriers + run table
+constexpr int kMeta = 256;             // barriers and the TMEM address
 constexpr int kSmem = kOS * kOpStage + kRS * kRawStage + kMeta + 1024;
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
@@ -263,12 +269,20 @@ __device__ __forceinline__ bool wait_count(const int* c, int target, volatile in
   return true;
 }
 
-}  // namespace
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(su32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+// arrive on `bar` once every cp.async this thread issued so far has landed
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(bar)) : "memory");
+}
 
 __global__ void __launch_bounds__(kThreads, 1)
-tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restrict__ delta,
+tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore, long long ng,
            const Tile4* __restrict__ tiles, int ntiles, const Row4* __restrict__ rows,
-           const int* __restrict__ colslot, const int* __restrict__ slots, int nsingle, int cplx, int nsplit,
+           const int* __restrict__ cols, const int* __restrict__ slots, int nsingle, int cplx, int nsplit,
            double* __restrict__ T, int* cnt, int* err_flag) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -281,9 +295,6 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
   uint64_t* op_empty = bars + 2 * kRS + kOS;
   uint64_t* acc_full = bars + 2 * kRS + 2 * kOS;
   uint32_t* tmem_slot = (uint32_t*)(acc_full + 1);
-  int* run_start = (int*)(bars + 32);            // loader-private run table
-  int* run_len = run_start + kTcMaxSlots;
-  int* run_slot = run_len + kTcMaxSlots;
   volatile int* err = err_flag;
 
   const int tid = threadIdx.x;
@@ -292,16 +303,16 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
   const long long nrounds = (nunits + gridDim.x - 1) / gridDim.x;
   const long long nk_unit = ((ng / kKX) + nsplit - 1) / nsplit;
   const int epochs = (int)((nk_unit + kTcEpoch - 1) / kTcEpoch);
+  const int bparts = cplx ? 2 : 1;  // B rows per column single
 
   if (tid == 0) {
-    // producer-side barriers count one arrival per producer warp
     for (int i = 0; i < kRS; ++i) {
-      mbar_init(&raw_full[i], 1);
-      mbar_init(&raw_empty[i], kProd / 32);
+      mbar_init(&raw_full[i], kLoaders);       // one cp.async completion per loader thread
+      mbar_init(&raw_empty[i], kProdWarps);    // one arrival per producer warp
     }
     for (int i = 0; i < kOS; ++i) {
-      mbar_init(&op_full[i], kProd / 32);
-      mbar_init(&op_empty[i], 1);
+      mbar_init(&op_full[i], kProdWarps);
+      mbar_init(&op_empty[i], 1);              // tcgen05.commit
     }
     mbar_init(acc_full, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -316,41 +327,40 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;  // inner accumulator at column 0, outer at column 64
 
-  if (warp == kLoadWarp) {
-    // ------------------------------------------------------------- loader --
+  if (warp >= kLoad0) {
+    // ------------------------------------------------------------ loaders --
+    const int li = tid - kLoad0 * 32;  // 0..127
+    const int ck = li & 15;            // 16-byte chunk within a 256-byte row
+    const int rq = li >> 4;            // 0..7: rows rq, rq + 8, ...
     uint32_t g = 0;
     bool ok = true;
     for (long long rd = 0; rd < nrounds && ok; ++rd) {
       const long long u = rd * gridDim.x + blockIdx.x;
       Unit it{0, 0, 0};
       Tile4 tl{};
-      int nruns = 0;
+      int asi[kTcMaxRowSlots / 8], bsi[8];
       if (u < nunits) {
         it = unit_of(u, ntiles, nsplit, ng);
         tl = tiles[it.tile];
-        if (lane == 0) {
-          // runs of consecutive store indices in the tile's (sorted) slot list
-          for (int k = 0; k < tl.nuniq; ++k) {
-            const int v = slots[tl.uniq0 + k];
-            if (nruns > 0 && v == run_start[nruns - 1] + run_len[nruns - 1]) {
-              ++run_len[nruns - 1];
-            } else {
-              run_start[nruns] = v;
-              run_len[nruns] = 1;
-              run_slot[nruns] = k;
-              ++nruns;
-            }
-          }
-        }
-        nruns = __shfl_sync(0xffffffffu, nruns, 0);
-        __syncwarp();
       }
-      const uint32_t bytes = kRawD + (uint32_t)tl.nuniq * kKX * 8;
+      const int N = u < nunits ? n_mma(tl, cplx) : 0;
+#pragma unroll
+      for (int k = 0; k < kTcMaxRowSlots / 8; ++k) {
+        const int sl = rq + 8 * k;
+        asi[k] = sl < tl.nuniq ? slots[tl.uniq0 + sl] : -1;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int c = rq + 8 * k;                      // B row
+        const int cs = cplx ? (c >> 1) : c;            // column single
+        bsi[k] = (c < N && cs < tl.ncols) ? cols[tl.col0 + cs] * bparts + (cplx ? (c & 1) : 0)
+                                          : (c < N ? -2 : -1);
+      }
       for (int e = 0; e < epochs && ok; ++e) {
         const long long ce = rd * epochs + e;  // global epoch index
         if (ce >= kLag) {
           int good = 1;
-          if (lane == 0) good = wait_count(&cnt[ce - kLag], (int)gridDim.x, err, 13);
+          if (lane == 0) good = wait_count(&cnt[ce - kLag], (int)gridDim.x * kLoadWarps, err, 13);
           if (!__shfl_sync(0xffffffffu, good, 0)) {
             ok = false;
             break;
@@ -359,36 +369,34 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
         const int kb1 = min(it.nk, (e + 1) * kTcEpoch);
         for (int kb = e * kTcEpoch; kb < kb1; ++kb, ++g) {
           const int rs = g % kRS;
-          const uint32_t ph = (g / kRS) & 1;
-          int good = 1;
-          if (lane == 0) good = mbar_wait(&raw_empty[rs], ph ^ 1, err, 11);
-          if (!__shfl_sync(0xffffffffu, good, 0)) {
+          if (!mbar_wait(&raw_empty[rs], ((g / kRS) & 1) ^ 1, err, 11)) {
             ok = false;
             break;
           }
           uint8_t* st = raw_base + rs * kRawStage;
-          if (lane == 0) mbar_expect_tx(&raw_full[rs], bytes);
-          __syncwarp();
-          const long long x = it.x0 + (long long)kb * kKX;
-          const long long slab = (x >> 5) * (long long)nsingle;  // start of this K-block in the blocked store
-          for (int r = lane; r <= nruns; r += 32) {
-            if (r == nruns) {
-              bulk_g2s(st, delta + x, kRawD, &raw_full[rs]);
+          const long long xb = (it.x0 >> 5) + kb;  // K-block index in the blocked stores
+#pragma unroll
+          for (int k = 0; k < kTcMaxRowSlots / 8; ++k)
+            if (asi[k] >= 0)
+              cp_async16(st + (rq + 8 * k) * 256 + ck * 16,
+                         astore + (xb * nsingle + asi[k]) * 64 + ck * 4, 16);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            if (bsi[k] == -1) continue;
+            uint8_t* dst = st + kRawA + (rq + 8 * k) * 256 + ck * 16;
+            if (bsi[k] >= 0) {
+              cp_async16(dst, bstore + (xb * nsingle * bparts + bsi[k]) * 256 + ck * 16, 16);
             } else {
-              bulk_g2s(st + kRawD + run_slot[r] * kKX * 8, astore + (slab + run_start[r]) * kKX,
-                       (uint32_t)run_len[r] * kKX * 8, &raw_full[rs]);
+              cp_async16(dst, bstore, 0);  // zero-filled padding row
             }
           }
+          cp_async_arrive(&raw_full[rs]);
         }
         __syncwarp();
         if (lane == 0) atomicAdd(&cnt[ce], 1);
       }
     }
-    // drain: wait (bounded) for every issued stage's copies to land
-    if (lane == 0) {
-      const uint32_t first = g > kRS ? g - kRS : 0;
-      for (uint32_t h = first; h < g; ++h) mbar_wait(&raw_full[h % kRS], (h / kRS) & 1, err, 12);
-    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
   } else if (warp == kMmaWarp) {
     // ---------------------------------------------------------------- MMA --
     if (lane == 0) {
@@ -426,23 +434,21 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
   } else {
     // ---------------------------------------------------------- producers --
     const int h = tid & 7;       // points 4h .. 4h+3 of the K-block
-    const int g = (tid >> 3) & 31;
-    const int kk = tid >> 8;     // 0: rows 0..63, 1: rows 64..127
-    const int quarter = warp & 3, part = warp >> 2;  // TMEM lane quarter, column quarter
+    const int g = tid >> 3;      // 0..31
+    const int quarter = warp & 3, part = warp >> 2;  // TMEM lane quarter, column half
     uint32_t gr = 0, q = 0, f = 0;
     bool ok = true;
     for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
       const Unit it = unit_of(u, ntiles, nsplit, ng);
       const Tile4 tl = tiles[it.tile];
       const int N = n_mma(tl, cplx);
-      // A rows of this thread (4 passes) and their staged slots / conjugation
-      int au1[2], au2[2];
-      uint64_t as1[2], as2[2], ans2[2];
-      uint32_t aoffr[2], aoffi[2];
-      bool aval[2];
+      int au1[4], au2[4];
+      uint64_t as1[4], as2[4], ans2[4];
+      uint32_t aoffr[4], aoffi[4];
+      bool aval[4];
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int r = pass_row(g, 2 * kk + k);
+      for (int k = 0; k < 4; ++k) {
+        const int r = pass_row(g, k);
         aval[k] = r < tl.nrows;
         const Row4 rw = aval[k] ? rows[tl.row0 + r] : Row4{0, 0, 0, 1.f};
         au1[k] = rw.u1;
@@ -454,21 +460,6 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
         aoffr[k] = swz(r, h >> 1) + 8 * (h & 1);
         aoffi[k] = swz(r, 4 + (h >> 1)) + 8 * (h & 1);
       }
-      // B rows of this thread: 3D column c = pass_row(g, kk) (0..63); 2D column single g
-      // (threads of kk = 0 only) -> rows 2g and 2g+1
-      int bslot[2];
-      bool bval[2], bact[2];
-      uint32_t boffr[2], boffi[2];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int c = cplx ? (2 * g + k) : pass_row(g, kk);
-        const int cs = cplx ? g : c;
-        bact[k] = (cplx ? kk == 0 : k == 0) && c < N;
-        bval[k] = bact[k] && cs < tl.ncols;
-        bslot[k] = bval[k] ? colslot[tl.colslot0 + cs] : 0;
-        boffr[k] = swz(c, h >> 1) + 8 * (h & 1);
-        boffi[k] = swz(c, 4 + (h >> 1)) + 8 * (h & 1);
-      }
       bool first_flush = true;
       for (int kb = 0; kb < it.nk; ++kb, ++gr, ++q) {
         const int rs = gr % kRS, os = q % kOS;
@@ -478,20 +469,25 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
           break;
         }
         const uint8_t* raw = raw_base + rs * kRawStage;
-        const float4* D4 = (const float4*)raw;
-        const float4* U4 = (const float4*)(raw + kRawD);
+        const float4* U4 = (const float4*)raw;
         uint8_t* op = op_base + os * kOpStage;
+        // ---- B: swizzle the precomputed rows into the operand tile ----
+        for (int ch = tid; ch < N * 16; ch += kProd) {
+          const int c = ch >> 4, pc = ch & 15, j = pc & 7, hl = pc >> 3;
+          const uint4 v = *(const uint4*)(raw + kRawA + c * 256 + pc * 16);
+          *(uint4*)(op + 2 * kATile + hl * kBTile + swz(c, j)) = v;
+        }
         // ---- A: pair products, all loads first ----
-        float4 r1[2], i1[2], r2[2], i2[2];
+        float4 r1[4], i1[4], r2[4], i2[4];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < 4; ++k) {
           r1[k] = U4[au1[k] * 16 + h];
           i1[k] = U4[au1[k] * 16 + 8 + h];
           r2[k] = U4[au2[k] * 16 + h];
           i2[k] = U4[au2[k] * 16 + 8 + h];
         }
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < 4; ++k) {
           uint32_t hr[2] = {0, 0}, lr[2] = {0, 0}, hi[2] = {0, 0}, li[2] = {0, 0};
           if (aval[k]) {
 #pragma unroll
@@ -512,58 +508,6 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
           *(uint2*)(op + aoffi[k]) = make_uint2(hi[0], hi[1]);
           *(uint2*)(op + kATile + aoffi[k]) = make_uint2(li[0], li[1]);
         }
-        // ---- B: delta * a of the column singles ----
-        {
-          const float4 d4 = D4[h];
-          const uint64_t d01 = pk(d4.x, d4.y), d23 = pk(d4.z, d4.w);
-          if (cplx) {
-            if (bact[0]) {
-              uint32_t vr_h[2] = {0, 0}, vr_l[2] = {0, 0}, vi_h[2] = {0, 0}, vi_l[2] = {0, 0};
-              if (bval[0]) {
-                const float4 ra = U4[bslot[0] * 16 + h], ia = U4[bslot[0] * 16 + 8 + h];
-                split_pair(mul2(d01, pk(ra.x, ra.y)), vr_h[0], vr_l[0]);
-                split_pair(mul2(d23, pk(ra.z, ra.w)), vr_h[1], vr_l[1]);
-                split_pair(mul2(d01, pk(ia.x, ia.y)), vi_h[0], vi_l[0]);
-                split_pair(mul2(d23, pk(ia.z, ia.w)), vi_h[1], vi_l[1]);
-              }
-              const uint32_t sg = 0x80008000u;  // negate both bf16 halves
-              uint8_t* bh = op + 2 * kATile;
-              uint8_t* bl = bh + kBTile;
-              // row 2g: (Re v, -Im v) -> real part of the output
-              *(uint2*)(bh + boffr[0]) = make_uint2(vr_h[0], vr_h[1]);
-              *(uint2*)(bl + boffr[0]) = make_uint2(vr_l[0], vr_l[1]);
-              *(uint2*)(bh + boffi[0]) = make_uint2(vi_h[0] ^ sg, vi_h[1] ^ sg);
-              *(uint2*)(bl + boffi[0]) = make_uint2(vi_l[0] ^ sg, vi_l[1] ^ sg);
-              // row 2g+1: (Im v, Re v) -> imaginary part of the output
-              if (bact[1]) {
-                *(uint2*)(bh + boffr[1]) = make_uint2(vi_h[0], vi_h[1]);
-                *(uint2*)(bl + boffr[1]) = make_uint2(vi_l[0], vi_l[1]);
-                *(uint2*)(bh + boffi[1]) = make_uint2(vr_h[0], vr_h[1]);
-                *(uint2*)(bl + boffi[1]) = make_uint2(vr_l[0], vr_l[1]);
-              }
-            }
-          } else {
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-              if (!bact[k]) continue;
-              uint32_t vr_h[2] = {0, 0}, vr_l[2] = {0, 0}, vi_h[2] = {0, 0}, vi_l[2] = {0, 0};
-              if (bval[k]) {
-                const float4 ra = U4[bslot[k] * 16 + h], ia = U4[bslot[k] * 16 + 8 + h];
-                split_pair(mul2(d01, pk(ra.x, ra.y)), vr_h[0], vr_l[0]);
-                split_pair(mul2(d23, pk(ra.z, ra.w)), vr_h[1], vr_l[1]);
-                split_pair(mul2(d01, pk(ia.x, ia.y)), vi_h[0], vi_l[0]);
-                split_pair(mul2(d23, pk(ia.z, ia.w)), vi_h[1], vi_l[1]);
-              }
-              const uint32_t sg = 0x80008000u;
-              uint8_t* bh = op + 2 * kATile;
-              uint8_t* bl = bh + kBTile;
-              *(uint2*)(bh + boffr[k]) = make_uint2(vr_h[0], vr_h[1]);
-              *(uint2*)(bl + boffr[k]) = make_uint2(vr_l[0], vr_l[1]);
-              *(uint2*)(bh + boffi[k]) = make_uint2(vi_h[0] ^ sg, vi_h[1] ^ sg);
-              *(uint2*)(bl + boffi[k]) = make_uint2(vi_l[0] ^ sg, vi_l[1] ^ sg);
-            }
-          }
-        }
         // publish this warp's operand writes to the tensor core (async proxy)
         // and release the raw stage: one arrival per warp
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -581,26 +525,26 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
           }
           ++f;
           tc_fence_after();
-          const int qc = N >> 2;  // columns of this thread's quarter (N is a multiple of 16)
+          const int hc = N >> 1;  // columns of this thread's half (N is a multiple of 16)
           const int row = quarter * 32 + lane;
           const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-          for (int c0 = 0; c0 < qc; c0 += 4) {
-            const int col = part * qc + c0;
-            float in[4], out[4];
-            tmem_ld4(tmem + lane_addr + col, in);
+          for (int c0 = 0; c0 < hc; c0 += 8) {
+            const int col = part * hc + c0;
+            float in[8], out[8];
+            tmem_ld8(tmem + lane_addr + col, in);
             if (first_flush) {
 #pragma unroll
-              for (int e = 0; e < 4; ++e) out[e] = in[e];
+              for (int e = 0; e < 8; ++e) out[e] = in[e];
             } else {
-              tmem_ld4(tmem + lane_addr + 64 + col, out);
+              tmem_ld8(tmem + lane_addr + 64 + col, out);
 #pragma unroll
-              for (int e = 0; e < 4; ++e) out[e] += in[e];
+              for (int e = 0; e < 8; ++e) out[e] += in[e];
             }
             if (!last) {
-              tmem_st4(tmem + lane_addr + 64 + col, out);
+              tmem_st8(tmem + lane_addr + 64 + col, out);
             } else if (row < tl.nrows) {
 #pragma unroll
-              for (int e = 0; e < 4; ++e) {
+              for (int e = 0; e < 8; ++e) {
                 const int c = col + e;
                 if (cplx) {
                   if ((c >> 1) < tl.ncols)
@@ -623,11 +567,55 @@ tc4_kernel(const float2* __restrict__ astore, long long ng, const float* __restr
   if (warp == kMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
 }
 
-cudaError_t launch_tc4(const float2* astore, long long ng, const float* delta, const Tile4* tiles, int ntiles,
-                       const Row4* rows, const int* colslot, const int* slots, int nsingle, int complex_out,
-                       int nsplit, double* T, int* cnt, int* err, int nsm, cudaStream_t st) {
+// B operand rows of every single and K-block: v = delta * a; 3D row
+// (Re v, -Im v), 2D rows (Re v, -Im v) and (Im v, Re v); each row 64 bf16 hi
+// then 64 bf16 lo (256 bytes), in the blocked order of the coefficient store.
+__global__ void bsplit_kernel(const float* __restrict__ astore, const float* __restrict__ delta, long long nkb,
+                              int nsingle, int cplx, uint32_t* __restrict__ bstore) {
+  const long long nrow = nkb * nsingle;  // (K-block, single) pairs
+  const int sub = threadIdx.x & 15;      // points 2 sub, 2 sub + 1
+  for (long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 4; r < nrow;
+       r += ((long long)gridDim.x * blockDim.x) >> 4) {
+    const long long xb = r / nsingle;
+    const float* a = astore + r * 64;
+    const float2 re = *(const float2*)(a + 2 * sub), im = *(const float2*)(a + 32 + 2 * sub);
+    const float2 d = *(const float2*)(delta + xb * 32 + 2 * sub);
+    uint32_t rh, rl, ih, il;
+    split_pair(pk(d.x * re.x, d.y * re.y), rh, rl);
+    split_pair(pk(d.x * im.x, d.y * im.y), ih, il);
+    uint32_t* o = bstore + r * (cplx ? 128 : 64);
+    const uint32_t sg = 0x80008000u;
+    o[sub] = rh;
+    o[16 + sub] = ih ^ sg;
+    o[32 + sub] = rl;
+    o[48 + sub] = il ^ sg;
+    if (cplx) {
+      o[64 + sub] = ih;
+      o[80 + sub] = rh;
+      o[96 + sub] = il;
+      o[112 + sub] = rl;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_tc4(const float2* astore, const void* bstore, const float* delta, long long ng,
+                       const Tile4* tiles, int ntiles, const Row4* rows, const int* cols, const int* slots,
+                       int nsingle, int complex_out, int nsplit, double* T, int* cnt, int* err, int nsm,
+                       cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   if (ng % kKX) return cudaErrorInvalidValue;
+  // B operand of every single, once per field
+  {
+    const long long nkb = ng / kKX;
+    long long blocks = (nkb * nsingle * 16 + 255) / 256;
+    if (blocks > (long long)nsm * 32) blocks = (long long)nsm * 32;
+    bsplit_kernel<<<(unsigned)blocks, 256, 0, st>>>((const float*)astore, delta, nkb, nsingle, complex_out,
+                                                    (uint32_t*)bstore);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(tc4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
@@ -638,11 +626,12 @@ cudaError_t launch_tc4(const float2* astore, long long ng, const float* delta, c
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc4_kernel, kThreads, kSmem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  // every CTA takes part in every round so that the progress counters fill up
-  const int grid = nsm;
-  void* args[] = {(void*)&astore, (void*)&ng,     (void*)&delta, (void*)&tiles, (void*)&ntiles,
-                  (void*)&rows,   (void*)&colslot, (void*)&slots, (void*)&nsingle, (void*)&complex_out,
-                  (void*)&nsplit, (void*)&T,      (void*)&cnt,   (void*)&err};
+  const float* af = (const float*)astore;
+  const uint8_t* bs = (const uint8_t*)bstore;
+  const int grid = nsm;  // every CTA takes part in every round so that the progress counters fill up
+  void* args[] = {(void*)&af,    (void*)&bs,     (void*)&ng,    (void*)&tiles, (void*)&ntiles,
+                  (void*)&rows,  (void*)&cols,   (void*)&slots, (void*)&nsingle, (void*)&complex_out,
+                  (void*)&nsplit, (void*)&T,     (void*)&cnt,   (void*)&err};
   e = cudaLaunchCooperativeKernel((const void*)tc4_kernel, dim3(grid), dim3(kThreads), args, kSmem, st);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
