@@ -13,15 +13,15 @@
 // B depends only on the column single and the K-block, so bsplit_kernel writes
 // it once per field (bf16 hi/lo rows in the blocked order); A depends on the
 // row pair and is formed on chip.  Roles of a persistent CTA (one per SM):
-//   warps 9-12 loaders: per-thread 16-byte cp.async of each K-block's raw FP32
+//   warps 17-20 loaders: per-thread 16-byte cp.async of each K-block's raw FP32
 //              row singles and precomputed B rows into a 4-deep ring; each
 //              thread's copies complete onto the stage's mbarrier (noinc);
-//   warps 0-7  producers: copy the B rows into the 128-byte-swizzled K-major
+//   warps 0-15 producers: copy the B rows into the 128-byte-swizzled K-major
 //              operand tiles, form the bf16 hi/lo A tile (packed f32x2
 //              arithmetic) in a 2-deep ring; every 64 K-blocks they fold the
 //              TMEM accumulator into a second TMEM accumulator, and at the end
 //              of a work unit add it to T in FP64;
-//   warp 8     MMA issuer: one thread issues 12 tcgen05.mma (M=128, K=16) per
+//   warp 16    MMA issuer: one thread issues 12 tcgen05.mma (M=128, K=16) per
 //              K-block and commits to the mbarriers that free the operand stage
 //              and publish the accumulator.
 // Work units (tile, x-split) are dealt round-robin to a cooperative grid of one
@@ -42,10 +42,10 @@ constexpr int kRS = 4;                 // raw stages
 constexpr int kOS = 2;                 // operand stages
 constexpr int kFlush = 64;             // K-blocks per inner accumulation range
 constexpr int kKX = 32;                // grid points per K-block (64 bf16 = one 128-B row)
-constexpr int kProdWarps = 8;          // producer warps 0..7
+constexpr int kProdWarps = 16;         // producer warps 0..15
 constexpr int kProd = kProdWarps * 32;
-constexpr int kMmaWarp = kProdWarps;   // warp 8
-constexpr int kLoadWarps = 4;          // warps 9..12
+constexpr int kMmaWarp = kProdWarps;   // warp 16
+constexpr int kLoadWarps = 4;          // warps 17..20
 constexpr int kLoad0 = kMmaWarp + 1;
 constexpr int kLoaders = kLoadWarps * 32;
 constexpr int kThreads = (kProdWarps + 1 + kLoadWarps) * 32;
@@ -434,21 +434,22 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
   } else {
     // ---------------------------------------------------------- producers --
     const int h = tid & 7;       // points 4h .. 4h+3 of the K-block
-    const int g = tid >> 3;      // 0..31
-    const int quarter = warp & 3, part = warp >> 2;  // TMEM lane quarter, column half
+    const int g = (tid >> 3) & 31;
+    const int kk = tid >> 8;     // 0: rows 0..63, 1: rows 64..127
+    const int quarter = warp & 3, part = warp >> 2;  // TMEM lane quarter, column quarter
     uint32_t gr = 0, q = 0, f = 0;
     bool ok = true;
     for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
       const Unit it = unit_of(u, ntiles, nsplit, ng);
       const Tile4 tl = tiles[it.tile];
       const int N = n_mma(tl, cplx);
-      int au1[4], au2[4];
-      uint64_t as1[4], as2[4], ans2[4];
-      uint32_t aoffr[4], aoffi[4];
-      bool aval[4];
+      int au1[2], au2[2];
+      uint64_t as1[2], as2[2], ans2[2];
+      uint32_t aoffr[2], aoffi[2];
+      bool aval[2];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int r = pass_row(g, k);
+      for (int k = 0; k < 2; ++k) {
+        const int r = pass_row(g, 2 * kk + k);
         aval[k] = r < tl.nrows;
         const Row4 rw = aval[k] ? rows[tl.row0 + r] : Row4{0, 0, 0, 1.f};
         au1[k] = rw.u1;
@@ -478,16 +479,16 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
           *(uint4*)(op + 2 * kATile + hl * kBTile + swz(c, j)) = v;
         }
         // ---- A: pair products, all loads first ----
-        float4 r1[4], i1[4], r2[4], i2[4];
+        float4 r1[2], i1[2], r2[2], i2[2];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 2; ++k) {
           r1[k] = U4[au1[k] * 16 + h];
           i1[k] = U4[au1[k] * 16 + 8 + h];
           r2[k] = U4[au2[k] * 16 + h];
           i2[k] = U4[au2[k] * 16 + 8 + h];
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 2; ++k) {
           uint32_t hr[2] = {0, 0}, lr[2] = {0, 0}, hi[2] = {0, 0}, li[2] = {0, 0};
           if (aval[k]) {
 #pragma unroll
@@ -525,26 +526,26 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
           }
           ++f;
           tc_fence_after();
-          const int hc = N >> 1;  // columns of this thread's half (N is a multiple of 16)
+          const int qc = N >> 2;  // columns of this thread's quarter (N is a multiple of 16)
           const int row = quarter * 32 + lane;
           const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-          for (int c0 = 0; c0 < hc; c0 += 8) {
-            const int col = part * hc + c0;
-            float in[8], out[8];
-            tmem_ld8(tmem + lane_addr + col, in);
+          for (int c0 = 0; c0 < qc; c0 += 4) {
+            const int col = part * qc + c0;
+            float in[4], out[4];
+            tmem_ld4(tmem + lane_addr + col, in);
             if (first_flush) {
 #pragma unroll
-              for (int e = 0; e < 8; ++e) out[e] = in[e];
+              for (int e = 0; e < 4; ++e) out[e] = in[e];
             } else {
-              tmem_ld8(tmem + lane_addr + 64 + col, out);
+              tmem_ld4(tmem + lane_addr + 64 + col, out);
 #pragma unroll
-              for (int e = 0; e < 8; ++e) out[e] += in[e];
+              for (int e = 0; e < 4; ++e) out[e] += in[e];
             }
             if (!last) {
-              tmem_st8(tmem + lane_addr + 64 + col, out);
+              tmem_st4(tmem + lane_addr + 64 + col, out);
             } else if (row < tl.nrows) {
 #pragma unroll
-              for (int e = 0; e < 8; ++e) {
+              for (int e = 0; e < 4; ++e) {
                 const int c = col + e;
                 if (cplx) {
                   if ((c >> 1) < tl.ncols)
