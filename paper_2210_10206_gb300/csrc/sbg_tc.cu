@@ -16,9 +16,10 @@
 //   warps 17-20 loaders: per-thread 16-byte cp.async of each K-block's raw FP32
 //              row singles and precomputed B rows into a 4-deep ring; each
 //              thread's copies complete onto the stage's mbarrier (noinc);
-//   warps 0-15 producers: copy the B rows into the 128-byte-swizzled K-major
-//              operand tiles, form the bf16 hi/lo A tile (packed f32x2
-//              arithmetic) in a 2-deep ring; every 64 K-blocks they fold the
+//   warps 0-15 producers: copy the B rows into 128-byte-swizzled K-major tiles
+//              in shared memory and write the bf16 hi/lo A tile (formed with
+//              packed f32x2 arithmetic, one row per TMEM lane) straight into
+//              tensor memory, in a 4-deep ring; every 64 K-blocks they fold the
 //              TMEM accumulator into a second TMEM accumulator, and at the end
 //              of a work unit add it to T in FP64;
 //   warp 16    MMA issuer: one thread issues 12 tcgen05.mma (M=128, K=16) per
@@ -39,7 +40,7 @@ namespace sbg {
 namespace {
 
 constexpr int kRS = 4;                 // raw stages
-constexpr int kOS = 2;                 // operand stages
+constexpr int kOS = 4;                 // operand stages (A in TMEM, B in shared memory)
 constexpr int kFlush = 64;             // K-blocks per inner accumulation range
 constexpr int kKX = 32;                // grid points per K-block (64 bf16 = one 128-B row)
 constexpr int kProdWarps = 16;         // producer warps 0..15
@@ -49,9 +50,12 @@ constexpr int kLoadWarps = 4;          // warps 17..20
 constexpr int kLoad0 = kMmaWarp + 1;
 constexpr int kLoaders = kLoadWarps * 32;
 constexpr int kThreads = (kProdWarps + 1 + kLoadWarps) * 32;
-constexpr int kATile = 128 * 128;      // bytes of one 128-row bf16 K-block tile
-constexpr int kBTile = 64 * 128;       // bytes of one <=64-row tile
-constexpr int kOpStage = 2 * kATile + 2 * kBTile;
+constexpr int kBTile = 64 * 128;       // bytes of one <=64-row bf16 K-block tile
+constexpr int kOpStage = 2 * kBTile;   // B hi and lo
+// TMEM columns: inner accumulator [0, 64), outer accumulator [64, 128), then
+// one 64-column A stage per operand stage (32 columns hi, 32 lo: 64 bf16 each)
+constexpr int kTmemA0 = 128;
+constexpr int kTmemCols = 512;
 constexpr int kRawA = kTcMaxRowSlots * kKX * 8;  // FP32 (re, im) row singles
 constexpr int kRawB = 64 * 256;                  // bf16 hi/lo B rows (unswizzled)
 constexpr int kRawStage = kRawA + kRawB;
@@ -190,6 +194,20 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
+// D += A B with A (128 x 16 bf16) in tensor memory, B in shared memory
+__device__ __forceinline__ void mma_bf16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc,
+                                            uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void tmem_st4_nw(uint32_t taddr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(a), "r"(b),
+               "r"(c), "r"(d)
+               : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
                : "memory");
@@ -252,6 +270,15 @@ __device__ __forceinline__ Unit unit_of(long long u, int ntiles, int nsplit, lon
 __device__ __forceinline__ int n_mma(const Tile4& t, int cplx) {
   const int nb = cplx ? 2 * t.ncols : t.ncols;
   return (nb + 15) & ~15;
+}
+
+// One lane of the warp polls the barrier; the others wait at __syncwarp, which
+// also orders their later shared-memory reads after the observed phase.
+__device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t parity, volatile int* err, int code) {
+  int good = 1;
+  if ((threadIdx.x & 31) == 0) good = mbar_wait(b, parity, err, code);
+  __syncwarp();
+  return __shfl_sync(0xffffffffu, good, 0) != 0;
 }
 
 // Bounded wait for a global progress counter written by other CTAs.
@@ -319,7 +346,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
   }
   if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                 "r"(128));
+                 "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
@@ -369,7 +396,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
         const int kb1 = min(it.nk, (e + 1) * kTcEpoch);
         for (int kb = e * kTcEpoch; kb < kb1; ++kb, ++g) {
           const int rs = g % kRS;
-          if (!mbar_wait(&raw_empty[rs], ((g / kRS) & 1) ^ 1, err, 11)) {
+          if (!warp_wait(&raw_empty[rs], ((g / kRS) & 1) ^ 1, err, 11)) {
             ok = false;
             break;
           }
@@ -378,7 +405,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
 #pragma unroll
           for (int k = 0; k < kTcMaxRowSlots / 8; ++k)
             if (asi[k] >= 0)
-              cp_async16(st + (rq + 8 * k) * 256 + ck * 16,
+              cp_async16(st + (rq + 8 * k) * 256 + ((ck ^ (rq & 7)) << 4),
                          astore + (xb * nsingle + asi[k]) * 64 + ck * 4, 16);
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
@@ -415,8 +442,8 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
             break;
           }
           tc_fence_after();
-          const uint32_t base = su32(op_base + os * kOpStage);
-          const uint32_t a_hi = base, a_lo = base + kATile, b_hi = base + 2 * kATile, b_lo = b_hi + kBTile;
+          const uint32_t b_hi = su32(op_base + os * kOpStage), b_lo = b_hi + kBTile;
+          const uint32_t a_hi = tmem + kTmemA0 + 64 * os, a_lo = a_hi + 32;
           const bool first = (kb % kFlush) == 0;
 #pragma unroll
           for (int p = 0; p < 3; ++p) {
@@ -424,7 +451,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
             const uint32_t b = p == 1 ? b_lo : b_hi;
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-              mma_bf16(tmem, sdesc(a + 32 * k), sdesc(b + 32 * k), idesc, (first && p == 0 && k == 0) ? 0u : 1u);
+              mma_bf16_ts(tmem, a + 8 * k, sdesc(b + 32 * k), idesc, (first && p == 0 && k == 0) ? 0u : 1u);
           }
           mma_commit(&op_empty[os]);
           if ((kb + 1) % kFlush == 0 || kb + 1 == it.nk) mma_commit(acc_full);
@@ -433,42 +460,32 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
     }
   } else {
     // ---------------------------------------------------------- producers --
-    const int h = tid & 7;       // points 4h .. 4h+3 of the K-block
-    const int g = (tid >> 3) & 31;
-    const int kk = tid >> 8;     // 0: rows 0..63, 1: rows 64..127
-    const int quarter = warp & 3, part = warp >> 2;  // TMEM lane quarter, column quarter
+    const int quarter = warp & 3;        // TMEM lane quarter = rows 32 quarter .. +31
+    const int part = warp >> 2;          // points 8 part .. 8 part + 7; epilogue column quarter
+    const int row = quarter * 32 + lane; // the A row (TMEM lane) this thread writes
+    const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     uint32_t gr = 0, q = 0, f = 0;
     bool ok = true;
     for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
       const Unit it = unit_of(u, ntiles, nsplit, ng);
       const Tile4 tl = tiles[it.tile];
       const int N = n_mma(tl, cplx);
-      int au1[2], au2[2];
-      uint64_t as1[2], as2[2], ans2[2];
-      uint32_t aoffr[2], aoffi[2];
-      bool aval[2];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int r = pass_row(g, 2 * kk + k);
-        aval[k] = r < tl.nrows;
-        const Row4 rw = aval[k] ? rows[tl.row0 + r] : Row4{0, 0, 0, 1.f};
-        au1[k] = rw.u1;
-        au2[k] = rw.u2;
-        const float s1 = (rw.flags & 1) ? -1.f : 1.f, s2 = (rw.flags & 2) ? -1.f : 1.f;
-        as1[k] = pk(s1, s1);
-        as2[k] = pk(s2, s2);
-        ans2[k] = pk(-s2, -s2);
-        aoffr[k] = swz(r, h >> 1) + 8 * (h & 1);
-        aoffi[k] = swz(r, 4 + (h >> 1)) + 8 * (h & 1);
-      }
+      const bool aval = row < tl.nrows;
+      const Row4 rw = aval ? rows[tl.row0 + row] : Row4{0, 0, 0, 1.f};
+      const float s1 = (rw.flags & 1) ? -1.f : 1.f, s2 = (rw.flags & 2) ? -1.f : 1.f;
+      const uint64_t as1 = pk(s1, s1), as2 = pk(s2, s2), ans2 = pk(-s2, -s2);
+      // swizzled 16-byte chunks of this thread's points in the raw row singles
+      const int c1a = (2 * part) ^ (rw.u1 & 7), c1b = (2 * part + 1) ^ (rw.u1 & 7);
+      const int c2a = (2 * part) ^ (rw.u2 & 7), c2b = (2 * part + 1) ^ (rw.u2 & 7);
       bool first_flush = true;
       for (int kb = 0; kb < it.nk; ++kb, ++gr, ++q) {
         const int rs = gr % kRS, os = q % kOS;
-        if (!mbar_wait(&raw_full[rs], (gr / kRS) & 1, err, 31) ||
-            !mbar_wait(&op_empty[os], ((q / kOS) & 1) ^ 1, err, 32)) {
+        if (!warp_wait(&raw_full[rs], (gr / kRS) & 1, err, 31) ||
+            !warp_wait(&op_empty[os], ((q / kOS) & 1) ^ 1, err, 32)) {
           ok = false;
           break;
         }
+        tc_fence_after();
         const uint8_t* raw = raw_base + rs * kRawStage;
         const float4* U4 = (const float4*)raw;
         uint8_t* op = op_base + os * kOpStage;
@@ -476,39 +493,38 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
         for (int ch = tid; ch < N * 16; ch += kProd) {
           const int c = ch >> 4, pc = ch & 15, j = pc & 7, hl = pc >> 3;
           const uint4 v = *(const uint4*)(raw + kRawA + c * 256 + pc * 16);
-          *(uint4*)(op + 2 * kATile + hl * kBTile + swz(c, j)) = v;
+          *(uint4*)(op + hl * kBTile + swz(c, j)) = v;
         }
-        // ---- A: pair products, all loads first ----
-        float4 r1[2], i1[2], r2[2], i2[2];
+        // ---- A: 8 pair products of this thread's row, to TMEM ----
+        const float4 ra0 = U4[rw.u1 * 16 + c1a], ra1 = U4[rw.u1 * 16 + c1b];
+        const float4 ia0 = U4[rw.u1 * 16 + 8 + c1a], ia1 = U4[rw.u1 * 16 + 8 + c1b];
+        const float4 rb0 = U4[rw.u2 * 16 + c2a], rb1 = U4[rw.u2 * 16 + c2b];
+        const float4 ib0 = U4[rw.u2 * 16 + 8 + c2a], ib1 = U4[rw.u2 * 16 + 8 + c2b];
+        const float fr1[8] = {ra0.x, ra0.y, ra0.z, ra0.w, ra1.x, ra1.y, ra1.z, ra1.w};
+        const float fi1[8] = {ia0.x, ia0.y, ia0.z, ia0.w, ia1.x, ia1.y, ia1.z, ia1.w};
+        const float fr2[8] = {rb0.x, rb0.y, rb0.z, rb0.w, rb1.x, rb1.y, rb1.z, rb1.w};
+        const float fi2[8] = {ib0.x, ib0.y, ib0.z, ib0.w, ib1.x, ib1.y, ib1.z, ib1.w};
+        uint32_t hr[4], lr[4], hi[4], li[4];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          r1[k] = U4[au1[k] * 16 + h];
-          i1[k] = U4[au1[k] * 16 + 8 + h];
-          r2[k] = U4[au2[k] * 16 + h];
-          i2[k] = U4[au2[k] * 16 + 8 + h];
+        for (int p2 = 0; p2 < 4; ++p2) {
+          const uint64_t ar = pk(fr1[2 * p2], fr1[2 * p2 + 1]);
+          const uint64_t ai = mul2(pk(fi1[2 * p2], fi1[2 * p2 + 1]), as1);
+          const uint64_t br = pk(fr2[2 * p2], fr2[2 * p2 + 1]);
+          const uint64_t bi0 = pk(fi2[2 * p2], fi2[2 * p2 + 1]);
+          const uint64_t bi = mul2(bi0, as2), nbi = mul2(bi0, ans2);
+          const uint64_t pr = fma2(ar, br, mul2(ai, nbi));   // ar br - ai bi
+          const uint64_t pi = fma2(ar, bi, mul2(ai, br));    // ar bi + ai br
+          split_pair(pr, hr[p2], lr[p2]);
+          split_pair(pi, hi[p2], li[p2]);
+          if (!aval) hr[p2] = lr[p2] = hi[p2] = li[p2] = 0u;
         }
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          uint32_t hr[2] = {0, 0}, lr[2] = {0, 0}, hi[2] = {0, 0}, li[2] = {0, 0};
-          if (aval[k]) {
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-              const uint64_t ar = p ? pk(r1[k].z, r1[k].w) : pk(r1[k].x, r1[k].y);
-              const uint64_t ai = mul2(p ? pk(i1[k].z, i1[k].w) : pk(i1[k].x, i1[k].y), as1[k]);
-              const uint64_t br = p ? pk(r2[k].z, r2[k].w) : pk(r2[k].x, r2[k].y);
-              const uint64_t bi0 = p ? pk(i2[k].z, i2[k].w) : pk(i2[k].x, i2[k].y);
-              const uint64_t bi = mul2(bi0, as2[k]), nbi = mul2(bi0, ans2[k]);
-              const uint64_t pr = fma2(ar, br, mul2(ai, nbi));   // ar br - ai bi
-              const uint64_t pi = fma2(ar, bi, mul2(ai, br));    // ar bi + ai br
-              split_pair(pr, hr[p], lr[p]);
-              split_pair(pi, hi[p], li[p]);
-            }
-          }
-          *(uint2*)(op + aoffr[k]) = make_uint2(hr[0], hr[1]);
-          *(uint2*)(op + kATile + aoffr[k]) = make_uint2(lr[0], lr[1]);
-          *(uint2*)(op + aoffi[k]) = make_uint2(hi[0], hi[1]);
-          *(uint2*)(op + kATile + aoffi[k]) = make_uint2(li[0], li[1]);
-        }
+        const uint32_t acol = tmem + lane_addr + kTmemA0 + 64 * os + 4 * part;
+        tmem_st4_nw(acol, hr[0], hr[1], hr[2], hr[3]);            // hi, real parts
+        tmem_st4_nw(acol + 16, hi[0], hi[1], hi[2], hi[3]);       // hi, imaginary parts
+        tmem_st4_nw(acol + 32, lr[0], lr[1], lr[2], lr[3]);       // lo, real parts
+        tmem_st4_nw(acol + 48, li[0], li[1], li[2], li[3]);       // lo, imaginary parts
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
         // publish this warp's operand writes to the tensor core (async proxy)
         // and release the raw stage: one arrival per warp
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -520,15 +536,13 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
         // ---- fold the inner accumulator every kFlush K-blocks ----
         const bool last = kb + 1 == it.nk;
         if ((kb + 1) % kFlush == 0 || last) {
-          if (!mbar_wait(acc_full, f & 1, err, 33)) {
+          if (!warp_wait(acc_full, f & 1, err, 33)) {
             ok = false;
             break;
           }
           ++f;
           tc_fence_after();
           const int qc = N >> 2;  // columns of this thread's quarter (N is a multiple of 16)
-          const int row = quarter * 32 + lane;
-          const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
           for (int c0 = 0; c0 < qc; c0 += 4) {
             const int col = part * qc + c0;
             float in[4], out[4];
@@ -565,7 +579,8 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == kMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+  if (warp == kMmaWarp)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
 // B operand rows of every single and K-block: v = delta * a; 3D row
