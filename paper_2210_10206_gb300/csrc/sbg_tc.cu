@@ -13,15 +13,19 @@
 // B depends only on the column single and the K-block, so bsplit_kernel writes
 // it once per field (bf16 hi/lo rows in the blocked order); A depends on the
 // row pair and is formed on chip.  Roles of a persistent CTA (one per SM):
-//   warps 17-20 loaders: per-thread 16-byte cp.async of each K-block's raw FP32
-//              row singles and precomputed B rows into a 4-deep ring; each
-//              thread's copies complete onto the stage's mbarrier (noinc);
-//   warps 0-15 producers: copy the B rows into 128-byte-swizzled K-major tiles
-//              in shared memory and write the bf16 hi/lo A tile (formed with
-//              packed f32x2 arithmetic, one row per TMEM lane) straight into
-//              tensor memory, in a 4-deep ring; every 64 K-blocks they fold the
-//              TMEM accumulator into a second TMEM accumulator, and at the end
-//              of a work unit add it to T in FP64;
+//   warps 17-19 loaders: per-thread 16-byte cp.async of each K-block's raw FP32
+//              row singles into two stages per producer group; each thread's
+//              copies complete onto the stage's mbarrier (noinc);
+//   warps 0-15 producers, in 4 groups of 4 warps: group g takes the K-blocks
+//              kb = g (mod 4) of every unit and owns operand stage g, so four
+//              K-blocks are in flight.  For its K-block a group stores the B rows
+//              (prefetched from L2 into registers during its previous K-block)
+//              into a 128-byte-swizzled K-major tile in shared memory and writes the
+//              bf16 hi/lo A tile (formed with packed f32x2 arithmetic, one row
+//              per TMEM lane) straight into tensor memory.  Group 0 also folds
+//              each 64-K-block range's TMEM accumulator (two, alternating) into
+//              the outer TMEM accumulator and, at the end of a unit, adds it to
+//              T in FP64;
 //   warp 16    MMA issuer: one thread issues 12 tcgen05.mma (M=128, K=16) per
 //              K-block and commits to the mbarriers that free the operand stage
 //              and publish the accumulator.
@@ -39,26 +43,27 @@ namespace sbg {
 
 namespace {
 
-constexpr int kRS = 4;                 // raw stages
-constexpr int kOS = 4;                 // operand stages (A in TMEM, B in shared memory)
+constexpr int kGroups = 4;             // producer groups; group g owns operand stage g
+constexpr int kRS = 2 * kGroups;       // raw stages: two per group (2g, 2g + 1)
+constexpr int kOS = kGroups;           // operand stages (A in TMEM, B in shared memory)
 constexpr int kFlush = 64;             // K-blocks per inner accumulation range
 constexpr int kKX = 32;                // grid points per K-block (64 bf16 = one 128-B row)
 constexpr int kProdWarps = 16;         // producer warps 0..15
 constexpr int kProd = kProdWarps * 32;
 constexpr int kMmaWarp = kProdWarps;   // warp 16
-constexpr int kLoadWarps = 4;          // warps 17..20
+constexpr int kLoadWarps = 3;          // warps 17..19
 constexpr int kLoad0 = kMmaWarp + 1;
 constexpr int kLoaders = kLoadWarps * 32;
 constexpr int kThreads = (kProdWarps + 1 + kLoadWarps) * 32;
 constexpr int kBTile = 64 * 128;       // bytes of one <=64-row bf16 K-block tile
 constexpr int kOpStage = 2 * kBTile;   // B hi and lo
-// TMEM columns: inner accumulator [0, 64), outer accumulator [64, 128), then
-// one 64-column A stage per operand stage (32 columns hi, 32 lo: 64 bf16 each)
-constexpr int kTmemA0 = 128;
+// TMEM columns: two inner accumulators [0, 64) and [64, 128) (alternate
+// 64-K-block ranges), the outer accumulator [128, 192), then one 64-column A
+// stage per operand stage (32 columns hi, 32 lo: 64 bf16 each)
+constexpr int kTmemOuter = 128;
+constexpr int kTmemA0 = 192;
 constexpr int kTmemCols = 512;
-constexpr int kRawA = kTcMaxRowSlots * kKX * 8;  // FP32 (re, im) row singles
-constexpr int kRawB = 64 * 256;                  // bf16 hi/lo B rows (unswizzled)
-constexpr int kRawStage = kRawA + kRawB;
+constexpr int kRawStage = kTcMaxRowSlots * kKX * 8;  // FP32 (re, im) row singles
 constexpr int kLag = 4;                // epochs a loader may run ahead of the slowest CTA
 constexpr int kMeta = 256;             // barriers and the TMEM address
 constexpr int kSmem = kOS * kOpStage + kRS * kRawStage + kMeta + 1024;
@@ -320,8 +325,8 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
   uint64_t* raw_empty = bars + kRS;
   uint64_t* op_full = bars + 2 * kRS;
   uint64_t* op_empty = bars + 2 * kRS + kOS;
-  uint64_t* acc_full = bars + 2 * kRS + 2 * kOS;
-  uint32_t* tmem_slot = (uint32_t*)(acc_full + 1);
+  uint64_t* acc_full = bars + 2 * kRS + 2 * kOS;  // [2], one per inner accumulator
+  uint32_t* tmem_slot = (uint32_t*)(acc_full + 2);
   volatile int* err = err_flag;
 
   const int tid = threadIdx.x;
@@ -334,14 +339,15 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
 
   if (tid == 0) {
     for (int i = 0; i < kRS; ++i) {
-      mbar_init(&raw_full[i], kLoaders);       // one cp.async completion per loader thread
-      mbar_init(&raw_empty[i], kProdWarps);    // one arrival per producer warp
+      mbar_init(&raw_full[i], kLoaders);              // one cp.async completion per loader thread
+      mbar_init(&raw_empty[i], kProdWarps / kGroups); // one arrival per warp of the owning group
     }
     for (int i = 0; i < kOS; ++i) {
-      mbar_init(&op_full[i], kProdWarps);
-      mbar_init(&op_empty[i], 1);              // tcgen05.commit
+      mbar_init(&op_full[i], kProdWarps / kGroups);
+      mbar_init(&op_empty[i], 1);                     // tcgen05.commit
     }
-    mbar_init(acc_full, 1);
+    mbar_init(&acc_full[0], 1);
+    mbar_init(&acc_full[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == kMmaWarp) {
@@ -356,32 +362,26 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
 
   if (warp >= kLoad0) {
     // ------------------------------------------------------------ loaders --
-    const int li = tid - kLoad0 * 32;  // 0..127
+    const int li = tid - kLoad0 * 32;  // 0 .. kLoaders - 1
     const int ck = li & 15;            // 16-byte chunk within a 256-byte row
-    const int rq = li >> 4;            // 0..7: rows rq, rq + 8, ...
-    uint32_t g = 0;
+    const int rq = li >> 4;            // slots rq, rq + kLoaders / 16, ...
+    constexpr int kSlotStep = kLoaders / 16;
+    constexpr int kSlotIter = (kTcMaxRowSlots + kSlotStep - 1) / kSlotStep;
+    uint32_t gcount[kGroups] = {0, 0, 0, 0};  // K-blocks loaded so far for each producer group
     bool ok = true;
     for (long long rd = 0; rd < nrounds && ok; ++rd) {
       const long long u = rd * gridDim.x + blockIdx.x;
       Unit it{0, 0, 0};
       Tile4 tl{};
-      int asi[kTcMaxRowSlots / 8], bsi[8];
+      int asi[kSlotIter];
       if (u < nunits) {
         it = unit_of(u, ntiles, nsplit, ng);
         tl = tiles[it.tile];
       }
-      const int N = u < nunits ? n_mma(tl, cplx) : 0;
 #pragma unroll
-      for (int k = 0; k < kTcMaxRowSlots / 8; ++k) {
-        const int sl = rq + 8 * k;
+      for (int k = 0; k < kSlotIter; ++k) {
+        const int sl = rq + kSlotStep * k;
         asi[k] = sl < tl.nuniq ? slots[tl.uniq0 + sl] : -1;
-      }
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int c = rq + 8 * k;                      // B row
-        const int cs = cplx ? (c >> 1) : c;            // column single
-        bsi[k] = (c < N && cs < tl.ncols) ? cols[tl.col0 + cs] * bparts + (cplx ? (c & 1) : 0)
-                                          : (c < N ? -2 : -1);
       }
       for (int e = 0; e < epochs && ok; ++e) {
         const long long ce = rd * epochs + e;  // global epoch index
@@ -394,28 +394,21 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
           }
         }
         const int kb1 = min(it.nk, (e + 1) * kTcEpoch);
-        for (int kb = e * kTcEpoch; kb < kb1; ++kb, ++g) {
-          const int rs = g % kRS;
-          if (!warp_wait(&raw_empty[rs], ((g / kRS) & 1) ^ 1, err, 11)) {
+        for (int kb = e * kTcEpoch; kb < kb1; ++kb) {
+          const int gg = kb % kGroups;
+          const uint32_t n = gcount[gg]++;
+          const int rs = 2 * gg + (n & 1);
+          if (!warp_wait(&raw_empty[rs], ((n >> 1) & 1) ^ 1, err, 11)) {
             ok = false;
             break;
           }
           uint8_t* st = raw_base + rs * kRawStage;
           const long long xb = (it.x0 >> 5) + kb;  // K-block index in the blocked stores
 #pragma unroll
-          for (int k = 0; k < kTcMaxRowSlots / 8; ++k)
+          for (int k = 0; k < kSlotIter; ++k) {
+            const int sl = rq + kSlotStep * k;
             if (asi[k] >= 0)
-              cp_async16(st + (rq + 8 * k) * 256 + ((ck ^ (rq & 7)) << 4),
-                         astore + (xb * nsingle + asi[k]) * 64 + ck * 4, 16);
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            if (bsi[k] == -1) continue;
-            uint8_t* dst = st + kRawA + (rq + 8 * k) * 256 + ck * 16;
-            if (bsi[k] >= 0) {
-              cp_async16(dst, bstore + (xb * nsingle * bparts + bsi[k]) * 256 + ck * 16, 16);
-            } else {
-              cp_async16(dst, bstore, 0);  // zero-filled padding row
-            }
+              cp_async16(st + sl * 256 + ((ck ^ (sl & 7)) << 4), astore + (xb * nsingle + asi[k]) * 64 + ck * 4, 16);
           }
           cp_async_arrive(&raw_full[rs]);
         }
@@ -427,7 +420,8 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
   } else if (warp == kMmaWarp) {
     // ---------------------------------------------------------------- MMA --
     if (lane == 0) {
-      uint32_t q = 0;
+      uint32_t uses[kOS] = {0, 0, 0, 0};
+      uint32_t R = 0;  // ranges issued so far (selects the inner accumulator)
       bool ok = true;
       for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
         const Unit it = unit_of(u, ntiles, nsplit, ng);
@@ -435,15 +429,16 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
         const int N = n_mma(tl, cplx);
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
-        for (int kb = 0; kb < it.nk; ++kb, ++q) {
-          const int os = q % kOS;
-          if (!mbar_wait(&op_full[os], (q / kOS) & 1, err, 21)) {
+        for (int kb = 0; kb < it.nk; ++kb) {
+          const int os = kb % kOS;
+          if (!mbar_wait(&op_full[os], uses[os]++ & 1, err, 21)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t b_hi = su32(op_base + os * kOpStage), b_lo = b_hi + kBTile;
           const uint32_t a_hi = tmem + kTmemA0 + 64 * os, a_lo = a_hi + 32;
+          const uint32_t dacc = tmem + 64 * ((R + kb / kFlush) & 1);
           const bool first = (kb % kFlush) == 0;
 #pragma unroll
           for (int p = 0; p < 3; ++p) {
@@ -451,129 +446,166 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
             const uint32_t b = p == 1 ? b_lo : b_hi;
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-              mma_bf16_ts(tmem, a + 8 * k, sdesc(b + 32 * k), idesc, (first && p == 0 && k == 0) ? 0u : 1u);
+              mma_bf16_ts(dacc, a + 8 * k, sdesc(b + 32 * k), idesc, (first && p == 0 && k == 0) ? 0u : 1u);
           }
           mma_commit(&op_empty[os]);
-          if ((kb + 1) % kFlush == 0 || kb + 1 == it.nk) mma_commit(acc_full);
+          if ((kb + 1) % kFlush == 0 || kb + 1 == it.nk) mma_commit(&acc_full[(R + kb / kFlush) & 1]);
         }
+        R += (it.nk + kFlush - 1) / kFlush;
       }
     }
   } else {
     // ---------------------------------------------------------- producers --
     const int quarter = warp & 3;        // TMEM lane quarter = rows 32 quarter .. +31
-    const int part = warp >> 2;          // points 8 part .. 8 part + 7; epilogue column quarter
+    const int grp = warp >> 2;           // producer group: K-blocks kb = grp (mod 4), stage grp
+    const int gtid = tid & 127;          // thread index within the group
     const int row = quarter * 32 + lane; // the A row (TMEM lane) this thread writes
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-    uint32_t gr = 0, q = 0, f = 0;
+    const int os = grp;
+    uint32_t uses = 0;                   // K-blocks this group has produced so far
+    uint32_t R = 0;                      // ranges of earlier units (group 0 bookkeeping)
     bool ok = true;
     for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
       const Unit it = unit_of(u, ntiles, nsplit, ng);
       const Tile4 tl = tiles[it.tile];
       const int N = n_mma(tl, cplx);
+      const int nranges = (it.nk + kFlush - 1) / kFlush;
       const bool aval = row < tl.nrows;
       const Row4 rw = aval ? rows[tl.row0 + row] : Row4{0, 0, 0, 1.f};
       const float s1 = (rw.flags & 1) ? -1.f : 1.f, s2 = (rw.flags & 2) ? -1.f : 1.f;
       const uint64_t as1 = pk(s1, s1), as2 = pk(s2, s2), ans2 = pk(-s2, -s2);
-      // swizzled 16-byte chunks of this thread's points in the raw row singles
-      const int c1a = (2 * part) ^ (rw.u1 & 7), c1b = (2 * part + 1) ^ (rw.u1 & 7);
-      const int c2a = (2 * part) ^ (rw.u2 & 7), c2b = (2 * part + 1) ^ (rw.u2 & 7);
-      bool first_flush = true;
-      for (int kb = 0; kb < it.nk; ++kb, ++gr, ++q) {
-        const int rs = gr % kRS, os = q % kOS;
-        if (!warp_wait(&raw_full[rs], (gr / kRS) & 1, err, 31) ||
-            !warp_wait(&op_empty[os], ((q / kOS) & 1) ^ 1, err, 32)) {
+      const int x1 = rw.u1 & 7, x2 = rw.u2 & 7;  // raw-stage chunk swizzle of the two singles
+      // B rows this thread moves: row c = (gtid >> 4) + 8k, 16-byte chunk gtid & 15
+      int bsi[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int c = (gtid >> 4) + 8 * k;
+        const int cs = cplx ? (c >> 1) : c;
+        bsi[k] = (c < N && cs < tl.ncols) ? cols[tl.col0 + cs] * bparts + (cplx ? (c & 1) : 0)
+                                          : (c < N ? -2 : -1);
+      }
+      uint4 vb[8];
+      auto load_b = [&](int kbb) {
+        const long long xb = (it.x0 >> 5) + kbb;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          vb[k] = bsi[k] >= 0 ? __ldg((const uint4*)(bstore + (xb * nsingle * bparts + bsi[k]) * 256) + (gtid & 15))
+                              : make_uint4(0, 0, 0, 0);
+      };
+      if (grp < it.nk) load_b(grp);
+      int flushed = 0;                              // ranges of this unit already folded (group 0)
+      // fold range i of this unit: inner accumulator -> outer (or -> T for the last range)
+      auto fold = [&](int i) -> bool {
+        const uint32_t Rg = R + i;
+        if (!warp_wait(&acc_full[Rg & 1], (Rg >> 1) & 1, err, 33)) return false;
+        tc_fence_after();
+        const bool last = i + 1 == nranges;
+        const uint32_t inner = tmem + lane_addr + 64 * (Rg & 1);
+        const uint32_t outer = tmem + lane_addr + kTmemOuter;
+        for (int c0 = 0; c0 < N; c0 += 8) {
+          float in[8], out[8];
+          tmem_ld8(inner + c0, in);
+          if (i == 0) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) out[e] = in[e];
+          } else {
+            tmem_ld8(outer + c0, out);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) out[e] += in[e];
+          }
+          if (!last) {
+            tmem_st8(outer + c0, out);
+          } else if (aval) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int c = c0 + e;
+              if (cplx) {
+                if ((c >> 1) < tl.ncols)
+                  atomicAdd(&T[(tl.tout + (long long)row * tl.ncols + (c >> 1)) * 2 + (c & 1)], (double)out[e]);
+              } else if (c < tl.ncols) {
+                atomicAdd(&T[tl.tout + (long long)row * tl.ncols + c], (double)out[e]);
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        return true;
+      };
+      for (int kb = grp; kb < it.nk && ok; kb += kGroups) {
+        // group 0 produces the first K-block of every range: fold range i - 2 first, whose
+        // inner accumulator that range reuses
+        if (grp == 0 && kb % kFlush == 0 && kb / kFlush >= 2) {
+          if (!fold(kb / kFlush - 2)) {
+            ok = false;
+            break;
+          }
+          flushed = kb / kFlush - 1;
+        }
+        const int rs = 2 * grp + (uses & 1);
+        if (!warp_wait(&raw_full[rs], (uses >> 1) & 1, err, 31) || !warp_wait(&op_empty[os], (uses & 1) ^ 1, err, 32)) {
           ok = false;
           break;
         }
+        ++uses;
         tc_fence_after();
         const uint8_t* raw = raw_base + rs * kRawStage;
         const float4* U4 = (const float4*)raw;
         uint8_t* op = op_base + os * kOpStage;
-        // ---- B: swizzle the precomputed rows into the operand tile ----
-        for (int ch = tid; ch < N * 16; ch += kProd) {
-          const int c = ch >> 4, pc = ch & 15, j = pc & 7, hl = pc >> 3;
-          const uint4 v = *(const uint4*)(raw + kRawA + c * 256 + pc * 16);
-          *(uint4*)(op + hl * kBTile + swz(c, j)) = v;
-        }
-        // ---- A: 8 pair products of this thread's row, to TMEM ----
-        const float4 ra0 = U4[rw.u1 * 16 + c1a], ra1 = U4[rw.u1 * 16 + c1b];
-        const float4 ia0 = U4[rw.u1 * 16 + 8 + c1a], ia1 = U4[rw.u1 * 16 + 8 + c1b];
-        const float4 rb0 = U4[rw.u2 * 16 + c2a], rb1 = U4[rw.u2 * 16 + c2b];
-        const float4 ib0 = U4[rw.u2 * 16 + 8 + c2a], ib1 = U4[rw.u2 * 16 + 8 + c2b];
-        const float fr1[8] = {ra0.x, ra0.y, ra0.z, ra0.w, ra1.x, ra1.y, ra1.z, ra1.w};
-        const float fi1[8] = {ia0.x, ia0.y, ia0.z, ia0.w, ia1.x, ia1.y, ia1.z, ia1.w};
-        const float fr2[8] = {rb0.x, rb0.y, rb0.z, rb0.w, rb1.x, rb1.y, rb1.z, rb1.w};
-        const float fi2[8] = {ib0.x, ib0.y, ib0.z, ib0.w, ib1.x, ib1.y, ib1.z, ib1.w};
-        uint32_t hr[4], lr[4], hi[4], li[4];
+        // ---- B: store the prefetched rows into the swizzled operand tile, prefetch the next ----
+        {
+          const int pc = gtid & 15, j = pc & 7, hl = pc >> 3;
 #pragma unroll
-        for (int p2 = 0; p2 < 4; ++p2) {
-          const uint64_t ar = pk(fr1[2 * p2], fr1[2 * p2 + 1]);
-          const uint64_t ai = mul2(pk(fi1[2 * p2], fi1[2 * p2 + 1]), as1);
-          const uint64_t br = pk(fr2[2 * p2], fr2[2 * p2 + 1]);
-          const uint64_t bi0 = pk(fi2[2 * p2], fi2[2 * p2 + 1]);
-          const uint64_t bi = mul2(bi0, as2), nbi = mul2(bi0, ans2);
-          const uint64_t pr = fma2(ar, br, mul2(ai, nbi));   // ar br - ai bi
-          const uint64_t pi = fma2(ar, bi, mul2(ai, br));    // ar bi + ai br
-          split_pair(pr, hr[p2], lr[p2]);
-          split_pair(pi, hi[p2], li[p2]);
-          if (!aval) hr[p2] = lr[p2] = hi[p2] = li[p2] = 0u;
+          for (int k = 0; k < 8; ++k)
+            if (bsi[k] != -1) *(uint4*)(op + hl * kBTile + swz((gtid >> 4) + 8 * k, j)) = vb[k];
+          if (kb + kGroups < it.nk) load_b(kb + kGroups);
         }
-        const uint32_t acol = tmem + lane_addr + kTmemA0 + 64 * os + 4 * part;
-        tmem_st4_nw(acol, hr[0], hr[1], hr[2], hr[3]);            // hi, real parts
-        tmem_st4_nw(acol + 16, hi[0], hi[1], hi[2], hi[3]);       // hi, imaginary parts
-        tmem_st4_nw(acol + 32, lr[0], lr[1], lr[2], lr[3]);       // lo, real parts
-        tmem_st4_nw(acol + 48, li[0], li[1], li[2], li[3]);       // lo, imaginary parts
+        // ---- A: the 32 pair products of this thread's row, to TMEM ----
+        const uint32_t acol = tmem + lane_addr + kTmemA0 + 64 * os;
+#pragma unroll 1
+        for (int cq = 0; cq < 4; ++cq) {  // points 8 cq .. 8 cq + 7
+          const float4 ra0 = U4[rw.u1 * 16 + ((2 * cq) ^ x1)], ra1 = U4[rw.u1 * 16 + ((2 * cq + 1) ^ x1)];
+          const float4 ia0 = U4[rw.u1 * 16 + 8 + ((2 * cq) ^ x1)], ia1 = U4[rw.u1 * 16 + 8 + ((2 * cq + 1) ^ x1)];
+          const float4 rb0 = U4[rw.u2 * 16 + ((2 * cq) ^ x2)], rb1 = U4[rw.u2 * 16 + ((2 * cq + 1) ^ x2)];
+          const float4 ib0 = U4[rw.u2 * 16 + 8 + ((2 * cq) ^ x2)], ib1 = U4[rw.u2 * 16 + 8 + ((2 * cq + 1) ^ x2)];
+          const float fr1[8] = {ra0.x, ra0.y, ra0.z, ra0.w, ra1.x, ra1.y, ra1.z, ra1.w};
+          const float fi1[8] = {ia0.x, ia0.y, ia0.z, ia0.w, ia1.x, ia1.y, ia1.z, ia1.w};
+          const float fr2[8] = {rb0.x, rb0.y, rb0.z, rb0.w, rb1.x, rb1.y, rb1.z, rb1.w};
+          const float fi2[8] = {ib0.x, ib0.y, ib0.z, ib0.w, ib1.x, ib1.y, ib1.z, ib1.w};
+          uint32_t hr[4], lr[4], hi[4], li[4];
+#pragma unroll
+          for (int p2 = 0; p2 < 4; ++p2) {
+            const uint64_t ar = pk(fr1[2 * p2], fr1[2 * p2 + 1]);
+            const uint64_t ai = mul2(pk(fi1[2 * p2], fi1[2 * p2 + 1]), as1);
+            const uint64_t br = pk(fr2[2 * p2], fr2[2 * p2 + 1]);
+            const uint64_t bi0 = pk(fi2[2 * p2], fi2[2 * p2 + 1]);
+            const uint64_t bi = mul2(bi0, as2), nbi = mul2(bi0, ans2);
+            const uint64_t pr = fma2(ar, br, mul2(ai, nbi));   // ar br - ai bi
+            const uint64_t pi = fma2(ar, bi, mul2(ai, br));    // ar bi + ai br
+            split_pair(pr, hr[p2], lr[p2]);
+            split_pair(pi, hi[p2], li[p2]);
+            if (!aval) hr[p2] = lr[p2] = hi[p2] = li[p2] = 0u;
+          }
+          tmem_st4_nw(acol + 4 * cq, hr[0], hr[1], hr[2], hr[3]);        // hi, real parts
+          tmem_st4_nw(acol + 16 + 4 * cq, hi[0], hi[1], hi[2], hi[3]);   // hi, imaginary parts
+          tmem_st4_nw(acol + 32 + 4 * cq, lr[0], lr[1], lr[2], lr[3]);   // lo, real parts
+          tmem_st4_nw(acol + 48 + 4 * cq, li[0], li[1], li[2], li[3]);   // lo, imaginary parts
+        }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
-        // publish this warp's operand writes to the tensor core (async proxy)
-        // and release the raw stage: one arrival per warp
+        // publish the B tile to the tensor core (async proxy), release the raw stage
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(&op_full[os]);
           mbar_arrive(&raw_empty[rs]);
         }
-        // ---- fold the inner accumulator every kFlush K-blocks ----
-        const bool last = kb + 1 == it.nk;
-        if ((kb + 1) % kFlush == 0 || last) {
-          if (!warp_wait(acc_full, f & 1, err, 33)) {
-            ok = false;
-            break;
-          }
-          ++f;
-          tc_fence_after();
-          const int qc = N >> 2;  // columns of this thread's quarter (N is a multiple of 16)
-          for (int c0 = 0; c0 < qc; c0 += 4) {
-            const int col = part * qc + c0;
-            float in[4], out[4];
-            tmem_ld4(tmem + lane_addr + col, in);
-            if (first_flush) {
-#pragma unroll
-              for (int e = 0; e < 4; ++e) out[e] = in[e];
-            } else {
-              tmem_ld4(tmem + lane_addr + 64 + col, out);
-#pragma unroll
-              for (int e = 0; e < 4; ++e) out[e] += in[e];
-            }
-            if (!last) {
-              tmem_st4(tmem + lane_addr + 64 + col, out);
-            } else if (row < tl.nrows) {
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const int c = col + e;
-                if (cplx) {
-                  if ((c >> 1) < tl.ncols)
-                    atomicAdd(&T[(tl.tout + (long long)row * tl.ncols + (c >> 1)) * 2 + (c & 1)], (double)out[e]);
-                } else if (c < tl.ncols) {
-                  atomicAdd(&T[tl.tout + (long long)row * tl.ncols + c], (double)out[e]);
-                }
-              }
-            }
-          }
-          first_flush = false;
-          tc_fence_before();
-        }
       }
+      // group 0: fold the ranges not folded yet, the last one into T
+      if (grp == 0 && ok) {
+        for (int i = flushed; i < nranges && ok; ++i)
+          if (!fold(i)) ok = false;
+      }
+      R += nranges;
     }
   }
   tc_fence_before();
