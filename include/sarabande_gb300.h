@@ -149,6 +149,16 @@ sbg_status sbg_projected_batch(sbg_context* ctx, const sbg_field2d* fields, int 
  * launched.  *n_stages is set to the count written (8); ms_per_stage must hold 8. */
 sbg_status sbg_last_timings(const sbg_context* ctx, double* ms_per_stage, int* n_stages);
 
+/* Device time (ms, CUDA events on the context's stream) of the 4PCF
+ * contraction kernel alone in the last measurement call: the tensor-core
+ * kernel for SBG_PREC_BF16X3, the SIMT launches for SBG_PREC_FP32 (the sum
+ * over the pair products of Eq. mu, Sec. 2.3 / Eq. proj_4pcf_coeff, Sec. 2.4,
+ * before the coupling step).  It is
+ * part of stage [5] of sbg_last_timings; the rest of that stage is the B
+ * operand split and the coupling.  *ms is 0 when the call computed no 4PCF.
+ * Errors: SBG_ERR_INVALID_ARG for a null pointer. */
+sbg_status sbg_last_contraction_ms(const sbg_context* ctx, double* ms);
+
 /* Projected 3PCF that allocates no device memory (the paper has no
  * counterpart: this entry point exists for callers that cannot call cudaMalloc
  * during a measurement, e.g. code running inside a pre-sized memory pool or an

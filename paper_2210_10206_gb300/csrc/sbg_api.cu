@@ -8,6 +8,7 @@
 //   3PCF: delta-weighted Gram of each group (Algorithms 5, 7)
 //   4PCF: pair x single contraction over x (Algorithms 6, 8) + FP64 couplings.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -137,6 +138,9 @@ struct sbg_context {
   long long nlaunch = 0;   // kernels launched by the current/last measurement call
   long long last_launches = 0;
   cudaEvent_t ev[kStages + 1] = {};
+  cudaEvent_t kev[2] = {};      // around the 4PCF contraction kernel(s)
+  bool kev_used = false;
+  double contraction_ms = 0.0;
   std::map<std::string, DevBuf> bufs;
   // full-plan cache
   std::string gkey;
@@ -144,6 +148,10 @@ struct sbg_context {
   bool gcached = false;
   std::string t4key;
   Tables4* t4 = nullptr;
+  // pinned host staging for results and status words, so downloads are plain
+  // DMA on the stream and the host copies out after the stream is idle
+  void* hpin = nullptr;
+  size_t hpin_bytes = 0;
 };
 
 namespace {
@@ -222,6 +230,90 @@ int store_index(int dim, int nb, int l, int m_abs, int b) {
   return dim == 3 ? ((l * (l + 1) / 2 + m_abs) * nb + b) : (m_abs * nb + b);
 }
 
+// Shared-memory slots of the staged row singles of one tensor-core tile.  A
+// quarter-warp of producer threads (8 consecutive rows) reads the same 16-byte
+// chunk of the first single of each of its rows, then of the second; the raw
+// stage stores chunk k of slot s at chunk k ^ (s & 7) of its 256-byte row, so
+// two distinct singles read together collide in a bank only when their slots
+// agree mod 8 (their colour).  Colours are chosen greedily, singles shared by
+// the most quarter-warp groups first, best of a few tie-breaking orders; colour
+// c owns slots c, c + 8, ...  Unused slots hold -1 (not loaded).
+sbg_status colour_slots(sbg_context* ctx, Tables4& t, Tile4& tl, const std::map<int, int>& local) {
+  const int nl = (int)local.size();
+  const int cap = kTcMaxRowSlots / 8;
+  std::vector<int> store(nl);
+  for (const auto& kv : local) store[kv.second] = kv.first;
+  std::vector<std::vector<int>> groups;       // distinct local singles per (quarter-warp, operand)
+  std::vector<std::vector<int>> member(nl);   // groups containing each single
+  for (int q = 0; q < tl.nrows; q += 8)
+    for (int k = 0; k < 2; ++k) {
+      std::vector<int> g;
+      for (int r = q; r < std::min(q + 8, tl.nrows); ++r) {
+        const Row4& rw = t.rows[tl.row0 + r];
+        const int u = k ? rw.u2 : rw.u1;
+        if (std::find(g.begin(), g.end(), u) == g.end()) g.push_back(u);
+      }
+      for (int u : g) member[u].push_back((int)groups.size());
+      groups.push_back(std::move(g));
+    }
+  std::vector<int> base(nl);
+  for (int i = 0; i < nl; ++i) base[i] = i;
+  std::stable_sort(base.begin(), base.end(), [&](int a, int b) { return member[a].size() > member[b].size(); });
+  std::vector<int> best_col;
+  long long best_cost = LLONG_MAX;
+  uint32_t rng = 12345u;
+  for (int trial = 0; trial < 16; ++trial) {
+    std::vector<int> col(nl, -1), left(8, cap), tie(nl);
+    for (int i = 0; i < nl; ++i) {
+      rng = rng * 1664525u + 1013904223u;
+      tie[i] = (int)(rng >> 8);
+    }
+    for (int u : base) {
+      int score[8] = {0};
+      for (int gi : member[u])
+        for (int o : groups[gi])
+          if (col[o] >= 0) ++score[col[o]];
+      int pick = -1;
+      for (int c = 0; c < 8; ++c) {
+        const int cc = (c + tie[u]) & 7;  // rotate the tie-break per single and trial
+        if (!left[cc]) continue;
+        if (pick < 0 || score[cc] < score[pick]) pick = cc;
+      }
+      if (pick < 0)
+        for (int c = 0; c < 8; ++c)
+          if (left[c]) { pick = c; break; }
+      col[u] = pick;
+      --left[pick];
+    }
+    long long cost = 0;
+    for (const auto& g : groups) {
+      int cnt[8] = {0}, mx = 0;
+      for (int u : g) mx = std::max(mx, ++cnt[col[u]]);
+      cost += mx;
+    }
+    if (cost < best_cost) {
+      best_cost = cost;
+      best_col = col;
+    }
+  }
+  std::vector<int> slot(nl), used(8, 0);
+  int nslot = 0;
+  for (int u = 0; u < nl; ++u) {
+    slot[u] = best_col[u] + 8 * used[best_col[u]]++;
+    nslot = std::max(nslot, slot[u] + 1);
+  }
+  if (nslot > kTcMaxRowSlots) return fail(ctx, SBG_ERR_INTERNAL, "4PCF tiling: slot colouring overflow");
+  for (int r = tl.row0; r < tl.row0 + tl.nrows; ++r) {
+    t.rows[r].u1 = slot[t.rows[r].u1];
+    t.rows[r].u2 = slot[t.rows[r].u2];
+  }
+  std::vector<int> slots(nslot, -1);
+  for (int u = 0; u < nl; ++u) slots[slot[u]] = store[u];
+  tl.nuniq = nslot;
+  for (int v : slots) t.uniq.push_back(v);
+  return SBG_OK;
+}
+
 // Build the pair x single contraction tables of the 4PCF and the coupling CSR.
 // T[s1, s2, s3] = sum_x delta a_s1 a_s2 a_s3 is symmetric under permutations of
 // its singles s = (l, m, b) and T[-M] = conj T[M] (real delta), so the computed
@@ -294,8 +386,17 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
           for (int bb = b1; bb < nb; ++bb) {
             if (half(b1) != half(bb)) continue;
             for (int a1 = 0; a1 < na; ++a1)
-              for (int a2 = (bb == b1 ? a1 : 0); a2 < na; ++a2)
-                if (angs[a1].m + angs[a2].m == -m3) bk.rows.push_back({a1, b1, a2, bb});
+              for (int a2 = (bb == b1 ? a1 : 0); a2 < na; ++a2) {
+                if (angs[a1].m + angs[a2].m != -m3) continue;
+                if (m3 == 0) {
+                  // the row with every m negated gives conj of this row's entries:
+                  // keep one of the two (the lookup finds it through M -> -M)
+                  int f1 = ang_index(angs[a1].l, -angs[a1].m), f2 = ang_index(angs[a2].l, -angs[a2].m);
+                  if (bb == b1 && f2 < f1) std::swap(f1, f2);
+                  if (f1 < a1 || (f1 == a1 && f2 < a2)) continue;
+                }
+                bk.rows.push_back({a1, b1, a2, bb});
+              }
           }
       }
       bk.ncols = (nb - bk.bcol0) * (int)bk.l3s.size();
@@ -358,20 +459,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
         if (nr == 0) return fail(ctx, SBG_ERR_INTERNAL, "4PCF tiling: a row needs more staged singles than allowed");
         tl.nrows = nr;
         tl.nuniq = (int)local.size();
-        if (tc) {
-          // slots sorted by store index so that consecutive singles form one copy
-          std::vector<int> order;
-          for (auto& kv : local) order.push_back(kv.first);  // std::map iterates in key order
-          std::map<int, int> pos;
-          for (int k = 0; k < (int)order.size(); ++k) pos[order[k]] = k;
-          std::vector<int> remap(local.size());
-          for (auto& kv : local) remap[kv.second] = pos[kv.first];
-          for (int k = tl.row0; k < tl.row0 + nr; ++k) {
-            t.rows[k].u1 = remap[t.rows[k].u1];
-            t.rows[k].u2 = remap[t.rows[k].u2];
-          }
-          for (int v : order) t.uniq.push_back(v);
-        }
+        if (tc) ST(colour_slots(ctx, t, tl, local));
         tl.tout = so;
         bk.slabs.push_back({rstart, nr, c0, nc, so, tl.row0});
         so += (long long)nr * nc;
@@ -576,6 +664,20 @@ sbg_status check_edges(sbg_context* ctx, const double* edges, int nb, int n) {
   return SBG_OK;
 }
 
+// Pinned host staging of at least `bytes` bytes (grown, never shrunk).
+sbg_status host_staging(sbg_context* ctx, size_t bytes, void** out) {
+  if (bytes > ctx->hpin_bytes) {
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (ctx->hpin) cudaFreeHost(ctx->hpin);
+    ctx->hpin = nullptr;
+    ctx->hpin_bytes = 0;
+    CU(cudaMallocHost(&ctx->hpin, bytes));
+    ctx->hpin_bytes = bytes;
+  }
+  *out = ctx->hpin;
+  return SBG_OK;
+}
+
 sbg_status finish_timings(sbg_context* ctx) {
   CU(cudaStreamSynchronize(ctx->stream));
   ctx->last_launches = ctx->nlaunch;
@@ -586,6 +688,15 @@ sbg_status finish_timings(sbg_context* ctx) {
       ms = 0.f;
     }
     ctx->timings[i] = ms;
+  }
+  ctx->contraction_ms = 0.0;
+  if (ctx->kev_used) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->kev[0], ctx->kev[1]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = 0.f;
+    }
+    ctx->contraction_ms = ms;
   }
   return SBG_OK;
 }
@@ -608,6 +719,7 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
       if (vb[b] == 0.0) return fail(ctx, SBG_ERR_EMPTY_BIN, "bin " + std::to_string(b) + " holds no cell");
 
   for (int i = 0; i <= kStages; ++i) rec(ctx, i);  // reset
+  ctx->kev_used = false;
   ctx->nlaunch = 0;
   rec(ctx, 0);
   // ---- inputs ----
@@ -762,13 +874,18 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
       ctx->nlaunch += 1;  // bsplit_kernel
       KL(launch_tc4(d_astore, d_bstore, d_delta, ng, (const Tile4*)t.d_tiles[0].p, ntl, (const Row4*)t.d_rows.p,
                     (const int*)t.d_cols.p, (const int*)t.d_uniq.p, nsingle, cplx, best, d_T, d_cnt, d_err,
-                    ctx->nsm, ctx->stream));
-      int herr = 0;
-      CU(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+                    ctx->nsm, ctx->stream, ctx->kev[0], ctx->kev[1]));
+      ctx->kev_used = true;
+      int* perr;
+      ST(host_staging(ctx, 64, (void**)&perr));
+      CU(cudaMemcpyAsync(perr, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
       CU(cudaStreamSynchronize(ctx->stream));
+      const int herr = *perr;
       if (herr) return fail(ctx, SBG_ERR_TIMEOUT, "tensor-core 4PCF kernel gave up waiting (code " + std::to_string(herr) + ")");
     } else {
       const int tcg[3] = {4, 8, 16};
+      CU(cudaEventRecord(ctx->kev[0], ctx->stream));
+      ctx->kev_used = true;
       for (int k = 0; k < 3; ++k) {
         const int ntl = (int)t.tiles[k].size();
         if (!ntl) continue;
@@ -777,6 +894,7 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
                         (const int*)t.d_cols.p, (const int*)t.d_uniq.p, cplx, tcg[k], nsplit, nsingle, d_T,
                         ctx->stream));
       }
+      CU(cudaEventRecord(ctx->kev[1], ctx->stream));
     }
     ST(buf(ctx, "z4", (size_t)t.nout * 8 * (cplx ? 2 : 1), (void**)&d_z4));
     KL(launch_couple(d_T, cplx, (const int*)t.d_ptr.p, (const int*)t.d_idx.p, (const double*)t.d_coef.p, t.nout, d_z4,
@@ -788,21 +906,26 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
   }
   rec(ctx, 6);
   // ---- 3PCF finish + downloads ----
+  const int ncomp3 = dim == 3 ? 1 : 2;
+  const size_t z3bytes = do3 ? (size_t)(lmax3 + 1) * nb * nb * 8 * ncomp3 : 0;
+  const size_t z4bytes = do4 ? (size_t)ctx->t4->nout * 8 * (dim == 2 ? 2 : 1) : 0;
+  const size_t z3off = 0, z4off = (z3bytes + 255) / 256 * 256;
+  unsigned char* hst;
+  ST(host_staging(ctx, z4off + z4bytes + 64, (void**)&hst));
   if (do3) {
     double* d_z3;
-    const int nl = dim == 3 ? lmax3 + 1 : lmax3 + 1;
-    const int ncomp = dim == 3 ? 1 : 2;
-    ST(buf(ctx, "z3", (size_t)nl * nb * nb * 8 * ncomp, (void**)&d_z3));
+    const int nl = lmax3 + 1;
+    ST(buf(ctx, "z3", z3bytes, (void**)&d_z3));
     KL(launch_finish3(d_S, dim == 3, lmax3, nb, d_z3, ctx->stream));
-    if (flags & SBG_NORMALIZED) KL(launch_normalize(d_z3, nl, nb, 3, ncomp, d_acc, (double)ng, d_vb, ctx->stream));
-    CU(cudaMemcpyAsync(zeta3, d_z3, (size_t)nl * nb * nb * 8 * ncomp, cudaMemcpyDeviceToHost, ctx->stream));
+    if (flags & SBG_NORMALIZED) KL(launch_normalize(d_z3, nl, nb, 3, ncomp3, d_acc, (double)ng, d_vb, ctx->stream));
+    CU(cudaMemcpyAsync(hst + z3off, d_z3, z3bytes, cudaMemcpyDeviceToHost, ctx->stream));
   }
-  if (do4) {
-    const int cplx = dim == 2 ? 1 : 0;
-    CU(cudaMemcpyAsync(zeta4, d_z4, (size_t)ctx->t4->nout * 8 * (cplx ? 2 : 1), cudaMemcpyDeviceToHost, ctx->stream));
-  }
+  if (do4) CU(cudaMemcpyAsync(hst + z4off, d_z4, z4bytes, cudaMemcpyDeviceToHost, ctx->stream));
   rec(ctx, 7);
-  return finish_timings(ctx);
+  ST(finish_timings(ctx));
+  if (do3) std::memcpy(zeta3, hst + z3off, z3bytes);
+  if (do4) std::memcpy(zeta4, hst + z4off, z4bytes);
+  return SBG_OK;
 }
 
 }  // namespace
@@ -835,6 +958,12 @@ sbg_status sbg_create(int cuda_device, size_t hbm_budget_bytes, sbg_context** ou
       return SBG_ERR_CUDA;
     }
   }
+  for (int i = 0; i < 2; ++i) {
+    if (cudaEventCreate(&ctx->kev[i]) != cudaSuccess) {
+      sbg_destroy(ctx);
+      return SBG_ERR_CUDA;
+    }
+  }
   *out = ctx;
   return SBG_OK;
 }
@@ -846,8 +975,11 @@ void sbg_destroy(sbg_context* ctx) {
   for (auto& kv : ctx->bufs) dev_free(ctx, kv.second);
   dev_free(ctx, ctx->gcache);
   free_tables4(ctx, ctx->t4);
+  if (ctx->hpin) cudaFreeHost(ctx->hpin);
   for (int i = 0; i <= kStages; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  for (int i = 0; i < 2; ++i)
+    if (ctx->kev[i]) cudaEventDestroy(ctx->kev[i]);
   if (ctx->own) cudaStreamDestroy(ctx->own);
   delete ctx;
 }
@@ -971,6 +1103,12 @@ sbg_status sbg_last_timings(const sbg_context* ctx, double* ms_per_stage, int* n
   for (int i = 0; i < kStages; ++i) ms_per_stage[i] = ctx->timings[i];
   ms_per_stage[kStages] = (double)ctx->last_launches;
   *n_stages = kStages + 1;
+  return SBG_OK;
+}
+
+sbg_status sbg_last_contraction_ms(const sbg_context* ctx, double* ms) {
+  if (!ctx || !ms) return SBG_ERR_INVALID_ARG;
+  *ms = ctx->contraction_ms;
   return SBG_OK;
 }
 

@@ -58,7 +58,7 @@ constexpr int kTcEpoch = 256;       // K-blocks between progress checkpoints of 
 cudaError_t launch_tc4(const float2* astore, const void* bstore, const float* delta, long long ng,
                        const Tile4* tiles, int ntiles, const Row4* rows, const int* cols, const int* slots,
                        int nsingle, int complex_out, int nsplit, double* T, int* cnt, int* err, int nsm,
-                       cudaStream_t st);
+                       cudaStream_t st, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 
 // ---- finalisation ----
 // zeta[o] = sum_{e in [ptr[o], ptr[o+1])} coef[e] * T[idx[e]] (idx < 0: conj of T[-idx-1]).

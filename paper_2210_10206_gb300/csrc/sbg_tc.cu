@@ -49,7 +49,6 @@ constexpr int kOS = kGroups;           // operand stages (A in TMEM, B in shared
 constexpr int kFlush = 64;             // K-blocks per inner accumulation range
 constexpr int kKX = 32;                // grid points per K-block (64 bf16 = one 128-B row)
 constexpr int kProdWarps = 16;         // producer warps 0..15
-constexpr int kProd = kProdWarps * 32;
 constexpr int kMmaWarp = kProdWarps;   // warp 16
 constexpr int kLoadWarps = 3;          // warps 17..19
 constexpr int kLoad0 = kMmaWarp + 1;
@@ -83,10 +82,6 @@ __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
-               : "memory");
-}
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -119,25 +114,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
   }
 }
 
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(dst)),
-      "l"(src), "r"(bytes), "r"(su32(bar))
-      : "memory");
-}
-
 __device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
   uint32_t r;
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
   return r;
 }
-// split (re, im) into bf16x2 hi and lo words (re in the low half)
-__device__ __forceinline__ void split2(float re, float im, uint32_t& hi, uint32_t& lo) {
-  hi = bf16x2_rn(re, im);
-  const float hr = __uint_as_float(hi << 16), hi_ = __uint_as_float(hi & 0xffff0000u);
-  lo = bf16x2_rn(re - hr, im - hi_);
-}
-
 // packed f32x2 arithmetic (two FP32 lanes per instruction)
 __device__ __forceinline__ uint64_t pk(float a, float b) {
   uint64_t r;
@@ -173,15 +154,6 @@ __device__ __forceinline__ void split_pair(uint64_t v, uint32_t& hi, uint32_t& l
   lo = bf16x2_rn(l0, l1);
 }
 
-// Row (A) or column (B) handled by producer thread group g in pass k: each warp's
-// four rows are two with (row & 7) < 4 and two with (row & 7) >= 4, so that the
-// real-part chunks of a 128-byte swizzled row land in disjoint bank halves.
-__device__ __forceinline__ int pass_row(int g, int k) {
-  const int perm = (k & 1) ? ((g & 3) == 0 ? 2 : (g & 3) == 1 ? 6 : (g & 3) == 2 ? 3 : 7)
-                           : ((g & 3) == 0 ? 0 : (g & 3) == 1 ? 4 : (g & 3) == 2 ? 1 : 5);
-  return ((g >> 2) + 8 * (k >> 1)) * 8 + perm;
-}
-
 __device__ __forceinline__ uint32_t swz(int row, int chunk) {
   return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
 }
@@ -192,13 +164,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
 // D += A B with A (128 x 16 bf16) in tensor memory, B in shared memory
 __device__ __forceinline__ void mma_bf16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc,
                                             uint32_t acc) {
@@ -220,22 +185,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
-  uint32_t r[4];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_st4(uint32_t taddr, const float (&v)[4]) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
-               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-               "r"(__float_as_uint(v[3]))
-               : "memory");
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   uint32_t r[8];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
@@ -471,7 +420,8 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
       const int N = n_mma(tl, cplx);
       const int nranges = (it.nk + kFlush - 1) / kFlush;
       const bool aval = row < tl.nrows;
-      const Row4 rw = aval ? rows[tl.row0 + row] : Row4{0, 0, 0, 1.f};
+      // a padding row repeats row 0: its accumulator row is never read out
+      const Row4 rw = rows[tl.row0 + (aval ? row : 0)];
       const float s1 = (rw.flags & 1) ? -1.f : 1.f, s2 = (rw.flags & 2) ? -1.f : 1.f;
       const uint64_t as1 = pk(s1, s1), as2 = pk(s2, s2), ans2 = pk(-s2, -s2);
       const int x1 = rw.u1 & 7, x2 = rw.u2 & 7;  // raw-stage chunk swizzle of the two singles
@@ -583,7 +533,6 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
             const uint64_t pi = fma2(ar, bi, mul2(ai, br));    // ar bi + ai br
             split_pair(pr, hr[p2], lr[p2]);
             split_pair(pi, hi[p2], li[p2]);
-            if (!aval) hr[p2] = lr[p2] = hi[p2] = li[p2] = 0u;
           }
           tmem_st4_nw(acol + 4 * cq, hr[0], hr[1], hr[2], hr[3]);        // hi, real parts
           tmem_st4_nw(acol + 16 + 4 * cq, hi[0], hi[1], hi[2], hi[3]);   // hi, imaginary parts
@@ -651,7 +600,7 @@ __global__ void bsplit_kernel(const float* __restrict__ astore, const float* __r
 cudaError_t launch_tc4(const float2* astore, const void* bstore, const float* delta, long long ng,
                        const Tile4* tiles, int ntiles, const Row4* rows, const int* cols, const int* slots,
                        int nsingle, int complex_out, int nsplit, double* T, int* cnt, int* err, int nsm,
-                       cudaStream_t st) {
+                       cudaStream_t st, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   if (ntiles <= 0) return cudaSuccess;
   if (ng % kKX) return cudaErrorInvalidValue;
   // B operand of every single, once per field
@@ -680,8 +629,10 @@ cudaError_t launch_tc4(const float2* astore, const void* bstore, const float* de
   void* args[] = {(void*)&af,    (void*)&bs,     (void*)&ng,    (void*)&tiles, (void*)&ntiles,
                   (void*)&rows,  (void*)&cols,   (void*)&slots, (void*)&nsingle, (void*)&complex_out,
                   (void*)&nsplit, (void*)&T,     (void*)&cnt,   (void*)&err};
+  if (ev_begin && (e = cudaEventRecord(ev_begin, st)) != cudaSuccess) return e;
   e = cudaLaunchCooperativeKernel((const void*)tc4_kernel, dim3(grid), dim3(kThreads), args, kSmem, st);
   if (e != cudaSuccess) return e;
+  if (ev_end && (e = cudaEventRecord(ev_end, st)) != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

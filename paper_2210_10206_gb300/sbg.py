@@ -67,6 +67,8 @@ def lib():
         L.sbg_projected_batch.restype = st
         L.sbg_last_timings.argtypes = [vp, vp, ctypes.POINTER(i)]
         L.sbg_last_timings.restype = st
+        L.sbg_last_contraction_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.sbg_last_contraction_ms.restype = st
         L.sbg_projected3_noalloc.argtypes = [vp, i, ctypes.c_int64, vp, i, i, ctypes.c_uint, vp, vp]
         L.sbg_projected3_noalloc.restype = st
         _lib = L
@@ -209,6 +211,12 @@ def sbg_last_timings(h):
     n = ctypes.c_int()
     lib().sbg_last_timings(h, out.ctypes.data, ctypes.byref(n))
     return out[: n.value]
+
+
+def sbg_last_contraction_ms(h):
+    out = ctypes.c_double()
+    lib().sbg_last_contraction_ms(h, ctypes.byref(out))
+    return out.value
 
 
 def sbg_projected3_noalloc(field, edges, mmax, flags, zeta3, stream=0):
