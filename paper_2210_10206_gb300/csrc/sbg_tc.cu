@@ -6,8 +6,8 @@
 // contraction).  As a real GEMM over K = 64 per 32-point K-block:
 // A[r] = (Re P(x0..x31), Im P(x0..x31)), B[c] = (Re(delta a), -Im(delta a)); 2D adds
 // the column (Im(delta a), Re(delta a)) for Im.  Each operand is split into
-// bf16 hi + lo and D += Ahi Bhi + Ahi Blo + Alo Bhi (three MMAs into one TMEM
-// accumulator).  The row signs (-1)^m of a_{l,-m} are applied in the FP64
+// bf16 hi + lo and D += Ahi Bhi + Ahi Blo + Alo Bhi (three products summed in
+// TMEM).  The row signs (-1)^m of a_{l,-m} are applied in the FP64
 // coupling step, not here.
 //
 // B depends only on the column single and the K-block, so bsplit_kernel writes
@@ -23,12 +23,15 @@
 //              into a 128-byte-swizzled K-major tile in shared memory and writes the
 //              bf16 hi/lo A tile (formed with packed f32x2 arithmetic, one row
 //              per TMEM lane) straight into tensor memory.  Group 0 also folds
-//              each 64-K-block range's TMEM accumulator (two, alternating) into
-//              the outer TMEM accumulator and, at the end of a unit, adds it to
-//              T in FP64;
-//   warp 16    MMA issuer: one thread issues 12 tcgen05.mma (M=128, K=16) per
-//              K-block and commits to the mbarriers that free the operand stage
-//              and publish the accumulator.
+//              each 64-K-block range's TMEM accumulator into the outer TMEM
+//              accumulator (before it forms the first K-block of the next
+//              range, which reuses the inner one) and, at the end of a unit,
+//              adds it to T in FP64;
+//   warp 16    MMA issuer: one thread issues 8 tcgen05.mma (M=128, K=16) per
+//              K-block, Ahi [Bhi | Blo] (N = 2n) and Alo Bhi (N = n) per K step
+//              (the cost of an MMA hardly grows with N up to 128, so fewer,
+//              wider MMAs are faster), and commits to the mbarriers that free
+//              the operand stage and publish the accumulator.
 // Work units (tile, x-split) are dealt round-robin to a cooperative grid of one
 // CTA per SM; the loaders of all CTAs advance through x together (a CTA may run
 // at most four 256-K-block epochs ahead of the slowest), so that the singles of
@@ -54,11 +57,11 @@ constexpr int kLoadWarps = 3;          // warps 17..19
 constexpr int kLoad0 = kMmaWarp + 1;
 constexpr int kLoaders = kLoadWarps * 32;
 constexpr int kThreads = (kProdWarps + 1 + kLoadWarps) * 32;
-constexpr int kBTile = 64 * 128;       // bytes of one <=64-row bf16 K-block tile
-constexpr int kOpStage = 2 * kBTile;   // B hi and lo
-// TMEM columns: two inner accumulators [0, 64) and [64, 128) (alternate
-// 64-K-block ranges), the outer accumulator [128, 192), then one 64-column A
-// stage per operand stage (32 columns hi, 32 lo: 64 bf16 each)
+constexpr int kOpStage = 128 * 128;   // B tile: n hi rows, then n lo rows (n <= 64), 128 B each
+// TMEM columns: the inner accumulator [0, 128) of the current 64-K-block range
+// (columns [0, n) collect Ahi Bhi + Alo Bhi, [n, 2n) Ahi Blo), the outer
+// accumulator [128, 192), then one 64-column A stage per operand stage
+// (32 columns hi, 32 lo: 64 bf16 each)
 constexpr int kTmemOuter = 128;
 constexpr int kTmemA0 = 192;
 constexpr int kTmemCols = 512;
@@ -82,34 +85,32 @@ __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
+// Test the phase; if it is not complete the thread may sleep until it
+// completes or kSuspendNs pass (the hardware wakes it on completion), so a
+// waiting warp takes no issue slots from the warps doing the work.
+constexpr uint32_t kSuspendNs = 100000;
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(su32(b)), "r"(parity)
+      : "r"(su32(b)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
-// Bounded wait; false if this or another thread of the grid gave up.  The
-// clock and the grid's error word (an L2 round trip) are consulted only every
-// 256 polls so that a wait that succeeds soon costs no more than the polls.
+// Bounded wait; false if this or another thread of the grid gave up (after
+// 1 s of %globaltimer, or when the grid's error word is set).
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* err, int code) {
   if (mbar_try(b, parity)) return true;
-  unsigned long long t0 = 0;
-  for (uint32_t it = 1;; ++it) {
+  const unsigned long long t0 = gtime();
+  for (;;) {
     if (mbar_try(b, parity)) return true;
-    if ((it & 255u) == 0) {
-      const unsigned long long now = gtime();
-      if (t0 == 0) {
-        t0 = now;
-      } else if (now - t0 > kWaitNs) {
-        atomicCAS((int*)err, 0, code);
-        return false;
-      }
-      if (*err) return false;
+    if (*err) return false;
+    if (gtime() - t0 > kWaitNs) {
+      atomicCAS((int*)err, 0, code);
+      return false;
     }
   }
 }
@@ -274,8 +275,8 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
   uint64_t* raw_empty = bars + kRS;
   uint64_t* op_full = bars + 2 * kRS;
   uint64_t* op_empty = bars + 2 * kRS + kOS;
-  uint64_t* acc_full = bars + 2 * kRS + 2 * kOS;  // [2], one per inner accumulator
-  uint32_t* tmem_slot = (uint32_t*)(acc_full + 2);
+  uint64_t* acc_full = bars + 2 * kRS + 2 * kOS;  // a range's MMAs are complete
+  uint32_t* tmem_slot = (uint32_t*)(acc_full + 1);
   volatile int* err = err_flag;
 
   const int tid = threadIdx.x;
@@ -295,8 +296,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
       mbar_init(&op_full[i], kProdWarps / kGroups);
       mbar_init(&op_empty[i], 1);                     // tcgen05.commit
     }
-    mbar_init(&acc_full[0], 1);
-    mbar_init(&acc_full[1], 1);
+    mbar_init(acc_full, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == kMmaWarp) {
@@ -307,7 +307,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tmem_slot;  // inner accumulator at column 0, outer at column 64
+  const uint32_t tmem = *tmem_slot;  // base of the 512 allocated columns
 
   if (warp >= kLoad0) {
     // ------------------------------------------------------------ loaders --
@@ -370,14 +370,16 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
     // ---------------------------------------------------------------- MMA --
     if (lane == 0) {
       uint32_t uses[kOS] = {0, 0, 0, 0};
-      uint32_t R = 0;  // ranges issued so far (selects the inner accumulator)
       bool ok = true;
       for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
         const Unit it = unit_of(u, ntiles, nsplit, ng);
         const Tile4 tl = tiles[it.tile];
         const int N = n_mma(tl, cplx);
+        // BF16 inputs, FP32 accumulator, K-major A and B, M = 128; N = n for
+        // Alo Bhi and N = 2n for Ahi [Bhi | Blo]
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
+        const uint32_t idesc2 = (idesc & ~(0x3Fu << 17)) | ((uint32_t)((2 * N) >> 3) << 17);
         for (int kb = 0; kb < it.nk; ++kb) {
           const int os = kb % kOS;
           if (!mbar_wait(&op_full[os], uses[os]++ & 1, err, 21)) {
@@ -385,22 +387,18 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
             break;
           }
           tc_fence_after();
-          const uint32_t b_hi = su32(op_base + os * kOpStage), b_lo = b_hi + kBTile;
+          const uint32_t b = su32(op_base + os * kOpStage);
           const uint32_t a_hi = tmem + kTmemA0 + 64 * os, a_lo = a_hi + 32;
-          const uint32_t dacc = tmem + 64 * ((R + kb / kFlush) & 1);
           const bool first = (kb % kFlush) == 0;
+          // two MMAs per 16-wide K step: Ahi meets Bhi and Blo in one (N = 2n)
 #pragma unroll
-          for (int p = 0; p < 3; ++p) {
-            const uint32_t a = p == 2 ? a_lo : a_hi;
-            const uint32_t b = p == 1 ? b_lo : b_hi;
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-              mma_bf16_ts(dacc, a + 8 * k, sdesc(b + 32 * k), idesc, (first && p == 0 && k == 0) ? 0u : 1u);
+          for (int k = 0; k < 4; ++k) {
+            mma_bf16_ts(tmem, a_hi + 8 * k, sdesc(b + 32 * k), idesc2, (first && k == 0) ? 0u : 1u);
+            mma_bf16_ts(tmem, a_lo + 8 * k, sdesc(b + 32 * k), idesc, 1u);
           }
           mma_commit(&op_empty[os]);
-          if ((kb + 1) % kFlush == 0 || kb + 1 == it.nk) mma_commit(&acc_full[(R + kb / kFlush) & 1]);
+          if ((kb + 1) % kFlush == 0 || kb + 1 == it.nk) mma_commit(acc_full);
         }
-        R += (it.nk + kFlush - 1) / kFlush;
       }
     }
   } else {
@@ -447,14 +445,17 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
       // fold range i of this unit: inner accumulator -> outer (or -> T for the last range)
       auto fold = [&](int i) -> bool {
         const uint32_t Rg = R + i;
-        if (!warp_wait(&acc_full[Rg & 1], (Rg >> 1) & 1, err, 33)) return false;
+        if (!warp_wait(acc_full, Rg & 1, err, 33)) return false;
         tc_fence_after();
         const bool last = i + 1 == nranges;
-        const uint32_t inner = tmem + lane_addr + 64 * (Rg & 1);
+        const uint32_t inner = tmem + lane_addr;
         const uint32_t outer = tmem + lane_addr + kTmemOuter;
         for (int c0 = 0; c0 < N; c0 += 8) {
-          float in[8], out[8];
+          float in[8], lo[8], out[8];
           tmem_ld8(inner + c0, in);
+          tmem_ld8(inner + N + c0, lo);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) in[e] += lo[e];
           if (i == 0) {
 #pragma unroll
             for (int e = 0; e < 8; ++e) out[e] = in[e];
@@ -481,15 +482,17 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
         tc_fence_before();
         return true;
       };
+      // B tile destination of this thread's 16-byte chunk of row gtid >> 4 (+ 8 k)
+      uint8_t* const bdst = op_base + os * kOpStage + swz(gtid >> 4, gtid & 7) + ((gtid >> 3) & 1) * N * 128;
       for (int kb = grp; kb < it.nk && ok; kb += kGroups) {
-        // group 0 produces the first K-block of every range: fold range i - 2 first, whose
-        // inner accumulator that range reuses
-        if (grp == 0 && kb % kFlush == 0 && kb / kFlush >= 2) {
-          if (!fold(kb / kFlush - 2)) {
+        // group 0 produces the first K-block of every range: fold the previous
+        // range first, whose inner accumulator this range overwrites
+        if (grp == 0 && kb % kFlush == 0 && kb / kFlush >= 1) {
+          if (!fold(kb / kFlush - 1)) {
             ok = false;
             break;
           }
-          flushed = kb / kFlush - 1;
+          flushed = kb / kFlush;
         }
         const int rs = 2 * grp + (uses & 1);
         if (!warp_wait(&raw_full[rs], (uses >> 1) & 1, err, 31) || !warp_wait(&op_empty[os], (uses & 1) ^ 1, err, 32)) {
@@ -500,15 +503,11 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
         tc_fence_after();
         const uint8_t* raw = raw_base + rs * kRawStage;
         const float4* U4 = (const float4*)raw;
-        uint8_t* op = op_base + os * kOpStage;
         // ---- B: store the prefetched rows into the swizzled operand tile, prefetch the next ----
-        {
-          const int pc = gtid & 15, j = pc & 7, hl = pc >> 3;
 #pragma unroll
-          for (int k = 0; k < 8; ++k)
-            if (bsi[k] != -1) *(uint4*)(op + hl * kBTile + swz((gtid >> 4) + 8 * k, j)) = vb[k];
-          if (kb + kGroups < it.nk) load_b(kb + kGroups);
-        }
+        for (int k = 0; k < 8; ++k)
+          if (bsi[k] != -1) *(uint4*)(bdst + 1024 * k) = vb[k];
+        if (kb + kGroups < it.nk) load_b(kb + kGroups);
         // ---- A: the 32 pair products of this thread's row, to TMEM ----
         const uint32_t acol = tmem + lane_addr + kTmemA0 + 64 * os;
 #pragma unroll 1
