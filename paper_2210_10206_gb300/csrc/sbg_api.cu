@@ -233,9 +233,9 @@ int store_index(int dim, int nb, int l, int m_abs, int b) {
 // Shared-memory slots of the staged row singles of one tensor-core tile.  A
 // quarter-warp of producer threads (8 consecutive rows) reads the same 16-byte
 // chunk of the first single of each of its rows, then of the second; the raw
-// stage stores chunk k of slot s at chunk k ^ (s & 7) of its 256-byte row, so
-// two distinct singles read together collide in a bank only when their slots
-// agree mod 8 (their colour).  Colours are chosen greedily, singles shared by
+// stage pads each slot's 256-byte row to 272 bytes, so chunk k of slot s lies in
+// bank quad (s + k) mod 8 and two distinct singles read together collide in a
+// bank only when their slots agree mod 8 (their colour).  Colours are chosen greedily, singles shared by
 // the most quarter-warp groups first, best of a few tie-breaking orders; colour
 // c owns slots c, c + 8, ...  Unused slots hold -1 (not loaded).
 sbg_status colour_slots(sbg_context* ctx, Tables4& t, Tile4& tl, const std::map<int, int>& local) {

@@ -65,7 +65,11 @@ constexpr int kOpStage = 128 * 128;   // B tile: n hi rows, then n lo rows (n <=
 constexpr int kTmemOuter = 128;
 constexpr int kTmemA0 = 192;
 constexpr int kTmemCols = 512;
-constexpr int kRawStage = kTcMaxRowSlots * kKX * 8;  // FP32 (re, im) row singles
+// FP32 (re, im) row singles, 256 bytes each, padded to 272 bytes: chunk k of
+// slot s then falls in bank quad (s + k) mod 8, so the eight rows a
+// quarter-warp reads at once are conflict-free when their slots differ mod 8
+constexpr int kRawRow = kKX * 8 + 16;
+constexpr int kRawStage = kTcMaxRowSlots * kRawRow;
 constexpr int kLag = 4;                // epochs a loader may run ahead of the slowest CTA
 constexpr int kMeta = 256;             // barriers and the TMEM address
 constexpr int kSmem = kOS * kOpStage + kRS * kRawStage + kMeta + 1024;
@@ -357,7 +361,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
           for (int k = 0; k < kSlotIter; ++k) {
             const int sl = rq + kSlotStep * k;
             if (asi[k] >= 0)
-              cp_async16(st + sl * 256 + ((ck ^ (sl & 7)) << 4), astore + (xb * nsingle + asi[k]) * 64 + ck * 4, 16);
+              cp_async16(st + sl * kRawRow + ck * 16, astore + (xb * nsingle + asi[k]) * 64 + ck * 4, 16);
           }
           cp_async_arrive(&raw_full[rs]);
         }
@@ -422,23 +426,27 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
       const Row4 rw = rows[tl.row0 + (aval ? row : 0)];
       const float s1 = (rw.flags & 1) ? -1.f : 1.f, s2 = (rw.flags & 2) ? -1.f : 1.f;
       const uint64_t as1 = pk(s1, s1), as2 = pk(s2, s2), ans2 = pk(-s2, -s2);
-      const int x1 = rw.u1 & 7, x2 = rw.u2 & 7;  // raw-stage chunk swizzle of the two singles
-      // B rows this thread moves: row c = (gtid >> 4) + 8k, 16-byte chunk gtid & 15
-      int bsi[8];
+      const int r1 = rw.u1 * kRawRow, r2 = rw.u2 * kRawRow;  // the two singles in a raw stage
+      // B rows this thread moves: row c = (gtid >> 4) + 8k (stored when c < n),
+      // 16-byte chunk gtid & 15; bof = byte offset of that chunk in a K-block's
+      // slab of the B store, or -1 for a zero row (c beyond the tile's columns)
+      int bof[8];
+      unsigned bst = 0;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int c = (gtid >> 4) + 8 * k;
         const int cs = cplx ? (c >> 1) : c;
-        bsi[k] = (c < N && cs < tl.ncols) ? cols[tl.col0 + cs] * bparts + (cplx ? (c & 1) : 0)
-                                          : (c < N ? -2 : -1);
+        bof[k] = (c < N && cs < tl.ncols) ? (cols[tl.col0 + cs] * bparts + (cplx ? (c & 1) : 0)) * 256 + (gtid & 15) * 16
+                                          : -1;
+        if (c < N) bst |= 1u << k;
       }
       uint4 vb[8];
+      const long long bslab = (long long)nsingle * bparts * 256;  // bytes per K-block
       auto load_b = [&](int kbb) {
-        const long long xb = (it.x0 >> 5) + kbb;
+        const uint8_t* bx = bstore + ((it.x0 >> 5) + kbb) * bslab;
 #pragma unroll
         for (int k = 0; k < 8; ++k)
-          vb[k] = bsi[k] >= 0 ? __ldg((const uint4*)(bstore + (xb * nsingle * bparts + bsi[k]) * 256) + (gtid & 15))
-                              : make_uint4(0, 0, 0, 0);
+          vb[k] = bof[k] >= 0 ? __ldg((const uint4*)(bx + bof[k])) : make_uint4(0, 0, 0, 0);
       };
       if (grp < it.nk) load_b(grp);
       int flushed = 0;                              // ranges of this unit already folded (group 0)
@@ -502,20 +510,19 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
         ++uses;
         tc_fence_after();
         const uint8_t* raw = raw_base + rs * kRawStage;
-        const float4* U4 = (const float4*)raw;
         // ---- B: store the prefetched rows into the swizzled operand tile, prefetch the next ----
 #pragma unroll
         for (int k = 0; k < 8; ++k)
-          if (bsi[k] != -1) *(uint4*)(bdst + 1024 * k) = vb[k];
+          if (bst & (1u << k)) *(uint4*)(bdst + 1024 * k) = vb[k];
         if (kb + kGroups < it.nk) load_b(kb + kGroups);
         // ---- A: the 32 pair products of this thread's row, to TMEM ----
         const uint32_t acol = tmem + lane_addr + kTmemA0 + 64 * os;
 #pragma unroll 1
         for (int cq = 0; cq < 4; ++cq) {  // points 8 cq .. 8 cq + 7
-          const float4 ra0 = U4[rw.u1 * 16 + ((2 * cq) ^ x1)], ra1 = U4[rw.u1 * 16 + ((2 * cq + 1) ^ x1)];
-          const float4 ia0 = U4[rw.u1 * 16 + 8 + ((2 * cq) ^ x1)], ia1 = U4[rw.u1 * 16 + 8 + ((2 * cq + 1) ^ x1)];
-          const float4 rb0 = U4[rw.u2 * 16 + ((2 * cq) ^ x2)], rb1 = U4[rw.u2 * 16 + ((2 * cq + 1) ^ x2)];
-          const float4 ib0 = U4[rw.u2 * 16 + 8 + ((2 * cq) ^ x2)], ib1 = U4[rw.u2 * 16 + 8 + ((2 * cq + 1) ^ x2)];
+          const float4* p1 = (const float4*)(raw + r1 + 32 * cq);  // Re at +0, Im at +128 bytes
+          const float4* p2 = (const float4*)(raw + r2 + 32 * cq);
+          const float4 ra0 = p1[0], ra1 = p1[1], ia0 = p1[8], ia1 = p1[9];
+          const float4 rb0 = p2[0], rb1 = p2[1], ib0 = p2[8], ib1 = p2[9];
           const float fr1[8] = {ra0.x, ra0.y, ra0.z, ra0.w, ra1.x, ra1.y, ra1.z, ra1.w};
           const float fi1[8] = {ia0.x, ia0.y, ia0.z, ia0.w, ia1.x, ia1.y, ia1.z, ia1.w};
           const float fr2[8] = {rb0.x, rb0.y, rb0.z, rb0.w, rb1.x, rb1.y, rb1.z, rb1.w};
