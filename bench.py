@@ -100,40 +100,77 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------- oracle leg --
-def oracle_sample(field, edges):
+def oracle_sample(field, edges, heavy=True):
     """Time the FP64 oracle, as it stands, on a bounded sample of one 256^3
     4PCF field and scale to fields/s.  Per field the oracle runs
     O.kernel_full for each (l, m in -l..l) (25 at lmax 4), O.a_coefficient for
     each of those kernels' 10 bins (250), and O.triple_sum for each of the 804
-    (Lambda, M) terms over all grid points.  The sample times one call of
-    each, the last on a 1/32 slab of the grid, and scales by those counts."""
+    (Lambda, M) terms over all grid points.  The sample times three kernel
+    builds, four convolutions and two triple sums on 1/8 of the grid (about
+    10-30 s of host work), and scales each by its count per field; the light
+    sample (one of each, the triple sum on 1/32 of the grid) is the per-step
+    work of the reference arm."""
     from oracle import sarabande_oracle as O
     t0 = time.perf_counter()
     d, _ = O.preprocess(field)
+    lms = [(1, 1), (2, -1), (4, 3)] if heavy else [(1, 1)]
     tk0 = time.perf_counter()
-    ks = O.kernel_full(d.shape, edges, 1, 1)
-    tk = time.perf_counter() - tk0
+    ks = [O.kernel_full(d.shape, edges, l, m) for (l, m) in lms]
+    tk = (time.perf_counter() - tk0) / len(lms)
     ta0 = time.perf_counter()
-    a0 = O.a_coefficient(d, ks[3])
-    ta = time.perf_counter() - ta0
+    picks = [(0, 3), (1, 6), (2, 8), (2, 9)] if heavy else [(0, 3), (0, 3)]
+    a = [O.a_coefficient(d, ks[i][b]) for (i, b) in picks[:4 if heavy else 1]]
+    a = a + a if len(a) == 1 else a
+    ta = (time.perf_counter() - ta0) / (4 if heavy else 1)
     ng = d.size
-    slab = ng // 32
+    frac = 8 if heavy else 32
+    slab = ng // frac
     dd = d.reshape(1, -1)[:, :slab]
-    A = np.stack([a0.ravel()[:slab]] * NB)
+    A1 = np.stack([a[0].ravel()[:slab]] * NB)
+    A2 = np.stack([a[1].ravel()[:slab]] * NB)
     tb0 = time.perf_counter()
-    O.triple_sum(dd, A, A, A)
-    tb = (time.perf_counter() - tb0) * 32
+    O.triple_sum(dd, A1, A2, A2)
+    if heavy:
+        O.triple_sum(dd, A1, A1, A2)
+    tb = (time.perf_counter() - tb0) / (2 if heavy else 1) * frac
     n_k = (LMAX4 + 1) ** 2
     n_a = n_k * NB
     n_terms = sum(1 for (l1, l2, l3) in O.lambda_list(LMAX4) for m1 in range(-l1, l1 + 1)
                   for m2 in range(-l2, l2 + 1) if abs(m1 + m2) <= l3)
     per_field = n_k * tk + n_a * ta + n_terms * tb
     return {"value": 1.0 / per_field, "unit": "fields/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"one 256^3 lognormal field, lmax 4, 10 bins: {n_k} x O.kernel_full, {n_a} x "
-                       f"O.a_coefficient and {n_terms} x O.triple_sum, each timed once (triple_sum on a "
-                       f"1/32 slab); per field {per_field:.0f} s extrapolated from "
+            "sample": (f"one 256^3 lognormal field, lmax 4, 10 bins: {len(lms)} of its {n_k} O.kernel_full, "
+                       f"{4 if heavy else 1} of its {n_a} O.a_coefficient and {2 if heavy else 1} of its "
+                       f"{n_terms} O.triple_sum (on 1/{frac} of the grid, scaled x{frac}); per field "
+                       f"{per_field:.0f} s extrapolated from "
                        f"{time.perf_counter() - t0:.1f} s of oracle work"),
             "seconds_per_field": per_field}
+
+
+def profiled_traffic(grid):
+    """DRAM bytes of one tc4_kernel launch from the committed ncu summary,
+    scaled from its grid to `grid` by the number of points; None when the
+    kernel or its tables changed since the capture (source hashes differ)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "tc4_kernel_traffic.txt")
+    try:
+        lines = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    except OSError:
+        return None
+    kv = {}
+    for parts in lines:
+        if parts[0] == "sha256":
+            src = os.path.join(ROOT, parts[1])
+            try:
+                if hashlib.sha256(open(src, "rb").read()).hexdigest() != parts[2]:
+                    return None
+            except OSError:
+                return None
+        else:
+            kv[parts[0]] = float(parts[1])
+    if "grid" not in kv:
+        return None
+    return (kv["dram_bytes_read"] + kv["dram_bytes_write"]) * (grid / kv["grid"]) ** 3
 
 
 def field_for(rank, grid=256):
@@ -179,9 +216,9 @@ def run_reference(args):
     field, edges = field_for(0)
     times = []
     for _ in range(args.warmup):
-        oracle_sample(field, edges)
+        oracle_sample(field, edges, heavy=False)
     for _ in range(args.steps):
-        times.append(oracle_sample(field, edges))
+        times.append(oracle_sample(field, edges, heavy=False))
     per = statistics.mean(t["seconds_per_field"] for t in times)
     v = 1.0 / per
     cb = dict(times[-1])
@@ -274,17 +311,19 @@ def run_gpu(args):
         peak = props.multi_processor_count * 128 * 2 * mhz * 1e6 / 1e12
         peak_src = f"derived: {props.multi_processor_count} SMs x 128 lanes x 2 x {mhz:.0f} MHz"
     achieved = alg_flops / (kernel_ms * 1e-3) / 1e12
+    traffic = profiled_traffic(args.grid) if prec_name == "bf16x3" else None
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-            "traffic": None,
+            "traffic": traffic,
             "kernel": "tc4_kernel" if prec_name == "bf16x3" else "simt4_kernel (3 launches)",
             "peak_source": peak_src, "alg_flops_per_launch": alg_flops, "avg_ms": kernel_ms}
     hbm = peaks.get("hbm_gbs", 6787.9)
     out = {"metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "bf16x3" if prec_name == "bf16x3" else "f32", "data": "synthetic",
-           "config": {"workload": "full 3D 4PCF, 256^3 float32 lognormal (sigma_G 1.5, P~k^-11/3), lmax 4, "
-                                  "10 linear bins 2..32", "grid": 256, "nbins": NB, "lmax4": LMAX4,
-                      "precision": prec_name, "l2": "inputs larger than L2 (20 GB of coefficients per step)",
+           "config": {"workload": f"full 3D 4PCF, {args.grid}^3 float32 lognormal (sigma_G 1.5, P~k^-11/3), "
+                                  "lmax 4, 10 linear bins 2..32", "grid": args.grid, "nbins": NB, "lmax4": LMAX4,
+                      "precision": prec_name,
+                      "l2": f"inputs larger than L2 ({150 * 8 * ng / 1e9:.1f} GB of coefficients per step)",
                       "kernel_spectra": "cached in the plan (Algorithm 1 run once per geometry)"},
            "roofline": roof,
            "stages_ms": {"preprocess": float(stages[:, 0].mean()), "fft_delta": float(stages[:, 1].mean()),
