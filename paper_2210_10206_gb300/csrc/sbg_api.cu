@@ -115,14 +115,17 @@ struct Tables4 {
   // host
   std::vector<Tile4> tiles[3];  // by tcg class 4, 8, 16
   std::vector<Row4> rows;
-  std::vector<int> cols, uniq, colslot;
+  std::vector<int> cols, uniq;
+  std::vector<BGroup> bgroups;  // tensor-core tiles: column groups and their B images
+  long long img_stride = 0;     // bytes of B images per K-block
+  int chunks_per_kb = 0;
   std::vector<int> ptr, idx;
   std::vector<double> coef;
   long long tcount = 0;  // outputs of T (complex counted once)
   bool tc = false;       // tiles built for the tensor-core kernel
   int nout = 0;
   // device
-  DevBuf d_tiles[3], d_rows, d_cols, d_uniq, d_colslot, d_ptr, d_idx, d_coef;
+  DevBuf d_tiles[3], d_rows, d_cols, d_uniq, d_bgroups, d_ptr, d_idx, d_coef;
 };
 
 }  // namespace
@@ -418,6 +421,18 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
       const int cls = tc ? 0 : (nc <= 16 ? 0 : (nc <= 32 ? 1 : 2));
       const int TR = tc ? 128 : (cls == 0 ? 256 : (cls == 1 ? 128 : 64));
       const int col0 = (int)t.cols.size();
+      int bgroup = -1;
+      if (tc) {
+        BGroup g{};
+        g.col0 = col0;
+        g.ncols = nc;
+        g.n = ((dim == 2 ? 2 * nc : nc) + 15) & ~15;
+        g.off = t.img_stride;
+        t.img_stride += (long long)g.n * 256;
+        t.chunks_per_kb += g.n * 8;
+        bgroup = (int)t.bgroups.size();
+        t.bgroups.push_back(g);
+      }
       for (int c = c0; c < c0 + nc; ++c) {
         const int b3 = bk.bcol0 + c / (int)bk.l3s.size();
         const int l3 = bk.l3s[c % bk.l3s.size()];
@@ -430,6 +445,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
         tl.col0 = col0;
         tl.ncols = nc;
         tl.uniq0 = (int)t.uniq.size();
+        tl.bgroup = bgroup;
         std::map<int, int> local;
         int nr = 0;
         const int rstart = r;
@@ -567,7 +583,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
   ST(upload(ctx, t.d_rows, t.rows));
   ST(upload(ctx, t.d_cols, t.cols));
   ST(upload(ctx, t.d_uniq, t.uniq));
-  ST(upload(ctx, t.d_colslot, t.colslot));
+  ST(upload(ctx, t.d_bgroups, t.bgroups));
   ST(upload(ctx, t.d_ptr, t.ptr));
   ST(upload(ctx, t.d_idx, t.idx));
   ST(upload(ctx, t.d_coef, t.coef));
@@ -580,7 +596,7 @@ void free_tables4(sbg_context* ctx, Tables4* t) {
   dev_free(ctx, t->d_rows);
   dev_free(ctx, t->d_cols);
   dev_free(ctx, t->d_uniq);
-  dev_free(ctx, t->d_colslot);
+  dev_free(ctx, t->d_bgroups);
   dev_free(ctx, t->d_ptr);
   dev_free(ctx, t->d_idx);
   dev_free(ctx, t->d_coef);
@@ -869,10 +885,11 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
       const long long epochs = rounds * ((nk_unit + kTcEpoch - 1) / kTcEpoch) + 4;
       ST(buf(ctx, "tccnt", (size_t)epochs * 4, (void**)&d_cnt));
       CU(cudaMemsetAsync(d_cnt, 0, (size_t)epochs * 4, ctx->stream));
-      void* d_bstore;
-      ST(buf(ctx, "bstore", (size_t)nsingle * ng * 8 * (cplx ? 2 : 1), &d_bstore));
-      ctx->nlaunch += 1;  // bsplit_kernel
-      KL(launch_tc4(d_astore, d_bstore, d_delta, ng, (const Tile4*)t.d_tiles[0].p, ntl, (const Row4*)t.d_rows.p,
+      void* d_bimg;
+      ST(buf(ctx, "bimg", (size_t)(ng / 32) * (size_t)t.img_stride, &d_bimg));
+      ctx->nlaunch += 1;  // bimage_kernel
+      KL(launch_tc4(d_astore, d_bimg, (const BGroup*)t.d_bgroups.p, (int)t.bgroups.size(), t.chunks_per_kb,
+                    t.img_stride, d_delta, ng, (const Tile4*)t.d_tiles[0].p, ntl, (const Row4*)t.d_rows.p,
                     (const int*)t.d_cols.p, (const int*)t.d_uniq.p, nsingle, cplx, best, d_T, d_cnt, d_err,
                     ctx->nsm, ctx->stream, ctx->kev[0], ctx->kev[1]));
       ctx->kev_used = true;

@@ -30,7 +30,7 @@ struct Tile4 {
   int row0, nrows;     // rows of the global row table
   int col0, ncols;     // cols of the global col table
   int uniq0, nuniq;    // staged singles (store indices); tensor-core tiles: sorted slot list
-  int colslot0;        // tensor-core tiles: slot of each column (colslot table)
+  int bgroup;          // tensor-core tiles: the B image (column group) of the tile
   int pad;
   long long tout;      // offset (in outputs) of this tile's [nrows][ncols] block of T
 };
@@ -46,19 +46,30 @@ cudaError_t launch_simt4(const float2* astore, long long ng, const float* delta,
                          int tcg, int nsplit, int nsingle, double* T, cudaStream_t st);
 
 // Tensor-core (tcgen05) split-BF16 version of the same contraction (sbg_tc.cu).
-// Tiles of <= 128 rows whose row singles (<= kTcMaxRowSlots, sorted store
-// indices in `slots`) are staged per K-block, and <= 64 B rows (3D: columns;
-// 2D: two per column).  bstore (nsingle * ng * 8 bytes, x2 for 2D) receives the
-// bf16 B operand of every single.  *err is set (never cleared) if a bounded
-// wait inside the kernel expired.
+// Tiles of <= 128 rows whose row singles (<= kTcMaxRowSlots, in the slot order
+// given by `slots`, -1 for an unused slot) are staged per K-block.  The tiles
+// of one column group share their columns (<= 64 B rows: 3D one per column,
+// 2D two); per K-block the group's B operand is an image of n hi rows then n
+// lo rows of 128 bytes (n = B rows rounded up to 16) at byte `off` of the
+// K-block's img_stride-byte slab of `bimg` (nkb * img_stride bytes, written by
+// the launcher).  *err is set (never cleared) if a bounded wait inside the
+// kernel expired.
 constexpr int kTcMaxRowSlots = 56;  // row singles staged per K-block
 constexpr int kTcEpoch = 256;       // K-blocks between progress checkpoints of the lag limiter
+struct BGroup {
+  int col0, ncols;     // columns (global col table)
+  int n;               // B rows of the MMA (multiple of 16, <= 64)
+  int pad;
+  long long off;       // byte offset of the image in a K-block's slab
+};
 // Units (tile, x-split) are spread over a cooperative grid of one CTA per SM;
 // cnt holds one progress counter per (round, epoch), zeroed by the caller.
-cudaError_t launch_tc4(const float2* astore, const void* bstore, const float* delta, long long ng,
-                       const Tile4* tiles, int ntiles, const Row4* rows, const int* cols, const int* slots,
-                       int nsingle, int complex_out, int nsplit, double* T, int* cnt, int* err, int nsm,
-                       cudaStream_t st, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
+// chunks_per_kb = 8 * sum of the groups' n.
+cudaError_t launch_tc4(const float2* astore, void* bimg, const BGroup* bgroups, int nbgroups, int chunks_per_kb,
+                       long long img_stride, const float* delta, long long ng, const Tile4* tiles, int ntiles,
+                       const Row4* rows, const int* cols, const int* slots, int nsingle, int complex_out,
+                       int nsplit, double* T, int* cnt, int* err, int nsm, cudaStream_t st,
+                       cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 
 // ---- finalisation ----
 // zeta[o] = sum_{e in [ptr[o], ptr[o+1])} coef[e] * T[idx[e]] (idx < 0: conj of T[-idx-1]).

@@ -53,10 +53,11 @@ constexpr int kFlush = 64;             // K-blocks per inner accumulation range
 constexpr int kKX = 32;                // grid points per K-block (64 bf16 = one 128-B row)
 constexpr int kProdWarps = 16;         // producer warps 0..15
 constexpr int kMmaWarp = kProdWarps;   // warp 16
-constexpr int kLoadWarps = 3;          // warps 17..19
+constexpr int kLoadWarps = 2;          // warps 17..18: raw A singles
 constexpr int kLoad0 = kMmaWarp + 1;
 constexpr int kLoaders = kLoadWarps * 32;
-constexpr int kThreads = (kProdWarps + 1 + kLoadWarps) * 32;
+constexpr int kBWarp = kLoad0 + kLoadWarps;  // warp 19: B tiles
+constexpr int kThreads = (kBWarp + 1) * 32;
 constexpr int kOpStage = 128 * 128;   // B tile: n hi rows, then n lo rows (n <= 64), 128 B each
 // TMEM columns: the inner accumulator [0, 128) of the current 64-K-block range
 // (columns [0, n) collect Ahi Bhi + Alo Bhi, [n, 2n) Ahi Blo), the outer
@@ -93,6 +94,18 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
 // completes or kSuspendNs pass (the hardware wakes it on completion), so a
 // waiting warp takes no issue slots from the warps doing the work.
 constexpr uint32_t kSuspendNs = 100000;
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
+               : "memory");
+}
+// bytes (multiple of 16) from global to shared memory on the async proxy,
+// completing as transaction bytes on `bar`
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(bar))
+      : "memory");
+}
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -157,10 +170,6 @@ __device__ __forceinline__ void split_pair(uint64_t v, uint32_t& hi, uint32_t& l
   float l0, l1;
   upk(sub2(v, hf), l0, l1);
   lo = bf16x2_rn(l0, l1);
-}
-
-__device__ __forceinline__ uint32_t swz(int row, int chunk) {
-  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
 }
 
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -266,9 +275,9 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore, long long ng,
-           const Tile4* __restrict__ tiles, int ntiles, const Row4* __restrict__ rows,
-           const int* __restrict__ cols, const int* __restrict__ slots, int nsingle, int cplx, int nsplit,
+tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, const BGroup* __restrict__ bgroups,
+           long long img_stride, long long ng, const Tile4* __restrict__ tiles, int ntiles,
+           const Row4* __restrict__ rows, const int* __restrict__ slots, int nsingle, int cplx, int nsplit,
            double* __restrict__ T, int* cnt, int* err_flag) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -279,7 +288,8 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
   uint64_t* raw_empty = bars + kRS;
   uint64_t* op_full = bars + 2 * kRS;
   uint64_t* op_empty = bars + 2 * kRS + kOS;
-  uint64_t* acc_full = bars + 2 * kRS + 2 * kOS;  // a range's MMAs are complete
+  uint64_t* b_full = bars + 2 * kRS + 2 * kOS;    // B tile landed (transaction bytes)
+  uint64_t* acc_full = b_full + kOS;              // a range's MMAs are complete
   uint32_t* tmem_slot = (uint32_t*)(acc_full + 1);
   volatile int* err = err_flag;
 
@@ -289,7 +299,6 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
   const long long nrounds = (nunits + gridDim.x - 1) / gridDim.x;
   const long long nk_unit = ((ng / kKX) + nsplit - 1) / nsplit;
   const int epochs = (int)((nk_unit + kTcEpoch - 1) / kTcEpoch);
-  const int bparts = cplx ? 2 : 1;  // B rows per column single
 
   if (tid == 0) {
     for (int i = 0; i < kRS; ++i) {
@@ -300,6 +309,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
       mbar_init(&op_full[i], kProdWarps / kGroups);
       mbar_init(&op_empty[i], 1);                     // tcgen05.commit
     }
+    for (int i = 0; i < kOS; ++i) mbar_init(&b_full[i], 1);  // expect_tx arrival + bytes
     mbar_init(acc_full, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -313,7 +323,35 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;  // base of the 512 allocated columns
 
-  if (warp >= kLoad0) {
+  if (warp == kBWarp) {
+    // ------------------------------------------------------------ B tiles --
+    // One bulk copy per K-block of the tile's pre-swizzled B image (2n rows of
+    // 128 bytes) into operand stage kb % 4, once the MMAs of K-block kb - 4 have
+    // released it.
+    if (lane == 0) {
+      uint32_t issued[kOS] = {0, 0, 0, 0};
+      bool ok = true;
+      for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        const Unit it = unit_of(u, ntiles, nsplit, ng);
+        const Tile4 tl = tiles[it.tile];
+        const BGroup bg = bgroups[tl.bgroup];
+        const uint32_t bytes = (uint32_t)bg.n * 256;
+        for (int kb = 0; kb < it.nk; ++kb) {
+          const int os = kb % kOS;
+          if (!mbar_wait(&op_empty[os], (issued[os] & 1) ^ 1, err, 41)) {
+            ok = false;
+            break;
+          }
+          ++issued[os];
+          mbar_expect_tx(&b_full[os], bytes);
+          bulk_g2s(op_base + os * kOpStage, bimg + ((it.x0 >> 5) + kb) * img_stride + bg.off, bytes, &b_full[os]);
+        }
+      }
+      // every copy issued has landed before the CTA may exit
+      for (int os = 0; os < kOS; ++os)
+        if (issued[os]) mbar_wait(&b_full[os], (issued[os] - 1) & 1, err, 42);
+    }
+  } else if (warp >= kLoad0) {
     // ------------------------------------------------------------ loaders --
     const int li = tid - kLoad0 * 32;  // 0 .. kLoaders - 1
     const int ck = li & 15;            // 16-byte chunk within a 256-byte row
@@ -386,10 +424,11 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
         const uint32_t idesc2 = (idesc & ~(0x3Fu << 17)) | ((uint32_t)((2 * N) >> 3) << 17);
         for (int kb = 0; kb < it.nk; ++kb) {
           const int os = kb % kOS;
-          if (!mbar_wait(&op_full[os], uses[os]++ & 1, err, 21)) {
+          if (!mbar_wait(&op_full[os], uses[os] & 1, err, 21) || !mbar_wait(&b_full[os], uses[os] & 1, err, 22)) {
             ok = false;
             break;
           }
+          ++uses[os];
           tc_fence_after();
           const uint32_t b = su32(op_base + os * kOpStage);
           const uint32_t a_hi = tmem + kTmemA0 + 64 * os, a_lo = a_hi + 32;
@@ -409,7 +448,6 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
     // ---------------------------------------------------------- producers --
     const int quarter = warp & 3;        // TMEM lane quarter = rows 32 quarter .. +31
     const int grp = warp >> 2;           // producer group: K-blocks kb = grp (mod 4), stage grp
-    const int gtid = tid & 127;          // thread index within the group
     const int row = quarter * 32 + lane; // the A row (TMEM lane) this thread writes
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     const int os = grp;
@@ -427,28 +465,6 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
       const float s1 = (rw.flags & 1) ? -1.f : 1.f, s2 = (rw.flags & 2) ? -1.f : 1.f;
       const uint64_t as1 = pk(s1, s1), as2 = pk(s2, s2), ans2 = pk(-s2, -s2);
       const int r1 = rw.u1 * kRawRow, r2 = rw.u2 * kRawRow;  // the two singles in a raw stage
-      // B rows this thread moves: row c = (gtid >> 4) + 8k (stored when c < n),
-      // 16-byte chunk gtid & 15; bof = byte offset of that chunk in a K-block's
-      // slab of the B store, or -1 for a zero row (c beyond the tile's columns)
-      int bof[8];
-      unsigned bst = 0;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int c = (gtid >> 4) + 8 * k;
-        const int cs = cplx ? (c >> 1) : c;
-        bof[k] = (c < N && cs < tl.ncols) ? (cols[tl.col0 + cs] * bparts + (cplx ? (c & 1) : 0)) * 256 + (gtid & 15) * 16
-                                          : -1;
-        if (c < N) bst |= 1u << k;
-      }
-      uint4 vb[8];
-      const long long bslab = (long long)nsingle * bparts * 256;  // bytes per K-block
-      auto load_b = [&](int kbb) {
-        const uint8_t* bx = bstore + ((it.x0 >> 5) + kbb) * bslab;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          vb[k] = bof[k] >= 0 ? __ldg((const uint4*)(bx + bof[k])) : make_uint4(0, 0, 0, 0);
-      };
-      if (grp < it.nk) load_b(grp);
       int flushed = 0;                              // ranges of this unit already folded (group 0)
       // fold range i of this unit: inner accumulator -> outer (or -> T for the last range)
       auto fold = [&](int i) -> bool {
@@ -490,8 +506,6 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
         tc_fence_before();
         return true;
       };
-      // B tile destination of this thread's 16-byte chunk of row gtid >> 4 (+ 8 k)
-      uint8_t* const bdst = op_base + os * kOpStage + swz(gtid >> 4, gtid & 7) + ((gtid >> 3) & 1) * N * 128;
       for (int kb = grp; kb < it.nk && ok; kb += kGroups) {
         // group 0 produces the first K-block of every range: fold the previous
         // range first, whose inner accumulator this range overwrites
@@ -510,11 +524,6 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
         ++uses;
         tc_fence_after();
         const uint8_t* raw = raw_base + rs * kRawStage;
-        // ---- B: store the prefetched rows into the swizzled operand tile, prefetch the next ----
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (bst & (1u << k)) *(uint4*)(bdst + 1024 * k) = vb[k];
-        if (kb + kGroups < it.nk) load_b(kb + kGroups);
         // ---- A: the 32 pair products of this thread's row, to TMEM ----
         const uint32_t acol = tmem + lane_addr + kTmemA0 + 64 * os;
 #pragma unroll 1
@@ -547,8 +556,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
-        // publish the B tile to the tensor core (async proxy), release the raw stage
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        // publish the A tile to the MMA issuer, release the raw stage
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(&op_full[os]);
@@ -570,52 +578,70 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bstore,
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-// B operand rows of every single and K-block: v = delta * a; 3D row
-// (Re v, -Im v), 2D rows (Re v, -Im v) and (Im v, Re v); each row 64 bf16 hi
-// then 64 bf16 lo (256 bytes), in the blocked order of the coefficient store.
-__global__ void bsplit_kernel(const float* __restrict__ astore, const float* __restrict__ delta, long long nkb,
-                              int nsingle, int cplx, uint32_t* __restrict__ bstore) {
-  const long long nrow = nkb * nsingle;  // (K-block, single) pairs
-  const int sub = threadIdx.x & 15;      // points 2 sub, 2 sub + 1
-  for (long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 4; r < nrow;
-       r += ((long long)gridDim.x * blockDim.x) >> 4) {
-    const long long xb = r / nsingle;
-    const float* a = astore + r * 64;
-    const float2 re = *(const float2*)(a + 2 * sub), im = *(const float2*)(a + 32 + 2 * sub);
-    const float2 d = *(const float2*)(delta + xb * 32 + 2 * sub);
-    uint32_t rh, rl, ih, il;
-    split_pair(pk(d.x * re.x, d.y * re.y), rh, rl);
-    split_pair(pk(d.x * im.x, d.y * im.y), ih, il);
-    uint32_t* o = bstore + r * (cplx ? 128 : 64);
-    const uint32_t sg = 0x80008000u;
-    o[sub] = rh;
-    o[16 + sub] = ih ^ sg;
-    o[32 + sub] = rl;
-    o[48 + sub] = il ^ sg;
-    if (cplx) {
-      o[64 + sub] = ih;
-      o[80 + sub] = rh;
-      o[96 + sub] = il;
-      o[112 + sub] = rl;
+// B image of every K-block: for each column group (the columns shared by the
+// tiles of one m3 block), 2n rows of 64 bf16 in the 128-byte-swizzled K-major
+// layout the MMA reads, rows [0, n) the hi parts and rows [n, 2n) the lo parts
+// of the B rows (3D column c: (Re v, -Im v) of single cols[col0 + c]; 2D column
+// c: (Re v, -Im v) for even c and (Im v, Re v) for odd c of single
+// cols[col0 + c / 2]; v = delta * a; zero past the group's columns).  One
+// thread writes one 16-byte chunk (8 K values) of a hi row and of its lo row.
+__global__ void bimage_kernel(const float* __restrict__ astore, const float* __restrict__ delta, long long nkb,
+                              int nsingle, int cplx, const BGroup* __restrict__ groups, const int* __restrict__ cols,
+                              int chunks_per_kb, long long img_stride, uint8_t* __restrict__ bimg) {
+  const long long total = nkb * chunks_per_kb;
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total;
+       w += (long long)gridDim.x * blockDim.x) {
+    const long long xb = w / chunks_per_kb;
+    int r = (int)(w - xb * chunks_per_kb);
+    int g = 0;
+    while (r >= groups[g].n * 8) {
+      r -= groups[g].n * 8;
+      ++g;
     }
+    const BGroup bg = groups[g];
+    const int c = r >> 3, j = r & 7;
+    const int second = j >> 2, p0 = (j & 3) * 8;  // K values 8j..8j+7: points p0.. of one half
+    const int cs = cplx ? (c >> 1) : c;
+    uint4 hi = make_uint4(0, 0, 0, 0), lo = make_uint4(0, 0, 0, 0);
+    if (cs < bg.ncols) {
+      const float* a = astore + (xb * nsingle + cols[bg.col0 + cs]) * 64;
+      const float4* ap = (const float4*)(a + (((cplx && (c & 1)) ? !second : second) ? 32 : 0) + p0);
+      const float4* dp = (const float4*)(delta + xb * 32 + p0);
+      // component: Re v for (even, first half) and (odd, second half); Im v otherwise,
+      // negated for (even, second half)
+      const float sg = (!(cplx && (c & 1)) && second) ? -1.f : 1.f;
+      const float4 a0 = ap[0], a1 = ap[1], d0 = dp[0], d1 = dp[1];
+      uint32_t h[4], l[4];
+      split_pair(pk(sg * (d0.x * a0.x), sg * (d0.y * a0.y)), h[0], l[0]);
+      split_pair(pk(sg * (d0.z * a0.z), sg * (d0.w * a0.w)), h[1], l[1]);
+      split_pair(pk(sg * (d1.x * a1.x), sg * (d1.y * a1.y)), h[2], l[2]);
+      split_pair(pk(sg * (d1.z * a1.z), sg * (d1.w * a1.w)), h[3], l[3]);
+      hi = make_uint4(h[0], h[1], h[2], h[3]);
+      lo = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+    uint8_t* img = bimg + xb * img_stride + bg.off;
+    const int pos = (j ^ (c & 7)) << 4;  // rows c and n + c share c & 7 (n is a multiple of 16)
+    *(uint4*)(img + c * 128 + pos) = hi;
+    *(uint4*)(img + (bg.n + c) * 128 + pos) = lo;
   }
 }
 
 }  // namespace
 
-cudaError_t launch_tc4(const float2* astore, const void* bstore, const float* delta, long long ng,
-                       const Tile4* tiles, int ntiles, const Row4* rows, const int* cols, const int* slots,
-                       int nsingle, int complex_out, int nsplit, double* T, int* cnt, int* err, int nsm,
-                       cudaStream_t st, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+cudaError_t launch_tc4(const float2* astore, void* bimg, const BGroup* bgroups, int nbgroups, int chunks_per_kb,
+                       long long img_stride, const float* delta, long long ng, const Tile4* tiles, int ntiles,
+                       const Row4* rows, const int* cols, const int* slots, int nsingle, int complex_out,
+                       int nsplit, double* T, int* cnt, int* err, int nsm, cudaStream_t st, cudaEvent_t ev_begin,
+                       cudaEvent_t ev_end) {
   if (ntiles <= 0) return cudaSuccess;
-  if (ng % kKX) return cudaErrorInvalidValue;
-  // B operand of every single, once per field
+  if (ng % kKX || nbgroups <= 0 || chunks_per_kb <= 0 || img_stride % 1024) return cudaErrorInvalidValue;
+  // B images of every K-block, once per field
   {
     const long long nkb = ng / kKX;
-    long long blocks = (nkb * nsingle * 16 + 255) / 256;
+    long long blocks = (nkb * chunks_per_kb + 255) / 256;
     if (blocks > (long long)nsm * 32) blocks = (long long)nsm * 32;
-    bsplit_kernel<<<(unsigned)blocks, 256, 0, st>>>((const float*)astore, delta, nkb, nsingle, complex_out,
-                                                    (uint32_t*)bstore);
+    bimage_kernel<<<(unsigned)blocks, 256, 0, st>>>((const float*)astore, delta, nkb, nsingle, complex_out,
+                                                    bgroups, cols, chunks_per_kb, img_stride, (uint8_t*)bimg);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -630,11 +656,11 @@ cudaError_t launch_tc4(const float2* astore, const void* bstore, const float* de
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const float* af = (const float*)astore;
-  const uint8_t* bs = (const uint8_t*)bstore;
+  const uint8_t* bi = (const uint8_t*)bimg;
   const int grid = nsm;  // every CTA takes part in every round so that the progress counters fill up
-  void* args[] = {(void*)&af,    (void*)&bs,     (void*)&ng,    (void*)&tiles, (void*)&ntiles,
-                  (void*)&rows,  (void*)&cols,   (void*)&slots, (void*)&nsingle, (void*)&complex_out,
-                  (void*)&nsplit, (void*)&T,     (void*)&cnt,   (void*)&err};
+  void* args[] = {(void*)&af,    (void*)&bi,      (void*)&bgroups, (void*)&img_stride, (void*)&ng,
+                  (void*)&tiles, (void*)&ntiles,  (void*)&rows,    (void*)&slots,      (void*)&nsingle,
+                  (void*)&complex_out, (void*)&nsplit, (void*)&T,  (void*)&cnt,        (void*)&err};
   if (ev_begin && (e = cudaEventRecord(ev_begin, st)) != cudaSuccess) return e;
   e = cudaLaunchCooperativeKernel((const void*)tc4_kernel, dim3(grid), dim3(kThreads), args, kSmem, st);
   if (e != cudaSuccess) return e;
