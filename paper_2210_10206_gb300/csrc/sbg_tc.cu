@@ -23,7 +23,7 @@
 //              into a 128-byte-swizzled K-major tile in shared memory and writes the
 //              bf16 hi/lo A tile (formed with packed f32x2 arithmetic, one row
 //              per TMEM lane) straight into tensor memory.  Group 0 also folds
-//              each 64-K-block range's TMEM accumulator into the outer TMEM
+//              each 256-K-block range's TMEM accumulator into the outer TMEM
 //              accumulator (before it forms the first K-block of the next
 //              range, which reuses the inner one) and, at the end of a unit,
 //              adds it to T in FP64;
@@ -49,7 +49,7 @@ namespace {
 constexpr int kGroups = 4;             // producer groups; group g owns operand stage g
 constexpr int kRS = 2 * kGroups;       // raw stages: two per group (2g, 2g + 1)
 constexpr int kOS = kGroups;           // operand stages (A in TMEM, B in shared memory)
-constexpr int kFlush = 64;             // K-blocks per inner accumulation range
+constexpr int kFlush = 256;            // K-blocks per inner accumulation range
 constexpr int kKX = 32;                // grid points per K-block (64 bf16 = one 128-B row)
 constexpr int kProdWarps = 16;         // producer warps 0..15
 constexpr int kMmaWarp = kProdWarps;   // warp 16
@@ -59,7 +59,7 @@ constexpr int kLoaders = kLoadWarps * 32;
 constexpr int kBWarp = kLoad0 + kLoadWarps;  // warp 19: B tiles
 constexpr int kThreads = (kBWarp + 1) * 32;
 constexpr int kOpStage = 128 * 128;   // B tile: n hi rows, then n lo rows (n <= 64), 128 B each
-// TMEM columns: the inner accumulator [0, 128) of the current 64-K-block range
+// TMEM columns: the inner accumulator [0, 128) of the current 256-K-block range
 // (columns [0, n) collect Ahi Bhi + Alo Bhi, [n, 2n) Ahi Blo), the outer
 // accumulator [128, 192), then one 64-column A stage per operand stage
 // (32 columns hi, 32 lo: 64 bf16 each)
@@ -430,14 +430,16 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
           }
           ++uses[os];
           tc_fence_after();
-          const uint32_t b = su32(op_base + os * kOpStage);
+          // B descriptor of the stage; K step k starts 32 bytes further (+2 in
+          // the descriptor's 16-byte address field, which cannot carry out)
+          const uint64_t bd = sdesc(su32(op_base + os * kOpStage));
           const uint32_t a_hi = tmem + kTmemA0 + 64 * os, a_lo = a_hi + 32;
-          const bool first = (kb % kFlush) == 0;
+          const uint32_t acc0 = (kb % kFlush) == 0 ? 0u : 1u;
           // two MMAs per 16-wide K step: Ahi meets Bhi and Blo in one (N = 2n)
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            mma_bf16_ts(tmem, a_hi + 8 * k, sdesc(b + 32 * k), idesc2, (first && k == 0) ? 0u : 1u);
-            mma_bf16_ts(tmem, a_lo + 8 * k, sdesc(b + 32 * k), idesc, 1u);
+            mma_bf16_ts(tmem, a_hi + 8 * k, bd + 2 * k, idesc2, k == 0 ? acc0 : 1u);
+            mma_bf16_ts(tmem, a_lo + 8 * k, bd + 2 * k, idesc, 1u);
           }
           mma_commit(&op_empty[os]);
           if ((kb + 1) % kFlush == 0 || kb + 1 == it.nk) mma_commit(acc_full);
