@@ -10,28 +10,32 @@
 // TMEM).  The row signs (-1)^m of a_{l,-m} are applied in the FP64
 // coupling step, not here.
 //
-// B depends only on the column single and the K-block, so bsplit_kernel writes
-// it once per field (bf16 hi/lo rows in the blocked order); A depends on the
-// row pair and is formed on chip.  Roles of a persistent CTA (one per SM):
-//   warps 17-19 loaders: per-thread 16-byte cp.async of each K-block's raw FP32
-//              row singles into two stages per producer group; each thread's
-//              copies complete onto the stage's mbarrier (noinc);
+// B depends only on the column group (the columns shared by the tiles of one
+// m3 block) and the K-block, so bimage_kernel writes it once per field as an
+// image of the swizzled shared-memory tile; A depends on the row pair and is
+// formed on chip.  Operand stage g (an A tile in TMEM plus a B tile in shared
+// memory) belongs to producer group g, so every stage is filled by one group
+// in order and no waiter can be two mbarrier phases ahead.  Roles of a
+// persistent CTA (one per SM):
 //   warps 0-15 producers, in 4 groups of 4 warps: group g takes the K-blocks
-//              kb = g (mod 4) of every unit and owns operand stage g, so four
-//              K-blocks are in flight.  For its K-block a group stores the B rows
-//              (prefetched from L2 into registers during its previous K-block)
-//              into a 128-byte-swizzled K-major tile in shared memory and writes the
-//              bf16 hi/lo A tile (formed with packed f32x2 arithmetic, one row
-//              per TMEM lane) straight into tensor memory.  Group 0 also folds
-//              each 256-K-block range's TMEM accumulator into the outer TMEM
-//              accumulator (before it forms the first K-block of the next
-//              range, which reuses the inner one) and, at the end of a unit,
-//              adds it to T in FP64;
+//              kb = g (mod 4) of every unit and writes their bf16 hi/lo A tile
+//              (formed with packed f32x2 arithmetic from the FP32 singles in a
+//              raw stage, one row per TMEM lane) straight into tensor memory.
+//              Group 0 also folds each 256-K-block range's TMEM accumulator
+//              into the outer TMEM accumulator (before it forms the first
+//              K-block of the next range, which reuses the inner one) and, at
+//              the end of a unit, adds it to T in FP64;
 //   warp 16    MMA issuer: one thread issues 8 tcgen05.mma (M=128, K=16) per
 //              K-block, Ahi [Bhi | Blo] (N = 2n) and Alo Bhi (N = n) per K step
 //              (the cost of an MMA hardly grows with N up to 128, so fewer,
 //              wider MMAs are faster), and commits to the mbarriers that free
-//              the operand stage and publish the accumulator.
+//              the operand stage and publish the accumulator;
+//   warps 17-18 loaders: per-thread 16-byte cp.async of each K-block's raw
+//              FP32 row singles into two raw stages per producer group; each
+//              thread's copies complete onto the stage's mbarrier (noinc);
+//   warp 19    B loader: one bulk copy (cp.async.bulk) per K-block of the
+//              tile's B image into the operand stage, once the MMAs that last
+//              read that stage have completed.
 // Work units (tile, x-split) are dealt round-robin to a cooperative grid of one
 // CTA per SM; the loaders of all CTAs advance through x together (a CTA may run
 // at most four 256-K-block epochs ahead of the slowest), so that the singles of
@@ -72,7 +76,7 @@ constexpr int kTmemCols = 512;
 constexpr int kRawRow = kKX * 8 + 16;
 constexpr int kRawStage = kTcMaxRowSlots * kRawRow;
 constexpr int kLag = 4;                // epochs a loader may run ahead of the slowest CTA
-constexpr int kMeta = 256;             // barriers and the TMEM address
+constexpr int kMeta = 512;             // barriers (2 kRS + 3 kOS + 1) and the TMEM address
 constexpr int kSmem = kOS * kOpStage + kRS * kRawStage + kMeta + 1024;
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
