@@ -105,25 +105,25 @@ def oracle_sample(field, edges, heavy=True):
     4PCF field and scale to fields/s.  Per field the oracle runs
     O.kernel_full for each (l, m in -l..l) (25 at lmax 4), O.a_coefficient for
     each of those kernels' 10 bins (250), and O.triple_sum for each of the 804
-    (Lambda, M) terms over all grid points.  The sample times three kernel
-    builds, four convolutions and two triple sums on 1/8 of the grid (about
+    (Lambda, M) terms over all grid points.  The sample times six kernel
+    builds, eight convolutions and two triple sums on 1/4 of the grid (about
     10-30 s of host work), and scales each by its count per field; the light
     sample (one of each, the triple sum on 1/32 of the grid) is the per-step
     work of the reference arm."""
     from oracle import sarabande_oracle as O
     t0 = time.perf_counter()
     d, _ = O.preprocess(field)
-    lms = [(1, 1), (2, -1), (4, 3)] if heavy else [(1, 1)]
+    lms = [(1, 1), (2, -1), (3, 0), (3, 2), (4, -3), (4, 3)] if heavy else [(1, 1)]
     tk0 = time.perf_counter()
     ks = [O.kernel_full(d.shape, edges, l, m) for (l, m) in lms]
     tk = (time.perf_counter() - tk0) / len(lms)
     ta0 = time.perf_counter()
-    picks = [(0, 3), (1, 6), (2, 8), (2, 9)] if heavy else [(0, 3), (0, 3)]
-    a = [O.a_coefficient(d, ks[i][b]) for (i, b) in picks[:4 if heavy else 1]]
+    picks = [(0, 3), (1, 6), (2, 8), (3, 9), (4, 2), (5, 5), (5, 7), (2, 0)] if heavy else [(0, 3)]
+    a = [O.a_coefficient(d, ks[i][b]) for (i, b) in picks]
     a = a + a if len(a) == 1 else a
-    ta = (time.perf_counter() - ta0) / (4 if heavy else 1)
+    ta = (time.perf_counter() - ta0) / len(picks)
     ng = d.size
-    frac = 8 if heavy else 32
+    frac = 4 if heavy else 32
     slab = ng // frac
     dd = d.reshape(1, -1)[:, :slab]
     A1 = np.stack([a[0].ravel()[:slab]] * NB)
@@ -140,7 +140,7 @@ def oracle_sample(field, edges, heavy=True):
     per_field = n_k * tk + n_a * ta + n_terms * tb
     return {"value": 1.0 / per_field, "unit": "fields/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": (f"one 256^3 lognormal field, lmax 4, 10 bins: {len(lms)} of its {n_k} O.kernel_full, "
-                       f"{4 if heavy else 1} of its {n_a} O.a_coefficient and {2 if heavy else 1} of its "
+                       f"{len(picks)} of its {n_a} O.a_coefficient and {2 if heavy else 1} of its "
                        f"{n_terms} O.triple_sum (on 1/{frac} of the grid, scaled x{frac}); per field "
                        f"{per_field:.0f} s extrapolated from "
                        f"{time.perf_counter() - t0:.1f} s of oracle work"),
