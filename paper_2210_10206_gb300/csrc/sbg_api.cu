@@ -626,7 +626,7 @@ void rec(sbg_context* ctx, int i) { cudaEventRecord(ctx->ev[i], ctx->stream); }
 // blocked coefficient store (singles single0 .. single0 + batch - 1 of nsingle).
 sbg_status fft3(sbg_context* ctx, int n, int sign, int first_load, const void* in, float2* out, const float2* mul,
                 const float2* shared, int batch, const float2* tw, float2* final_out = nullptr, int nsingle = 0,
-                int single0 = 0) {
+                int single0 = 0, int prune_r = -1) {
   const long long ng = (long long)n * n * n;
   FftPass p{};
   p.twiddle = tw;
@@ -636,12 +636,18 @@ sbg_status fft3(sbg_context* ctx, int n, int sign, int first_load, const void* i
   // z axis (strided by n^2), fused first-pass load
   p.in = in; p.out = out; p.mul = mul; p.shared = shared; p.load = first_load;
   p.outer = 1; p.inner = (long long)n * n;
+  // prune_r >= 0: the input is zero beyond minimum-image distance prune_r on
+  // every axis, so z-lines outside the (y, x) support and, after that pass,
+  // y-lines outside the x support stay zero and are skipped
+  if (prune_r >= 0) { p.prune_mode = 1; p.prune_r = prune_r; }
   KL(fft_axis_pass(n, p, ctx->stream));
   // y axis
   p.in = out; p.load = LOAD_COMPLEX; p.mul = nullptr; p.shared = nullptr;
   p.outer = n; p.inner = n;
+  if (prune_r >= 0) p.prune_mode = 2;
   KL(fft_axis_pass(n, p, ctx->stream));
   // x axis (contiguous)
+  p.prune_mode = 0;
   p.outer = (long long)n * n; p.inner = 1;
   if (final_out) {
     p.out = final_out; p.out_blocked = 1; p.nsingle = nsingle; p.single0 = single0;
@@ -787,7 +793,9 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
       while ((l + 1) * (l + 2) / 2 <= g) ++l;
       const int m = g - l * (l + 1) / 2;
       KL(launch_kgen3d(n, l, m, ylm_norm(l, m), d_e2, nb, inv_ng, dst, ctx->stream));
-      ST(fft3(ctx, n, +1, LOAD_COMPLEX, dst, dst, nullptr, nullptr, nb, d_tw));
+      // the kernels vanish beyond the last edge: prune the zero lines
+      const int rmax = std::min(n / 2 - 1, (int)std::ceil(edges[nb]));
+      ST(fft3(ctx, n, +1, LOAD_COMPLEX, dst, dst, nullptr, nullptr, nb, d_tw, nullptr, 0, 0, rmax));
     } else {
       KL(launch_kgen2d(n, g, d_e2, nb, inv_ng, dst, ctx->stream));
       ST(fft2(ctx, n, +1, LOAD_COMPLEX, dst, dst, nullptr, nullptr, nb, ng, d_tw));

@@ -36,6 +36,13 @@ struct FftPass {
   int out_blocked;
   int nsingle;
   int single0;
+  // Strided passes only: skip line groups that are known to be all zero (a
+  // kernel whose support lies within minimum-image distance prune_r of the
+  // origin on every axis; the skipped lines must already hold zeros).
+  //   prune_mode 1: inner index = y * N + x (first pass of a 3D transform);
+  //   prune_mode 2: inner index = x (second pass).
+  int prune_mode;
+  int prune_r;
 };
 
 // Blocked coefficient store (float view): for each 32-point K-block xb and

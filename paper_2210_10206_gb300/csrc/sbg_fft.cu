@@ -150,6 +150,16 @@ fft_axis_kernel(FftPass p) {
     const long long tiles = p.inner / TL;
     const long long o = blockIdx.x / tiles;
     const long long i0 = (blockIdx.x % tiles) * TL;
+    if (p.prune_mode) {
+      // the whole CTA leaves together: the test depends on blockIdx only
+      const long long x0 = p.prune_mode == 1 ? i0 % N : i0;
+      bool zero = x0 > p.prune_r && x0 + TL - 1 < N - p.prune_r;
+      if (p.prune_mode == 1) {
+        const long long y = i0 / N;
+        zero = zero || (y > p.prune_r && y < N - p.prune_r);
+      }
+      if (zero) return;
+    }
     base = o * (long long)N * p.inner + i0 + l;
     estride = p.inner;
   }

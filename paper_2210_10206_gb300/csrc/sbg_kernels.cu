@@ -206,7 +206,9 @@ __global__ void __launch_bounds__(256) gram3_kernel(const float2* __restrict__ a
 cudaError_t launch_gram3(const float2* a, long long ng, int nb, const float* delta, double* S, int nsingle,
                          int single0, cudaStream_t st) {
   if (nb > kGramMaxNb || nb * (nb + 1) / 2 > 256) return cudaErrorInvalidValue;
-  long long blocks = (ng + 4095) / 4096;
+  // about 4 chunks per CTA on small grids (a CTA's chunks run one after another),
+  // at most 8 CTAs per SM of cross-CTA FP64 atomics on large ones
+  long long blocks = (ng + 4 * kGramChunk - 1) / (4 * kGramChunk);
   if (blocks > 152 * 8) blocks = 152 * 8;
   gram3_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, ng, nb, delta, S, nsingle, single0);
   return cudaGetLastError();
