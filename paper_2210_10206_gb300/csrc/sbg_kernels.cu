@@ -152,7 +152,9 @@ constexpr int kGramMaxNb = 32;
 __global__ void __launch_bounds__(256) gram3_kernel(const float2* __restrict__ a, long long ng, int nb,
                                                     const float* __restrict__ delta, double* __restrict__ S,
                                                     int nsingle, int single0) {
-  __shared__ float2 sa[kGramMaxNb][kGramChunk];
+  // rows padded by one element: the threads of a warp read the same point of
+  // up to 20 different bins, which a 512-byte row stride would put in one bank
+  __shared__ float2 sa[kGramMaxNb][kGramChunk + 1];
   __shared__ float sd[kGramChunk];
   const int npairs = nb * (nb + 1) / 2;
   // pair index -> (b1, b2)
