@@ -120,7 +120,9 @@ def test_full_3pcf_only_and_4pcf_only_agree_with_combined(ctx):
     a3, a4 = ctx.full(f, edges, lmax3=3, lmax4=2)
     b3, _ = ctx.full(f, edges, lmax3=3)
     _, c4 = ctx.full(f, edges, lmax4=2)
-    assert np.array_equal(a3, b3)
+    # same sums through two coefficient layouts; FP64 atomics across CTAs add
+    # in no fixed order, so agreement is to rounding, not bitwise
+    assert _err(b3, a3) < 1e-12
     assert _err(c4, a4) < 1e-12
 
 
@@ -147,7 +149,8 @@ def test_device_field_matches_host_field(ctx):
     edges = [1.0, 3.0, 6.0, 9.0]
     h3, h4 = ctx.full(f, edges, lmax3=2, lmax4=2)
     d3, d4 = ctx.full(torch.from_numpy(f).cuda(), edges, lmax3=2, lmax4=2)
-    assert np.array_equal(h3, d3) and np.array_equal(h4, d4)
+    # FP64 atomics across CTAs add in no fixed order: agreement to rounding
+    assert _err(d3, h3) < 1e-12 and _err(d4, h4) < 1e-12
 
 
 def test_shift_and_rotation_invariance_on_gpu(ctx):
