@@ -144,7 +144,8 @@ cudaError_t launch_kgen2d(int n, int m, const double* e2_dev, int nb, double sca
 
 // ------------------------------------------------------------------ gram3 --
 // One CTA sweeps a contiguous x-range in chunks of 64 points staged in shared
-// memory; thread p owns bin pair p (b1 <= b2), accumulating FP32 over each
+// memory (the next chunk is fetched into registers while the current one is
+// summed); thread p owns bin pair p (b1 <= b2), accumulating FP32 over each
 // chunk and FP64 across chunks.
 constexpr int kGramChunk = 64;
 constexpr int kGramMaxNb = 32;
@@ -166,14 +167,19 @@ __global__ void __launch_bounds__(256) gram3_kernel(const float2* __restrict__ a
   const long long per = (ng + gridDim.x - 1) / gridDim.x;
   const long long x0 = blockIdx.x * per, x1 = min(ng, x0 + per);
   double accr = 0.0, acci = 0.0;
-  for (long long xc = x0; xc < x1; xc += kGramChunk) {
+  // the next chunk is fetched into registers while the current one is summed
+  constexpr int kPer = kGramMaxNb * kGramChunk / 256;
+  float2 pre[kPer];
+  float pd = 0.f;
+  auto fetch = [&](long long xc) {
     const int cnt = (int)min((long long)kGramChunk, x1 - xc);
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb * kGramChunk; i += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int i = threadIdx.x + 256 * k;
       const int b = i / kGramChunk, xx = i % kGramChunk;
-      const long long x = xc + xx;
       float2 v = make_float2(0.f, 0.f);
-      if (xx < cnt) {
+      if (b < nb && xx < cnt) {
+        const long long x = xc + xx;
         if (nsingle) {
           const float* f = reinterpret_cast<const float*>(a) + blocked_re(x, single0 + b, nsingle);
           v = make_float2(f[0], f[32]);
@@ -181,10 +187,21 @@ __global__ void __launch_bounds__(256) gram3_kernel(const float2* __restrict__ a
           v = a[(long long)b * ng + x];
         }
       }
-      sa[b][xx] = v;
+      pre[k] = v;
     }
-    for (int i = threadIdx.x; i < kGramChunk; i += blockDim.x) sd[i] = i < cnt ? delta[xc + i] : 0.f;
+    pd = threadIdx.x < cnt ? delta[xc + threadIdx.x] : 0.f;
+  };
+  if (x0 < x1) fetch(x0);
+  for (long long xc = x0; xc < x1; xc += kGramChunk) {
+    __syncthreads();  // the previous chunk has been summed
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int i = threadIdx.x + 256 * k;
+      if (i < nb * kGramChunk) sa[i / kGramChunk][i % kGramChunk] = pre[k];
+    }
+    if (threadIdx.x < kGramChunk) sd[threadIdx.x] = pd;
     __syncthreads();
+    if (xc + kGramChunk < x1) fetch(xc + kGramChunk);
     if (threadIdx.x < npairs) {
       float sr = 0.f, si = 0.f;
 #pragma unroll 8
