@@ -138,7 +138,15 @@ typedef struct {
 } sbg_field2d;
 
 /* Many projected fields of uneven sizes (e.g. simulation snapshots) measured in
- * one call with shared nbins, mmax, precision and flags. */
+ * one call with shared nbins, mmax, precision and flags (the batch of Sec. 4,
+ * each field as in sbg_projected).  Each entry's field and edges are read as
+ * for sbg_projected; its zeta3 / zeta4 receive that field's outputs.  Fields
+ * are queued back to back on the context's stream: field i + 1 is queued
+ * before field i's results are copied to the caller, so all outputs are valid
+ * only when the call returns.  sbg_last_timings then reports the stages summed
+ * over the fields.  Errors: as sbg_projected, with the field's index in
+ * sbg_last_error; SBG_ERR_TIMEOUT if any field's tensor-core kernel gave up
+ * waiting.  Output contents are unspecified after an error. */
 sbg_status sbg_projected_batch(sbg_context* ctx, const sbg_field2d* fields, int nfields, int nbins, int mmax,
                                sbg_precision prec, unsigned flags);
 

@@ -140,8 +140,12 @@ struct sbg_context {
   double timings[kStages] = {0};
   long long nlaunch = 0;   // kernels launched by the current/last measurement call
   long long last_launches = 0;
-  cudaEvent_t ev[kStages + 1] = {};
-  cudaEvent_t kev[2] = {};      // around the 4PCF contraction kernel(s)
+  // two sets of timing events: a batch keeps one field in flight while the
+  // previous one is completed; ev / kev point at the set of the current call
+  cudaEvent_t evs[2][kStages + 1] = {};
+  cudaEvent_t kevs[2][2] = {};
+  cudaEvent_t* ev = evs[0];
+  cudaEvent_t* kev = kevs[0];   // around the 4PCF contraction kernel(s)
   bool kev_used = false;
   double contraction_ms = 0.0;
   std::map<std::string, DevBuf> bufs;
@@ -155,6 +159,21 @@ struct sbg_context {
   // DMA on the stream and the host copies out after the stream is idle
   void* hpin = nullptr;
   size_t hpin_bytes = 0;
+  // batch pipelining: with `defer` set, a measurement call stages its results
+  // in pinned slot `cur` and returns without waiting; the batch loop completes
+  // it after the next field has been queued
+  struct Pending {
+    bool live = false;
+    double* zeta3 = nullptr;
+    double* zeta4 = nullptr;
+    size_t off3 = 0, off4 = 0, b3 = 0, b4 = 0;
+    long long launches = 0;
+    bool kev_used = false;
+  };
+  bool defer = false;
+  int cur = 0;
+  size_t slot_bytes = 0;
+  Pending pend[2];
 };
 
 namespace {
@@ -874,7 +893,7 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
     if (tc) {
       int* d_err;
       ST(buf(ctx, "err", 16, (void**)&d_err));
-      CU(cudaMemsetAsync(d_err, 0, 16, ctx->stream));
+      if (!ctx->defer) CU(cudaMemsetAsync(d_err, 0, 16, ctx->stream));  // a batch clears it once
       const int ntl = (int)t.tiles[0].size();
       const long long kblocks = ng / 32;
       // x-splits per tile: units = ntl * nsplit spread evenly over the CTAs
@@ -901,12 +920,15 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
                     (const int*)t.d_cols.p, (const int*)t.d_uniq.p, nsingle, cplx, best, d_T, d_cnt, d_err,
                     ctx->nsm, ctx->stream, ctx->kev[0], ctx->kev[1]));
       ctx->kev_used = true;
-      int* perr;
-      ST(host_staging(ctx, 64, (void**)&perr));
-      CU(cudaMemcpyAsync(perr, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-      CU(cudaStreamSynchronize(ctx->stream));
-      const int herr = *perr;
-      if (herr) return fail(ctx, SBG_ERR_TIMEOUT, "tensor-core 4PCF kernel gave up waiting (code " + std::to_string(herr) + ")");
+      if (!ctx->defer) {  // a batch reads the flag once, after its last field
+        int* perr;
+        ST(host_staging(ctx, 64, (void**)&perr));
+        CU(cudaMemcpyAsync(perr, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        const int herr = *perr;
+        if (herr)
+          return fail(ctx, SBG_ERR_TIMEOUT, "tensor-core 4PCF kernel gave up waiting (code " + std::to_string(herr) + ")");
+      }
     } else {
       const int tcg[3] = {4, 8, 16};
       CU(cudaEventRecord(ctx->kev[0], ctx->stream));
@@ -936,7 +958,12 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
   const size_t z4bytes = do4 ? (size_t)ctx->t4->nout * 8 * (dim == 2 ? 2 : 1) : 0;
   const size_t z3off = 0, z4off = (z3bytes + 255) / 256 * 256;
   unsigned char* hst;
-  ST(host_staging(ctx, z4off + z4bytes + 64, (void**)&hst));
+  if (ctx->defer) {
+    if (z4off + z4bytes > ctx->slot_bytes) return fail(ctx, SBG_ERR_INTERNAL, "batch staging slot too small");
+    hst = (unsigned char*)ctx->hpin + 64 + (size_t)ctx->cur * ctx->slot_bytes;
+  } else {
+    ST(host_staging(ctx, z4off + z4bytes + 64, (void**)&hst));
+  }
   if (do3) {
     double* d_z3;
     const int nl = lmax3 + 1;
@@ -947,6 +974,19 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
   }
   if (do4) CU(cudaMemcpyAsync(hst + z4off, d_z4, z4bytes, cudaMemcpyDeviceToHost, ctx->stream));
   rec(ctx, 7);
+  if (ctx->defer) {
+    sbg_context::Pending& pd = ctx->pend[ctx->cur];
+    pd.live = true;
+    pd.zeta3 = do3 ? zeta3 : nullptr;
+    pd.zeta4 = do4 ? zeta4 : nullptr;
+    pd.off3 = z3off;
+    pd.off4 = z4off;
+    pd.b3 = z3bytes;
+    pd.b4 = z4bytes;
+    pd.launches = ctx->nlaunch;
+    pd.kev_used = ctx->kev_used;
+    return SBG_OK;
+  }
   ST(finish_timings(ctx));
   if (do3) std::memcpy(zeta3, hst + z3off, z3bytes);
   if (do4) std::memcpy(zeta4, hst + z4off, z4bytes);
@@ -977,16 +1017,18 @@ sbg_status sbg_create(int cuda_device, size_t hbm_budget_bytes, sbg_context** ou
     return SBG_ERR_CUDA;
   }
   ctx->stream = ctx->own;
-  for (int i = 0; i <= kStages; ++i) {
-    if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) {
-      sbg_destroy(ctx);
-      return SBG_ERR_CUDA;
+  for (int k = 0; k < 2; ++k) {
+    for (int i = 0; i <= kStages; ++i) {
+      if (cudaEventCreate(&ctx->evs[k][i]) != cudaSuccess) {
+        sbg_destroy(ctx);
+        return SBG_ERR_CUDA;
+      }
     }
-  }
-  for (int i = 0; i < 2; ++i) {
-    if (cudaEventCreate(&ctx->kev[i]) != cudaSuccess) {
-      sbg_destroy(ctx);
-      return SBG_ERR_CUDA;
+    for (int i = 0; i < 2; ++i) {
+      if (cudaEventCreate(&ctx->kevs[k][i]) != cudaSuccess) {
+        sbg_destroy(ctx);
+        return SBG_ERR_CUDA;
+      }
     }
   }
   *out = ctx;
@@ -1001,10 +1043,12 @@ void sbg_destroy(sbg_context* ctx) {
   dev_free(ctx, ctx->gcache);
   free_tables4(ctx, ctx->t4);
   if (ctx->hpin) cudaFreeHost(ctx->hpin);
-  for (int i = 0; i <= kStages; ++i)
-    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
-  for (int i = 0; i < 2; ++i)
-    if (ctx->kev[i]) cudaEventDestroy(ctx->kev[i]);
+  for (int k = 0; k < 2; ++k) {
+    for (int i = 0; i <= kStages; ++i)
+      if (ctx->evs[k][i]) cudaEventDestroy(ctx->evs[k][i]);
+    for (int i = 0; i < 2; ++i)
+      if (ctx->kevs[k][i]) cudaEventDestroy(ctx->kevs[k][i]);
+  }
   if (ctx->own) cudaStreamDestroy(ctx->own);
   delete ctx;
 }
@@ -1106,20 +1150,82 @@ sbg_status sbg_projected_batch(sbg_context* ctx, const sbg_field2d* fields, int 
   if (!ctx) return SBG_ERR_INVALID_ARG;
   ctx->err.clear();
   if (!fields || nfields < 1) return fail(ctx, SBG_ERR_INVALID_ARG, "fields/nfields");
+  if (nbins < 1 || nbins > kMaxBins || mmax < 0) return fail(ctx, SBG_ERR_INVALID_ARG, "nbins/mmax");
+  // Fields are queued back to back: field i + 1 is queued before field i's
+  // results are waited for and copied out of their pinned staging slot, so
+  // the GPU runs while the host prepares the next field.
+  const size_t w = 2 * (size_t)mmax + 1;
+  const size_t b3 = (flags & SBG_3PCF) ? (size_t)(mmax + 1) * nbins * nbins * 16 : 0;
+  const size_t b4 = (flags & SBG_4PCF) ? w * w * nbins * nbins * nbins * 16 : 0;
+  ctx->slot_bytes = (b3 + 255) / 256 * 256 + b4 + 256;
+  void* hs;
+  ST(host_staging(ctx, 64 + 2 * ctx->slot_bytes, &hs));
+  int* d_err;
+  ST(buf(ctx, "err", 16, (void**)&d_err));
+  CU(cudaMemsetAsync(d_err, 0, 16, ctx->stream));
   double acc[kStages] = {0};
   long long nl = 0;
+  double kms = 0.0;
+  auto complete = [&](int slot) -> sbg_status {
+    sbg_context::Pending& pd = ctx->pend[slot];
+    if (!pd.live) return SBG_OK;
+    pd.live = false;
+    CU(cudaEventSynchronize(ctx->evs[slot][kStages]));
+    for (int k = 0; k < kStages; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ctx->evs[slot][k], ctx->evs[slot][k + 1]) != cudaSuccess) {
+        cudaGetLastError();
+        ms = 0.f;
+      }
+      acc[k] += ms;
+    }
+    if (pd.kev_used) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ctx->kevs[slot][0], ctx->kevs[slot][1]) == cudaSuccess) kms += ms;
+      else cudaGetLastError();
+    }
+    nl += pd.launches;
+    const unsigned char* hst = (const unsigned char*)ctx->hpin + 64 + (size_t)slot * ctx->slot_bytes;
+    if (pd.zeta3) std::memcpy(pd.zeta3, hst + pd.off3, pd.b3);
+    if (pd.zeta4) std::memcpy(pd.zeta4, hst + pd.off4, pd.b4);
+    return SBG_OK;
+  };
+  auto finish = [&](sbg_status s) -> sbg_status {
+    cudaStreamSynchronize(ctx->stream);
+    ctx->pend[0].live = ctx->pend[1].live = false;
+    ctx->defer = false;
+    ctx->cur = 0;
+    ctx->ev = ctx->evs[0];
+    ctx->kev = ctx->kevs[0];
+    return s;
+  };
+  ctx->defer = true;
   for (int i = 0; i < nfields; ++i) {
+    const int slot = i & 1;
+    ctx->cur = slot;
+    ctx->ev = ctx->evs[slot];
+    ctx->kev = ctx->kevs[slot];
     sbg_status s = sbg_projected(ctx, fields[i].field, fields[i].dtype, fields[i].shape, fields[i].edges, nbins, mmax,
                                  prec, flags, fields[i].zeta3, fields[i].zeta4);
     if (s != SBG_OK) {
       ctx->err = "field " + std::to_string(i) + ": " + ctx->err;
-      return s;
+      return finish(s);
     }
-    for (int k = 0; k < kStages; ++k) acc[k] += ctx->timings[k];
-    nl += ctx->last_launches;
+    if (i > 0) {
+      s = complete(slot ^ 1);
+      if (s != SBG_OK) return finish(s);
+    }
   }
+  sbg_status s = complete((nfields - 1) & 1);
+  if (s != SBG_OK) return finish(s);
+  int* perr = (int*)ctx->hpin;
+  CU(cudaMemcpyAsync(perr, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  finish(SBG_OK);
+  if (*perr)
+    return fail(ctx, SBG_ERR_TIMEOUT, "tensor-core 4PCF kernel gave up waiting (code " + std::to_string(*perr) + ")");
   for (int k = 0; k < kStages; ++k) ctx->timings[k] = acc[k];
   ctx->last_launches = nl;
+  ctx->contraction_ms = kms;
   return SBG_OK;
 }
 
