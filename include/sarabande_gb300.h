@@ -138,8 +138,9 @@ typedef struct {
 } sbg_field2d;
 
 /* Many projected fields of uneven sizes (e.g. simulation snapshots) measured in
- * one call with shared nbins, mmax, precision and flags (the batch of Sec. 4,
- * each field as in sbg_projected).  Each entry's field and edges are read as
+ * one call with shared nbins, mmax, precision and flags (the paper measures
+ * one field per run; each field here is computed as in sbg_projected, Secs.
+ * 2.2 and 2.4).  Each entry's field and edges are read as
  * for sbg_projected; its zeta3 / zeta4 receive that field's outputs.  Fields
  * are queued back to back on the context's stream: field i + 1 is queued
  * before field i's results are copied to the caller, so all outputs are valid
