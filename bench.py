@@ -213,7 +213,7 @@ def run_reference(args):
     ws, rank, _ = dist_setup(args)
     if rank != 0:
         return
-    field, edges = field_for(0)
+    field, edges = field_for(0, args.grid)
     times = []
     for _ in range(args.warmup):
         oracle_sample(field, edges, heavy=False)
@@ -227,8 +227,8 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "fields/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "full 3D 4PCF, 256^3 float32 lognormal (sigma_G 1.5, P~k^-11/3), "
-                                  "lmax 4, 10 linear bins 2..32", "grid": 256, "nbins": NB, "lmax4": LMAX4},
+           "config": {"workload": f"full 3D 4PCF, {args.grid}^3 float32 lognormal (sigma_G 1.5, P~k^-11/3), "
+                                  "lmax 4, 10 linear bins 2..32", "grid": args.grid, "nbins": NB, "lmax4": LMAX4},
            "cpu_baseline": cb, "e2e": {"value": v, "unit": "fields/s", "h2d_bytes_per_step": 0,
                                        "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
