@@ -2,7 +2,7 @@
 bins 2..32), the full 3D path (delta -> delta-hat -> 150 convolution
 coefficient arrays -> pair x single contraction -> couplings) through the C ABI.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x3|fp32] [--impl gpu|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x3|tf32x3|fp32] [--impl gpu|reference]
 
 One JSON line on rank 0.  `value` is device-timed throughput with the field
 already in HBM; `e2e` is the same call with a pinned host field (host->device
@@ -43,9 +43,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--prec", default="auto", choices=["auto", "bf16x3", "fp32"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "bf16x3", "tf32x3", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--compare", type=int, default=1, help="also time the other precision (default on)")
+    ap.add_argument("--compare", type=int, default=1, help="also time the other precisions (default on)")
     ap.add_argument("--grid", type=int, default=256, help="grid side (256 is the benchmark workload; "
                     "smaller sides are for profiling captures only)")
     return ap.parse_args()
@@ -245,7 +245,8 @@ def run_gpu(args):
     prec_name = args.prec
     if prec_name == "auto":
         prec_name = "bf16x3" if getattr(sbg, "HAS_BF16X3", False) else "fp32"
-    prec = sbg.SBG_PREC_BF16X3 if prec_name == "bf16x3" else sbg.SBG_PREC_FP32
+    precs = {"bf16x3": sbg.SBG_PREC_BF16X3, "tf32x3": sbg.SBG_PREC_TF32X3, "fp32": sbg.SBG_PREC_FP32}
+    prec = precs[prec_name]
     ctx = sbg.Context(local)
     dfield = torch.from_numpy(field).cuda()
     flags = sbg.SBG_SUBTRACT_MEAN | sbg.SBG_4PCF
@@ -300,26 +301,31 @@ def run_gpu(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    if prec_name == "bf16x3":
-        bound, unit = "tensor", "TFLOP/s"
-        peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        peak_src = "of measured" if "bf16_tflops_sustained" in peaks else "of fallback"
-    else:
+    def peak_of(name):
+        if name == "bf16x3":
+            return ("tensor", peaks.get("bf16_tflops_sustained", 1700.0),
+                    "of measured" if "bf16_tflops_sustained" in peaks else "of fallback")
+        if name == "tf32x3":
+            # TF32 tensor rate = the measured BF16 rate x the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
+            b = peaks.get("bf16_tflops_sustained", 1700.0)
+            return ("tensor", b * 1.1 / 2.25, "of measured BF16 sustained x 1.1/2.25 (nominal TF32/BF16)")
         # FP32 SIMT: SMs x 128 FP32 lanes x 2 flops x the SM clock sampled under load
-        bound, unit = "alu", "TFLOP/s"
         mhz = clk["sm_mhz"] or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1447.0)
-        peak = props.multi_processor_count * 128 * 2 * mhz * 1e6 / 1e12
-        peak_src = f"derived: {props.multi_processor_count} SMs x 128 lanes x 2 x {mhz:.0f} MHz"
+        return ("alu", props.multi_processor_count * 128 * 2 * mhz * 1e6 / 1e12,
+                f"derived: {props.multi_processor_count} SMs x 128 lanes x 2 x {mhz:.0f} MHz")
+
+    bound, peak, peak_src = peak_of(prec_name)
+    unit = "TFLOP/s"
     achieved = alg_flops / (kernel_ms * 1e-3) / 1e12
     traffic = profiled_traffic(args.grid) if prec_name == "bf16x3" else None
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
             "traffic": traffic,
-            "kernel": "tc4_kernel" if prec_name == "bf16x3" else "simt4_kernel (3 launches)",
+            "kernel": "tc4_kernel" if prec_name != "fp32" else "simt4_kernel (3 launches)",
             "peak_source": peak_src, "alg_flops_per_launch": alg_flops, "avg_ms": kernel_ms}
     hbm = peaks.get("hbm_gbs", 6787.9)
     out = {"metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "bf16x3" if prec_name == "bf16x3" else "f32", "data": "synthetic",
+           "vs_baseline": None, "dtype": prec_name if prec_name != "fp32" else "f32", "data": "synthetic",
            "config": {"workload": f"full 3D 4PCF, {args.grid}^3 float32 lognormal (sigma_G 1.5, P~k^-11/3), "
                                   "lmax 4, 10 linear bins 2..32", "grid": args.grid, "nbins": NB, "lmax4": LMAX4,
                       "precision": prec_name,
@@ -338,22 +344,28 @@ def run_gpu(args):
            "e2e": {"value": ws * 1000.0 / e_ms, "unit": "fields/s", "h2d_bytes_per_step": int(field.nbytes),
                    "d2h_bytes_per_step": int(z4.nbytes)},
            "gpu_launches": launches, "clocks": clk, "wall_s_timed": wall}
-    # ---- the other precision of the same path, same workload (split-BF16 vs FP32) ----
+    # ---- the other precisions of the same path, same workload (split BF16 / split TF32 / FP32) ----
     if args.compare:
-        other = "fp32" if prec_name == "bf16x3" else "bf16x3"
-        oprec = sbg.SBG_PREC_FP32 if other == "fp32" else sbg.SBG_PREC_BF16X3
-        for _ in range(2):
-            sbg.sbg_full(ctx.h, dfield, edges, 0, LMAX4, oprec, flags, None, z4)
-        ost = []
-        for _ in range(max(1, min(args.steps, 3))):
-            sbg.sbg_full(ctx.h, dfield, edges, 0, LMAX4, oprec, flags, None, z4)
-            ost.append(sbg.sbg_last_timings(ctx.h))
-        ost = np.array(ost)
-        oms = float(ost[:, :7].sum(1).mean())
-        ocomb = float(ost[:, 5].mean())
-        out["compare"] = {"precision": other, "value": 1000.0 / oms, "ms_per_step": oms, "combination_ms": ocomb,
-                          "combination_achieved_tflops": alg_flops / (ocomb * 1e-3) / 1e12,
-                          "speedup_of_headline": oms / step_ms}
+        out["compare"] = []
+        for other in [n for n in ("fp32", "tf32x3", "bf16x3") if n != prec_name]:
+            oprec = precs[other]
+            for _ in range(2):
+                sbg.sbg_full(ctx.h, dfield, edges, 0, LMAX4, oprec, flags, None, z4)
+            ost, okern = [], []
+            for _ in range(max(1, min(args.steps, 3))):
+                sbg.sbg_full(ctx.h, dfield, edges, 0, LMAX4, oprec, flags, None, z4)
+                ost.append(sbg.sbg_last_timings(ctx.h))
+                okern.append(sbg.sbg_last_contraction_ms(ctx.h))
+            ost = np.array(ost)
+            oms = float(ost[:, :7].sum(1).mean())
+            kms = float(np.mean(okern))
+            obound, opeak, osrc = peak_of(other)
+            oach = alg_flops / (kms * 1e-3) / 1e12
+            out["compare"].append({"precision": other, "value": 1000.0 / oms, "ms_per_step": oms,
+                                   "contraction_kernel_ms": kms, "achieved_tflops": oach,
+                                   "roofline": {"bound": obound, "peak": opeak, "frac": oach / opeak,
+                                                "peak_source": osrc},
+                                   "headline_speedup_over_it": oms / step_ms})
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = oracle_sample(field, edges)
         out["cpu_baseline"].pop("seconds_per_field", None)

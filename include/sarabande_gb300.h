@@ -57,8 +57,11 @@ typedef enum { SBG_F32 = 0, SBG_F64 = 1 } sbg_dtype;
 /* Arithmetic of the 4PCF combination (FFTs are FP32, final sums FP64).
  * FP32: SIMT FP32 products and accumulation.
  * BF16X3: tcgen05 tensor cores, each operand split into bf16 hi + lo, three
- *         products hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM. */
-typedef enum { SBG_PREC_FP32 = 0, SBG_PREC_BF16X3 = 1 } sbg_precision;
+ *         products hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM.
+ * TF32X3: the same with tf32 hi + lo (hi rounded to 10 mantissa bits, lo the
+ *         exact remainder): more accurate, about twice the MMA work.
+ * (2 is reserved.) */
+typedef enum { SBG_PREC_FP32 = 0, SBG_PREC_BF16X3 = 1, SBG_PREC_TF32X3 = 3 } sbg_precision;
 
 enum {
   SBG_3PCF = 1u,            /* NPCF = 3 (Sec. 3.3 `NPCF`)                          */
@@ -160,7 +163,7 @@ sbg_status sbg_last_timings(const sbg_context* ctx, double* ms_per_stage, int* n
 
 /* Device time (ms, CUDA events on the context's stream) of the 4PCF
  * contraction kernel alone in the last measurement call: the tensor-core
- * kernel for SBG_PREC_BF16X3, the SIMT launches for SBG_PREC_FP32 (the sum
+ * kernel for SBG_PREC_BF16X3 / TF32X3, the SIMT launches for SBG_PREC_FP32 (the sum
  * over the pair products of Eq. mu, Sec. 2.3 / Eq. proj_4pcf_coeff, Sec. 2.4,
  * before the coupling step).  It is
  * part of stage [5] of sbg_last_timings; the rest of that stage is the B

@@ -883,7 +883,8 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
   // ---- 4PCF ----
   double* d_z4 = nullptr;
   if (do4) {
-    const bool tc = prec == SBG_PREC_BF16X3;
+    const bool tc = prec != SBG_PREC_FP32;         // split BF16 or split TF32 on the tensor cores
+    const bool tf = prec == SBG_PREC_TF32X3;
     ST(ensure_tables4(ctx, dim, nb, lmax4, tc));
     Tables4& t = *ctx->t4;
     const int cplx = dim == 2 ? 1 : 0;
@@ -913,12 +914,12 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
       ST(buf(ctx, "tccnt", (size_t)epochs * 4, (void**)&d_cnt));
       CU(cudaMemsetAsync(d_cnt, 0, (size_t)epochs * 4, ctx->stream));
       void* d_bimg;
-      ST(buf(ctx, "bimg", (size_t)(ng / 32) * (size_t)t.img_stride, &d_bimg));
+      ST(buf(ctx, "bimg", (size_t)(ng / 32) * (size_t)t.img_stride * (tf ? 2 : 1), &d_bimg));
       ctx->nlaunch += 1;  // bimage_kernel
       KL(launch_tc4(d_astore, d_bimg, (const BGroup*)t.d_bgroups.p, (int)t.bgroups.size(), t.chunks_per_kb,
                     t.img_stride, d_delta, ng, (const Tile4*)t.d_tiles[0].p, ntl, (const Row4*)t.d_rows.p,
                     (const int*)t.d_cols.p, (const int*)t.d_uniq.p, nsingle, cplx, best, d_T, d_cnt, d_err,
-                    ctx->nsm, ctx->stream, ctx->kev[0], ctx->kev[1]));
+                    ctx->nsm, ctx->stream, ctx->kev[0], ctx->kev[1], tf ? 1 : 0));
       ctx->kev_used = true;
       if (!ctx->defer) {  // a batch reads the flag once, after its last field
         int* perr;
@@ -1109,7 +1110,8 @@ sbg_status sbg_full(sbg_context* ctx, const void* field, sbg_dtype dtype, const 
   ctx->err.clear();
   if (!field || !shape || !edges) return fail(ctx, SBG_ERR_INVALID_ARG, "null field, shape or edges");
   if (dtype != SBG_F32 && dtype != SBG_F64) return fail(ctx, SBG_ERR_INVALID_ARG, "dtype");
-  if (prec != SBG_PREC_FP32 && prec != SBG_PREC_BF16X3) return fail(ctx, SBG_ERR_INVALID_ARG, "precision");
+  if (prec != SBG_PREC_FP32 && prec != SBG_PREC_BF16X3 && prec != SBG_PREC_TF32X3)
+    return fail(ctx, SBG_ERR_INVALID_ARG, "precision");
   if (flags & ~31u) return fail(ctx, SBG_ERR_INVALID_ARG, "unknown flag bits");
   if (!(flags & (SBG_3PCF | SBG_4PCF))) return fail(ctx, SBG_ERR_INVALID_ARG, "neither SBG_3PCF nor SBG_4PCF");
   if (nbins < 1 || nbins > kMaxBins) return fail(ctx, SBG_ERR_INVALID_ARG, "nbins must be 1..20");
@@ -1130,7 +1132,8 @@ sbg_status sbg_projected(sbg_context* ctx, const void* field, sbg_dtype dtype, c
   ctx->err.clear();
   if (!field || !shape || !edges) return fail(ctx, SBG_ERR_INVALID_ARG, "null field, shape or edges");
   if (dtype != SBG_F32 && dtype != SBG_F64) return fail(ctx, SBG_ERR_INVALID_ARG, "dtype");
-  if (prec != SBG_PREC_FP32 && prec != SBG_PREC_BF16X3) return fail(ctx, SBG_ERR_INVALID_ARG, "precision");
+  if (prec != SBG_PREC_FP32 && prec != SBG_PREC_BF16X3 && prec != SBG_PREC_TF32X3)
+    return fail(ctx, SBG_ERR_INVALID_ARG, "precision");
   if (flags & ~31u) return fail(ctx, SBG_ERR_INVALID_ARG, "unknown flag bits");
   if (!(flags & (SBG_3PCF | SBG_4PCF))) return fail(ctx, SBG_ERR_INVALID_ARG, "neither SBG_3PCF nor SBG_4PCF");
   if (nbins < 1 || nbins > kMaxBins) return fail(ctx, SBG_ERR_INVALID_ARG, "nbins must be 1..20");

@@ -52,8 +52,9 @@ cudaError_t launch_simt4(const float2* astore, long long ng, const float* delta,
 // 2D two); per K-block the group's B operand is an image of n hi rows then n
 // lo rows of 128 bytes (n = B rows rounded up to 16) at byte `off` of the
 // K-block's img_stride-byte slab of `bimg` (nkb * img_stride bytes, written by
-// the launcher).  *err is set (never cleared) if a bounded wait inside the
-// kernel expired.
+// the launcher).  tf32 != 0 selects split TF32 products: every image, offset
+// and stride is twice as large (bimg must hold 2 * nkb * img_stride bytes).
+// *err is set (never cleared) if a bounded wait inside the kernel expired.
 constexpr int kTcMaxRowSlots = 56;  // row singles staged per K-block
 constexpr int kTcEpoch = 256;       // K-blocks between progress checkpoints of the lag limiter
 struct BGroup {
@@ -69,7 +70,7 @@ cudaError_t launch_tc4(const float2* astore, void* bimg, const BGroup* bgroups, 
                        long long img_stride, const float* delta, long long ng, const Tile4* tiles, int ntiles,
                        const Row4* rows, const int* cols, const int* slots, int nsingle, int complex_out,
                        int nsplit, double* T, int* cnt, int* err, int nsm, cudaStream_t st,
-                       cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
+                       cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr, int tf32 = 0);
 
 // ---- finalisation ----
 // zeta[o] = sum_{e in [ptr[o], ptr[o+1])} coef[e] * T[idx[e]] (idx < 0: conj of T[-idx-1]).

@@ -50,10 +50,7 @@ namespace sbg {
 
 namespace {
 
-constexpr int kGroups = 4;             // producer groups; group g owns operand stage g
-constexpr int kRS = 2 * kGroups;       // raw stages: two per group (2g, 2g + 1)
-constexpr int kOS = kGroups;           // operand stages (A in TMEM, B in shared memory)
-constexpr int kFlush = 256;            // K-blocks per inner accumulation range
+constexpr int kRS = 8;                // raw stages, split evenly over the producer groups
 constexpr int kKX = 32;                // grid points per K-block (64 bf16 = one 128-B row)
 constexpr int kProdWarps = 16;         // producer warps 0..15
 constexpr int kMmaWarp = kProdWarps;   // warp 16
@@ -62,7 +59,36 @@ constexpr int kLoad0 = kMmaWarp + 1;
 constexpr int kLoaders = kLoadWarps * 32;
 constexpr int kBWarp = kLoad0 + kLoadWarps;  // warp 19: B tiles
 constexpr int kThreads = (kBWarp + 1) * 32;
-constexpr int kOpStage = 128 * 128;   // B tile: n hi rows, then n lo rows (n <= 64), 128 B each
+// Per precision of the split products:
+//   split BF16 (kind::f16): 4 producer groups of 4 warps, K = 16 per MMA, an A
+//     tile of 64 TMEM columns (32 hi, 32 lo) and B rows of one 128-byte atom;
+//   split TF32 (kind::tf32): 2 groups of 8 warps (two warps per TMEM lane
+//     quarter, each forming half of the points), K = 8 per MMA, an A tile of
+//     128 columns (64 hi, 64 lo) and B rows of two 128-byte atoms (K 0..31 and
+//     32..63).
+// Either way operand stage g belongs to group g, the A tiles fill TMEM columns
+// [192, 448) and the B tiles 64 KB of shared memory.
+template <bool TF>
+struct Cfg {
+  static constexpr int kGroups = TF ? 2 : 4;
+  static constexpr int kWarps = 16 / kGroups;          // producer warps per group
+  static constexpr int kParts = kWarps / 4;            // point ranges per TMEM lane quarter
+  static constexpr int kOS = kGroups;                  // operand stages
+  static constexpr int kRawPer = kRS / kGroups;        // raw stages per group
+  static constexpr int kAtoms = TF ? 2 : 1;            // 128-byte swizzle atoms per B row (64 K values)
+  static constexpr int kACols = 64 * kAtoms;           // TMEM columns of an A tile (hi then lo)
+  static constexpr int kOpStage = 128 * 128 * kAtoms;  // B tile: n hi rows, then n lo rows (n <= 64)
+  static constexpr int kKSteps = TF ? 8 : 4;           // MMA K steps per K-block
+  static constexpr uint32_t kFmt = TF ? 2u : 1u;       // A/B format in the instruction descriptor
+  // K-blocks per TMEM accumulation range before the fold into the outer
+  // accumulator (FP32 with round-to-nearest on the CUDA cores).  The error of
+  // the tensor core's accumulation grows with the range: measured on the 32^3
+  // test field, split TF32 reaches 3.2e-5 of max|zeta| with 256-K-block ranges,
+  // 7.6e-6 with 32 and 2.1e-6 with 8, at 240 / 250 / 282 ms per 256^3 field.
+  // Split TF32 is the accurate option, so its ranges are 8 K-blocks; split BF16
+  // keeps 256 (1.9e-5, its bf16 split dominates).
+  static constexpr int kFlush = TF ? 8 : 256;
+};
 // TMEM columns: the inner accumulator [0, 128) of the current 256-K-block range
 // (columns [0, n) collect Ahi Bhi + Alo Bhi, [n, 2n) Ahi Blo), the outer
 // accumulator [128, 192), then one 64-column A stage per operand stage
@@ -76,8 +102,9 @@ constexpr int kTmemCols = 512;
 constexpr int kRawRow = kKX * 8 + 16;
 constexpr int kRawStage = kTcMaxRowSlots * kRawRow;
 constexpr int kLag = 4;                // epochs a loader may run ahead of the slowest CTA
-constexpr int kMeta = 512;             // barriers (2 kRS + 3 kOS + 1) and the TMEM address
-constexpr int kSmem = kOS * kOpStage + kRS * kRawStage + kMeta + 1024;
+constexpr int kMeta = 512;             // barriers (2 kRS + 3 * 4 + 1) and the TMEM address
+constexpr int kOpBytes = 4 * 128 * 128;  // B tiles of every operand stage (both precisions)
+constexpr int kSmem = kOpBytes + kRS * kRawStage + kMeta + 1024;
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -182,14 +209,36 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// D += A B with A (128 x 16 bf16) in tensor memory, B in shared memory
-__device__ __forceinline__ void mma_bf16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc,
-                                            uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "r"(tmem_a), "l"(b), "r"(idesc), "r"(acc));
+// D += A B with A (128 x K) in tensor memory, B in shared memory; K = 16 bf16
+// (kind::f16) or 8 tf32 (kind::tf32)
+template <bool TF>
+__device__ __forceinline__ void mma_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (TF) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(b), "r"(idesc), "r"(acc));
+  }
+}
+// v rounded to TF32 (10 explicit mantissa bits), as an FP32 bit pattern
+__device__ __forceinline__ float tf32_rna(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ void tmem_st8_nw(uint32_t taddr, const float (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+               "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+               : "memory");
 }
 __device__ __forceinline__ void tmem_st4_nw(uint32_t taddr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(a), "r"(b),
@@ -278,15 +327,19 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(bar)) : "memory");
 }
 
+template <bool TF>
 __global__ void __launch_bounds__(kThreads, 1)
 tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, const BGroup* __restrict__ bgroups,
            long long img_stride, long long ng, const Tile4* __restrict__ tiles, int ntiles,
            const Row4* __restrict__ rows, const int* __restrict__ slots, int nsingle, int cplx, int nsplit,
            double* __restrict__ T, int* cnt, int* err_flag) {
+  using C = Cfg<TF>;
+  constexpr int kGroups = C::kGroups, kOS = C::kOS, kOpStage = C::kOpStage, kRawPer = C::kRawPer;
+  constexpr int kFlush = C::kFlush;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* op_base = sm;
-  uint8_t* raw_base = sm + kOS * kOpStage;
+  uint8_t* raw_base = sm + kOpBytes;
   uint64_t* bars = (uint64_t*)(raw_base + kRS * kRawStage);
   uint64_t* raw_full = bars;
   uint64_t* raw_empty = bars + kRS;
@@ -307,10 +360,10 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
   if (tid == 0) {
     for (int i = 0; i < kRS; ++i) {
       mbar_init(&raw_full[i], kLoaders);              // one cp.async completion per loader thread
-      mbar_init(&raw_empty[i], kProdWarps / kGroups); // one arrival per warp of the owning group
+      mbar_init(&raw_empty[i], C::kWarps);            // one arrival per warp of the owning group
     }
     for (int i = 0; i < kOS; ++i) {
-      mbar_init(&op_full[i], kProdWarps / kGroups);
+      mbar_init(&op_full[i], C::kWarps);
       mbar_init(&op_empty[i], 1);                     // tcgen05.commit
     }
     for (int i = 0; i < kOS; ++i) mbar_init(&b_full[i], 1);  // expect_tx arrival + bytes
@@ -333,13 +386,13 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
     // 128 bytes) into operand stage kb % 4, once the MMAs of K-block kb - 4 have
     // released it.
     if (lane == 0) {
-      uint32_t issued[kOS] = {0, 0, 0, 0};
+      uint32_t issued[kOS] = {};
       bool ok = true;
       for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
         const Unit it = unit_of(u, ntiles, nsplit, ng);
         const Tile4 tl = tiles[it.tile];
         const BGroup bg = bgroups[tl.bgroup];
-        const uint32_t bytes = (uint32_t)bg.n * 256;
+        const uint32_t bytes = (uint32_t)bg.n * 256 * C::kAtoms;
         for (int kb = 0; kb < it.nk; ++kb) {
           const int os = kb % kOS;
           if (!mbar_wait(&op_empty[os], (issued[os] & 1) ^ 1, err, 41)) {
@@ -348,7 +401,8 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
           }
           ++issued[os];
           mbar_expect_tx(&b_full[os], bytes);
-          bulk_g2s(op_base + os * kOpStage, bimg + ((it.x0 >> 5) + kb) * img_stride + bg.off, bytes, &b_full[os]);
+          bulk_g2s(op_base + os * kOpStage, bimg + ((it.x0 >> 5) + kb) * img_stride + bg.off * C::kAtoms, bytes,
+                   &b_full[os]);
         }
       }
       // every copy issued has landed before the CTA may exit
@@ -362,7 +416,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
     const int rq = li >> 4;            // slots rq, rq + kLoaders / 16, ...
     constexpr int kSlotStep = kLoaders / 16;
     constexpr int kSlotIter = (kTcMaxRowSlots + kSlotStep - 1) / kSlotStep;
-    uint32_t gcount[kGroups] = {0, 0, 0, 0};  // K-blocks loaded so far for each producer group
+    uint32_t gcount[kGroups] = {};  // K-blocks loaded so far for each producer group
     bool ok = true;
     for (long long rd = 0; rd < nrounds && ok; ++rd) {
       const long long u = rd * gridDim.x + blockIdx.x;
@@ -392,8 +446,8 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
         for (int kb = e * kTcEpoch; kb < kb1; ++kb) {
           const int gg = kb % kGroups;
           const uint32_t n = gcount[gg]++;
-          const int rs = 2 * gg + (n & 1);
-          if (!warp_wait(&raw_empty[rs], ((n >> 1) & 1) ^ 1, err, 11)) {
+          const int rs = kRawPer * gg + (int)(n % kRawPer);
+          if (!warp_wait(&raw_empty[rs], ((n / kRawPer) & 1) ^ 1, err, 11)) {
             ok = false;
             break;
           }
@@ -415,7 +469,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
   } else if (warp == kMmaWarp) {
     // ---------------------------------------------------------------- MMA --
     if (lane == 0) {
-      uint32_t uses[kOS] = {0, 0, 0, 0};
+      uint32_t uses[kOS] = {};
       bool ok = true;
       for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
         const Unit it = unit_of(u, ntiles, nsplit, ng);
@@ -423,7 +477,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
         const int N = n_mma(tl, cplx);
         // BF16 inputs, FP32 accumulator, K-major A and B, M = 128; N = n for
         // Alo Bhi and N = 2n for Ahi [Bhi | Blo]
-        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+        const uint32_t idesc = (1u << 4) | (C::kFmt << 7) | (C::kFmt << 10) | ((uint32_t)(N >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
         const uint32_t idesc2 = (idesc & ~(0x3Fu << 17)) | ((uint32_t)((2 * N) >> 3) << 17);
         for (int kb = 0; kb < it.nk; ++kb) {
@@ -436,14 +490,17 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
           tc_fence_after();
           // B descriptor of the stage; K step k starts 32 bytes further (+2 in
           // the descriptor's 16-byte address field, which cannot carry out)
+          // (an atom of 2n rows x 128 B holds 32 K values, of 4 K steps for TF32)
           const uint64_t bd = sdesc(su32(op_base + os * kOpStage));
-          const uint32_t a_hi = tmem + kTmemA0 + 64 * os, a_lo = a_hi + 32;
+          const uint32_t a_hi = tmem + kTmemA0 + C::kACols * os, a_lo = a_hi + C::kACols / 2;
           const uint32_t acc0 = (kb % kFlush) == 0 ? 0u : 1u;
-          // two MMAs per 16-wide K step: Ahi meets Bhi and Blo in one (N = 2n)
+          // two MMAs per K step: Ahi meets Bhi and Blo in one (N = 2n); a K step
+          // is 8 TMEM columns of A in both precisions
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            mma_bf16_ts(tmem, a_hi + 8 * k, bd + 2 * k, idesc2, k == 0 ? acc0 : 1u);
-            mma_bf16_ts(tmem, a_lo + 8 * k, bd + 2 * k, idesc, 1u);
+          for (int k = 0; k < C::kKSteps; ++k) {
+            const uint64_t bk = bd + 2 * (k & 3) + (uint64_t)((k >> 2) * 2 * N * 128 / 16);
+            mma_ts<TF>(tmem, a_hi + 8 * k, bk, idesc2, k == 0 ? acc0 : 1u);
+            mma_ts<TF>(tmem, a_lo + 8 * k, bk, idesc, 1u);
           }
           mma_commit(&op_empty[os]);
           if ((kb + 1) % kFlush == 0 || kb + 1 == it.nk) mma_commit(acc_full);
@@ -453,7 +510,8 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
   } else {
     // ---------------------------------------------------------- producers --
     const int quarter = warp & 3;        // TMEM lane quarter = rows 32 quarter .. +31
-    const int grp = warp >> 2;           // producer group: K-blocks kb = grp (mod 4), stage grp
+    const int grp = warp / C::kWarps;    // producer group: K-blocks kb = grp (mod kGroups), stage grp
+    const int part = (warp % C::kWarps) >> 2;  // which 32 / kParts points of the K-block this warp forms
     const int row = quarter * 32 + lane; // the A row (TMEM lane) this thread writes
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     const int os = grp;
@@ -514,16 +572,18 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
       };
       for (int kb = grp; kb < it.nk && ok; kb += kGroups) {
         // group 0 produces the first K-block of every range: fold the previous
-        // range first, whose inner accumulator this range overwrites
-        if (grp == 0 && kb % kFlush == 0 && kb / kFlush >= 1) {
+        // range first, whose inner accumulator this range overwrites (the warps
+        // of part 0 fold; the MMA waits for every warp of the group anyway)
+        if (grp == 0 && part == 0 && kb % kFlush == 0 && kb / kFlush >= 1) {
           if (!fold(kb / kFlush - 1)) {
             ok = false;
             break;
           }
           flushed = kb / kFlush;
         }
-        const int rs = 2 * grp + (uses & 1);
-        if (!warp_wait(&raw_full[rs], (uses >> 1) & 1, err, 31) || !warp_wait(&op_empty[os], (uses & 1) ^ 1, err, 32)) {
+        const int rs = kRawPer * grp + (int)(uses % kRawPer);
+        if (!warp_wait(&raw_full[rs], (uses / kRawPer) & 1, err, 31) ||
+            !warp_wait(&op_empty[os], (uses & 1) ^ 1, err, 32)) {
           ok = false;
           break;
         }
@@ -531,9 +591,9 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
         tc_fence_after();
         const uint8_t* raw = raw_base + rs * kRawStage;
         // ---- A: the 32 pair products of this thread's row, to TMEM ----
-        const uint32_t acol = tmem + lane_addr + kTmemA0 + 64 * os;
+        const uint32_t acol = tmem + lane_addr + kTmemA0 + C::kACols * os;
 #pragma unroll 1
-        for (int cq = 0; cq < 4; ++cq) {  // points 8 cq .. 8 cq + 7
+        for (int cq = part * (4 / C::kParts); cq < (part + 1) * (4 / C::kParts); ++cq) {  // points 8 cq .. +7
           const float4* p1 = (const float4*)(raw + r1 + 32 * cq);  // Re at +0, Im at +128 bytes
           const float4* p2 = (const float4*)(raw + r2 + 32 * cq);
           const float4 ra0 = p1[0], ra1 = p1[1], ia0 = p1[8], ia1 = p1[9];
@@ -542,7 +602,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
           const float fi1[8] = {ia0.x, ia0.y, ia0.z, ia0.w, ia1.x, ia1.y, ia1.z, ia1.w};
           const float fr2[8] = {rb0.x, rb0.y, rb0.z, rb0.w, rb1.x, rb1.y, rb1.z, rb1.w};
           const float fi2[8] = {ib0.x, ib0.y, ib0.z, ib0.w, ib1.x, ib1.y, ib1.z, ib1.w};
-          uint32_t hr[4], lr[4], hi[4], li[4];
+          uint64_t prs[4], pis[4];
 #pragma unroll
           for (int p2 = 0; p2 < 4; ++p2) {
             const uint64_t ar = pk(fr1[2 * p2], fr1[2 * p2 + 1]);
@@ -550,15 +610,39 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
             const uint64_t br = pk(fr2[2 * p2], fr2[2 * p2 + 1]);
             const uint64_t bi0 = pk(fi2[2 * p2], fi2[2 * p2 + 1]);
             const uint64_t bi = mul2(bi0, as2), nbi = mul2(bi0, ans2);
-            const uint64_t pr = fma2(ar, br, mul2(ai, nbi));   // ar br - ai bi
-            const uint64_t pi = fma2(ar, bi, mul2(ai, br));    // ar bi + ai br
-            split_pair(pr, hr[p2], lr[p2]);
-            split_pair(pi, hi[p2], li[p2]);
+            prs[p2] = fma2(ar, br, mul2(ai, nbi));   // ar br - ai bi
+            pis[p2] = fma2(ar, bi, mul2(ai, br));    // ar bi + ai br
           }
-          tmem_st4_nw(acol + 4 * cq, hr[0], hr[1], hr[2], hr[3]);        // hi, real parts
-          tmem_st4_nw(acol + 16 + 4 * cq, hi[0], hi[1], hi[2], hi[3]);   // hi, imaginary parts
-          tmem_st4_nw(acol + 32 + 4 * cq, lr[0], lr[1], lr[2], lr[3]);   // lo, real parts
-          tmem_st4_nw(acol + 48 + 4 * cq, li[0], li[1], li[2], li[3]);   // lo, imaginary parts
+          if constexpr (TF) {
+            // A K order: Re x0..x31 then Im x0..x31, one tf32 per column; hi in
+            // columns [0, 64), lo = value - hi in [64, 128)
+            float hr[8], lr[8], hi[8], li[8];
+#pragma unroll
+            for (int p2 = 0; p2 < 4; ++p2) {
+              float r0, r1, i0, i1;
+              upk(prs[p2], r0, r1);
+              upk(pis[p2], i0, i1);
+              hr[2 * p2] = tf32_rna(r0); hr[2 * p2 + 1] = tf32_rna(r1);
+              hi[2 * p2] = tf32_rna(i0); hi[2 * p2 + 1] = tf32_rna(i1);
+              upk(sub2(prs[p2], pk(hr[2 * p2], hr[2 * p2 + 1])), lr[2 * p2], lr[2 * p2 + 1]);
+              upk(sub2(pis[p2], pk(hi[2 * p2], hi[2 * p2 + 1])), li[2 * p2], li[2 * p2 + 1]);
+            }
+            tmem_st8_nw(acol + 8 * cq, hr);        // hi, real parts
+            tmem_st8_nw(acol + 32 + 8 * cq, hi);   // hi, imaginary parts
+            tmem_st8_nw(acol + 64 + 8 * cq, lr);   // lo, real parts
+            tmem_st8_nw(acol + 96 + 8 * cq, li);   // lo, imaginary parts
+          } else {
+            uint32_t hr[4], lr[4], hi[4], li[4];
+#pragma unroll
+            for (int p2 = 0; p2 < 4; ++p2) {
+              split_pair(prs[p2], hr[p2], lr[p2]);
+              split_pair(pis[p2], hi[p2], li[p2]);
+            }
+            tmem_st4_nw(acol + 4 * cq, hr[0], hr[1], hr[2], hr[3]);        // hi, real parts
+            tmem_st4_nw(acol + 16 + 4 * cq, hi[0], hi[1], hi[2], hi[3]);   // hi, imaginary parts
+            tmem_st4_nw(acol + 32 + 4 * cq, lr[0], lr[1], lr[2], lr[3]);   // lo, real parts
+            tmem_st4_nw(acol + 48 + 4 * cq, li[0], li[1], li[2], li[3]);   // lo, imaginary parts
+          }
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
@@ -570,7 +654,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
         }
       }
       // group 0: fold the ranges not folded yet, the last one into T
-      if (grp == 0 && ok) {
+      if (grp == 0 && part == 0 && ok) {
         for (int i = flushed; i < nranges && ok; ++i)
           if (!fold(i)) ok = false;
       }
@@ -585,51 +669,114 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
 }
 
 // B image of every K-block: for each column group (the columns shared by the
-// tiles of one m3 block), 2n rows of 64 bf16 in the 128-byte-swizzled K-major
+// tiles of one m3 block), 2n rows of 64 values in the 128-byte-swizzled K-major
 // layout the MMA reads, rows [0, n) the hi parts and rows [n, 2n) the lo parts
 // of the B rows (3D column c: (Re v, -Im v) of single cols[col0 + c]; 2D column
 // c: (Re v, -Im v) for even c and (Im v, Re v) for odd c of single
-// cols[col0 + c / 2]; v = delta * a; zero past the group's columns).  One
-// thread writes one 16-byte chunk (8 K values) of a hi row and of its lo row.
+// cols[col0 + c / 2]; v = delta * a; zero past the group's columns).  BF16: one
+// 128-byte atom per row; TF32: two atoms (K 0..31, then K 32..63), each 2n rows.
+// One thread writes one 16-byte chunk of a hi row and of its lo row.
+template <bool TF>
 __global__ void bimage_kernel(const float* __restrict__ astore, const float* __restrict__ delta, long long nkb,
                               int nsingle, int cplx, const BGroup* __restrict__ groups, const int* __restrict__ cols,
                               int chunks_per_kb, long long img_stride, uint8_t* __restrict__ bimg) {
+  constexpr int kAtoms = Cfg<TF>::kAtoms;
+  constexpr int kPer = TF ? 4 : 8;  // values per 16-byte chunk
   const long long total = nkb * chunks_per_kb;
   for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total;
        w += (long long)gridDim.x * blockDim.x) {
     const long long xb = w / chunks_per_kb;
     int r = (int)(w - xb * chunks_per_kb);
     int g = 0;
-    while (r >= groups[g].n * 8) {
-      r -= groups[g].n * 8;
+    while (r >= groups[g].n * 8 * kAtoms) {
+      r -= groups[g].n * 8 * kAtoms;
       ++g;
     }
     const BGroup bg = groups[g];
-    const int c = r >> 3, j = r & 7;
-    const int second = j >> 2, p0 = (j & 3) * 8;  // K values 8j..8j+7: points p0.. of one half
+    const int c = r / (8 * kAtoms), j = r % (8 * kAtoms);
+    const int atom = j >> 3, jj = j & 7;
+    const int k0 = TF ? 32 * atom + 4 * jj : 8 * jj;  // first K value of the chunk
+    const int second = k0 >> 5, p0 = k0 & 31;          // K 32..63: the second half of the row
     const int cs = cplx ? (c >> 1) : c;
     uint4 hi = make_uint4(0, 0, 0, 0), lo = make_uint4(0, 0, 0, 0);
     if (cs < bg.ncols) {
       const float* a = astore + (xb * nsingle + cols[bg.col0 + cs]) * 64;
-      const float4* ap = (const float4*)(a + (((cplx && (c & 1)) ? !second : second) ? 32 : 0) + p0);
-      const float4* dp = (const float4*)(delta + xb * 32 + p0);
+      const float* ap = a + (((cplx && (c & 1)) ? !second : second) ? 32 : 0) + p0;
+      const float* dp = delta + xb * 32 + p0;
       // component: Re v for (even, first half) and (odd, second half); Im v otherwise,
       // negated for (even, second half)
       const float sg = (!(cplx && (c & 1)) && second) ? -1.f : 1.f;
-      const float4 a0 = ap[0], a1 = ap[1], d0 = dp[0], d1 = dp[1];
-      uint32_t h[4], l[4];
-      split_pair(pk(sg * (d0.x * a0.x), sg * (d0.y * a0.y)), h[0], l[0]);
-      split_pair(pk(sg * (d0.z * a0.z), sg * (d0.w * a0.w)), h[1], l[1]);
-      split_pair(pk(sg * (d1.x * a1.x), sg * (d1.y * a1.y)), h[2], l[2]);
-      split_pair(pk(sg * (d1.z * a1.z), sg * (d1.w * a1.w)), h[3], l[3]);
-      hi = make_uint4(h[0], h[1], h[2], h[3]);
-      lo = make_uint4(l[0], l[1], l[2], l[3]);
+      if constexpr (TF) {
+        const float4 a0 = *(const float4*)ap, d0 = *(const float4*)dp;
+        const float v[4] = {sg * (d0.x * a0.x), sg * (d0.y * a0.y), sg * (d0.z * a0.z), sg * (d0.w * a0.w)};
+        float h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          h[e] = tf32_rna(v[e]);
+          l[e] = v[e] - h[e];
+        }
+        hi = make_uint4(__float_as_uint(h[0]), __float_as_uint(h[1]), __float_as_uint(h[2]), __float_as_uint(h[3]));
+        lo = make_uint4(__float_as_uint(l[0]), __float_as_uint(l[1]), __float_as_uint(l[2]), __float_as_uint(l[3]));
+      } else {
+        const float4 a0 = ((const float4*)ap)[0], a1 = ((const float4*)ap)[1];
+        const float4 d0 = ((const float4*)dp)[0], d1 = ((const float4*)dp)[1];
+        uint32_t h[4], l[4];
+        split_pair(pk(sg * (d0.x * a0.x), sg * (d0.y * a0.y)), h[0], l[0]);
+        split_pair(pk(sg * (d0.z * a0.z), sg * (d0.w * a0.w)), h[1], l[1]);
+        split_pair(pk(sg * (d1.x * a1.x), sg * (d1.y * a1.y)), h[2], l[2]);
+        split_pair(pk(sg * (d1.z * a1.z), sg * (d1.w * a1.w)), h[3], l[3]);
+        hi = make_uint4(h[0], h[1], h[2], h[3]);
+        lo = make_uint4(l[0], l[1], l[2], l[3]);
+      }
+      (void)kPer;
     }
-    uint8_t* img = bimg + xb * img_stride + bg.off;
-    const int pos = (j ^ (c & 7)) << 4;  // rows c and n + c share c & 7 (n is a multiple of 16)
+    uint8_t* img = bimg + xb * img_stride + bg.off * kAtoms + atom * (2 * bg.n * 128);
+    const int pos = (jj ^ (c & 7)) << 4;  // rows c and n + c share c & 7 (n is a multiple of 16)
     *(uint4*)(img + c * 128 + pos) = hi;
     *(uint4*)(img + (bg.n + c) * 128 + pos) = lo;
   }
+}
+
+template <bool TF>
+cudaError_t launch_tc4_t(const float2* astore, void* bimg, const BGroup* bgroups, int chunks_per_kb,
+                         long long img_stride, const float* delta, long long ng, const Tile4* tiles, int ntiles,
+                         const Row4* rows, const int* cols, const int* slots, int nsingle, int complex_out,
+                         int nsplit, double* T, int* cnt, int* err, int nsm, cudaStream_t st, cudaEvent_t ev_begin,
+                         cudaEvent_t ev_end) {
+  constexpr int kAtoms = Cfg<TF>::kAtoms;
+  const long long stride = img_stride * kAtoms;  // the tables give BF16 image offsets
+  // B images of every K-block, once per field
+  {
+    const long long nkb = ng / kKX;
+    const int cpk = chunks_per_kb * kAtoms;
+    long long blocks = (nkb * cpk + 255) / 256;
+    if (blocks > (long long)nsm * 32) blocks = (long long)nsm * 32;
+    bimage_kernel<TF><<<(unsigned)blocks, 256, 0, st>>>((const float*)astore, delta, nkb, nsingle, complex_out,
+                                                        bgroups, cols, cpk, stride, (uint8_t*)bimg);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(tc4_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc4_kernel<TF>, kThreads, kSmem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const float* af = (const float*)astore;
+  const uint8_t* bi = (const uint8_t*)bimg;
+  const int grid = nsm;  // every CTA takes part in every round so that the progress counters fill up
+  void* args[] = {(void*)&af,    (void*)&bi,      (void*)&bgroups, (void*)&stride,     (void*)&ng,
+                  (void*)&tiles, (void*)&ntiles,  (void*)&rows,    (void*)&slots,      (void*)&nsingle,
+                  (void*)&complex_out, (void*)&nsplit, (void*)&T,  (void*)&cnt,        (void*)&err};
+  if (ev_begin && (e = cudaEventRecord(ev_begin, st)) != cudaSuccess) return e;
+  e = cudaLaunchCooperativeKernel((const void*)tc4_kernel<TF>, dim3(grid), dim3(kThreads), args, kSmem, st);
+  if (e != cudaSuccess) return e;
+  if (ev_end && (e = cudaEventRecord(ev_end, st)) != cudaSuccess) return e;
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -638,40 +785,14 @@ cudaError_t launch_tc4(const float2* astore, void* bimg, const BGroup* bgroups, 
                        long long img_stride, const float* delta, long long ng, const Tile4* tiles, int ntiles,
                        const Row4* rows, const int* cols, const int* slots, int nsingle, int complex_out,
                        int nsplit, double* T, int* cnt, int* err, int nsm, cudaStream_t st, cudaEvent_t ev_begin,
-                       cudaEvent_t ev_end) {
+                       cudaEvent_t ev_end, int tf32) {
   if (ntiles <= 0) return cudaSuccess;
   if (ng % kKX || nbgroups <= 0 || chunks_per_kb <= 0 || img_stride % 1024) return cudaErrorInvalidValue;
-  // B images of every K-block, once per field
-  {
-    const long long nkb = ng / kKX;
-    long long blocks = (nkb * chunks_per_kb + 255) / 256;
-    if (blocks > (long long)nsm * 32) blocks = (long long)nsm * 32;
-    bimage_kernel<<<(unsigned)blocks, 256, 0, st>>>((const float*)astore, delta, nkb, nsingle, complex_out,
-                                                    bgroups, cols, chunks_per_kb, img_stride, (uint8_t*)bimg);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(tc4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc4_kernel, kThreads, kSmem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const float* af = (const float*)astore;
-  const uint8_t* bi = (const uint8_t*)bimg;
-  const int grid = nsm;  // every CTA takes part in every round so that the progress counters fill up
-  void* args[] = {(void*)&af,    (void*)&bi,      (void*)&bgroups, (void*)&img_stride, (void*)&ng,
-                  (void*)&tiles, (void*)&ntiles,  (void*)&rows,    (void*)&slots,      (void*)&nsingle,
-                  (void*)&complex_out, (void*)&nsplit, (void*)&T,  (void*)&cnt,        (void*)&err};
-  if (ev_begin && (e = cudaEventRecord(ev_begin, st)) != cudaSuccess) return e;
-  e = cudaLaunchCooperativeKernel((const void*)tc4_kernel, dim3(grid), dim3(kThreads), args, kSmem, st);
-  if (e != cudaSuccess) return e;
-  if (ev_end && (e = cudaEventRecord(ev_end, st)) != cudaSuccess) return e;
-  return cudaGetLastError();
+  if (tf32)
+    return launch_tc4_t<true>(astore, bimg, bgroups, chunks_per_kb, img_stride, delta, ng, tiles, ntiles, rows, cols,
+                              slots, nsingle, complex_out, nsplit, T, cnt, err, nsm, st, ev_begin, ev_end);
+  return launch_tc4_t<false>(astore, bimg, bgroups, chunks_per_kb, img_stride, delta, ng, tiles, ntiles, rows, cols,
+                             slots, nsingle, complex_out, nsplit, T, cnt, err, nsm, st, ev_begin, ev_end);
 }
 
 }  // namespace sbg

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_PKG, "libsarabande_gb300.so")
 
 SBG_OK = 0
 SBG_F32, SBG_F64 = 0, 1
-SBG_PREC_FP32, SBG_PREC_BF16X3 = 0, 1
+SBG_PREC_FP32, SBG_PREC_BF16X3, SBG_PREC_TF32X3 = 0, 1, 3
 HAS_BF16X3 = True  # the tcgen05 split-BF16 4PCF combination is built in
 SBG_3PCF, SBG_4PCF, SBG_NORMALIZED, SBG_SUBTRACT_MEAN, SBG_FIELD_ON_DEVICE = 1, 2, 4, 8, 16
 STATUS = {0: "SBG_OK", -1: "SBG_ERR_INVALID_ARG", -2: "SBG_ERR_UNSUPPORTED_SHAPE", -3: "SBG_ERR_BIN_RANGE",

@@ -1,5 +1,5 @@
 """Error per coefficient of the full 3D 4PCF against the FP64 oracle, for the
-FP32 and split-BF16 combination paths, on a 32^3 field with the benchmark's
+FP32, split-BF16 and split-TF32 combination paths, on a 32^3 field with the benchmark's
 spectrum (lognormal sigma_G 1.5, P ~ k^-11/3), lmax 4 and 10 bins (2..15).
 
 Reported (printed; run pytest with -s to see them) per precision: the
@@ -7,7 +7,7 @@ largest and the 99th-percentile ratio |zeta_gpu - zeta_oracle| / max|zeta|
 over all coefficients, and the cancellation ratio
 R = max over coefficients of sum_x sum_M |C delta a a a| / max|zeta|, which
 says how much of the summed magnitude cancels.  Asserted: the max ratio is
-within 1e-5 (FP32) / 1e-4 (split-BF16)."""
+within 1e-5 (FP32, split TF32) / 1e-4 (split BF16)."""
 import numpy as np
 import pytest
 
@@ -53,7 +53,8 @@ def test_error_per_coefficient():
     scale = np.abs(ref).max()
     R = _abs_sums(delta, EDGES, LMAX).max() / scale
     ctx = sbg.Context(0)
-    for name, prec, tol in (("fp32", sbg.SBG_PREC_FP32, 1e-5), ("bf16x3", sbg.SBG_PREC_BF16X3, 1e-4)):
+    for name, prec, tol in (("fp32", sbg.SBG_PREC_FP32, 1e-5), ("bf16x3", sbg.SBG_PREC_BF16X3, 1e-4),
+                            ("tf32x3", sbg.SBG_PREC_TF32X3, 1e-5)):
         _, z4 = ctx.full(torch.from_numpy(f).cuda(), EDGES, lmax4=LMAX, prec=prec)
         ratio = np.abs(z4 - ref).ravel() / scale
         print(f"\n4PCF 32^3 lmax {LMAX} {name}: max {ratio.max():.3e}  p99 {np.percentile(ratio, 99):.3e}  "

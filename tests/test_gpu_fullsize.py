@@ -1,6 +1,7 @@
 """Parity at the benchmark's full size, in the launch configuration bench.py
 times (256^3 float32 lognormal field, 10 linear bins 2..32, lmax 4, 4PCF only,
-mean subtracted, field resident on the device): sampled zeta_Lambda^{b1 b2 b3}
+mean subtracted, field resident on the device; FP32, split BF16 and split TF32):
+sampled zeta_Lambda^{b1 b2 b3}
 entries are recomputed one by one by the FP64 oracle; the whole tensor is
 checked for the symmetries that hold at any size."""
 import numpy as np
@@ -27,7 +28,8 @@ def full256():
     ctx = sbg.Context(0)
     d = torch.from_numpy(f).cuda()
     out = {}
-    for name, prec in (("fp32", sbg.SBG_PREC_FP32), ("bf16x3", sbg.SBG_PREC_BF16X3)):
+    for name, prec in (("fp32", sbg.SBG_PREC_FP32), ("bf16x3", sbg.SBG_PREC_BF16X3),
+                       ("tf32x3", sbg.SBG_PREC_TF32X3)):
         _, z4 = ctx.full(d, edges, lmax4=4, prec=prec)
         out[name] = z4
     ctx.close()
@@ -39,7 +41,7 @@ def full256():
 def test_sampled_entries_match_oracle(full256):
     out, ref = full256
     lams = O.lambda_list(4)
-    for name, tol in (("fp32", 1e-5), ("bf16x3", 1e-4)):
+    for name, tol in (("fp32", 1e-5), ("bf16x3", 1e-4), ("tf32x3", 1e-5)):
         z4 = out[name]
         scale = np.abs(z4).max()
         for (lam, b1, b2, b3), r in zip(ENTRIES, ref):
@@ -50,7 +52,7 @@ def test_sampled_entries_match_oracle(full256):
 def test_permutation_symmetry_at_full_size(full256):
     out, _ = full256
     lams = O.lambda_list(4)
-    for name, tol in (("fp32", 1e-5), ("bf16x3", 1e-4)):
+    for name, tol in (("fp32", 1e-5), ("bf16x3", 1e-4), ("tf32x3", 1e-5)):
         z4 = out[name]
         scale = np.abs(z4).max()
         for i, (l1, l2, l3) in enumerate(lams):
