@@ -171,6 +171,24 @@ sbg_status sbg_last_timings(const sbg_context* ctx, double* ms_per_stage, int* n
  * Errors: SBG_ERR_INVALID_ARG for a null pointer. */
 sbg_status sbg_last_contraction_ms(const sbg_context* ctx, double* ms);
 
+/* Tile plan of the 4PCF combination, on the host only (no context, no GPU,
+ * no device memory).  It builds the tables that sbg_full (dim 3, order lmax =
+ * lmax4) or sbg_projected (dim 2, lmax = mmax) uses for nbins bins at
+ * precision prec, and so checks that every output term of Algorithm 6 (full,
+ * Eq. mu, Sec. 2.3) or Algorithm 8 (projected, Eq. proj_4pcf_coeff, Sec. 2.4)
+ * finds its entry among the computed pair x single products.  Outputs (each
+ * may be NULL):
+ *   ntiles   : tiles of the contraction kernel (tensor-core tiles hold 128
+ *              pair rows);
+ *   nrows    : pair rows formed;
+ *   covering : which pair rows the tensor-core tiles use: 0 = every pair within
+ *              one half of the bins, 1 = a greedy cover of the needed triples;
+ *              the plan keeps the one with fewer tiles (0 for SBG_PREC_FP32).
+ * Errors: SBG_ERR_INVALID_ARG for dim not 2 or 3, nbins outside 1..20, lmax
+ * outside 0..5 (3D) or 0..10 (2D) or an unknown precision; SBG_ERR_INTERNAL
+ * if a term finds no entry (a defect of the plan). */
+sbg_status sbg_plan4_info(int dim, int nbins, int lmax, sbg_precision prec, int* ntiles, int* nrows, int* covering);
+
 /* Projected 3PCF that allocates no device memory (the paper has no
  * counterpart: this entry point exists for callers that cannot call cudaMalloc
  * during a measurement, e.g. code running inside a pre-sized memory pool or an

@@ -13,7 +13,10 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <queue>
 #include <string>
+#include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "sarabande_gb300.h"
@@ -123,6 +126,7 @@ struct Tables4 {
   std::vector<double> coef;
   long long tcount = 0;  // outputs of T (complex counted once)
   bool tc = false;       // tiles built for the tensor-core kernel
+  int covering = 0;      // tensor-core rows: 0 pairs within a bin half, 1 greedy cover
   int nout = 0;
   // device
   DevBuf d_tiles[3], d_rows, d_cols, d_uniq, d_bgroups, d_ptr, d_idx, d_coef;
@@ -338,16 +342,18 @@ sbg_status colour_slots(sbg_context* ctx, Tables4& t, Tile4& tl, const std::map<
 
 // Build the pair x single contraction tables of the 4PCF and the coupling CSR.
 // T[s1, s2, s3] = sum_x delta a_s1 a_s2 a_s3 is symmetric under permutations of
-// its singles s = (l, m, b) and T[-M] = conj T[M] (real delta), so the computed
-// set is: for each m3 >= 0 and bin b2, rows (alpha1, b1 <= b2, alpha2) with
-// m1 + m2 = -m3 and cols (b3 >= b2, l3 >= m3).  Every needed triple maps into
-// it by sorting the singles by bin and, if the last single's m is negative,
-// negating every m (Re T unchanged; conj for the complex 2D T).
-//   tc = false: FP32 SIMT tiles, rows per tile 256/128/64 by column class,
-//               <= 128 staged singles per tile.
-//   tc = true : tensor-core tiles of 128 rows (M of the MMA), <= kTcMaxU staged
-//               singles, <= 64 B-operand rows (2D: 2 per column single).
-sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, bool tc) {
+// its singles s = (l, m, b) and T[-M] = conj T[M] (real delta), so a computed
+// entry (pair row, column single) serves every ordering of its triple and the
+// triple with all m negated (Re T unchanged; conj for the complex 2D T).  The
+// coupling CSR finds each needed triple by trying its orderings and signs.
+//   tc = false: FP32 SIMT tiles; for each m3 >= 0 and bin b2, rows (alpha1,
+//               b1 <= b2, alpha2) with m1 + m2 = -m3 and cols (b3 >= b2,
+//               l3 >= m3); rows per tile 256/128/64 by column class, <= 128
+//               staged singles per tile.
+//   tc = true : tensor-core tiles of 128 rows (M of the MMA), <= kTcMaxRowSlots
+//               staged singles, <= 64 B-operand rows (2D: 2 per column single);
+//               one block per m3 >= 0 with columns (b3, l3 >= m3).
+sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, bool tc, bool to_device = true) {
   struct Ang { int l, m; };
   std::vector<Ang> angs;
   if (dim == 3) {
@@ -357,10 +363,10 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
     for (int m = -L; m <= L; ++m) angs.push_back({-1, m});
   }
   const int na = (int)angs.size();
+  // position in angs: 3D l^2 + l + m, 2D m + L; -1 if there is none
   auto ang_index = [&](int l, int m) -> int {
-    for (int i = 0; i < na; ++i)
-      if (angs[i].l == l && angs[i].m == m) return i;
-    return -1;
+    if (dim == 3) return (l < 0 || l > L || std::abs(m) > l) ? -1 : l * l + l + m;
+    return (l != -1 || std::abs(m) > L) ? -1 : m + L;
   };
   // Two ways of choosing the formed pairs (rows) so that every canonical triple
   // has one of its pairs among the rows and its third single among the columns:
@@ -368,17 +374,20 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
   //                     columns (b3 >= b2, l3) -> one block per (m3, b2);
   //  tc = true (tensor): bins split in two halves; rows are pairs within one half
   //                     (any triple has two bins in the same half), columns are
-  //                     every (b3, l3) -> one block per m3 with uniform columns.
+  //                     every (b3, l3) -> one block per m3 with uniform columns;
+  //                     the greedy cover below replaces these rows when it packs
+  //                     into fewer tiles.
   auto half = [&](int b) { return b < (nb + 1) / 2 ? 0 : 1; };
   struct RowKey { int a1, b1, a2, b2; };
   struct Slab { int r0, nr, c0, nc; long long tout; int row0; };
   struct Block {
     int m3 = 0, b2 = 0;
     std::vector<RowKey> rows;
-    std::map<long long, int> row_of;
+    std::unordered_map<long long, int> row_of;
     std::vector<int> l3s;
     int ncols = 0, bcol0 = 0;  // columns: b3 in [bcol0, nb) x l3s, b3-major
     std::vector<Slab> slabs;
+    std::vector<std::vector<int>> slab_at;  // [column chunk][row] -> slab
   };
   auto rkey = [](int a1, int b1, int a2, int b2) -> long long {
     return (((long long)a1 * 64 + b1) * 4096 + a2) * 64 + b2;
@@ -422,15 +431,134 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
           }
       }
       bk.ncols = (nb - bk.bcol0) * (int)bk.l3s.size();
-      for (int r = 0; r < (int)bk.rows.size(); ++r) {
-        const RowKey& k = bk.rows[r];
-        bk.row_of[rkey(k.a1, k.b1, k.a2, k.b2)] = r;
-      }
       blocks.push_back(std::move(bk));
     }
-  long long so = 0;
   const int col_chunk = tc ? (dim == 2 ? 32 : 64) : 64;
   const int max_u = tc ? kTcMaxRowSlots : 128;
+  auto sidx = [&](int a, int b) { return store_index(dim, nb, angs[a].l, std::abs(angs[a].m), b); };
+  // tensor-core tiles of 128 rows that the packing below makes of a block's rows
+  auto count_tiles = [&](const std::vector<RowKey>& rows) -> long long {
+    long long n = 0;
+    int nr = 0;
+    std::vector<int> local;
+    auto has = [&](int v) { return std::find(local.begin(), local.end(), v) != local.end(); };
+    for (const RowKey& rk : rows) {
+      const int s1 = sidx(rk.a1, rk.b1), s2 = sidx(rk.a2, rk.b2);
+      const int need = (has(s1) ? 0 : 1) + ((has(s2) || s2 == s1) ? 0 : 1);
+      if (nr == 128 || (int)local.size() + need > max_u) {  // the row opens the next tile
+        ++n;
+        nr = 0;
+        local.clear();
+      }
+      if (!has(s1)) local.push_back(s1);
+      if (!has(s2)) local.push_back(s2);
+      ++nr;
+    }
+    return n + (nr ? 1 : 0);
+  };
+  if (tc) {
+    // Second covering for the tensor-core tiles: a greedy set cover of the
+    // triples the output needs.  A candidate row is a pair (s1, s2) with
+    // m1 + m2 = -m3 in block m3 >= 0; it covers the triples (s1, s2, s3) for
+    // every column s3 = (l3, m3, b3) of its block that the output needs (3D:
+    // l1 + l2 + l3 even and |l1 - l2| <= l3 <= l1 + l2, the terms of the even-
+    // parity 4PCF; 2D: every b3).  Triples are counted once up to the order of
+    // their singles and M -> -M.  Unlike the bin-half rows, any element of a
+    // triple may be its column and rows that meet no needed column are left
+    // out, so the greedy cover needs about half the rows at lmax 4.  The plan
+    // keeps whichever covering packs into fewer tiles.
+    std::vector<int> nega(na);
+    for (int a = 0; a < na; ++a) nega[a] = ang_index(angs[a].l, -angs[a].m);
+    const long long S = (long long)na * nb;
+    auto key3 = [&](int x, int y, int z) -> long long {  // single s = a * nb + b
+      int u[3] = {x, y, z}, v[3] = {nega[x / nb] * nb + x % nb, nega[y / nb] * nb + y % nb, nega[z / nb] * nb + z % nb};
+      std::sort(u, u + 3);
+      std::sort(v, v + 3);
+      if (std::lexicographical_compare(v, v + 3, u, u + 3)) std::copy(v, v + 3, u);
+      return ((long long)u[0] * S + u[1]) * S + u[2];
+    };
+    auto needed = [&](int l1, int l2, int l3) {
+      return dim == 2 || (((l1 + l2 + l3) & 1) == 0 && std::abs(l1 - l2) <= l3 && l3 <= l1 + l2);
+    };
+    auto canon = [](int a1, int b1, int a2, int b2) -> RowKey {  // b1 <= b2; a1 <= a2 when b1 == b2
+      if (b1 > b2 || (b1 == b2 && a1 > a2)) return {a2, b2, a1, b1};
+      return {a1, b1, a2, b2};
+    };
+    auto less = [](const RowKey& p, const RowKey& q) {
+      return std::make_tuple(p.a1, p.b1, p.a2, p.b2) < std::make_tuple(q.a1, q.b1, q.a2, q.b2);
+    };
+    struct Cand { int m3; RowKey rk; int off, n; };
+    std::vector<Cand> cands;
+    std::vector<int> cov;
+    std::unordered_map<long long, int> tid;
+    for (int m3 = 0; m3 <= L; ++m3)
+      for (int a1 = 0; a1 < na; ++a1)
+        for (int b1 = 0; b1 < nb; ++b1)
+          for (int a2 = 0; a2 < na; ++a2)
+            for (int b2 = 0; b2 < nb; ++b2) {
+              if (angs[a1].m + angs[a2].m != -m3) continue;
+              const RowKey rk{a1, b1, a2, b2};
+              const RowKey ck = canon(a1, b1, a2, b2);
+              if (ck.a1 != a1 || ck.b1 != b1 || ck.a2 != a2 || ck.b2 != b2) continue;  // the other order
+              // m3 = 0: the pair with every m negated covers the same triples
+              if (m3 == 0 && less(canon(nega[a1], b1, nega[a2], b2), rk)) continue;
+              const int off = (int)cov.size();
+              for (int l3 : blocks[m3].l3s) {
+                if (!needed(angs[a1].l, angs[a2].l, l3)) continue;
+                const int z = ang_index(l3, m3) * nb;
+                for (int b3 = 0; b3 < nb; ++b3) {
+                  auto ins = tid.emplace(key3(a1 * nb + b1, a2 * nb + b2, z + b3), (int)tid.size());
+                  cov.push_back(ins.first->second);
+                }
+              }
+              std::sort(cov.begin() + off, cov.end());
+              cov.erase(std::unique(cov.begin() + off, cov.end()), cov.end());
+              if ((int)cov.size() > off) cands.push_back({m3, rk, off, (int)cov.size() - off});
+            }
+    // lazy greedy: take the candidate covering the most uncovered triples
+    // (ties: the first enumerated); a popped count that went stale is pushed back
+    std::vector<char> done(tid.size(), 0);
+    long long left = (long long)tid.size();
+    std::priority_queue<std::pair<int, int>> heap;
+    for (int i = 0; i < (int)cands.size(); ++i) heap.push({cands[i].n, -i});
+    std::vector<std::vector<RowKey>> grows(blocks.size());
+    while (left > 0 && !heap.empty()) {
+      const auto top = heap.top();
+      heap.pop();
+      const Cand& c = cands[-top.second];
+      int fresh = 0;
+      for (int k = c.off; k < c.off + c.n; ++k) fresh += done[cov[k]] ? 0 : 1;
+      if (fresh == 0) continue;
+      if (fresh < top.first) {
+        heap.push({fresh, top.second});
+        continue;
+      }
+      for (int k = c.off; k < c.off + c.n; ++k) done[cov[k]] = 1;
+      left -= fresh;
+      grows[c.m3].push_back(c.rk);
+    }
+    if (left > 0) return fail(ctx, SBG_ERR_INTERNAL, "4PCF greedy covering left triples uncovered");
+    long long t_half = 0, t_greedy = 0;
+    for (size_t i = 0; i < blocks.size(); ++i) {
+      // rows sharing singles sit together: sorted by the stored index of each single
+      std::sort(grows[i].begin(), grows[i].end(), [&](const RowKey& p, const RowKey& q) {
+        return std::make_pair(sidx(p.a1, p.b1), sidx(p.a2, p.b2)) < std::make_pair(sidx(q.a1, q.b1), sidx(q.a2, q.b2));
+      });
+      t_half += count_tiles(blocks[i].rows);
+      t_greedy += count_tiles(grows[i]);
+    }
+    if (t_greedy < t_half)
+      for (size_t i = 0; i < blocks.size(); ++i) blocks[i].rows = std::move(grows[i]);
+    t.covering = t_greedy < t_half ? 1 : 0;
+  }
+  for (Block& bk : blocks) {
+    bk.row_of.reserve(bk.rows.size() * 2);
+    for (int r = 0; r < (int)bk.rows.size(); ++r) {
+      const RowKey& k = bk.rows[r];
+      bk.row_of[rkey(k.a1, k.b1, k.a2, k.b2)] = r;
+    }
+  }
+  long long so = 0;
   t.tc = tc;
   for (Block& bk : blocks) {
     const int nrows_blk = (int)bk.rows.size();
@@ -496,6 +624,9 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
         tl.nuniq = (int)local.size();
         if (tc) ST(colour_slots(ctx, t, tl, local));
         tl.tout = so;
+        if ((int)bk.slab_at.size() <= c0 / col_chunk) bk.slab_at.resize(c0 / col_chunk + 1);
+        bk.slab_at[c0 / col_chunk].resize(nrows_blk, -1);
+        for (int q = rstart; q < rstart + nr; ++q) bk.slab_at[c0 / col_chunk][q] = (int)bk.slabs.size();
         bk.slabs.push_back({rstart, nr, c0, nc, so, tl.row0});
         so += (long long)nr * nc;
         t.tiles[cls].push_back(tl);
@@ -523,14 +654,12 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
     if (z.b < bk.bcol0) return LLONG_MIN;
     const int l3pos = dim == 3 ? z.l - m3 : 0;
     const int col = (z.b - bk.bcol0) * (int)bk.l3s.size() + l3pos;
-    for (const Slab& sl : bk.slabs) {
-      if (row >= sl.r0 && row < sl.r0 + sl.nr && col >= sl.c0 && col < sl.c0 + sl.nc) {
-        const long long ti = sl.tout + (long long)(row - sl.r0) * sl.nc + (col - sl.c0);
-        if (rowsign) *rowsign = t.rows[sl.row0 + (row - sl.r0)].sign;
-        return neg ? -ti - 1 : ti;
-      }
-    }
-    return LLONG_MIN;
+    const int chunk = col / col_chunk;
+    if (col >= bk.ncols || chunk >= (int)bk.slab_at.size() || bk.slab_at[chunk][row] < 0) return LLONG_MIN;
+    const Slab& sl = bk.slabs[bk.slab_at[chunk][row]];
+    const long long ti = sl.tout + (long long)(row - sl.r0) * sl.nc + (col - sl.c0);
+    if (rowsign) *rowsign = t.rows[sl.row0 + (row - sl.r0)].sign;
+    return neg ? -ti - 1 : ti;
   };
   auto lookup = [&](Single s[3], float* rowsign) -> long long {
     static const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
@@ -539,11 +668,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
         Single x = s[p[0]], y = s[p[1]], z = s[p[2]];
         if (neg) { x.m = -x.m; y.m = -y.m; z.m = -z.m; }
         if (x.b > y.b) continue;
-        if (tc) {
-          if (half(x.b) != half(y.b)) continue;
-        } else {
-          if (z.b < y.b) continue;
-        }
+        if (!tc && z.b < y.b) continue;
         const long long ti = find_entry(x, y, z, neg != 0, rowsign);
         if (ti != LLONG_MIN) return ti;
       }
@@ -560,23 +685,27 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
       for (int l2 = 0; l2 <= L; ++l2)
         for (int l3 = std::abs(l1 - l2); l3 <= std::min(l1 + l2, L); ++l3) {
           if ((l1 + l2 + l3) & 1) continue;
+          struct Term { int m1, m2; double c; };
+          std::vector<Term> terms;  // the nonzero C^Lambda_M of this Lambda
+          for (int m1 = -l1; m1 <= l1; ++m1)
+            for (int m2 = -l2; m2 <= l2; ++m2) {
+              const int m3 = -(m1 + m2);
+              if (std::abs(m3) > l3) continue;
+              const double c = (((l1 + l2 + l3) & 1) ? -1.0 : 1.0) * three_j(l1, l2, l3, m1, m2, m3);
+              if (c != 0.0) terms.push_back({m1, m2, c});
+            }
           for (int b1 = 0; b1 < nb; ++b1)
             for (int b2 = 0; b2 < nb; ++b2)
               for (int b3 = 0; b3 < nb; ++b3) {
-                for (int m1 = -l1; m1 <= l1; ++m1)
-                  for (int m2 = -l2; m2 <= l2; ++m2) {
-                    const int m3 = -(m1 + m2);
-                    if (std::abs(m3) > l3) continue;
-                    const double c = (((l1 + l2 + l3) & 1) ? -1.0 : 1.0) * three_j(l1, l2, l3, m1, m2, m3);
-                    if (c == 0.0) continue;
-                    Single sg[3] = {{l1, m1, b1}, {l2, m2, b2}, {l3, m3, b3}};
-                    float rs = 1.0f;
-                    long long ti = lookup(sg, &rs);
-                    if (ti == LLONG_MIN) return fail(ctx, SBG_ERR_INTERNAL, "4PCF table lookup failed");
-                    if (ti < 0) ti = -ti - 1;  // Re T is invariant under M -> -M
-                    t.idx.push_back((int)ti);
-                    t.coef.push_back(tc ? c * rs : c);
-                  }
+                for (const Term& tm : terms) {
+                  Single sg[3] = {{l1, tm.m1, b1}, {l2, tm.m2, b2}, {l3, -(tm.m1 + tm.m2), b3}};
+                  float rs = 1.0f;
+                  long long ti = lookup(sg, &rs);
+                  if (ti == LLONG_MIN) return fail(ctx, SBG_ERR_INTERNAL, "4PCF table lookup failed");
+                  if (ti < 0) ti = -ti - 1;  // Re T is invariant under M -> -M
+                  t.idx.push_back((int)ti);
+                  t.coef.push_back(tc ? tm.c * rs : tm.c);
+                }
                 t.ptr.push_back((int)t.idx.size());
               }
         }
@@ -598,6 +727,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
             }
   }
   t.nout = (int)t.ptr.size() - 1;
+  if (!to_device) return SBG_OK;
   for (int k = 0; k < 3; ++k) ST(upload(ctx, t.d_tiles[k], t.tiles[k]));
   ST(upload(ctx, t.d_rows, t.rows));
   ST(upload(ctx, t.d_cols, t.cols));
@@ -1243,6 +1373,20 @@ sbg_status sbg_last_timings(const sbg_context* ctx, double* ms_per_stage, int* n
 sbg_status sbg_last_contraction_ms(const sbg_context* ctx, double* ms) {
   if (!ctx || !ms) return SBG_ERR_INVALID_ARG;
   *ms = ctx->contraction_ms;
+  return SBG_OK;
+}
+
+sbg_status sbg_plan4_info(int dim, int nbins, int lmax, sbg_precision prec, int* ntiles, int* nrows, int* covering) {
+  if ((dim != 2 && dim != 3) || nbins < 1 || nbins > kMaxBins || lmax < 0 || lmax > (dim == 3 ? kMaxL4 : kMaxM) ||
+      (prec != SBG_PREC_FP32 && prec != SBG_PREC_BF16X3 && prec != SBG_PREC_TF32X3))
+    return SBG_ERR_INVALID_ARG;
+  sbg_context host;  // receives the error text only: the tables stay on the host
+  Tables4 t;
+  const sbg_status s = build_tables4(&host, t, dim, nbins, lmax, prec != SBG_PREC_FP32, false);
+  if (s != SBG_OK) return s;
+  if (ntiles) *ntiles = (int)(t.tiles[0].size() + t.tiles[1].size() + t.tiles[2].size());
+  if (nrows) *nrows = (int)t.rows.size();
+  if (covering) *covering = t.covering;
   return SBG_OK;
 }
 

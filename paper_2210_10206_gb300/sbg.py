@@ -69,6 +69,8 @@ def lib():
         L.sbg_last_timings.restype = st
         L.sbg_last_contraction_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.sbg_last_contraction_ms.restype = st
+        L.sbg_plan4_info.argtypes = [i, i, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.sbg_plan4_info.restype = st
         L.sbg_projected3_noalloc.argtypes = [vp, i, ctypes.c_int64, vp, i, i, ctypes.c_uint, vp, vp]
         L.sbg_projected3_noalloc.restype = st
         _lib = L
@@ -217,6 +219,15 @@ def sbg_last_contraction_ms(h):
     out = ctypes.c_double()
     lib().sbg_last_contraction_ms(h, ctypes.byref(out))
     return out.value
+
+
+def sbg_plan4_info(dim, nbins, lmax, prec):
+    """(ntiles, nrows, covering) of the 4PCF tile plan; host only."""
+    nt, nr, cv = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    s = lib().sbg_plan4_info(dim, nbins, lmax, prec, ctypes.byref(nt), ctypes.byref(nr), ctypes.byref(cv))
+    if s != SBG_OK:
+        raise SbgError(s, "sbg_plan4_info")
+    return nt.value, nr.value, cv.value
 
 
 def sbg_projected3_noalloc(field, edges, mmax, flags, zeta3, stream=0):
