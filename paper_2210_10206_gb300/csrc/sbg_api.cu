@@ -574,6 +574,9 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
         g.col0 = col0;
         g.ncols = nc;
         g.n = ((dim == 2 ? 2 * nc : nc) + 15) & ~15;
+        // the kernel's B stage holds 2n rows of 128 bytes and its inner
+        // accumulator 3n TMEM columns: n <= 64
+        if (g.n > 64) return fail(ctx, SBG_ERR_INTERNAL, "tensor-core column group wider than 64");
         g.off = t.img_stride;
         t.img_stride += (long long)g.n * 256;
         t.chunks_per_kb += g.n * 8;

@@ -67,7 +67,7 @@ constexpr int kThreads = (kBWarp + 1) * 32;
 //     128 columns (64 hi, 64 lo) and B rows of two 128-byte atoms (K 0..31 and
 //     32..63).
 // Either way operand stage g belongs to group g, the A tiles fill TMEM columns
-// [192, 448) and the B tiles 64 KB of shared memory.
+// [256, 512) and the B tiles 64 KB of shared memory.
 template <bool TF>
 struct Cfg {
   static constexpr int kGroups = TF ? 2 : 4;
@@ -88,13 +88,17 @@ struct Cfg {
   // Split TF32 is the accurate option, so its ranges are 8 K-blocks; split BF16
   // keeps 256 (1.9e-5, its bf16 split dominates).
   static constexpr int kFlush = TF ? 8 : 256;
+  // group 0 forms the first K-block of every range (it folds the previous one)
+  static_assert(kFlush % kGroups == 0, "ranges must start on group 0's K-blocks");
 };
-// TMEM columns: the inner accumulator [0, 128) of the current 256-K-block range
-// (columns [0, n) collect Ahi Bhi + Alo Bhi, [n, 2n) Ahi Blo), the outer
-// accumulator [128, 192), then one 64-column A stage per operand stage
-// (32 columns hi, 32 lo: 64 bf16 each)
-constexpr int kTmemOuter = 128;
-constexpr int kTmemA0 = 192;
+// TMEM columns: the inner accumulator [0, 192) of the current range (columns
+// [0, n) collect Ahi Bhi, [n, 2n) Ahi Blo, [2n, 3n) Alo Bhi), the outer
+// accumulator [192, 256), then the A stages in [256, 512) (per operand stage
+// 64 columns for split BF16, 128 for split TF32).  Alo Bhi has columns of its
+// own so that its MMAs do not wait for the Ahi MMAs before them: the two
+// chains of dependent accumulations overlap in the tensor core.
+constexpr int kTmemOuter = 192;
+constexpr int kTmemA0 = 256;
 constexpr int kTmemCols = 512;
 // FP32 (re, im) row singles, 256 bytes each, padded to 272 bytes: chunk k of
 // slot s then falls in bank quad (s + k) mod 8, so the eight rows a
@@ -482,7 +486,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
         const uint32_t idesc2 = (idesc & ~(0x3Fu << 17)) | ((uint32_t)((2 * N) >> 3) << 17);
         for (int kb = 0; kb < it.nk; ++kb) {
           const int os = kb % kOS;
-          if (!mbar_wait(&op_full[os], uses[os] & 1, err, 21) || !mbar_wait(&b_full[os], uses[os] & 1, err, 22)) {
+          if (!mbar_wait(&op_full[os], uses[os] & 1, err, 21)) {  // A formed and (checked by a producer) B landed
             ok = false;
             break;
           }
@@ -494,13 +498,14 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
           const uint64_t bd = sdesc(su32(op_base + os * kOpStage));
           const uint32_t a_hi = tmem + kTmemA0 + C::kACols * os, a_lo = a_hi + C::kACols / 2;
           const uint32_t acc0 = (kb % kFlush) == 0 ? 0u : 1u;
-          // two MMAs per K step: Ahi meets Bhi and Blo in one (N = 2n); a K step
-          // is 8 TMEM columns of A in both precisions
+          // two MMAs per K step: Ahi meets Bhi and Blo in one (N = 2n) into
+          // columns [0, 2n), Alo meets Bhi into [2n, 3n); a K step is 8 TMEM
+          // columns of A in both precisions
 #pragma unroll
           for (int k = 0; k < C::kKSteps; ++k) {
             const uint64_t bk = bd + 2 * (k & 3) + (uint64_t)((k >> 2) * 2 * N * 128 / 16);
             mma_ts<TF>(tmem, a_hi + 8 * k, bk, idesc2, k == 0 ? acc0 : 1u);
-            mma_ts<TF>(tmem, a_lo + 8 * k, bk, idesc, 1u);
+            mma_ts<TF>(tmem + 2 * N, a_lo + 8 * k, bk, idesc, k == 0 ? acc0 : 1u);
           }
           mma_commit(&op_empty[os]);
           if ((kb + 1) % kFlush == 0 || kb + 1 == it.nk) mma_commit(acc_full);
@@ -540,10 +545,12 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
         const uint32_t outer = tmem + lane_addr + kTmemOuter;
         for (int c0 = 0; c0 < N; c0 += 8) {
           float in[8], lo[8], out[8];
+          float lo2[8];
           tmem_ld8(inner + c0, in);
           tmem_ld8(inner + N + c0, lo);
+          tmem_ld8(inner + 2 * N + c0, lo2);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) in[e] += lo[e];
+          for (int e = 0; e < 8; ++e) in[e] += lo[e] + lo2[e];
           if (i == 0) {
 #pragma unroll
             for (int e = 0; e < 8; ++e) out[e] = in[e];
@@ -646,6 +653,13 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
+        // the first warp of the group also sees this K-block's B tile land, so
+        // the MMA issuer waits on op_full alone (the copy of the stage's next
+        // K-block needs this op_full first, so the parity cannot run ahead)
+        if (warp % C::kWarps == 0 && !warp_wait(&b_full[os], (uses - 1) & 1, err, 34)) {
+          ok = false;
+          break;
+        }
         // publish the A tile to the MMA issuer, release the raw stage
         __syncwarp();
         if (lane == 0) {
