@@ -181,9 +181,11 @@ sbg_status sbg_last_contraction_ms(const sbg_context* ctx, double* ms);
  *   ntiles   : tiles of the contraction kernel (tensor-core tiles hold 128
  *              pair rows);
  *   nrows    : pair rows formed;
- *   covering : which pair rows the tensor-core tiles use: 0 = every pair within
- *              one half of the bins, 1 = a greedy cover of the needed triples;
- *              the plan keeps the one with fewer tiles (0 for SBG_PREC_FP32).
+ *   covering : which pair rows the tiles use: 0 = the structured rows (tensor
+ *              core: every pair within one half of the bins; FP32: pairs
+ *              b1 <= b2 against columns b3 >= b2), 1 = a greedy cover of the
+ *              needed triples; the plan keeps the one with fewer tiles (tensor
+ *              core) or fewer pair x column entries (FP32).
  * Errors: SBG_ERR_INVALID_ARG for dim not 2 or 3, nbins outside 1..20, lmax
  * outside 0..5 (3D) or 0..10 (2D) or an unknown precision; SBG_ERR_INTERNAL
  * if a term finds no entry (a defect of the plan). */

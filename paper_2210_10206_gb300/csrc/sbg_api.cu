@@ -126,7 +126,7 @@ struct Tables4 {
   std::vector<double> coef;
   long long tcount = 0;  // outputs of T (complex counted once)
   bool tc = false;       // tiles built for the tensor-core kernel
-  int covering = 0;      // tensor-core rows: 0 pairs within a bin half, 1 greedy cover
+  int covering = 0;      // 0: bin-half (tensor) or b3 >= b2 (SIMT) rows; 1: greedy cover
   int nout = 0;
   // device
   DevBuf d_tiles[3], d_rows, d_cols, d_uniq, d_bgroups, d_ptr, d_idx, d_coef;
@@ -348,7 +348,8 @@ sbg_status colour_slots(sbg_context* ctx, Tables4& t, Tile4& tl, const std::map<
 // coupling CSR finds each needed triple by trying its orderings and signs.
 //   tc = false: FP32 SIMT tiles; for each m3 >= 0 and bin b2, rows (alpha1,
 //               b1 <= b2, alpha2) with m1 + m2 = -m3 and cols (b3 >= b2,
-//               l3 >= m3); rows per tile 256/128/64 by column class, <= 128
+//               l3 >= m3), or the greedy cover below when it computes fewer
+//               entries; rows per tile 256/128/64 by column class, <= 128
 //               staged singles per tile.
 //   tc = true : tensor-core tiles of 128 rows (M of the MMA), <= kTcMaxRowSlots
 //               staged singles, <= 64 B-operand rows (2D: 2 per column single);
@@ -393,7 +394,8 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
     return (((long long)a1 * 64 + b1) * 4096 + a2) * 64 + b2;
   };
   std::vector<Block> blocks;
-  auto block_of = [&](int m3, int b2) -> int { return tc ? m3 : m3 * nb + b2; };
+  bool uniform = tc;  // one block per m3 >= 0 whose columns are every (b3, l3)
+  auto block_of = [&](int m3, int b2) -> int { return uniform ? m3 : m3 * nb + b2; };
   for (int m3 = 0; m3 <= L; ++m3)
     for (int b2 = 0; b2 < (tc ? 1 : nb); ++b2) {
       Block bk;
@@ -456,17 +458,29 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
     }
     return n + (nr ? 1 : 0);
   };
-  if (tc) {
-    // Second covering for the tensor-core tiles: a greedy set cover of the
-    // triples the output needs.  A candidate row is a pair (s1, s2) with
-    // m1 + m2 = -m3 in block m3 >= 0; it covers the triples (s1, s2, s3) for
+  {
+    // Second covering: a greedy set cover of the triples the output needs, in
+    // blocks of one m3 >= 0 with every (b3, l3) column.  A candidate row is a
+    // pair (s1, s2) with m1 + m2 = -m3; it covers the triples (s1, s2, s3) for
     // every column s3 = (l3, m3, b3) of its block that the output needs (3D:
     // l1 + l2 + l3 even and |l1 - l2| <= l3 <= l1 + l2, the terms of the even-
     // parity 4PCF; 2D: every b3).  Triples are counted once up to the order of
-    // their singles and M -> -M.  Unlike the bin-half rows, any element of a
-    // triple may be its column and rows that meet no needed column are left
-    // out, so the greedy cover needs about half the rows at lmax 4.  The plan
-    // keeps whichever covering packs into fewer tiles.
+    // their singles and M -> -M.  Any element of a triple may be its column and
+    // rows that meet no needed column are left out.  The tensor-core kernel
+    // pays per tile, so its greedy counts rows and the plan keeps the covering
+    // with fewer tiles (at lmax 4, 10 bins: 30 instead of 65); the SIMT kernel
+    // pays per (row, column) entry, so its greedy weighs a row by its block's
+    // columns and the plan keeps the covering with fewer entries (134,320
+    // instead of 239,360).
+    std::vector<int> l3_of[kMaxL4 > kMaxM ? kMaxL4 + 1 : kMaxM + 1];
+    for (int m3 = 0; m3 <= L; ++m3) {
+      if (dim == 3) {
+        for (int l3 = m3; l3 <= L; ++l3) l3_of[m3].push_back(l3);
+      } else {
+        l3_of[m3].push_back(-1);
+      }
+    }
+    auto ucols = [&](int m3) { return nb * (int)l3_of[m3].size(); };
     std::vector<int> nega(na);
     for (int a = 0; a < na; ++a) nega[a] = ang_index(angs[a].l, -angs[a].m);
     const long long S = (long long)na * nb;
@@ -503,7 +517,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
               // m3 = 0: the pair with every m negated covers the same triples
               if (m3 == 0 && less(canon(nega[a1], b1, nega[a2], b2), rk)) continue;
               const int off = (int)cov.size();
-              for (int l3 : blocks[m3].l3s) {
+              for (int l3 : l3_of[m3]) {
                 if (!needed(angs[a1].l, angs[a2].l, l3)) continue;
                 const int z = ang_index(l3, m3) * nb;
                 for (int b3 = 0; b3 < nb; ++b3) {
@@ -515,13 +529,15 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
               cov.erase(std::unique(cov.begin() + off, cov.end()), cov.end());
               if ((int)cov.size() > off) cands.push_back({m3, rk, off, (int)cov.size() - off});
             }
-    // lazy greedy: take the candidate covering the most uncovered triples
-    // (ties: the first enumerated); a popped count that went stale is pushed back
+    // lazy greedy: take the candidate with the most uncovered triples (SIMT:
+    // per column of its block; ties: the first enumerated); a popped value
+    // that went stale is pushed back
+    auto value = [&](const Cand& c, int fresh) { return tc ? (double)fresh : (double)fresh / ucols(c.m3); };
     std::vector<char> done(tid.size(), 0);
     long long left = (long long)tid.size();
-    std::priority_queue<std::pair<int, int>> heap;
-    for (int i = 0; i < (int)cands.size(); ++i) heap.push({cands[i].n, -i});
-    std::vector<std::vector<RowKey>> grows(blocks.size());
+    std::priority_queue<std::pair<double, int>> heap;
+    for (int i = 0; i < (int)cands.size(); ++i) heap.push({value(cands[i], cands[i].n), -i});
+    std::vector<std::vector<RowKey>> grows(L + 1);
     while (left > 0 && !heap.empty()) {
       const auto top = heap.top();
       heap.pop();
@@ -529,8 +545,8 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
       int fresh = 0;
       for (int k = c.off; k < c.off + c.n; ++k) fresh += done[cov[k]] ? 0 : 1;
       if (fresh == 0) continue;
-      if (fresh < top.first) {
-        heap.push({fresh, top.second});
+      if (value(c, fresh) < top.first) {
+        heap.push({value(c, fresh), top.second});
         continue;
       }
       for (int k = c.off; k < c.off + c.n; ++k) done[cov[k]] = 1;
@@ -538,18 +554,38 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
       grows[c.m3].push_back(c.rk);
     }
     if (left > 0) return fail(ctx, SBG_ERR_INTERNAL, "4PCF greedy covering left triples uncovered");
-    long long t_half = 0, t_greedy = 0;
-    for (size_t i = 0; i < blocks.size(); ++i) {
-      // rows sharing singles sit together: sorted by the stored index of each single
-      std::sort(grows[i].begin(), grows[i].end(), [&](const RowKey& p, const RowKey& q) {
+    // rows sharing singles sit together: sorted by the stored index of each single
+    for (auto& g : grows)
+      std::sort(g.begin(), g.end(), [&](const RowKey& p, const RowKey& q) {
         return std::make_pair(sidx(p.a1, p.b1), sidx(p.a2, p.b2)) < std::make_pair(sidx(q.a1, q.b1), sidx(q.a2, q.b2));
       });
-      t_half += count_tiles(blocks[i].rows);
-      t_greedy += count_tiles(grows[i]);
+    if (tc) {
+      long long t_half = 0, t_greedy = 0;
+      for (int m3 = 0; m3 <= L; ++m3) {
+        t_half += count_tiles(blocks[m3].rows);
+        t_greedy += count_tiles(grows[m3]);
+      }
+      if (t_greedy < t_half) {
+        for (int m3 = 0; m3 <= L; ++m3) blocks[m3].rows = std::move(grows[m3]);
+        t.covering = 1;
+      }
+    } else {
+      long long e_cur = 0, e_greedy = 0;
+      for (const Block& bk : blocks) e_cur += (long long)bk.rows.size() * bk.ncols;
+      for (int m3 = 0; m3 <= L; ++m3) e_greedy += (long long)grows[m3].size() * ucols(m3);
+      if (e_greedy < e_cur) {
+        std::vector<Block> ub(L + 1);
+        for (int m3 = 0; m3 <= L; ++m3) {
+          ub[m3].m3 = m3;
+          ub[m3].l3s = l3_of[m3];
+          ub[m3].ncols = ucols(m3);
+          ub[m3].rows = std::move(grows[m3]);
+        }
+        blocks = std::move(ub);
+        uniform = true;
+        t.covering = 1;
+      }
     }
-    if (t_greedy < t_half)
-      for (size_t i = 0; i < blocks.size(); ++i) blocks[i].rows = std::move(grows[i]);
-    t.covering = t_greedy < t_half ? 1 : 0;
   }
   for (Block& bk : blocks) {
     bk.row_of.reserve(bk.rows.size() * 2);
@@ -650,7 +686,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
     const Block& bk = blocks[bi];
     int i1 = ang_index(x.l, x.m), i2 = ang_index(y.l, y.m);
     int b1 = x.b, b2 = y.b;
-    if (tc && b1 == b2 && i2 < i1) std::swap(i1, i2);
+    if (uniform && b1 == b2 && i2 < i1) std::swap(i1, i2);
     auto it = bk.row_of.find(rkey(i1, b1, i2, b2));
     if (it == bk.row_of.end()) return LLONG_MIN;
     const int row = it->second;
@@ -671,7 +707,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
         Single x = s[p[0]], y = s[p[1]], z = s[p[2]];
         if (neg) { x.m = -x.m; y.m = -y.m; z.m = -z.m; }
         if (x.b > y.b) continue;
-        if (!tc && z.b < y.b) continue;
+        if (!uniform && z.b < y.b) continue;
         const long long ti = find_entry(x, y, z, neg != 0, rowsign);
         if (ti != LLONG_MIN) return ti;
       }

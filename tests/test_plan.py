@@ -27,9 +27,7 @@ GEOMETRIES = [(3, 1, 0), (3, 1, 4), (3, 2, 1), (3, 3, 5), (3, 5, 2), (3, 8, 4), 
 def test_every_term_finds_its_entry(sbg, dim, nb, lmax):
     for prec in (sbg.SBG_PREC_FP32, sbg.SBG_PREC_BF16X3, sbg.SBG_PREC_TF32X3):
         nt, nr, cov = sbg.sbg_plan4_info(dim, nb, lmax, prec)
-        assert nt >= 1 and nr >= 1
-        if prec == sbg.SBG_PREC_FP32:
-            assert cov == 0
+        assert nt >= 1 and nr >= 1 and cov in (0, 1)
     # both tensor-core precisions share one plan
     assert sbg.sbg_plan4_info(dim, nb, lmax, sbg.SBG_PREC_BF16X3) == sbg.sbg_plan4_info(dim, nb, lmax,
                                                                                          sbg.SBG_PREC_TF32X3)
@@ -63,6 +61,14 @@ def test_greedy_cover_at_the_benchmark_geometry(sbg):
     need = _needed_triples(4, 10)
     assert need == 72510  # of 73060 parity/triangle triples, 550 have only zero couplings
     assert nr * 3 * 10 >= need
+
+
+def test_fp32_plan_at_the_benchmark_geometry(sbg):
+    # the SIMT kernel pays per (row, column) entry: the column-weighted greedy
+    # cover computes 134,320 entries per point instead of 239,360 (17,600 rows
+    # b1 <= b2 against columns b3 >= b2)
+    nt, nr, cov = sbg.sbg_plan4_info(3, 10, 4, sbg.SBG_PREC_FP32)
+    assert cov == 1 and nr < 17600
 
 
 def test_plan_argument_errors(sbg):
