@@ -173,6 +173,20 @@ def profiled_traffic(grid):
     return (kv["dram_bytes_read"] + kv["dram_bytes_write"]) * (grid / kv["grid"]) ** 3
 
 
+def conv_bytes_per_point(lmax=LMAX4, nb=NB):
+    """HBM bytes per grid point of the convolution stage (a3): per coefficient
+    array three axis passes of 8 B read + 8 B write, plus the 8-B kernel
+    spectrum read in the first pass (56 B).  The m = 0 arrays are real and go
+    two per complex transform: per pair 16 B of spectra + 8 B of delta-hat read
+    and 8 B written in the first pass, 16 B in the second, 8 B read and two
+    8-B singles written in the last (72 B per pair)."""
+    total = 0
+    for l in range(lmax + 1):
+        total += l * nb * 56              # m = 1..l
+        total += (nb // 2) * 72 + (nb % 2) * 56  # m = 0, packed
+    return total
+
+
 def field_for(rank, grid=256):
     from paper_2210_10206_gb300 import synth
     w = dict(synth.WORKLOADS[WORKLOAD])
@@ -336,10 +350,8 @@ def run_gpu(args):
                          "plan": float(stages[:, 2].mean()), "convolutions": conv_ms,
                          "combination": comb_ms, "finalise": float(stages[:, 6].mean()),
                          "contraction_kernel": kernel_ms},
-           # convolution stage: 150 coefficient arrays x 3 axis passes x (8 B read + 8 B write) per point
-           # plus the kernel spectrum read (8 B) of the first pass
-           "conv_gbs": 150 * 56 * ng / (conv_ms * 1e-3) / 1e9 if conv_ms else None,
-           "conv_hbm_frac": (150 * 56 * ng / (conv_ms * 1e-3) / 1e9) / hbm if conv_ms else None,
+           "conv_gbs": conv_bytes_per_point() * ng / (conv_ms * 1e-3) / 1e9 if conv_ms else None,
+           "conv_hbm_frac": (conv_bytes_per_point() * ng / (conv_ms * 1e-3) / 1e9) / hbm if conv_ms else None,
            "cold_first_call_s": t_plan, "cold_plan_ms": float(cold_stages[2]),
            "e2e": {"value": ws * 1000.0 / e_ms, "unit": "fields/s", "h2d_bytes_per_step": int(field.nbytes),
                    "d2h_bytes_per_step": int(z4.nbytes)},

@@ -812,15 +812,23 @@ void rec(sbg_context* ctx, int i) { cudaEventRecord(ctx->ev[i], ctx->stream); }
 // -------------------------------------------------------- FFT helpers ----
 // 3D transform in three axis passes; with final_out the last pass writes the
 // blocked coefficient store (singles single0 .. single0 + batch - 1 of nsingle).
+// npack > 0 (with LOAD_MUL and final_out): the npack factor arrays give
+// transforms with real results, packed two per complex transform (LOAD_MUL2,
+// batch = (npack + 1) / 2) and written back as singles single0 .. + npack - 1.
 sbg_status fft3(sbg_context* ctx, int n, int sign, int first_load, const void* in, float2* out, const float2* mul,
                 const float2* shared, int batch, const float2* tw, float2* final_out = nullptr, int nsingle = 0,
-                int single0 = 0, int prune_r = -1) {
+                int single0 = 0, int prune_r = -1, int npack = 0) {
   const long long ng = (long long)n * n * n;
   FftPass p{};
   p.twiddle = tw;
   p.batch = batch;
   p.bstride = ng;
   p.sign = sign;
+  if (npack > 0) {
+    if (first_load != LOAD_MUL || !final_out || batch != (npack + 1) / 2) return fail(ctx, SBG_ERR_INTERNAL, "fft3 packing");
+    first_load = LOAD_MUL2;
+    p.npack = npack;
+  }
   // z axis (strided by n^2), fused first-pass load
   p.in = in; p.out = out; p.mul = mul; p.shared = shared; p.load = first_load;
   p.outer = 1; p.inner = (long long)n * n;
@@ -838,7 +846,7 @@ sbg_status fft3(sbg_context* ctx, int n, int sign, int first_load, const void* i
   p.prune_mode = 0;
   p.outer = (long long)n * n; p.inner = 1;
   if (final_out) {
-    p.out = final_out; p.out_blocked = 1; p.nsingle = nsingle; p.single0 = single0;
+    p.out = final_out; p.out_blocked = npack > 0 ? 2 : 1; p.nsingle = nsingle; p.single0 = single0;
   }
   KL(fft_axis_pass(n, p, ctx->stream));
   return SBG_OK;
@@ -846,19 +854,24 @@ sbg_status fft3(sbg_context* ctx, int n, int sign, int first_load, const void* i
 
 sbg_status fft2(sbg_context* ctx, int n, int sign, int first_load, const void* in, float2* out, const float2* mul,
                 const float2* shared, int batch, long long bstride, const float2* tw, float2* final_out = nullptr,
-                int nsingle = 0, int single0 = 0) {
+                int nsingle = 0, int single0 = 0, int npack = 0) {
   FftPass p{};
   p.twiddle = tw;
   p.batch = batch;
   p.bstride = bstride;
   p.sign = sign;
+  if (npack > 0) {  // as in fft3
+    if (first_load != LOAD_MUL || !final_out || batch != (npack + 1) / 2) return fail(ctx, SBG_ERR_INTERNAL, "fft2 packing");
+    first_load = LOAD_MUL2;
+    p.npack = npack;
+  }
   p.in = in; p.out = out; p.mul = mul; p.shared = shared; p.load = first_load;
   p.outer = 1; p.inner = n;  // y axis
   KL(fft_axis_pass(n, p, ctx->stream));
   p.in = out; p.load = LOAD_COMPLEX; p.mul = nullptr; p.shared = nullptr;
   p.outer = n; p.inner = 1;  // x axis
   if (final_out) {
-    p.out = final_out; p.out_blocked = 1; p.nsingle = nsingle; p.single0 = single0;
+    p.out = final_out; p.out_blocked = npack > 0 ? 2 : 1; p.nsingle = nsingle; p.single0 = single0;
   }
   KL(fft_axis_pass(n, p, ctx->stream));
   return SBG_OK;
@@ -1036,10 +1049,19 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
     }
     const bool stored = g < ngroups4;
     float2* fin = stored ? d_astore : nullptr;
+    // m = 0: the kernels are real (Y_l0 is real; e^{-i 0 phi} = 1), so with a
+    // real delta every a^b is real and two bins share one complex inverse
+    // transform; only for stored groups (the 3PCF Gram of the others reads the
+    // transform output directly)
+    int l0 = 0;
+    while (dim == 3 && (l0 + 1) * (l0 + 2) / 2 <= g) ++l0;
+    const bool m0 = dim == 3 ? g == l0 * (l0 + 1) / 2 : g == 0;
+    const int npack = stored && m0 ? nb : 0;
+    const int nbatch = npack ? (nb + 1) / 2 : nb;
     if (dim == 3) {
-      ST(fft3(ctx, n, +1, LOAD_MUL, nullptr, d_group, G, d_dhat, nb, d_tw, fin, nsingle, g * nb));
+      ST(fft3(ctx, n, +1, LOAD_MUL, nullptr, d_group, G, d_dhat, nbatch, d_tw, fin, nsingle, g * nb, -1, npack));
     } else {
-      ST(fft2(ctx, n, +1, LOAD_MUL, nullptr, d_group, G, d_dhat, nb, ng, d_tw, fin, nsingle, g * nb));
+      ST(fft2(ctx, n, +1, LOAD_MUL, nullptr, d_group, G, d_dhat, nbatch, ng, d_tw, fin, nsingle, g * nb, npack));
     }
     if (do3 && g < ngroups3) {
       double* Sg = d_S + (size_t)g * nb * nb * 2;

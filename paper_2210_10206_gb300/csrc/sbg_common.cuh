@@ -15,7 +15,10 @@ __host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return mak
 __host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 
 // Launch-time knobs shared by the FFT launchers.
-enum FftLoad { LOAD_COMPLEX = 0, LOAD_REAL = 1, LOAD_MUL = 2 };
+// LOAD_MUL2: batch j multiplies `shared` by mul_{2j} + i mul_{2j+1} (mul_{2j+1}
+// taken as 0 past npack arrays), so that two transforms with real results share
+// one complex transform
+enum FftLoad { LOAD_COMPLEX = 0, LOAD_REAL = 1, LOAD_MUL = 2, LOAD_MUL2 = 3 };
 
 // One axis pass of a batched 3D/2D complex FFT.  The array is viewed as
 // [batch][outer][N][inner]; the pass transforms along the N axis.
@@ -30,10 +33,13 @@ struct FftPass {
   int batch;
   int sign;              // -1 forward, +1 inverse (unnormalised)
   int load;              // FftLoad
-  // Contiguous (last) pass only: when out_blocked is set, batch b of the output
+  // Contiguous (last) pass only: with out_blocked = 1, batch b of the output
   // goes to the blocked coefficient store as single s = single0 + b (see
-  // blocked_re).
+  // blocked_re); with out_blocked = 2 (the packed batches of LOAD_MUL2), the
+  // real part of batch b goes to single0 + 2b and the imaginary part to
+  // single0 + 2b + 1 (if 2b + 1 < npack), each with imaginary part 0.
   int out_blocked;
+  int npack;
   int nsingle;
   int single0;
   // Strided passes only: skip line groups that are known to be all zero (a

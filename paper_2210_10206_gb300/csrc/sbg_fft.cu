@@ -133,7 +133,7 @@ template <int N, bool CONTIG> struct Geo {
   }
 };
 
-template <int N, bool CONTIG, int SIGN, int LOAD, bool OUTB>
+template <int N, bool CONTIG, int SIGN, int LOAD, int OUTB>
 __global__ void __launch_bounds__(Geo<N, CONTIG>::THREADS)
 fft_axis_kernel(FftPass p) {
   using G = Geo<N, CONTIG>;
@@ -179,6 +179,15 @@ fft_axis_kernel(FftPass p) {
         v[n2] = make_float2(__ldg(reinterpret_cast<const float*>(p.in) + boff + e), 0.0f);
       } else if (LOAD == LOAD_MUL) {
         v[n2] = cmul(__ldg(p.shared + e), __ldg(p.mul + boff + e));
+      } else if (LOAD == LOAD_MUL2) {
+        const long long ia = 2 * boff + e;
+        float2 f = __ldg(p.mul + ia);
+        if (2 * (int)blockIdx.y + 1 < p.npack) {
+          const float2 g = __ldg(p.mul + ia + p.bstride);
+          f.x -= g.y;
+          f.y += g.x;
+        }
+        v[n2] = cmul(__ldg(p.shared + e), f);
       } else {
         v[n2] = __ldg(reinterpret_cast<const float2*>(p.in) + boff + e);
       }
@@ -204,10 +213,20 @@ fft_axis_kernel(FftPass p) {
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       const long long e = base + (long long)(k2 + R2 * k1) * estride;
-      if (OUTB) {
+      if (OUTB == 1) {
         float* o = reinterpret_cast<float*>(p.out) + blocked_re(e, p.single0 + (int)blockIdx.y, p.nsingle);
         o[0] = u[k1].x;
         o[32] = u[k1].y;
+      } else if (OUTB == 2) {
+        const int s = p.single0 + 2 * (int)blockIdx.y;
+        float* o = reinterpret_cast<float*>(p.out) + blocked_re(e, s, p.nsingle);
+        o[0] = u[k1].x;
+        o[32] = 0.0f;
+        if (2 * (int)blockIdx.y + 1 < p.npack) {
+          o = reinterpret_cast<float*>(p.out) + blocked_re(e, s + 1, p.nsingle);
+          o[0] = u[k1].y;
+          o[32] = 0.0f;
+        }
       } else {
         p.out[boff + e] = u[k1];
       }
@@ -215,7 +234,7 @@ fft_axis_kernel(FftPass p) {
   }
 }
 
-template <int N, bool CONTIG, int SIGN, int LOAD, bool OUTB = false>
+template <int N, bool CONTIG, int SIGN, int LOAD, int OUTB = 0>
 static cudaError_t launch_t(const FftPass& p, cudaStream_t st) {
   using G = Geo<N, CONTIG>;
   auto kern = fft_axis_kernel<N, CONTIG, SIGN, LOAD, OUTB>;
@@ -241,7 +260,11 @@ static cudaError_t dispatch_n(const FftPass& p, cudaStream_t st) {
     if (p.load != LOAD_COMPLEX) return cudaErrorInvalidValue;
     if (p.out_blocked) {
       if (p.sign < 0) return cudaErrorInvalidValue;
-      return launch_t<N, true, 1, LOAD_COMPLEX, true>(p, st);
+      if (p.out_blocked == 2) {
+        if (p.npack < 1 || p.npack > 2 * p.batch) return cudaErrorInvalidValue;
+        return launch_t<N, true, 1, LOAD_COMPLEX, 2>(p, st);
+      }
+      return launch_t<N, true, 1, LOAD_COMPLEX, 1>(p, st);
     }
     return p.sign < 0 ? launch_t<N, true, -1, LOAD_COMPLEX>(p, st) : launch_t<N, true, 1, LOAD_COMPLEX>(p, st);
   }
@@ -252,6 +275,10 @@ static cudaError_t dispatch_n(const FftPass& p, cudaStream_t st) {
     return cudaErrorInvalidValue;
   }
   if (p.load == LOAD_MUL) return launch_t<N, false, 1, LOAD_MUL>(p, st);
+  if (p.load == LOAD_MUL2) {
+    if (p.npack < 1 || p.npack > 2 * p.batch) return cudaErrorInvalidValue;
+    return launch_t<N, false, 1, LOAD_MUL2>(p, st);
+  }
   if (p.load == LOAD_COMPLEX) return launch_t<N, false, 1, LOAD_COMPLEX>(p, st);
   return cudaErrorInvalidValue;
 }

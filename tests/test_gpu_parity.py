@@ -121,8 +121,11 @@ def test_full_3pcf_only_and_4pcf_only_agree_with_combined(ctx):
     b3, _ = ctx.full(f, edges, lmax3=3)
     _, c4 = ctx.full(f, edges, lmax4=2)
     # same sums through two coefficient layouts; FP64 atomics across CTAs add
-    # in no fixed order, so agreement is to rounding, not bitwise
-    assert _err(b3, a3) < 1e-12
+    # in no fixed order, so agreement is to rounding, not bitwise.  With a 4PCF
+    # the m = 0 coefficients come from transforms packed two real results per
+    # complex transform (a^b_l0 is real, Eq. almconv with a real kernel), without
+    # one from one transform each: the 3PCFs then agree to FP32 rounding
+    assert _err(b3, a3) < 1e-6
     assert _err(c4, a4) < 1e-12
 
 
