@@ -436,7 +436,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
       blocks.push_back(std::move(bk));
     }
   const int col_chunk = tc ? (dim == 2 ? 32 : 64) : 64;
-  const int max_u = tc ? kTcMaxRowSlots : 128;
+  const int max_u = tc ? kTcMaxRowSlots : kSimtMaxUniq;
   auto sidx = [&](int a, int b) { return store_index(dim, nb, angs[a].l, std::abs(angs[a].m), b); };
   // tensor-core tiles of 128 rows that the packing below makes of a block's rows
   auto count_tiles = [&](const std::vector<RowKey>& rows) -> long long {
@@ -1128,9 +1128,8 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
       for (int k = 0; k < 3; ++k) {
         const int ntl = (int)t.tiles[k].size();
         if (!ntl) continue;
-        int nsplit = (int)std::max<long long>(1, std::min<long long>(ng / 32, (152LL * 6 + ntl - 1) / ntl));
         KL(launch_simt4(d_astore, ng, d_delta, (const Tile4*)t.d_tiles[k].p, ntl, (const Row4*)t.d_rows.p,
-                        (const int*)t.d_cols.p, (const int*)t.d_uniq.p, cplx, tcg[k], nsplit, nsingle, d_T,
+                        (const int*)t.d_cols.p, (const int*)t.d_uniq.p, cplx, tcg[k], 0, nsingle, d_T, ctx->nsm,
                         ctx->stream));
       }
       CU(cudaEventRecord(ctx->kev[1], ctx->stream));

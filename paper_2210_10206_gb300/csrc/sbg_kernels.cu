@@ -1,5 +1,7 @@
 // Preprocessing, kernel generation, 3PCF Gram, FP32 SIMT 4PCF contraction and
 // FP64 finalisation kernels.
+#include <algorithm>
+
 #include "sbg_kernels.cuh"
 
 namespace sbg {
@@ -236,14 +238,29 @@ cudaError_t launch_gram3(const float2* a, long long ng, int nb, const float* del
 // ------------------------------------------------------------------ simt4 --
 // T[r][c] = sum_x delta(x) f1_r(x) f2_r(x) a_c(x): the pair-by-single contraction
 // of the 4PCF (Eq. mu of Sec. 2.3, Eq. proj_4pcf_coeff) as an FP32 SIMT GEMM over
-// x with the pair operand formed on chip.  Per 32-point chunk: the tile's unique
-// singles and its column singles are staged in shared memory, the pair products
-// P_r = delta f1 f2 are formed once, then each thread accumulates a 4x4 block of
-// rows x cols.  FP32 over 512-point spans, FP64 across spans and CTAs.
+// x with the pair operand formed on chip.  Per 32-point chunk the tile's row
+// singles, its column singles and delta are copied with cp.async into one of two
+// raw buffers while the previous chunk is computed; then the pair products
+// P_r = sign delta f1 f2 and the transposed columns are formed in shared memory
+// and each thread accumulates a 4x4 block of rows x cols.  FP32 over 512-point
+// spans, FP64 across spans and CTAs.
 constexpr int kX = 32;          // points per chunk
-constexpr int kMaxUniq = 128;   // staged singles per tile
 constexpr int kSpan = 16;       // chunks per FP32 span
-constexpr int kUS = kX + 1;     // padded row of a staged single (bank spread)
+constexpr int kRawF = 68;       // floats per raw row: Re x0..31, Im x0..31, pad (16-byte multiple)
+
+__device__ __forceinline__ void simt_cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+
+template <int TCG>
+struct SimtSmem {
+  static constexpr int TR = 4 * (256 / TCG), TC = 4 * TCG;
+  static constexpr int kRawU = kSimtMaxUniq * kRawF;  // floats of one raw row-single buffer
+  static constexpr int kRawC = TC * kRawF;             // floats of one raw column buffer
+  static constexpr int kRaw = kRawU + kRawC + kX;      // one raw buffer (+ delta)
+  static constexpr size_t kBytes = (size_t)(2 * kRaw) * 4 + (size_t)(kX * TR + kX * TC) * 8;
+};
 
 template <int TCG, bool CPLX>
 __global__ void __launch_bounds__(256) simt4_kernel(const float2* __restrict__ astore, long long ng,
@@ -251,19 +268,41 @@ __global__ void __launch_bounds__(256) simt4_kernel(const float2* __restrict__ a
                                                     const Row4* __restrict__ rows, const int* __restrict__ cols,
                                                     const int* __restrict__ uniq, int nsplit, int nsingle,
                                                     double* __restrict__ T) {
-  constexpr int TRG = 256 / TCG;
-  constexpr int TR = 4 * TRG, TC = 4 * TCG;
+  using SM = SimtSmem<TCG>;
+  constexpr int TR = SM::TR, TC = SM::TC;
   extern __shared__ float4 smem4[];
-  float2* Ps = reinterpret_cast<float2*>(smem4);            // [kX][TR]
-  float2* Cs = Ps + kX * TR;                                 // [kX][TC]
-  float2* Us = Cs + kX * TC;                                 // [kMaxUniq][kUS]
-  float* Ds = reinterpret_cast<float*>(Us + kMaxUniq * kUS);  // [kX]
+  float* raw = reinterpret_cast<float*>(smem4);                       // [2][kRaw]
+  float2* Ps = reinterpret_cast<float2*>(raw + 2 * SM::kRaw);         // [kX][TR]
+  float2* Cs = Ps + kX * TR;                                          // [kX][TC]
 
   const Tile4 tl = tiles[blockIdx.x];
+  // the plan keeps tiles within the staging buffers; a tile that is not is skipped
+  if (tl.nuniq > kSimtMaxUniq || tl.ncols > TC || tl.nrows > TR) return;
   const int tid = threadIdx.x;
   const int cg = tid % TCG, rg = tid / TCG;
   const long long per = ((ng / kX + nsplit - 1) / nsplit) * kX;
   const long long x0 = blockIdx.y * per, x1 = min(ng, x0 + per);
+
+  // copy chunk xc (raw blocked rows: 16 chunks of 16 B per single) into buffer b
+  auto stage = [&](long long xc, int b) {
+    float* ru = raw + b * SM::kRaw;
+    float* rc = ru + SM::kRawU;
+    float* rd = rc + SM::kRawC;
+    const float* base = reinterpret_cast<const float*>(astore) + (xc / kX) * (long long)nsingle * 64;
+    const int nu = tl.nuniq * 16, nc = tl.ncols * 16;
+    for (int i = tid; i < nu + nc + 8; i += 256) {
+      if (i < nu) {
+        simt_cp16(ru + (i >> 4) * kRawF + (i & 15) * 4, base + uniq[tl.uniq0 + (i >> 4)] * 64 + (i & 15) * 4);
+      } else if (i < nu + nc) {
+        const int k = i - nu;
+        simt_cp16(rc + (k >> 4) * kRawF + (k & 15) * 4, base + cols[tl.col0 + (k >> 4)] * 64 + (k & 15) * 4);
+      } else {
+        const int k = i - nu - nc;
+        simt_cp16(rd + k * 4, delta + xc + k * 4);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
 
   float acc[4][4][CPLX ? 2 : 1];
   double dacc[4][4][CPLX ? 2 : 1];
@@ -274,36 +313,37 @@ __global__ void __launch_bounds__(256) simt4_kernel(const float2* __restrict__ a
 #pragma unroll
       for (int c = 0; c < (CPLX ? 2 : 1); ++c) { acc[i][k][c] = 0.f; dacc[i][k][c] = 0.0; }
 
-  int span = 0;
-  for (long long xc = x0; xc < x1; xc += kX) {
+  int span = 0, b = 0;
+  if (x0 < x1) stage(x0, 0);
+  for (long long xc = x0; xc < x1; xc += kX, b ^= 1) {
+    // prefetch the next chunk into the other buffer (its last readers finished
+    // before the barrier that ended the previous iteration)
+    if (xc + kX < x1) {
+      stage(xc + kX, b ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
     __syncthreads();
-    // stage unique singles and delta
-    for (int i = tid; i < tl.nuniq * kX; i += 256) {
-      const int u = i / kX, xx = i % kX;
-      const float* f = reinterpret_cast<const float*>(astore) + blocked_re(xc + xx, uniq[tl.uniq0 + u], nsingle);
-      Us[u * kUS + xx] = make_float2(f[0], f[32]);
+    const float* ru = raw + b * SM::kRaw;
+    const float* rc = ru + SM::kRawU;
+    const float* rd = rc + SM::kRawC;
+    // columns, transposed to [x][c] (zero past the tile's columns)
+    for (int i = tid; i < TC * kX; i += 256) {
+      const int c = i % TC, xx = i / TC;
+      Cs[xx * TC + c] = c < tl.ncols ? make_float2(rc[c * kRawF + xx], rc[c * kRawF + 32 + xx]) : make_float2(0.f, 0.f);
     }
-    for (int i = tid; i < tl.ncols * kX; i += 256) {
-      const int c = i / kX, xx = i % kX;
-      const float* f = reinterpret_cast<const float*>(astore) + blocked_re(xc + xx, cols[tl.col0 + c], nsingle);
-      Cs[xx * TC + c] = make_float2(f[0], f[32]);
-    }
-    for (int i = tid; i < (TC - tl.ncols) * kX; i += 256) {
-      const int c = tl.ncols + i / kX, xx = i % kX;
-      Cs[xx * TC + c] = make_float2(0.f, 0.f);
-    }
-    if (tid < kX) Ds[tid] = delta[xc + tid];
-    __syncthreads();
-    // form pair products P_r(x) = sign * delta * f1 * f2
+    // pair products P_r(x) = sign * delta * f1 * f2
     for (int i = tid; i < TR * kX; i += 256) {
       const int r = i % TR, xx = i / TR;
       float2 p = make_float2(0.f, 0.f);
       if (r < tl.nrows) {
         const Row4 rw = rows[tl.row0 + r];
-        float2 f1 = Us[rw.u1 * kUS + xx], f2 = Us[rw.u2 * kUS + xx];
+        float2 f1 = make_float2(ru[rw.u1 * kRawF + xx], ru[rw.u1 * kRawF + 32 + xx]);
+        float2 f2 = make_float2(ru[rw.u2 * kRawF + xx], ru[rw.u2 * kRawF + 32 + xx]);
         if (rw.flags & 1) f1.y = -f1.y;
         if (rw.flags & 2) f2.y = -f2.y;
-        const float s = rw.sign * Ds[xx];
+        const float s = rw.sign * rd[xx];
         p = cmul(f1, f2);
         p.x *= s;
         p.y *= s;
@@ -335,6 +375,7 @@ __global__ void __launch_bounds__(256) simt4_kernel(const float2* __restrict__ a
 #pragma unroll
           for (int c = 0; c < (CPLX ? 2 : 1); ++c) { dacc[i][k][c] += acc[i][k][c]; acc[i][k][c] = 0.f; }
     }
+    __syncthreads();  // Ps, Cs and this raw buffer are free for the next chunk
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -356,15 +397,33 @@ __global__ void __launch_bounds__(256) simt4_kernel(const float2* __restrict__ a
 template <int TCG, bool CPLX>
 static cudaError_t simt4_t(const float2* astore, long long ng, const float* delta, const Tile4* tiles, int ntiles,
                           const Row4* rows, const int* cols, const int* uniq, int nsplit, int nsingle, double* T,
-                          cudaStream_t st) {
-  constexpr int TR = 4 * (256 / TCG), TC = 4 * TCG;
-  const size_t smem = (size_t)(kX * TR + kX * TC + kMaxUniq * kUS) * sizeof(float2) + kX * sizeof(float);
+                          int nsm, cudaStream_t st) {
+  const size_t smem = SimtSmem<TCG>::kBytes;
   auto kern = simt4_kernel<TCG, CPLX>;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
+  }
+  if (nsplit <= 0) {
+    // x-splits per tile so that the CTAs fill whole waves of the resident
+    // slots (SMs x CTAs per SM): the best fill over 2..8 waves, fewer on ties
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    if (e != cudaSuccess) return e;
+    const long long slots = (long long)nsm * (per_sm > 0 ? per_sm : 1), chunks = ng / kX;
+    double best = -1.0;
+    nsplit = 1;
+    for (int w = 2; w <= 8; ++w) {
+      const long long ns = std::max<long long>(1, std::min<long long>(chunks, slots * w / ntiles));
+      const long long units = ns * ntiles;
+      const double fill = (double)units / (double)(slots * ((units + slots - 1) / slots));
+      if (fill > best + 1e-3) {
+        best = fill;
+        nsplit = (int)ns;
+      }
+    }
   }
   dim3 grid((unsigned)ntiles, (unsigned)nsplit);
   kern<<<grid, 256, smem, st>>>(astore, ng, delta, tiles, rows, cols, uniq, nsplit, nsingle, T);
@@ -373,17 +432,17 @@ static cudaError_t simt4_t(const float2* astore, long long ng, const float* delt
 
 cudaError_t launch_simt4(const float2* astore, long long ng, const float* delta, const Tile4* tiles, int ntiles,
                          const Row4* rows, const int* cols, const int* uniq, int complex_out, int tcg, int nsplit,
-                         int nsingle, double* T, cudaStream_t st) {
+                         int nsingle, double* T, int nsm, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   if (ng % kX) return cudaErrorInvalidValue;
   if (complex_out) {
-    if (tcg == 4) return simt4_t<4, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, st);
-    if (tcg == 8) return simt4_t<8, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, st);
-    if (tcg == 16) return simt4_t<16, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, st);
+    if (tcg == 4) return simt4_t<4, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, st);
+    if (tcg == 8) return simt4_t<8, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, st);
+    if (tcg == 16) return simt4_t<16, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, st);
   } else {
-    if (tcg == 4) return simt4_t<4, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, st);
-    if (tcg == 8) return simt4_t<8, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, st);
-    if (tcg == 16) return simt4_t<16, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, st);
+    if (tcg == 4) return simt4_t<4, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, st);
+    if (tcg == 8) return simt4_t<8, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, st);
+    if (tcg == 16) return simt4_t<16, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, st);
   }
   return cudaErrorInvalidValue;
 }

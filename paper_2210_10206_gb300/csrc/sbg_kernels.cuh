@@ -41,9 +41,10 @@ struct Row4 {
 };
 
 // T[tile][r][c] (+)= Re or complex of sum_x delta * f1 * f2 * a_col.
+// nsplit <= 0: x-splits per tile chosen to fill whole waves of nsm SMs.
 cudaError_t launch_simt4(const float2* astore, long long ng, const float* delta, const Tile4* tiles,
                          int ntiles, const Row4* rows, const int* cols, const int* uniq, int complex_out,
-                         int tcg, int nsplit, int nsingle, double* T, cudaStream_t st);
+                         int tcg, int nsplit, int nsingle, double* T, int nsm, cudaStream_t st);
 
 // Tensor-core (tcgen05) split-BF16 version of the same contraction (sbg_tc.cu).
 // Tiles of <= 128 rows whose row singles (<= kTcMaxRowSlots, in the slot order
@@ -56,6 +57,7 @@ cudaError_t launch_simt4(const float2* astore, long long ng, const float* delta,
 // and stride is twice as large (bimg must hold 2 * nkb * img_stride bytes).
 // *err is set (never cleared) if a bounded wait inside the kernel expired.
 constexpr int kTcMaxRowSlots = 56;  // row singles staged per K-block
+constexpr int kSimtMaxUniq = 64;    // row singles staged per chunk by the FP32 SIMT kernel
 constexpr int kTcEpoch = 256;       // K-blocks between progress checkpoints of the lag limiter
 struct BGroup {
   int col0, ncols;     // columns (global col table)
