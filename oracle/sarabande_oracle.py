@@ -26,6 +26,8 @@ with its reason in the design notes of the repository):
   omits it).
 * Full 4PCF: even-parity Lambda in the loop order of Algorithm 6, the full sum
   over M with |m3| <= l3, coupling C^Lambda_M = (-1)^(l1+l2+l3) (3j) (Sec. 2.3).
+  Odd-parity Lambda (l1 + l2 + l3 odd) take E(Lambda) = -1 of Eq. mu; their
+  M-sum is imaginary for a real delta and is reported as its imaginary part.
 * Projected 4PCF: c_{-m} taken from its own kernel e^{+i m phi} (equal to
   conj(c_m), Sec. 2.2), all (m1, m2) with |m1|, |m2|, |m1 + m2| <= mmax.
 
@@ -43,6 +45,7 @@ __all__ = [
     "a_full", "c_projected", "zeta3_full", "zeta4_full", "zeta3_projected",
     "zeta4_projected", "lambda_list", "wigner3j", "coupling",
     "normalization", "preprocess", "brute_a", "zeta4_full_entries", "kernel_full_bin",
+    "lambda_list_odd", "zeta4_full_odd",
 ]
 
 
@@ -246,6 +249,19 @@ def lambda_list(lmax):
     return out
 
 
+def lambda_list_odd(lmax):
+    """Odd-parity Lambda = (l1, l2, l3): the loops of Algorithm 6 (l1, l2 in
+    0..lmax, l3 from |l1-l2| to min(l1+l2, lmax)) keeping l1+l2+l3 odd, the
+    Lambda with E(Lambda) = -1 in Eq. mu (Sec. 2.3)."""
+    out = []
+    for l1 in range(lmax + 1):
+        for l2 in range(lmax + 1):
+            for l3 in range(abs(l1 - l2), min(l1 + l2, lmax) + 1):
+                if (l1 + l2 + l3) % 2 == 1:
+                    out.append((l1, l2, l3))
+    return out
+
+
 def wigner3j(j1, j2, j3, m1, m2, m3):
     """Wigner 3j symbol by the Racah formula in exact rational arithmetic,
     returned as float (the 3j of the coupling in Sec. 2.3)."""
@@ -303,6 +319,32 @@ def zeta4_full(delta, edges, lmax, return_imag=False):
                     continue
                 z[i] += c * triple_sum(d, a[(l1, m1)], a[(l2, m2)], a[(l3, m3)])
     return (z.real, z.imag) if return_imag else z.real
+
+
+def zeta4_full_odd(delta, edges, lmax, return_real=False):
+    """Odd-parity 4PCF: zeta^{b1 b2 b3}_{l1 l2 l3} = sum_x delta(x) sum_M
+    E(Lambda) C^Lambda_M a^{b1}_{l1 m1} a^{b2}_{l2 m2} a^{b3}_{l3 m3} with
+    E(Lambda) = -1 (Eq. mu of Sec. 2.3), m3 = -(m1 + m2), |m3| <= l3, for the
+    odd Lambda of lambda_list_odd.  For a real delta the terms M and -M are
+    each other's negated conjugates, so the sum is imaginary: the coefficient is
+    returned as its imaginary part (with return_real, also the real part, which
+    is zero up to rounding).  Shape [nLambda_odd, nb, nb, nb], all bin triples."""
+    nb = len(edges) - 1
+    lams = lambda_list_odd(lmax)
+    a = _all_a(delta, edges, lmax)
+    d = delta.reshape(1, -1)
+    z = np.zeros((len(lams), nb, nb, nb), dtype=np.complex128)
+    for i, (l1, l2, l3) in enumerate(lams):
+        for m1 in range(-l1, l1 + 1):
+            for m2 in range(-l2, l2 + 1):
+                m3 = -(m1 + m2)
+                if abs(m3) > l3:
+                    continue
+                c = coupling(l1, l2, l3, m1, m2, m3)
+                if c == 0.0:
+                    continue
+                z[i] -= c * triple_sum(d, a[(l1, m1)], a[(l2, m2)], a[(l3, m3)])  # E(Lambda) = -1
+    return (z.imag, z.real) if return_real else z.imag
 
 
 def triple_sum(d, a1, a2, a3):

@@ -67,3 +67,21 @@ def test_off_by_one_bin_edge_is_caught(monkeypatch):
         return [(r2 >= e2[b]) & (r2 <= e2[b + 1]) for b in range(len(edges) - 1)]
     monkeypatch.setattr(O, "bin_masks", loose)
     assert _fails(pins.test_bin_counts_match_explicit_offsets)
+
+
+def test_odd_parity_sign_and_part_are_caught(monkeypatch):
+    # E(Lambda) dropped (the odd sum taken with +1), or the real part reported
+    orig = O.zeta4_full_odd
+
+    def no_parity_sign(delta, edges, lmax, return_real=False):
+        r = orig(delta, edges, lmax, return_real)
+        return (-r[0], -r[1]) if return_real else -r
+    monkeypatch.setattr(O, "zeta4_full_odd", no_parity_sign)
+    assert _fails(pins.test_zeta4_full_odd_brute_force_triple_sums)
+    monkeypatch.setattr(O, "zeta4_full_odd", orig)
+
+    def real_part(delta, edges, lmax, return_real=False):
+        im, re = orig(delta, edges, lmax, True)
+        return (re, im) if return_real else re
+    monkeypatch.setattr(O, "zeta4_full_odd", real_part)
+    assert _fails(pins.test_zeta4_full_odd_brute_force_triple_sums)

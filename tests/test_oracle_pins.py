@@ -280,6 +280,60 @@ def test_zeta4_full_brute_force_triple_sums():
                     assert abs(z[i, b1, b2, b3] - ref.real) <= 1e-12 * np.abs(z).max(), (lam, b1, b2, b3)
 
 
+def test_lambda_list_odd_enumeration():
+    # every odd (l1, l2, l3) obeying the triangle rule with each l <= lmax, once,
+    # in the loop order of Algorithm 6 (l1, then l2, then l3 ascending)
+    import itertools
+    for lmax in range(0, 6):
+        want = sorted(t for t in itertools.product(range(lmax + 1), repeat=3)
+                      if sum(t) % 2 == 1 and abs(t[0] - t[1]) <= t[2] <= t[0] + t[1])
+        got = O.lambda_list_odd(lmax)
+        assert got == want, lmax
+    assert O.lambda_list_odd(0) == [] and O.lambda_list_odd(1) == [(1, 1, 1)]
+
+
+def test_zeta4_full_odd_brute_force_triple_sums():
+    # P1 for the odd-parity 4PCF.  The a-coefficients carry Y* (Eq. almconv),
+    # so sum_M C a a a = sum_x delta sum_{r1,r2,r3} delta delta delta
+    # conj(P_Lambda); for odd Lambda conj(P_Lambda) = -P_Lambda (P is
+    # imaginary), and E(Lambda) = -1 of Eq. mu cancels that sign:
+    # zeta = sum delta delta delta delta P_Lambda, reported as its imaginary part
+    d = RNG.normal(size=(6, 6, 6))
+    edges = [0.5, 1.5, 2.0]
+    offs = _offsets_in_bins(d.shape, edges)
+    lmax = 2
+    z, zr = O.zeta4_full_odd(d, edges, lmax, return_real=True)
+    lams = O.lambda_list_odd(lmax)
+    assert len(lams) == 4 and np.abs(z).max() > 0
+    sh = [np.stack([_shift(d, r) for r in ob]).reshape(len(ob), -1) for ob in offs]
+    dd = d.reshape(-1)
+    for b1 in range(2):
+        for b2 in range(2):
+            for b3 in range(2):
+                F = np.einsum("x,ix,jx,kx->ijk", dd, sh[b1], sh[b2], sh[b3])
+                for i, lam in enumerate(lams):
+                    ref = np.sum(F * _P_lambda(lam, offs[b1], offs[b2], offs[b3]))
+                    assert abs(ref.real) < 1e-10 * max(1.0, abs(ref.imag))
+                    assert abs(z[i, b1, b2, b3] - ref.imag) <= 1e-12 * np.abs(z).max(), (lam, b1, b2, b3)
+    assert np.abs(zr).max() <= 1e-12 * np.abs(z).max()
+
+
+def test_zeta4_full_odd_parity_under_mirror_and_rotations():
+    # odd Lambda: a mirror flips the sign, proper rotations and shifts keep it;
+    # a mirror-symmetric field has no odd-parity 4PCF
+    d = RNG.normal(size=(8, 8, 8))
+    edges = [0.5, 1.5, 2.5, 3.5]
+    z = O.zeta4_full_odd(d, edges, 2)
+    assert np.abs(z).max() > 0
+    for t in [np.roll(d, (2, 1, 3), axis=(0, 1, 2)), np.rot90(d, 1, axes=(0, 1)), np.rot90(d, 1, axes=(1, 2))]:
+        assert _rel(O.zeta4_full_odd(np.ascontiguousarray(t), edges, 2), z) < 1e-11
+    for ax in range(3):
+        m = np.ascontiguousarray(np.flip(d, axis=ax))
+        assert _rel(O.zeta4_full_odd(m, edges, 2), -z) < 1e-11
+    sym = d + np.roll(np.flip(d, axis=2), 1, axis=2)  # f(z, y, -x) = f(z, y, x) on the periodic grid
+    assert np.abs(O.zeta4_full_odd(sym, edges, 2)).max() <= 1e-11 * np.abs(O.zeta4_full(sym, edges, 2)).max()
+
+
 def test_zeta4_full_l3_zero_reduces_to_weighted_3pcf():
     # P4: zeta_{l l 0}^{b1 b2 b3}[delta] = 3PCF_l^{b1 b2} with primary weight delta*S_b3/sqrt(4pi)
     d = RNG.normal(size=(8, 8, 8))
