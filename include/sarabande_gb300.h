@@ -117,6 +117,29 @@ sbg_status sbg_full(sbg_context* ctx, const void* field, sbg_dtype dtype, const 
                     const double* edges, int nbins, int lmax3, int lmax4, sbg_precision prec,
                     unsigned flags, double* zeta3, double* zeta4);
 
+/* Number of odd-parity Lambda (l1 + l2 + l3 odd, triangle rule, each l <=
+ * lmax) for lmax in 0..10: 1 at lmax 1, 4 at lmax 2, 23 at lmax 4. */
+sbg_status sbg_lambda_odd_count(int lmax, int* n_lambda);
+
+/* The odd-parity list as 3 ints per entry, in the loop order of Algorithm 6
+ * (as sbg_lambda_list): the first axis of zeta4_odd of sbg_full_odd. */
+sbg_status sbg_lambda_odd_list(int lmax, int* l123);
+
+/* Odd-parity full (3D) 4PCF (Eq. mu, Sec. 2.3, with E(Lambda) = -1: the Lambda
+ * that Algorithm 6 skips).  For a real field the sum over M of an odd Lambda is
+ * imaginary (the terms M and -M are each other's negated conjugates), so each
+ * coefficient is returned as its imaginary part:
+ *   zeta4_odd : out, [n_odd(lmax4)][nbins][nbins][nbins] real, Lambda order of
+ *               sbg_lambda_odd_list; zeta = Im sum_x delta sum_M E(Lambda)
+ *               C^Lambda_M a a a, every bin triple.
+ * field, dtype, shape, edges, nbins and prec as for sbg_full; lmax4 in 1..5;
+ * flags: SBG_SUBTRACT_MEAN, SBG_NORMALIZED, SBG_FIELD_ON_DEVICE (the 4PCF is
+ * implied).  A mirror image of the field flips the sign of every coefficient.
+ * Errors as for sbg_full. */
+sbg_status sbg_full_odd(sbg_context* ctx, const void* field, sbg_dtype dtype, const int64_t shape[3],
+                        const double* edges, int nbins, int lmax4, sbg_precision prec, unsigned flags,
+                        double* zeta4_odd);
+
 /* Projected (2D) 3PCF and 4PCF of one periodic field (Secs. 2.2 and 2.4;
  * Algorithms 2, 4, 7, 8).
  *   shape   : n0 = n1 = N, a power of two in 8..1024; nbins 1..20; mmax 0..10.
@@ -174,7 +197,8 @@ sbg_status sbg_last_contraction_ms(const sbg_context* ctx, double* ms);
 /* Tile plan of the 4PCF combination, on the host only (no context, no GPU,
  * no device memory).  It builds the tables that sbg_full (dim 3, order lmax =
  * lmax4) or sbg_projected (dim 2, lmax = mmax) uses for nbins bins at
- * precision prec, and so checks that every output term of Algorithm 6 (full,
+ * precision prec (odd = 1: the odd-parity tables of sbg_full_odd, dim 3
+ * only), and so checks that every output term of Algorithm 6 (full,
  * Eq. mu, Sec. 2.3) or Algorithm 8 (projected, Eq. proj_4pcf_coeff, Sec. 2.4)
  * finds its entry among the computed pair x single products.  Outputs (each
  * may be NULL):
@@ -187,9 +211,11 @@ sbg_status sbg_last_contraction_ms(const sbg_context* ctx, double* ms);
  *              needed triples; the plan keeps the one with fewer tiles (tensor
  *              core) or fewer pair x column entries (FP32).
  * Errors: SBG_ERR_INVALID_ARG for dim not 2 or 3, nbins outside 1..20, lmax
- * outside 0..5 (3D) or 0..10 (2D) or an unknown precision; SBG_ERR_INTERNAL
+ * outside 0..5 (3D) or 0..10 (2D), an unknown precision, or odd not 0 / 1 (1
+ * only with dim 3); SBG_ERR_INTERNAL
  * if a term finds no entry (a defect of the plan). */
-sbg_status sbg_plan4_info(int dim, int nbins, int lmax, sbg_precision prec, int* ntiles, int* nrows, int* covering);
+sbg_status sbg_plan4_info(int dim, int nbins, int lmax, sbg_precision prec, int odd, int* ntiles, int* nrows,
+                          int* covering);
 
 /* Projected 3PCF that allocates no device memory (the paper has no
  * counterpart: this entry point exists for callers that cannot call cudaMalloc

@@ -354,7 +354,11 @@ sbg_status colour_slots(sbg_context* ctx, Tables4& t, Tile4& tl, const std::map<
 //   tc = true : tensor-core tiles of 128 rows (M of the MMA), <= kTcMaxRowSlots
 //               staged singles, <= 64 B-operand rows (2D: 2 per column single);
 //               one block per m3 >= 0 with columns (b3, l3 >= m3).
-sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, bool tc, bool to_device = true) {
+sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, bool tc, bool odd = false,
+                         bool to_device = true) {
+  // complex T: the projected 4PCF, and the odd-parity 3D 4PCF (its M-sum is
+  // imaginary, Eq. mu with E(Lambda) = -1)
+  const bool cplx = dim == 2 || odd;
   struct Ang { int l, m; };
   std::vector<Ang> angs;
   if (dim == 3) {
@@ -435,7 +439,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
       bk.ncols = (nb - bk.bcol0) * (int)bk.l3s.size();
       blocks.push_back(std::move(bk));
     }
-  const int col_chunk = tc ? (dim == 2 ? 32 : 64) : 64;
+  const int col_chunk = tc ? (cplx ? 32 : 64) : 64;
   const int max_u = tc ? kTcMaxRowSlots : kSimtMaxUniq;
   auto sidx = [&](int a, int b) { return store_index(dim, nb, angs[a].l, std::abs(angs[a].m), b); };
   // tensor-core tiles of 128 rows that the packing below makes of a block's rows
@@ -492,7 +496,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
       return ((long long)u[0] * S + u[1]) * S + u[2];
     };
     auto needed = [&](int l1, int l2, int l3) {
-      return dim == 2 || (((l1 + l2 + l3) & 1) == 0 && std::abs(l1 - l2) <= l3 && l3 <= l1 + l2);
+      return dim == 2 || (((l1 + l2 + l3) & 1) == (odd ? 1 : 0) && std::abs(l1 - l2) <= l3 && l3 <= l1 + l2);
     };
     auto canon = [](int a1, int b1, int a2, int b2) -> RowKey {  // b1 <= b2; a1 <= a2 when b1 == b2
       if (b1 > b2 || (b1 == b2 && a1 > a2)) return {a2, b2, a1, b1};
@@ -609,7 +613,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
         BGroup g{};
         g.col0 = col0;
         g.ncols = nc;
-        g.n = ((dim == 2 ? 2 * nc : nc) + 15) & ~15;
+        g.n = ((cplx ? 2 * nc : nc) + 15) & ~15;
         // the kernel's B stage holds 2n rows of 128 bytes and its inner
         // accumulator 3n TMEM columns: n <= 64
         if (g.n > 64) return fail(ctx, SBG_ERR_INTERNAL, "tensor-core column group wider than 64");
@@ -723,14 +727,16 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
     for (int l1 = 0; l1 <= L; ++l1)
       for (int l2 = 0; l2 <= L; ++l2)
         for (int l3 = std::abs(l1 - l2); l3 <= std::min(l1 + l2, L); ++l3) {
-          if ((l1 + l2 + l3) & 1) continue;
+          if (((l1 + l2 + l3) & 1) != (odd ? 1 : 0)) continue;
           struct Term { int m1, m2; double c; };
-          std::vector<Term> terms;  // the nonzero C^Lambda_M of this Lambda
+          std::vector<Term> terms;  // the nonzero E(Lambda) C^Lambda_M of this Lambda
           for (int m1 = -l1; m1 <= l1; ++m1)
             for (int m2 = -l2; m2 <= l2; ++m2) {
               const int m3 = -(m1 + m2);
               if (std::abs(m3) > l3) continue;
-              const double c = (((l1 + l2 + l3) & 1) ? -1.0 : 1.0) * three_j(l1, l2, l3, m1, m2, m3);
+              // E(Lambda) C^Lambda_M = (-1)^(l1+l2+l3) (3j), times E = -1 for odd Lambda
+              const double c = (((l1 + l2 + l3) & 1) ? -1.0 : 1.0) * (odd ? -1.0 : 1.0) *
+                               three_j(l1, l2, l3, m1, m2, m3);
               if (c != 0.0) terms.push_back({m1, m2, c});
             }
           for (int b1 = 0; b1 < nb; ++b1)
@@ -741,7 +747,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
                   float rs = 1.0f;
                   long long ti = lookup(sg, &rs);
                   if (ti == LLONG_MIN) return fail(ctx, SBG_ERR_INTERNAL, "4PCF table lookup failed");
-                  if (ti < 0) ti = -ti - 1;  // Re T is invariant under M -> -M
+                  if (ti < 0 && !odd) ti = -ti - 1;  // Re T is invariant under M -> -M (odd: conj, kept)
                   t.idx.push_back((int)ti);
                   t.coef.push_back(tc ? tm.c * rs : tm.c);
                 }
@@ -791,13 +797,14 @@ void free_tables4(sbg_context* ctx, Tables4* t) {
   delete t;
 }
 
-sbg_status ensure_tables4(sbg_context* ctx, int dim, int nb, int L, bool tc) {
-  const std::string key = std::to_string(dim) + "/" + std::to_string(nb) + "/" + std::to_string(L) + (tc ? "/tc" : "/simt");
+sbg_status ensure_tables4(sbg_context* ctx, int dim, int nb, int L, bool tc, bool odd = false) {
+  const std::string key = std::to_string(dim) + "/" + std::to_string(nb) + "/" + std::to_string(L) + (tc ? "/tc" : "/simt") +
+                          (odd ? "/odd" : "");
   if (ctx->t4 && ctx->t4key == key) return SBG_OK;
   free_tables4(ctx, ctx->t4);
   ctx->t4 = nullptr;
   Tables4* t = new Tables4();
-  sbg_status s = build_tables4(ctx, *t, dim, nb, L, tc);
+  sbg_status s = build_tables4(ctx, *t, dim, nb, L, tc, odd);
   if (s != SBG_OK) {
     free_tables4(ctx, t);
     return s;
@@ -926,8 +933,10 @@ sbg_status finish_timings(sbg_context* ctx) {
 
 // ---------------------------------------------------------------- core ----
 // Shared by sbg_full (dim 3) and sbg_projected / batch (dim 2).
+// odd (dim 3, 4PCF only): the odd-parity Lambda, zeta4 receives Im of each coefficient
 sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype, int n, const double* edges, int nb,
-                   int lmax3, int lmax4, sbg_precision prec, unsigned flags, double* zeta3, double* zeta4) {
+                   int lmax3, int lmax4, sbg_precision prec, unsigned flags, double* zeta3, double* zeta4,
+                   bool odd = false) {
   const bool do3 = flags & SBG_3PCF, do4 = flags & SBG_4PCF;
   const long long ng = dim == 3 ? (long long)n * n * n : (long long)n * n;
   const int L = std::max(do3 ? lmax3 : 0, do4 ? lmax4 : 0);
@@ -1076,9 +1085,9 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
   if (do4) {
     const bool tc = prec != SBG_PREC_FP32;         // split BF16 or split TF32 on the tensor cores
     const bool tf = prec == SBG_PREC_TF32X3;
-    ST(ensure_tables4(ctx, dim, nb, lmax4, tc));
+    ST(ensure_tables4(ctx, dim, nb, lmax4, tc, odd));
     Tables4& t = *ctx->t4;
-    const int cplx = dim == 2 ? 1 : 0;
+    const int cplx = (dim == 2 || odd) ? 1 : 0;
     double* d_T;
     ST(buf(ctx, "T", (size_t)std::max<long long>(t.tcount, 1) * 8 * (cplx ? 2 : 1), (void**)&d_T));
     CU(cudaMemsetAsync(d_T, 0, (size_t)t.tcount * 8 * (cplx ? 2 : 1), ctx->stream));
@@ -1146,7 +1155,7 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
   // ---- 3PCF finish + downloads ----
   const int ncomp3 = dim == 3 ? 1 : 2;
   const size_t z3bytes = do3 ? (size_t)(lmax3 + 1) * nb * nb * 8 * ncomp3 : 0;
-  const size_t z4bytes = do4 ? (size_t)ctx->t4->nout * 8 * (dim == 2 ? 2 : 1) : 0;
+  const size_t z4bytes = do4 ? (size_t)ctx->t4->nout * 8 * ((dim == 2 || odd) ? 2 : 1) : 0;
   const size_t z3off = 0, z4off = (z3bytes + 255) / 256 * 256;
   unsigned char* hst;
   if (ctx->defer) {
@@ -1180,7 +1189,12 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
   }
   ST(finish_timings(ctx));
   if (do3) std::memcpy(zeta3, hst + z3off, z3bytes);
-  if (do4) std::memcpy(zeta4, hst + z4off, z4bytes);
+  if (do4 && odd) {
+    const double* zc = reinterpret_cast<const double*>(hst + z4off);
+    for (int o = 0; o < ctx->t4->nout; ++o) zeta4[o] = zc[2 * o + 1];  // the real parts are zero up to rounding
+  } else if (do4) {
+    std::memcpy(zeta4, hst + z4off, z4bytes);
+  }
   return SBG_OK;
 }
 
@@ -1278,6 +1292,32 @@ sbg_status sbg_lambda_count(int lmax, int* n_lambda) {
   return SBG_OK;
 }
 
+sbg_status sbg_lambda_odd_count(int lmax, int* n_lambda) {
+  if (!n_lambda || lmax < 0 || lmax > kMaxL3) return SBG_ERR_INVALID_ARG;
+  int c = 0;
+  for (int l1 = 0; l1 <= lmax; ++l1)
+    for (int l2 = 0; l2 <= lmax; ++l2)
+      for (int l3 = std::abs(l1 - l2); l3 <= std::min(l1 + l2, lmax); ++l3)
+        if ((l1 + l2 + l3) & 1) ++c;
+  *n_lambda = c;
+  return SBG_OK;
+}
+
+sbg_status sbg_lambda_odd_list(int lmax, int* l123) {
+  if (!l123 || lmax < 0 || lmax > kMaxL3) return SBG_ERR_INVALID_ARG;
+  int c = 0;
+  for (int l1 = 0; l1 <= lmax; ++l1)
+    for (int l2 = 0; l2 <= lmax; ++l2)
+      for (int l3 = std::abs(l1 - l2); l3 <= std::min(l1 + l2, lmax); ++l3)
+        if ((l1 + l2 + l3) & 1) {
+          l123[3 * c] = l1;
+          l123[3 * c + 1] = l2;
+          l123[3 * c + 2] = l3;
+          ++c;
+        }
+  return SBG_OK;
+}
+
 sbg_status sbg_lambda_list(int lmax, int* l123) {
   if (!l123 || lmax < 0 || lmax > kMaxL3) return SBG_ERR_INVALID_ARG;
   int c = 0;
@@ -1313,6 +1353,27 @@ sbg_status sbg_full(sbg_context* ctx, const void* field, sbg_dtype dtype, const 
   ST(check_edges(ctx, edges, nbins, n));
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SBG_ERR_CUDA, "cudaSetDevice");
   return measure(ctx, 3, field, dtype, n, edges, nbins, lmax3, lmax4, prec, flags, zeta3, zeta4);
+}
+
+sbg_status sbg_full_odd(sbg_context* ctx, const void* field, sbg_dtype dtype, const int64_t shape[3],
+                        const double* edges, int nbins, int lmax4, sbg_precision prec, unsigned flags,
+                        double* zeta4_odd) {
+  if (!ctx) return SBG_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!field || !shape || !edges || !zeta4_odd) return fail(ctx, SBG_ERR_INVALID_ARG, "null field, shape, edges or zeta4_odd");
+  if (dtype != SBG_F32 && dtype != SBG_F64) return fail(ctx, SBG_ERR_INVALID_ARG, "dtype");
+  if (prec != SBG_PREC_FP32 && prec != SBG_PREC_BF16X3 && prec != SBG_PREC_TF32X3)
+    return fail(ctx, SBG_ERR_INVALID_ARG, "precision");
+  if (flags & ~(unsigned)(SBG_NORMALIZED | SBG_SUBTRACT_MEAN | SBG_FIELD_ON_DEVICE))
+    return fail(ctx, SBG_ERR_INVALID_ARG, "unknown flag bits");
+  if (nbins < 1 || nbins > kMaxBins) return fail(ctx, SBG_ERR_INVALID_ARG, "nbins must be 1..20");
+  if (lmax4 < 1 || lmax4 > kMaxL4) return fail(ctx, SBG_ERR_INVALID_ARG, "lmax4 must be 1..5 (odd Lambda need l >= 1)");
+  if (!(shape[0] == shape[1] && shape[1] == shape[2]) || !pow2_in(shape[0], 8, 512))
+    return fail(ctx, SBG_ERR_UNSUPPORTED_SHAPE, "3D shape must be cubic with a power-of-two side in 8..512");
+  const int n = (int)shape[0];
+  ST(check_edges(ctx, edges, nbins, n));
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SBG_ERR_CUDA, "cudaSetDevice");
+  return measure(ctx, 3, field, dtype, n, edges, nbins, 0, lmax4, prec, flags | SBG_4PCF, nullptr, zeta4_odd, true);
 }
 
 sbg_status sbg_projected(sbg_context* ctx, const void* field, sbg_dtype dtype, const int64_t shape[2],
@@ -1436,13 +1497,15 @@ sbg_status sbg_last_contraction_ms(const sbg_context* ctx, double* ms) {
   return SBG_OK;
 }
 
-sbg_status sbg_plan4_info(int dim, int nbins, int lmax, sbg_precision prec, int* ntiles, int* nrows, int* covering) {
+sbg_status sbg_plan4_info(int dim, int nbins, int lmax, sbg_precision prec, int odd, int* ntiles, int* nrows,
+                          int* covering) {
   if ((dim != 2 && dim != 3) || nbins < 1 || nbins > kMaxBins || lmax < 0 || lmax > (dim == 3 ? kMaxL4 : kMaxM) ||
-      (prec != SBG_PREC_FP32 && prec != SBG_PREC_BF16X3 && prec != SBG_PREC_TF32X3))
+      (prec != SBG_PREC_FP32 && prec != SBG_PREC_BF16X3 && prec != SBG_PREC_TF32X3) || (odd != 0 && odd != 1) ||
+      (odd && dim != 3))
     return SBG_ERR_INVALID_ARG;
   sbg_context host;  // receives the error text only: the tables stay on the host
   Tables4 t;
-  const sbg_status s = build_tables4(&host, t, dim, nbins, lmax, prec != SBG_PREC_FP32, false);
+  const sbg_status s = build_tables4(&host, t, dim, nbins, lmax, prec != SBG_PREC_FP32, odd != 0, false);
   if (s != SBG_OK) return s;
   if (ntiles) *ntiles = (int)(t.tiles[0].size() + t.tiles[1].size() + t.tiles[2].size());
   if (nrows) *nrows = (int)t.rows.size();

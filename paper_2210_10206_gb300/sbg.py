@@ -69,7 +69,13 @@ def lib():
         L.sbg_last_timings.restype = st
         L.sbg_last_contraction_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.sbg_last_contraction_ms.restype = st
-        L.sbg_plan4_info.argtypes = [i, i, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.sbg_plan4_info.argtypes = [i, i, i, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.sbg_lambda_odd_count.argtypes = [i, ctypes.POINTER(i)]
+        L.sbg_lambda_odd_count.restype = st
+        L.sbg_lambda_odd_list.argtypes = [i, vp]
+        L.sbg_lambda_odd_list.restype = st
+        L.sbg_full_odd.argtypes = [vp, vp, i, vp, vp, i, i, i, ctypes.c_uint, vp]
+        L.sbg_full_odd.restype = st
         L.sbg_plan4_info.restype = st
         L.sbg_projected3_noalloc.argtypes = [vp, i, ctypes.c_int64, vp, i, i, ctypes.c_uint, vp, vp]
         L.sbg_projected3_noalloc.restype = st
@@ -119,6 +125,23 @@ def sbg_lambda_list(lmax):
     return out
 
 
+def sbg_lambda_odd_count(lmax):
+    n = ctypes.c_int()
+    s = lib().sbg_lambda_odd_count(lmax, ctypes.byref(n))
+    if s != SBG_OK:
+        raise SbgError(s, "sbg_lambda_odd_count")
+    return n.value
+
+
+def sbg_lambda_odd_list(lmax):
+    n = sbg_lambda_odd_count(lmax)
+    out = np.zeros((max(n, 1), 3), dtype=np.int32)
+    s = lib().sbg_lambda_odd_list(lmax, out.ctypes.data)
+    if s != SBG_OK:
+        raise SbgError(s, "sbg_lambda_odd_list")
+    return out[:n]
+
+
 def _field_ptr(field):
     """(pointer, dtype code, shape, on_device, keepalive)."""
     if hasattr(field, "data_ptr"):  # torch tensor
@@ -158,6 +181,22 @@ def sbg_full(h, field, edges, lmax3, lmax4, prec, flags, zeta3=None, zeta4=None)
     if s != SBG_OK:
         raise SbgError(s, sbg_last_error(h))
     return zeta3, zeta4
+
+
+def sbg_full_odd(h, field, edges, lmax4, prec, flags, zeta4_odd=None):
+    ptr, dt, shape, on_dev, keep = _field_ptr(field)
+    e = _edges(edges)
+    nb = len(e) - 1
+    if on_dev:
+        flags |= SBG_FIELD_ON_DEVICE
+    if zeta4_odd is None:
+        zeta4_odd = np.zeros((sbg_lambda_odd_count(lmax4), nb, nb, nb))
+    shp = (ctypes.c_int64 * 3)(*shape) if len(shape) == 3 else (ctypes.c_int64 * 3)(*(list(shape) + [0, 0, 0])[:3])
+    s = lib().sbg_full_odd(h, ptr, dt, shp, e.ctypes.data, nb, int(lmax4), prec, flags, zeta4_odd.ctypes.data)
+    del keep
+    if s != SBG_OK:
+        raise SbgError(s, sbg_last_error(h))
+    return zeta4_odd
 
 
 def sbg_projected(h, field, edges, mmax, prec, flags, zeta3=None, zeta4=None):
@@ -221,10 +260,10 @@ def sbg_last_contraction_ms(h):
     return out.value
 
 
-def sbg_plan4_info(dim, nbins, lmax, prec):
+def sbg_plan4_info(dim, nbins, lmax, prec, odd=0):
     """(ntiles, nrows, covering) of the 4PCF tile plan; host only."""
     nt, nr, cv = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    s = lib().sbg_plan4_info(dim, nbins, lmax, prec, ctypes.byref(nt), ctypes.byref(nr), ctypes.byref(cv))
+    s = lib().sbg_plan4_info(dim, nbins, lmax, prec, odd, ctypes.byref(nt), ctypes.byref(nr), ctypes.byref(cv))
     if s != SBG_OK:
         raise SbgError(s, "sbg_plan4_info")
     return nt.value, nr.value, cv.value
@@ -272,6 +311,9 @@ class Context:
         if lmax4 is not None:
             flags |= SBG_4PCF
         return sbg_full(self.h, field, edges, lmax3, lmax4, prec, flags)
+
+    def full_odd(self, field, edges, lmax4, prec=SBG_PREC_FP32, flags=SBG_SUBTRACT_MEAN):
+        return sbg_full_odd(self.h, field, edges, lmax4, prec, flags)
 
     def projected(self, field, edges, mmax, npcf=(3, 4), prec=SBG_PREC_FP32, flags=SBG_SUBTRACT_MEAN):
         if 3 in npcf:

@@ -46,6 +46,15 @@ def test_lambda_list_matches_oracle(sbg):
     assert sbg.sbg_lambda_count(3) == 23 and sbg.sbg_lambda_count(4) == 42
 
 
+def test_odd_lambda_list_matches_oracle(sbg):
+    for lmax in range(0, 8):
+        assert sbg.sbg_lambda_odd_count(lmax) == len(O.lambda_list_odd(lmax))
+        assert [tuple(r) for r in sbg.sbg_lambda_odd_list(lmax)] == O.lambda_list_odd(lmax)
+    assert sbg.sbg_lambda_odd_count(1) == 1 and sbg.sbg_lambda_odd_count(4) == 23
+    L = sbg.lib()
+    assert L.sbg_full_odd(None, None, 0, None, None, 1, 2, 0, 0, None) == -1
+
+
 def test_status_strings_and_argument_errors(sbg):
     assert sbg.sbg_status_string(-3) == "SBG_ERR_BIN_RANGE"
     assert sbg.sbg_status_string(0) == "SBG_OK"

@@ -28,6 +28,10 @@ def test_every_term_finds_its_entry(sbg, dim, nb, lmax):
     for prec in (sbg.SBG_PREC_FP32, sbg.SBG_PREC_BF16X3, sbg.SBG_PREC_TF32X3):
         nt, nr, cov = sbg.sbg_plan4_info(dim, nb, lmax, prec)
         assert nt >= 1 and nr >= 1 and cov in (0, 1)
+    if dim == 3 and lmax >= 1:  # the odd-parity tables of sbg_full_odd
+        for prec in (sbg.SBG_PREC_FP32, sbg.SBG_PREC_BF16X3):
+            nt, nr, cov = sbg.sbg_plan4_info(dim, nb, lmax, prec, 1)
+            assert nt >= 1 and nr >= 1
     # both tensor-core precisions share one plan
     assert sbg.sbg_plan4_info(dim, nb, lmax, sbg.SBG_PREC_BF16X3) == sbg.sbg_plan4_info(dim, nb, lmax,
                                                                                          sbg.SBG_PREC_TF32X3)
@@ -77,3 +81,5 @@ def test_plan_argument_errors(sbg):
             sbg.sbg_plan4_info(*args, sbg.SBG_PREC_BF16X3)
     with pytest.raises(sbg.SbgError):
         sbg.sbg_plan4_info(3, 10, 4, 2)  # precision 2 is not built
+    with pytest.raises(sbg.SbgError):
+        sbg.sbg_plan4_info(2, 10, 4, sbg.SBG_PREC_BF16X3, 1)  # odd parity is a 3D output
