@@ -356,9 +356,11 @@ sbg_status colour_slots(sbg_context* ctx, Tables4& t, Tile4& tl, const std::map<
 //               one block per m3 >= 0 with columns (b3, l3 >= m3).
 sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, bool tc, bool odd = false,
                          bool to_device = true) {
-  // complex T: the projected 4PCF, and the odd-parity 3D 4PCF (its M-sum is
-  // imaginary, Eq. mu with E(Lambda) = -1)
-  const bool cplx = dim == 2 || odd;
+  // complex T for the projected 4PCF; the odd-parity 3D 4PCF (whose M-sum is
+  // imaginary, Eq. mu with E(Lambda) = -1) keeps one real entry per (row,
+  // column), the imaginary part, and single-column B operands of the form
+  // (Im v, Re v)
+  const bool cplx = dim == 2;
   struct Ang { int l, m; };
   std::vector<Ang> angs;
   if (dim == 3) {
@@ -747,9 +749,13 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
                   float rs = 1.0f;
                   long long ti = lookup(sg, &rs);
                   if (ti == LLONG_MIN) return fail(ctx, SBG_ERR_INTERNAL, "4PCF table lookup failed");
-                  if (ti < 0 && !odd) ti = -ti - 1;  // Re T is invariant under M -> -M (odd: conj, kept)
+                  double sgn = 1.0;
+                  if (ti < 0) {  // the entry with every m negated holds the conjugate:
+                    ti = -ti - 1;  // Re T is the same, Im T (odd Lambda) changes sign
+                    if (odd) sgn = -1.0;
+                  }
                   t.idx.push_back((int)ti);
-                  t.coef.push_back(tc ? tm.c * rs : tm.c);
+                  t.coef.push_back(sgn * (tc ? tm.c * rs : tm.c));
                 }
                 t.ptr.push_back((int)t.idx.size());
               }
@@ -1087,7 +1093,9 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
     const bool tf = prec == SBG_PREC_TF32X3;
     ST(ensure_tables4(ctx, dim, nb, lmax4, tc, odd));
     Tables4& t = *ctx->t4;
-    const int cplx = (dim == 2 || odd) ? 1 : 0;
+    const int cplx = dim == 2 ? 1 : 0;
+    // kernel output mode: 0 Re (3D even), 1 complex (2D), 2 Im only (3D odd)
+    const int kmode = dim == 2 ? 1 : (odd ? 2 : 0);
     double* d_T;
     ST(buf(ctx, "T", (size_t)std::max<long long>(t.tcount, 1) * 8 * (cplx ? 2 : 1), (void**)&d_T));
     CU(cudaMemsetAsync(d_T, 0, (size_t)t.tcount * 8 * (cplx ? 2 : 1), ctx->stream));
@@ -1118,7 +1126,7 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
       ctx->nlaunch += 1;  // bimage_kernel
       KL(launch_tc4(d_astore, d_bimg, (const BGroup*)t.d_bgroups.p, (int)t.bgroups.size(), t.chunks_per_kb,
                     t.img_stride, d_delta, ng, (const Tile4*)t.d_tiles[0].p, ntl, (const Row4*)t.d_rows.p,
-                    (const int*)t.d_cols.p, (const int*)t.d_uniq.p, nsingle, cplx, best, d_T, d_cnt, d_err,
+                    (const int*)t.d_cols.p, (const int*)t.d_uniq.p, nsingle, kmode, best, d_T, d_cnt, d_err,
                     ctx->nsm, ctx->stream, ctx->kev[0], ctx->kev[1], tf ? 1 : 0));
       ctx->kev_used = true;
       if (!ctx->defer) {  // a batch reads the flag once, after its last field
@@ -1138,7 +1146,7 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
         const int ntl = (int)t.tiles[k].size();
         if (!ntl) continue;
         KL(launch_simt4(d_astore, ng, d_delta, (const Tile4*)t.d_tiles[k].p, ntl, (const Row4*)t.d_rows.p,
-                        (const int*)t.d_cols.p, (const int*)t.d_uniq.p, cplx, tcg[k], 0, nsingle, d_T, ctx->nsm,
+                        (const int*)t.d_cols.p, (const int*)t.d_uniq.p, kmode, tcg[k], 0, nsingle, d_T, ctx->nsm,
                         ctx->stream));
       }
       CU(cudaEventRecord(ctx->kev[1], ctx->stream));
@@ -1155,7 +1163,7 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
   // ---- 3PCF finish + downloads ----
   const int ncomp3 = dim == 3 ? 1 : 2;
   const size_t z3bytes = do3 ? (size_t)(lmax3 + 1) * nb * nb * 8 * ncomp3 : 0;
-  const size_t z4bytes = do4 ? (size_t)ctx->t4->nout * 8 * ((dim == 2 || odd) ? 2 : 1) : 0;
+  const size_t z4bytes = do4 ? (size_t)ctx->t4->nout * 8 * (dim == 2 ? 2 : 1) : 0;
   const size_t z3off = 0, z4off = (z3bytes + 255) / 256 * 256;
   unsigned char* hst;
   if (ctx->defer) {
@@ -1189,12 +1197,7 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
   }
   ST(finish_timings(ctx));
   if (do3) std::memcpy(zeta3, hst + z3off, z3bytes);
-  if (do4 && odd) {
-    const double* zc = reinterpret_cast<const double*>(hst + z4off);
-    for (int o = 0; o < ctx->t4->nout; ++o) zeta4[o] = zc[2 * o + 1];  // the real parts are zero up to rounding
-  } else if (do4) {
-    std::memcpy(zeta4, hst + z4off, z4bytes);
-  }
+  if (do4) std::memcpy(zeta4, hst + z4off, z4bytes);
   return SBG_OK;
 }
 

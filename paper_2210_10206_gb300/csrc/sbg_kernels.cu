@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(256) simt4_kernel(const float2* __restrict__ a
                                                     const float* __restrict__ delta, const Tile4* __restrict__ tiles,
                                                     const Row4* __restrict__ rows, const int* __restrict__ cols,
                                                     const int* __restrict__ uniq, int nsplit, int nsingle,
-                                                    double* __restrict__ T) {
+                                                    double* __restrict__ T, int imag) {
   using SM = SimtSmem<TCG>;
   constexpr int TR = SM::TR, TC = SM::TC;
   extern __shared__ float4 smem4[];
@@ -328,10 +328,16 @@ __global__ void __launch_bounds__(256) simt4_kernel(const float2* __restrict__ a
     const float* ru = raw + b * SM::kRaw;
     const float* rc = ru + SM::kRawU;
     const float* rd = rc + SM::kRawC;
-    // columns, transposed to [x][c] (zero past the tile's columns)
+    // columns, transposed to [x][c] (zero past the tile's columns); imag: a is
+    // stored as (Im a, -Re a), so that the real accumulation gives Im(P a)
     for (int i = tid; i < TC * kX; i += 256) {
       const int c = i % TC, xx = i / TC;
-      Cs[xx * TC + c] = c < tl.ncols ? make_float2(rc[c * kRawF + xx], rc[c * kRawF + 32 + xx]) : make_float2(0.f, 0.f);
+      float2 v = make_float2(0.f, 0.f);
+      if (c < tl.ncols) {
+        const float re = rc[c * kRawF + xx], im = rc[c * kRawF + 32 + xx];
+        v = imag ? make_float2(im, -re) : make_float2(re, im);
+      }
+      Cs[xx * TC + c] = v;
     }
     // pair products P_r(x) = sign * delta * f1 * f2
     for (int i = tid; i < TR * kX; i += 256) {
@@ -397,7 +403,7 @@ __global__ void __launch_bounds__(256) simt4_kernel(const float2* __restrict__ a
 template <int TCG, bool CPLX>
 static cudaError_t simt4_t(const float2* astore, long long ng, const float* delta, const Tile4* tiles, int ntiles,
                           const Row4* rows, const int* cols, const int* uniq, int nsplit, int nsingle, double* T,
-                          int nsm, cudaStream_t st) {
+                          int nsm, int imag, cudaStream_t st) {
   const size_t smem = SimtSmem<TCG>::kBytes;
   auto kern = simt4_kernel<TCG, CPLX>;
   static bool configured = false;
@@ -426,7 +432,7 @@ static cudaError_t simt4_t(const float2* astore, long long ng, const float* delt
     }
   }
   dim3 grid((unsigned)ntiles, (unsigned)nsplit);
-  kern<<<grid, 256, smem, st>>>(astore, ng, delta, tiles, rows, cols, uniq, nsplit, nsingle, T);
+  kern<<<grid, 256, smem, st>>>(astore, ng, delta, tiles, rows, cols, uniq, nsplit, nsingle, T, imag);
   return cudaGetLastError();
 }
 
@@ -434,15 +440,16 @@ cudaError_t launch_simt4(const float2* astore, long long ng, const float* delta,
                          const Row4* rows, const int* cols, const int* uniq, int complex_out, int tcg, int nsplit,
                          int nsingle, double* T, int nsm, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
-  if (ng % kX) return cudaErrorInvalidValue;
-  if (complex_out) {
-    if (tcg == 4) return simt4_t<4, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, st);
-    if (tcg == 8) return simt4_t<8, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, st);
-    if (tcg == 16) return simt4_t<16, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, st);
+  if (ng % kX || complex_out < 0 || complex_out > 2) return cudaErrorInvalidValue;
+  const int imag = complex_out == 2 ? 1 : 0;  // real T holding Im(P a)
+  if (complex_out == 1) {
+    if (tcg == 4) return simt4_t<4, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st);
+    if (tcg == 8) return simt4_t<8, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st);
+    if (tcg == 16) return simt4_t<16, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st);
   } else {
-    if (tcg == 4) return simt4_t<4, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, st);
-    if (tcg == 8) return simt4_t<8, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, st);
-    if (tcg == 16) return simt4_t<16, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, st);
+    if (tcg == 4) return simt4_t<4, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st);
+    if (tcg == 8) return simt4_t<8, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st);
+    if (tcg == 16) return simt4_t<16, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -40,8 +40,9 @@ struct Row4 {
   float sign;          // +-1 from a_{l,-m} = (-1)^m conj(a_{lm}) (3D)
 };
 
-// T[tile][r][c] (+)= Re or complex of sum_x delta * f1 * f2 * a_col.
-// nsplit <= 0: x-splits per tile chosen to fill whole waves of nsm SMs.
+// T[tile][r][c] (+)= sum_x delta * f1 * f2 * a_col: its real part
+// (complex_out 0), complex value (1, two doubles per entry) or imaginary part
+// (2).  nsplit <= 0: x-splits per tile chosen to fill whole waves of nsm SMs.
 cudaError_t launch_simt4(const float2* astore, long long ng, const float* delta, const Tile4* tiles,
                          int ntiles, const Row4* rows, const int* cols, const int* uniq, int complex_out,
                          int tcg, int nsplit, int nsingle, double* T, int nsm, cudaStream_t st);
@@ -67,7 +68,8 @@ struct BGroup {
 };
 // Units (tile, x-split) are spread over a cooperative grid of one CTA per SM;
 // cnt holds one progress counter per (round, epoch), zeroed by the caller.
-// chunks_per_kb = 8 * sum of the groups' n.
+// chunks_per_kb = 8 * sum of the groups' n.  complex_out as for launch_simt4:
+// 1 takes two B columns per single, 2 one column of the form (Im v, Re v).
 cudaError_t launch_tc4(const float2* astore, void* bimg, const BGroup* bgroups, int nbgroups, int chunks_per_kb,
                        long long img_stride, const float* delta, long long ng, const Tile4* tiles, int ntiles,
                        const Row4* rows, const int* cols, const int* slots, int nsingle, int complex_out,

@@ -711,15 +711,18 @@ __global__ void bimage_kernel(const float* __restrict__ astore, const float* __r
     const int atom = j >> 3, jj = j & 7;
     const int k0 = TF ? 32 * atom + 4 * jj : 8 * jj;  // first K value of the chunk
     const int second = k0 >> 5, p0 = k0 & 31;          // K 32..63: the second half of the row
-    const int cs = cplx ? (c >> 1) : c;
+    // columns of the (Im v, Re v) form: the odd ones of a complex group, and
+    // every one of an imaginary-only group (cplx = 2)
+    const bool imcol = cplx == 2 || (cplx == 1 && (c & 1));
+    const int cs = cplx == 1 ? (c >> 1) : c;
     uint4 hi = make_uint4(0, 0, 0, 0), lo = make_uint4(0, 0, 0, 0);
     if (cs < bg.ncols) {
       const float* a = astore + (xb * nsingle + cols[bg.col0 + cs]) * 64;
-      const float* ap = a + (((cplx && (c & 1)) ? !second : second) ? 32 : 0) + p0;
+      const float* ap = a + ((imcol ? !second : second) ? 32 : 0) + p0;
       const float* dp = delta + xb * 32 + p0;
       // component: Re v for (even, first half) and (odd, second half); Im v otherwise,
       // negated for (even, second half)
-      const float sg = (!(cplx && (c & 1)) && second) ? -1.f : 1.f;
+      const float sg = (!imcol && second) ? -1.f : 1.f;
       if constexpr (TF) {
         const float4 a0 = *(const float4*)ap, d0 = *(const float4*)dp;
         const float v[4] = {sg * (d0.x * a0.x), sg * (d0.y * a0.y), sg * (d0.z * a0.z), sg * (d0.w * a0.w)};
@@ -782,10 +785,11 @@ cudaError_t launch_tc4_t(const float2* astore, void* bimg, const BGroup* bgroups
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const float* af = (const float*)astore;
   const uint8_t* bi = (const uint8_t*)bimg;
+  const int ccols = complex_out == 1 ? 1 : 0;  // two B columns and complex T per single
   const int grid = nsm;  // every CTA takes part in every round so that the progress counters fill up
   void* args[] = {(void*)&af,    (void*)&bi,      (void*)&bgroups, (void*)&stride,     (void*)&ng,
                   (void*)&tiles, (void*)&ntiles,  (void*)&rows,    (void*)&slots,      (void*)&nsingle,
-                  (void*)&complex_out, (void*)&nsplit, (void*)&T,  (void*)&cnt,        (void*)&err};
+                  (void*)&ccols, (void*)&nsplit, (void*)&T,  (void*)&cnt,        (void*)&err};
   if (ev_begin && (e = cudaEventRecord(ev_begin, st)) != cudaSuccess) return e;
   e = cudaLaunchCooperativeKernel((const void*)tc4_kernel<TF>, dim3(grid), dim3(kThreads), args, kSmem, st);
   if (e != cudaSuccess) return e;

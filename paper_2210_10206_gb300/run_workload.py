@@ -13,6 +13,7 @@ Workloads (inputs from paper_2210_10206_gb300.synth, seeded):
                 call per --calls
   full512_3pcf  512^3 full 3PCF, lmax 10, 20 linear bins 2..62
   full256       256^3 full 4PCF, lmax 4, 10 linear bins 2..32
+  full256_odd   the odd-parity 4PCF (sbg_full_odd) of the same field
 The first call of a geometry also builds its plan (kernel spectra, tables)."""
 import argparse
 import json
@@ -26,7 +27,7 @@ PRECS = {"bf16x3": sbg.SBG_PREC_BF16X3, "tf32x3": sbg.SBG_PREC_TF32X3, "fp32": s
 
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_2210_10206_gb300.run_workload")
-    ap.add_argument("workload", choices=["batch64", "full512_3pcf", "full256"])
+    ap.add_argument("workload", choices=["batch64", "full512_3pcf", "full256", "full256_odd"])
     ap.add_argument("--calls", type=int, default=1)
     ap.add_argument("--prec", default="bf16x3", choices=sorted(PRECS))
     args = ap.parse_args(argv)
@@ -47,7 +48,10 @@ def main(argv=None):
     else:
         w = synth.WORKLOADS["full256"]
         d = torch.from_numpy(synth.workload_field("full256")).cuda()
-        call = lambda: ctx.full(d, w["edges"], lmax4=4, prec=prec)
+        if args.workload == "full256_odd":
+            call = lambda: ctx.full_odd(d, w["edges"], 4, prec=prec)
+        else:
+            call = lambda: ctx.full(d, w["edges"], lmax4=4, prec=prec)
     ms = []
     for _ in range(args.calls):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -59,7 +63,8 @@ def main(argv=None):
         ms.append(e0.elapsed_time(e1))
     print(json.dumps({"workload": args.workload, "prec": args.prec, "calls": args.calls,
                       "ms_per_call": [round(x, 3) for x in ms],
-                      "last_call_stage_ms": [round(float(x), 3) for x in np.asarray(ctx.timings())]}))
+                      "last_call_stage_ms": [round(float(x), 3) for x in np.asarray(ctx.timings())],
+                      "last_call_contraction_ms": round(sbg.sbg_last_contraction_ms(ctx.h), 3)}))
     ctx.close()
 
 
