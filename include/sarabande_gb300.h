@@ -117,6 +117,26 @@ sbg_status sbg_full(sbg_context* ctx, const void* field, sbg_dtype dtype, const 
                     const double* edges, int nbins, int lmax3, int lmax4, sbg_precision prec,
                     unsigned flags, double* zeta3, double* zeta4);
 
+/* Unique bin combinations in the 1D bin index of the paper's coefficient plots
+ * (Sec. 4.3, caption of Fig. normalization_projected; the bin loops of
+ * Algorithm 6): nested loops with b1 ascending from 0, b2 from b1 + 1 and, for
+ * the 4PCF, b3 from b2 + 1, so that no two bins of a combination coincide; the
+ * 1D index of a combination is its position in this list.  Host only.
+ *   order   : 3 (bin pairs of the 3PCF) or 4 (bin triples of the 4PCF)
+ *   n_index : out, nbins (nbins - 1) / 2 or nbins (nbins - 1) (nbins - 2) / 6
+ *   bins    : out, [n_index][order - 1] ints, or NULL to query n_index only
+ * Errors: SBG_ERR_INVALID_ARG for nbins outside 1..20 or another order. */
+sbg_status sbg_unique_bins(int nbins, int order, int* n_index, int* bins);
+
+/* The unique coefficients of a dense output in that 1D order: zeta holds
+ * nouter blocks of [nbins]^(order - 1) entries of ncomp doubles (1: real, 2:
+ * re, im), e.g. zeta3 of sbg_full (nouter = lmax3 + 1, order 3, ncomp 1) or
+ * zeta4 of sbg_projected (nouter = (2 mmax + 1)^2, order 4, ncomp 2); out
+ * receives [nouter][n_index][ncomp].  Host only; both pointers are host memory
+ * owned by the caller.  Errors: SBG_ERR_INVALID_ARG for a NULL pointer or
+ * arguments outside the ranges above. */
+sbg_status sbg_unique_gather(const double* zeta, long long nouter, int nbins, int order, int ncomp, double* out);
+
 /* Number of odd-parity Lambda (l1 + l2 + l3 odd, triangle rule, each l <=
  * lmax) for lmax in 0..10: 1 at lmax 1, 4 at lmax 2, 23 at lmax 4. */
 sbg_status sbg_lambda_odd_count(int lmax, int* n_lambda);

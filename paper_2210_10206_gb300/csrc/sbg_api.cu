@@ -1295,6 +1295,53 @@ sbg_status sbg_lambda_count(int lmax, int* n_lambda) {
   return SBG_OK;
 }
 
+sbg_status sbg_unique_bins(int nbins, int order, int* n_index, int* bins) {
+  if (!n_index || nbins < 1 || nbins > kMaxBins || (order != 3 && order != 4)) return SBG_ERR_INVALID_ARG;
+  int c = 0;
+  for (int b1 = 0; b1 < nbins; ++b1)
+    for (int b2 = b1 + 1; b2 < nbins; ++b2) {
+      if (order == 3) {
+        if (bins) {
+          bins[2 * c] = b1;
+          bins[2 * c + 1] = b2;
+        }
+        ++c;
+        continue;
+      }
+      for (int b3 = b2 + 1; b3 < nbins; ++b3) {
+        if (bins) {
+          bins[3 * c] = b1;
+          bins[3 * c + 1] = b2;
+          bins[3 * c + 2] = b3;
+        }
+        ++c;
+      }
+    }
+  *n_index = c;
+  return SBG_OK;
+}
+
+sbg_status sbg_unique_gather(const double* zeta, long long nouter, int nbins, int order, int ncomp, double* out) {
+  if (!zeta || !out || nouter < 0 || nbins < 1 || nbins > kMaxBins || (order != 3 && order != 4) ||
+      (ncomp != 1 && ncomp != 2))
+    return SBG_ERR_INVALID_ARG;
+  const long long inner = order == 3 ? (long long)nbins * nbins : (long long)nbins * nbins * nbins;
+  long long k = 0;
+  for (long long o = 0; o < nouter; ++o) {
+    const double* z = zeta + o * inner * ncomp;
+    for (int b1 = 0; b1 < nbins; ++b1)
+      for (int b2 = b1 + 1; b2 < nbins; ++b2) {
+        if (order == 3) {
+          for (int q = 0; q < ncomp; ++q) out[k++] = z[((long long)b1 * nbins + b2) * ncomp + q];
+          continue;
+        }
+        for (int b3 = b2 + 1; b3 < nbins; ++b3)
+          for (int q = 0; q < ncomp; ++q) out[k++] = z[(((long long)b1 * nbins + b2) * nbins + b3) * ncomp + q];
+      }
+  }
+  return SBG_OK;
+}
+
 sbg_status sbg_lambda_odd_count(int lmax, int* n_lambda) {
   if (!n_lambda || lmax < 0 || lmax > kMaxL3) return SBG_ERR_INVALID_ARG;
   int c = 0;

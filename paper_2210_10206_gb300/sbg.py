@@ -70,6 +70,10 @@ def lib():
         L.sbg_last_contraction_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.sbg_last_contraction_ms.restype = st
         L.sbg_plan4_info.argtypes = [i, i, i, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.sbg_unique_bins.argtypes = [i, i, ctypes.POINTER(i), vp]
+        L.sbg_unique_bins.restype = st
+        L.sbg_unique_gather.argtypes = [vp, ctypes.c_longlong, i, i, i, vp]
+        L.sbg_unique_gather.restype = st
         L.sbg_lambda_odd_count.argtypes = [i, ctypes.POINTER(i)]
         L.sbg_lambda_odd_count.restype = st
         L.sbg_lambda_odd_list.argtypes = [i, vp]
@@ -122,6 +126,35 @@ def sbg_lambda_list(lmax):
     s = lib().sbg_lambda_list(lmax, out.ctypes.data)
     if s != SBG_OK:
         raise SbgError(s, "sbg_lambda_list")
+    return out
+
+
+def sbg_unique_bins(nbins, order):
+    """[n_index, order - 1] bin combinations in the 1D bin-index order."""
+    n = ctypes.c_int()
+    s = lib().sbg_unique_bins(nbins, order, ctypes.byref(n), None)
+    if s != SBG_OK:
+        raise SbgError(s, "sbg_unique_bins")
+    out = np.zeros((max(n.value, 1), order - 1), dtype=np.int32)
+    s = lib().sbg_unique_bins(nbins, order, ctypes.byref(n), out.ctypes.data)
+    if s != SBG_OK:
+        raise SbgError(s, "sbg_unique_bins")
+    return out[:n.value]
+
+
+def sbg_unique_gather(zeta, order, ncomp=1):
+    """Unique coefficients of a dense output: zeta of shape [..., nbins x
+    (order - 1)] (plus a trailing axis of 2 when ncomp = 2) to [..., n_index]
+    (plus the trailing axis)."""
+    z = np.ascontiguousarray(zeta, dtype=np.float64)
+    nlead = z.ndim - (order - 1) - (1 if ncomp == 2 else 0)
+    nbins = z.shape[nlead]
+    nouter = int(np.prod(z.shape[:nlead])) if nlead else 1
+    n = len(sbg_unique_bins(nbins, order))
+    out = np.zeros(z.shape[:nlead] + (n,) + ((2,) if ncomp == 2 else ()))
+    s = lib().sbg_unique_gather(z.ctypes.data, nouter, nbins, order, ncomp, out.ctypes.data)
+    if s != SBG_OK:
+        raise SbgError(s, "sbg_unique_gather")
     return out
 
 

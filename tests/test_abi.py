@@ -55,6 +55,34 @@ def test_odd_lambda_list_matches_oracle(sbg):
     assert L.sbg_full_odd(None, None, 0, None, None, 1, 2, 0, 0, None) == -1
 
 
+def test_unique_bins_follow_the_papers_1d_index(sbg):
+    # nested loops b1 < b2 (< b3) of Algorithm 6's bin loops: lexicographic
+    # combinations without repeated bins
+    import itertools
+    for nb in (1, 2, 3, 10, 20):
+        for order, k in ((3, 2), (4, 3)):
+            got = [tuple(r) for r in sbg.sbg_unique_bins(nb, order)]
+            assert got == list(itertools.combinations(range(nb), k))
+    assert len(sbg.sbg_unique_bins(10, 3)) == 45 and len(sbg.sbg_unique_bins(10, 4)) == 120
+    with pytest.raises(sbg.SbgError):
+        sbg.sbg_unique_bins(10, 5)
+
+
+def test_unique_gather_picks_the_off_diagonal_entries(sbg):
+    import itertools
+    rng = np.random.default_rng(3)
+    z4 = rng.normal(size=(7, 6, 6, 6))
+    u = sbg.sbg_unique_gather(z4, 4)
+    idx = list(itertools.combinations(range(6), 3))
+    assert u.shape == (7, len(idx))
+    assert np.array_equal(u, np.stack([[z4[i][t] for t in idx] for i in range(7)]))
+    z3c = rng.normal(size=(4, 5, 5, 2))  # complex (re, im) projected 3PCF layout
+    u3 = sbg.sbg_unique_gather(z3c, 3, ncomp=2)
+    idx2 = list(itertools.combinations(range(5), 2))
+    assert u3.shape == (4, len(idx2), 2)
+    assert np.array_equal(u3, np.stack([[z3c[i][t] for t in idx2] for i in range(4)]))
+
+
 def test_status_strings_and_argument_errors(sbg):
     assert sbg.sbg_status_string(-3) == "SBG_ERR_BIN_RANGE"
     assert sbg.sbg_status_string(0) == "SBG_OK"
