@@ -197,6 +197,20 @@ typedef struct {
 sbg_status sbg_projected_batch(sbg_context* ctx, const sbg_field2d* fields, int nfields, int nbins, int mmax,
                                sbg_precision prec, unsigned flags);
 
+/* Projected 3PCF and 4PCF of every 2D slice of a 3D cube (Sec. 4 takes the
+ * projected statistics of one slice of a simulation cube), through the batch path
+ * of sbg_projected_batch: slice i is cube[i], the contiguous shape[1] x
+ * shape[2] block (take slices along another axis by transposing first).
+ *   cube   : [n0][n1][n2] of `dtype`, host pointer unless SBG_FIELD_ON_DEVICE;
+ *            n1 = n2, a power of two in 8..1024; n0 in 1..65536.
+ *   edges, nbins, mmax, prec, flags : as for sbg_projected, shared by every slice.
+ *   zeta3  : out (SBG_3PCF), [n0] blocks of sbg_projected's zeta3.
+ *   zeta4  : out (SBG_4PCF), [n0] blocks of sbg_projected's zeta4.
+ * Errors as for sbg_projected_batch (the message names the slice). */
+sbg_status sbg_projected_slices(sbg_context* ctx, const void* cube, sbg_dtype dtype, const int64_t shape[3],
+                                const double* edges, int nbins, int mmax, sbg_precision prec, unsigned flags,
+                                double* zeta3, double* zeta4);
+
 /* Device times (ms, CUDA events) of the stages of the last measurement call:
  * [0] upload+preprocess, [1] forward FFT of delta, [2] kernel spectra (plan),
  * [3] convolutions (inverse FFTs), [4] 3PCF Gram, [5] 4PCF combination,

@@ -1533,6 +1533,35 @@ sbg_status sbg_projected_batch(sbg_context* ctx, const sbg_field2d* fields, int 
   return SBG_OK;
 }
 
+sbg_status sbg_projected_slices(sbg_context* ctx, const void* cube, sbg_dtype dtype, const int64_t shape[3],
+                                const double* edges, int nbins, int mmax, sbg_precision prec, unsigned flags,
+                                double* zeta3, double* zeta4) {
+  if (!ctx) return SBG_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!cube || !shape || !edges) return fail(ctx, SBG_ERR_INVALID_ARG, "null cube, shape or edges");
+  if (dtype != SBG_F32 && dtype != SBG_F64) return fail(ctx, SBG_ERR_INVALID_ARG, "dtype");
+  if (shape[0] < 1 || shape[0] > 65536 || shape[1] < 1 || shape[2] < 1)
+    return fail(ctx, SBG_ERR_UNSUPPORTED_SHAPE, "cube shape");
+  if (((flags & SBG_3PCF) && !zeta3) || ((flags & SBG_4PCF) && !zeta4))
+    return fail(ctx, SBG_ERR_INVALID_ARG, "zeta3/zeta4");
+  // slice i = cube[i] (contiguous n1 x n2 block), outputs slice-major
+  const size_t elem = dtype == SBG_F64 ? 8 : 4;
+  const size_t w = 2 * (size_t)mmax + 1;
+  const size_t s3 = (size_t)(mmax + 1) * nbins * nbins * 2, s4 = w * w * nbins * nbins * nbins * 2;
+  std::vector<sbg_field2d> f((size_t)shape[0]);
+  for (int64_t i = 0; i < shape[0]; ++i) {
+    sbg_field2d& g = f[(size_t)i];
+    g.field = (const unsigned char*)cube + (size_t)i * (size_t)shape[1] * (size_t)shape[2] * elem;
+    g.dtype = dtype;
+    g.shape[0] = shape[1];
+    g.shape[1] = shape[2];
+    g.edges = edges;
+    g.zeta3 = (flags & SBG_3PCF) ? zeta3 + (size_t)i * s3 : nullptr;
+    g.zeta4 = (flags & SBG_4PCF) ? zeta4 + (size_t)i * s4 : nullptr;
+  }
+  return sbg_projected_batch(ctx, f.data(), (int)shape[0], nbins, mmax, prec, flags);
+}
+
 sbg_status sbg_last_timings(const sbg_context* ctx, double* ms_per_stage, int* n_stages) {
   if (!ctx || !ms_per_stage || !n_stages) return SBG_ERR_INVALID_ARG;
   for (int i = 0; i < kStages; ++i) ms_per_stage[i] = ctx->timings[i];

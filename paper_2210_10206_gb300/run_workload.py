@@ -14,6 +14,8 @@ Workloads (inputs from paper_2210_10206_gb300.synth, seeded):
   full512_3pcf  512^3 full 3PCF, lmax 10, 20 linear bins 2..62
   full256       256^3 full 4PCF, lmax 4, 10 linear bins 2..32
   full256_odd   the odd-parity 4PCF (sbg_full_odd) of the same field
+  slices256     projected 3PCF + 4PCF of all 256 slices of that field
+                (sbg_projected_slices), 10 log bins 2..32, mmax 10
 The first call of a geometry also builds its plan (kernel spectra, tables)."""
 import argparse
 import json
@@ -27,7 +29,7 @@ PRECS = {"bf16x3": sbg.SBG_PREC_BF16X3, "tf32x3": sbg.SBG_PREC_TF32X3, "fp32": s
 
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_2210_10206_gb300.run_workload")
-    ap.add_argument("workload", choices=["batch64", "full512_3pcf", "full256", "full256_odd"])
+    ap.add_argument("workload", choices=["batch64", "full512_3pcf", "full256", "full256_odd", "slices256"])
     ap.add_argument("--calls", type=int, default=1)
     ap.add_argument("--prec", default="bf16x3", choices=sorted(PRECS))
     args = ap.parse_args(argv)
@@ -41,6 +43,10 @@ def main(argv=None):
         fields = [f for f, _ in members]
         edges = [e for _, e in members]
         call = lambda: ctx.projected_batch(fields, edges, 10, 10, prec=prec)
+    elif args.workload == "slices256":
+        d = torch.from_numpy(synth.workload_field("full256")).cuda()
+        e = list(synth.edges_log(2.0, 32.0, 10))
+        call = lambda: ctx.projected_slices(d, e, 10, prec=prec)
     elif args.workload == "full512_3pcf":
         w = synth.WORKLOADS["full512"]
         d = torch.from_numpy(synth.workload_field("full512")).cuda()

@@ -70,6 +70,8 @@ def lib():
         L.sbg_last_contraction_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.sbg_last_contraction_ms.restype = st
         L.sbg_plan4_info.argtypes = [i, i, i, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.sbg_projected_slices.argtypes = [vp, vp, i, vp, vp, i, i, i, ctypes.c_uint, vp, vp]
+        L.sbg_projected_slices.restype = st
         L.sbg_unique_bins.argtypes = [i, i, ctypes.POINTER(i), vp]
         L.sbg_unique_bins.restype = st
         L.sbg_unique_gather.argtypes = [vp, ctypes.c_longlong, i, i, i, vp]
@@ -127,6 +129,29 @@ def sbg_lambda_list(lmax):
     if s != SBG_OK:
         raise SbgError(s, "sbg_lambda_list")
     return out
+
+
+def sbg_projected_slices(h, cube, edges, mmax, prec, flags, zeta3=None, zeta4=None):
+    ptr, dt, shape, on_dev, keep = _field_ptr(cube)
+    if len(shape) != 3:
+        raise ValueError("cube must be 3D")
+    e = _edges(edges)
+    nb = len(e) - 1
+    if on_dev:
+        flags |= SBG_FIELD_ON_DEVICE
+    w = 2 * mmax + 1
+    if (flags & SBG_3PCF) and zeta3 is None:
+        zeta3 = np.zeros((shape[0], mmax + 1, nb, nb, 2))
+    if (flags & SBG_4PCF) and zeta4 is None:
+        zeta4 = np.zeros((shape[0], w, w, nb, nb, nb, 2))
+    shp = (ctypes.c_int64 * 3)(*shape)
+    s = lib().sbg_projected_slices(h, ptr, dt, shp, e.ctypes.data, nb, mmax, prec, flags,
+                                   zeta3.ctypes.data if zeta3 is not None else None,
+                                   zeta4.ctypes.data if zeta4 is not None else None)
+    del keep
+    if s != SBG_OK:
+        raise SbgError(s, sbg_last_error(h))
+    return zeta3, zeta4
 
 
 def sbg_unique_bins(nbins, order):
@@ -362,6 +387,13 @@ class Context:
         if 4 in npcf:
             flags |= SBG_4PCF
         return sbg_projected_batch(self.h, fields, edges_list, nbins, mmax, prec, flags)
+
+    def projected_slices(self, cube, edges, mmax, npcf=(3, 4), prec=SBG_PREC_FP32, flags=SBG_SUBTRACT_MEAN):
+        if 3 in npcf:
+            flags |= SBG_3PCF
+        if 4 in npcf:
+            flags |= SBG_4PCF
+        return sbg_projected_slices(self.h, cube, edges, mmax, prec, flags)
 
     def timings(self):
         return sbg_last_timings(self.h)
