@@ -157,7 +157,11 @@ struct sbg_context {
   std::string gkey;
   DevBuf gcache;
   bool gcached = false;
-  std::string t4key;
+  // 4PCF tables of the last few geometries (dim, bins, order, kernel, parity),
+  // so that calls alternating between them (e.g. sbg_full and sbg_full_odd on
+  // each field) do not rebuild a plan per call; t4 is the current one
+  static constexpr int kT4Cache = 4;
+  std::vector<std::pair<std::string, Tables4*>> t4cache;  // most recently used first
   Tables4* t4 = nullptr;
   // pinned host staging for results and status words, so downloads are plain
   // DMA on the stream and the host copies out after the stream is idle
@@ -806,17 +810,27 @@ void free_tables4(sbg_context* ctx, Tables4* t) {
 sbg_status ensure_tables4(sbg_context* ctx, int dim, int nb, int L, bool tc, bool odd = false) {
   const std::string key = std::to_string(dim) + "/" + std::to_string(nb) + "/" + std::to_string(L) + (tc ? "/tc" : "/simt") +
                           (odd ? "/odd" : "");
-  if (ctx->t4 && ctx->t4key == key) return SBG_OK;
-  free_tables4(ctx, ctx->t4);
-  ctx->t4 = nullptr;
+  auto& cache = ctx->t4cache;
+  for (size_t i = 0; i < cache.size(); ++i)
+    if (cache[i].first == key) {
+      std::rotate(cache.begin(), cache.begin() + i, cache.begin() + i + 1);
+      ctx->t4 = cache.front().second;
+      return SBG_OK;
+    }
   Tables4* t = new Tables4();
   sbg_status s = build_tables4(ctx, *t, dim, nb, L, tc, odd);
   if (s != SBG_OK) {
     free_tables4(ctx, t);
     return s;
   }
+  cache.insert(cache.begin(), {key, t});
+  if ((int)cache.size() > sbg_context::kT4Cache) {
+    // the evicted tables may still be read by queued work of this stream
+    cudaStreamSynchronize(ctx->stream);
+    free_tables4(ctx, cache.back().second);
+    cache.pop_back();
+  }
   ctx->t4 = t;
-  ctx->t4key = key;
   return SBG_OK;
 }
 
@@ -1249,7 +1263,9 @@ void sbg_destroy(sbg_context* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (auto& kv : ctx->bufs) dev_free(ctx, kv.second);
   dev_free(ctx, ctx->gcache);
-  free_tables4(ctx, ctx->t4);
+  for (auto& kv : ctx->t4cache) free_tables4(ctx, kv.second);
+  ctx->t4cache.clear();
+  ctx->t4 = nullptr;
   if (ctx->hpin) cudaFreeHost(ctx->hpin);
   for (int k = 0; k < 2; ++k) {
     for (int i = 0; i <= kStages; ++i)

@@ -77,3 +77,19 @@ def test_odd_parity_flips_under_a_mirror_on_gpu(sbgm):
     assert np.abs(z).max() > 0
     assert _err(zm, -z) <= 1e-5
     assert np.abs(zs).max() <= 1e-5 * np.abs(ze).max()
+
+
+def test_alternating_even_and_odd_calls_reuse_their_plans(sbgm):
+    # both table sets stay cached: alternating calls give the same results
+    sbg = sbgm
+    f = synth.lognormal_field(63, (16, 16, 16), 1.0, -2.0, dtype=np.float64)
+    edges = [0.5, 2.0, 3.5, 6.0]
+    ctx = sbg.Context(0)
+    first_even = ctx.full(f, edges, lmax4=3, prec=sbg.SBG_PREC_BF16X3)[1]
+    first_odd = ctx.full_odd(f, edges, 3, prec=sbg.SBG_PREC_BF16X3)
+    for _ in range(2):
+        e = ctx.full(f, edges, lmax4=3, prec=sbg.SBG_PREC_BF16X3)[1]
+        o = ctx.full_odd(f, edges, 3, prec=sbg.SBG_PREC_BF16X3)
+        assert np.abs(e - first_even).max() <= 1e-12 * np.abs(first_even).max()
+        assert np.abs(o - first_odd).max() <= 1e-12 * np.abs(first_odd).max()
+    ctx.close()
