@@ -357,11 +357,21 @@ __global__ void __launch_bounds__(256) simt4_kernel(const float2* __restrict__ a
       Ps[xx * TR + r] = p;
     }
     __syncthreads();
+    // operands of point xx + 1 are loaded while point xx is accumulated
+    const float4* pr0 = reinterpret_cast<const float4*>(Ps + rg * 4);
+    const float4* cr0 = reinterpret_cast<const float4*>(Cs + cg * 4);
+    float4 np01 = pr0[0], np23 = pr0[1], nc01 = cr0[0], nc23 = cr0[1];
 #pragma unroll 4
     for (int xx = 0; xx < kX; ++xx) {
-      const float4* pr = reinterpret_cast<const float4*>(Ps + xx * TR + rg * 4);
-      const float4* cr = reinterpret_cast<const float4*>(Cs + xx * TC + cg * 4);
-      const float4 p01 = pr[0], p23 = pr[1], c01 = cr[0], c23 = cr[1];
+      const float4 p01 = np01, p23 = np23, c01 = nc01, c23 = nc23;
+      if (xx + 1 < kX) {
+        const float4* pr = reinterpret_cast<const float4*>(Ps + (xx + 1) * TR + rg * 4);
+        const float4* cr = reinterpret_cast<const float4*>(Cs + (xx + 1) * TC + cg * 4);
+        np01 = pr[0];
+        np23 = pr[1];
+        nc01 = cr[0];
+        nc23 = cr[1];
+      }
       const float2 P[4] = {{p01.x, p01.y}, {p01.z, p01.w}, {p23.x, p23.y}, {p23.z, p23.w}};
       const float2 C[4] = {{c01.x, c01.y}, {c01.z, c01.w}, {c23.x, c23.y}, {c23.z, c23.w}};
 #pragma unroll
