@@ -53,6 +53,7 @@ def test_odd_lambda_list_matches_oracle(sbg):
     assert sbg.sbg_lambda_odd_count(1) == 1 and sbg.sbg_lambda_odd_count(4) == 23
     L = sbg.lib()
     assert L.sbg_full_odd(None, None, 0, None, None, 1, 2, 0, 0, None) == -1
+    assert L.sbg_projected_slices(None, None, 0, None, None, 1, 2, 0, 3, None, None) == -1
 
 
 def test_unique_bins_follow_the_papers_1d_index(sbg):
