@@ -85,3 +85,48 @@ def test_odd_parity_sign_and_part_are_caught(monkeypatch):
         return (re, im) if return_real else re
     monkeypatch.setattr(O, "zeta4_full_odd", real_part)
     assert _fails(pins.test_zeta4_full_odd_brute_force_triple_sums)
+
+
+def test_normalization_mistakes_are_caught(monkeypatch):
+    # the normalisation of Sec. 2.5 with a bin volume one cell off, the
+    # continuous shell in place of the cell count, nbar per unit length instead
+    # of per cell, and one nbar V factor too many
+    orig_counts = O.bin_cell_counts
+    orig_norm = O.normalization
+
+    def plus_one(shape, edges):
+        return orig_counts(shape, edges) + 1
+    monkeypatch.setattr(O, "bin_cell_counts", plus_one)
+    assert _fails(pins.test_normalization_constant_field_closed_form)
+    monkeypatch.setattr(O, "bin_cell_counts", orig_counts)
+
+    def continuous(shape, edges):
+        e = np.asarray(edges, dtype=np.float64)
+        if len(shape) == 3:
+            return 4 * np.pi / 3 * (e[1:] ** 3 - e[:-1] ** 3)
+        return np.pi * (e[1:] ** 2 - e[:-1] ** 2)
+    monkeypatch.setattr(O, "bin_cell_counts", continuous)
+    assert _fails(pins.test_normalization_constant_field_closed_form)
+    monkeypatch.setattr(O, "bin_cell_counts", orig_counts)
+
+    def nbar_per_length(shape, edges, n_gal, order, bins):
+        return orig_norm(shape, edges, n_gal, order, bins) * (shape[0] ** (len(shape) - 1)) ** (order - 1)
+    monkeypatch.setattr(O, "normalization", nbar_per_length)
+    assert _fails(pins.test_normalization_constant_field_closed_form)
+    assert _fails(pins.test_normalized_projected_3pcf_approaches_particle_counting)
+
+    def extra_factor(shape, edges, n_gal, order, bins):
+        return orig_norm(shape, edges, n_gal, order, list(bins) + [bins[0]])
+    monkeypatch.setattr(O, "normalization", extra_factor)
+    assert _fails(pins.test_normalization_constant_field_closed_form)
+    assert _fails(pins.test_normalized_full_3pcf_approaches_particle_counting)
+
+
+def test_ngal_before_mean_subtraction_is_caught(monkeypatch):
+    orig = O.preprocess
+
+    def early(field, subtract_mean=True):
+        d, _ = orig(field, subtract_mean)
+        return d, float((np.asarray(field, dtype=np.float64) + 1.0).sum())
+    monkeypatch.setattr(O, "preprocess", early)
+    assert _fails(pins.test_ngal_after_mean_subtraction_is_grid_size)

@@ -521,16 +521,127 @@ def test_particle_direct_counting_projected():
 
 # ---------------------------------------------------------- normalisation --
 
-def test_normalization_matches_explicit_product():
-    shape = (16, 16, 16)
-    edges = [0.5, 1.5, 2.5, 4.0]
-    counts = [len(v) for v in _offsets_in_bins(shape, edges)]
-    d, ngal = O.preprocess(RNG.normal(size=shape))
-    assert abs(ngal - 16 ** 3) < 1e-9
-    nbar = ngal / 16 ** 3
-    assert O.normalization(shape, edges, ngal, 3, [0, 2]) == pytest.approx(ngal * nbar * counts[0] * nbar * counts[2])
-    assert O.normalization(shape, edges, ngal, 4, [0, 1, 2]) == pytest.approx(
-        ngal * nbar ** 3 * counts[0] * counts[1] * counts[2])
+def test_normalization_constant_field_closed_form():
+    # For a constant field delta = c (no mean subtraction) every binned
+    # coefficient is known in closed form: a^b_00 = c V_b Y_00, c^b_0 = c V_b
+    # with V_b the number of cells of bin b, N_gal = N_g (1 + c) and
+    # nbar = 1 + c (Eq. num_gals with L = N).  The normalised monopoles are then
+    # independent of the bins:  3PCF  c^3 / ((1 + c)^3 4 pi)  (full) and
+    # c^3 / (1 + c)^3 (projected); 4PCF (000) c^4 / ((1 + c)^4 (4 pi)^{3/2}).
+    # Any other bin measure (a cell more or less, the continuous shell), a
+    # wrong nbar or a wrong number of factors breaks these identities.
+    c = 0.75
+    shape3 = (12, 12, 12)
+    edges3 = [0.0, 1.5, 2.9, 4.5, 5.5]
+    d3, ngal3 = O.preprocess(np.full(shape3, c), subtract_mean=False)
+    assert ngal3 == pytest.approx(12 ** 3 * (1 + c), rel=1e-14)
+    z3 = O.zeta3_full(d3, edges3, 0)[0]
+    z4 = O.zeta4_full(d3, edges3, 0)[0]
+    nb = len(edges3) - 1
+    for b1 in range(nb):
+        for b2 in range(nb):
+            n3 = O.normalization(shape3, edges3, ngal3, 3, [b1, b2])
+            assert z3[b1, b2] / n3 == pytest.approx(c ** 3 / ((1 + c) ** 3 * 4 * math.pi), rel=1e-12)
+            for b3 in range(nb):
+                n4 = O.normalization(shape3, edges3, ngal3, 4, [b1, b2, b3])
+                assert z4[b1, b2, b3] / n4 == pytest.approx(c ** 4 / ((1 + c) ** 4 * (4 * math.pi) ** 1.5),
+                                                            rel=1e-12)
+    shape2 = (24, 24)
+    edges2 = [0.5, 2.0, 4.5, 7.0, 11.0]
+    d2, ngal2 = O.preprocess(np.full(shape2, c), subtract_mean=False)
+    p3 = O.zeta3_projected(d2, edges2, 0)[0]
+    for b1 in range(nb):
+        for b2 in range(nb):
+            n = O.normalization(shape2, edges2, ngal2, 3, [b1, b2])
+            assert p3[b1, b2].real / n == pytest.approx(c ** 3 / (1 + c) ** 3, rel=1e-12)
+            assert abs(p3[b1, b2].imag) < 1e-9 * abs(p3[b1, b2].real)
+
+
+def test_ngal_after_mean_subtraction_is_grid_size():
+    # Eq. num_gals evaluated after the mean is removed (Sec. 4.1) is exactly N_g,
+    # whatever the field's mean was; without subtraction it counts the field
+    from paper_2210_10206_gb300 import synth
+    f = synth.particle_field(21, (32, 32), 50)
+    _, ngal = O.preprocess(f, subtract_mean=True)
+    assert ngal == pytest.approx(32 * 32, rel=1e-13)
+    _, ngal_raw = O.preprocess(f, subtract_mean=False)
+    assert ngal_raw == pytest.approx(32 * 32 + 50, rel=1e-13)
+
+
+def _dc_projected3(pos, n, e2, nb, mmax):
+    """Direct counting over particle pairs around each primary (Sec. 4.3)."""
+    r = np.zeros((mmax + 1, nb, nb), dtype=np.complex128)
+    for p in pos:
+        sep = _min_image(pos - p, n)
+        q2 = (sep ** 2).sum(1)
+        phis = [np.arctan2(sep[:, 0], sep[:, 1])[(q2 > e2[b]) & (q2 <= e2[b + 1])] for b in range(nb)]
+        for m in range(mmax + 1):
+            cm = np.array([np.exp(-1j * m * ph).sum() for ph in phis])
+            r[m] += cm[:, None] * np.conj(cm)[None, :]
+    return r
+
+
+def test_normalized_projected_3pcf_approaches_particle_counting():
+    # Sec. 2.5 / Sec. 4.3 (Fig. normalization_projected): 41 unit-weight
+    # particles; the grid coefficients divided by N = N_gal prod nbar A_bin with
+    # A_bin = cell count (Eq. proj_b_area, proj_norm) against direct counting
+    # divided by the particle code's normalisation, whose bin areas are the
+    # continuous annuli pi (r+^2 - r-^2) and nbar = N_part / L^2.  Unnormalised
+    # they agree to rounding; normalised they differ by the lattice's
+    # approximation of each annulus, which shrinks as the cells get smaller
+    # (box and bins scaled together).
+    from paper_2210_10206_gb300 import synth
+    errs = []
+    for n in (64, 128, 256, 512):
+        edges = np.linspace(n / 32.0, 0.45 * n, 11)
+        f = synth.particle_field(13, (n, n), 41)
+        pos = np.argwhere(f > 0)
+        npart = len(pos)
+        nb, mmax = 10, 2
+        grid = O.zeta3_projected(f, edges, mmax)
+        dc = _dc_projected3(pos, n, O.snapped_edges_sq(edges), nb, mmax)
+        assert _rel(grid, dc) < 1e-12
+        nbar = npart / float(n * n)
+        area = math.pi * (edges[1:] ** 2 - edges[:-1] ** 2)
+        gn = np.empty_like(grid)
+        dn = np.empty_like(dc)
+        for b1 in range(nb):
+            for b2 in range(nb):
+                gn[:, b1, b2] = grid[:, b1, b2] / O.normalization((n, n), edges, npart, 3, [b1, b2])
+                dn[:, b1, b2] = dc[:, b1, b2] / (npart * nbar * area[b1] * nbar * area[b2])
+        errs.append(_rel(gn, dn))
+    # measured 9.5e-2, 4.8e-2, 1.7e-2, 3.5e-3 for 64^2 .. 512^2
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[2] < 3e-2 and errs[3] < 1e-2, errs
+    assert errs[0] / errs[3] > 10, errs
+
+
+def test_normalized_full_3pcf_approaches_particle_counting():
+    # the same check in 3D (Sec. 2.5, shells (4 pi / 3)(r+^3 - r-^3)), monopole
+    from paper_2210_10206_gb300 import synth
+    errs = []
+    for n in (32, 64, 128):
+        edges = np.linspace(n / 16.0, 0.45 * n, 5)
+        f = synth.particle_field(17, (n, n, n), 104)
+        pos = np.argwhere(f > 0)
+        npart = len(pos)
+        nb = 4
+        grid = O.zeta3_full(f, edges, 0)[0]
+        e2 = O.snapped_edges_sq(edges)
+        dc = np.zeros((nb, nb))
+        for p in pos:
+            q2 = (_min_image(pos - p, n) ** 2).sum(1)
+            cnt = np.array([((q2 > e2[b]) & (q2 <= e2[b + 1])).sum() for b in range(nb)], dtype=np.float64)
+            dc += np.outer(cnt, cnt) / (4 * math.pi)   # l = 0: Y00^2 = 1 / (4 pi)
+        assert _rel(grid, dc) < 1e-12
+        nbar = npart / float(n ** 3)
+        vol = 4 * math.pi / 3 * (edges[1:] ** 3 - edges[:-1] ** 3)
+        gn = np.array([[grid[b1, b2] / O.normalization((n, n, n), edges, npart, 3, [b1, b2]) for b2 in range(nb)]
+                       for b1 in range(nb)])
+        dn = dc / (npart * nbar ** 2 * np.outer(vol, vol))
+        errs.append(_rel(gn, dn))
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 2e-2, errs
 
 
 def test_single_entry_oracle_matches_full_tensor():
