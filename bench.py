@@ -37,6 +37,18 @@ ALG_TERMS_LM = 490
 ALG_BIN_TRIPLES = 220
 
 
+# Secondary workloads (--workload): inputs from paper_2210_10206_gb300.synth, seeded.
+#   batch64       64 projected fields of 128^2, 256^2, 512^2 and 1024^2 (16 each),
+#                 10 log bins 2..N/8, mmax 10, 3PCF + 4PCF: one sbg_projected_batch per call
+#   full512_3pcf  512^3 full 3PCF, lmax 10, 20 linear bins 2..62
+#   full256       256^3 full 4PCF, lmax 4, 10 linear bins 2..32 (the benchmark's call)
+#   full256_odd   the odd-parity 4PCF (sbg_full_odd) of the same field
+#   slices256     projected 3PCF + 4PCF of all 256 slices of that field
+#                 (sbg_projected_slices), 10 log bins 2..32, mmax 10
+# The first call of a geometry also builds its plan (kernel spectra, tables).
+WORKLOADS = ("batch64", "full512_3pcf", "full256", "full256_odd", "slices256")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -48,6 +60,10 @@ def parse():
     ap.add_argument("--compare", type=int, default=1, help="also time the other precisions (default on)")
     ap.add_argument("--grid", type=int, default=256, help="grid side (256 is the benchmark workload; "
                     "smaller sides are for profiling captures only)")
+    ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
+                    help="instead of the benchmark: time --calls measurement calls of another workload "
+                         "(parity workloads, e.g. for a launch list under a profiler) and print their times")
+    ap.add_argument("--calls", type=int, default=1, help="measurement calls of --workload")
     return ap.parse_args()
 
 
@@ -386,9 +402,58 @@ def run_gpu(args):
     ctx.close()
 
 
+def run_workload(args):
+    """Time `args.calls` measurement calls of a secondary workload on cuda:0
+    (CUDA events around each call) and print them with the stage timings of
+    the last call."""
+    import torch
+    from paper_2210_10206_gb300 import build, sbg, synth
+    build.build()
+    precs = {"bf16x3": sbg.SBG_PREC_BF16X3, "tf32x3": sbg.SBG_PREC_TF32X3, "fp32": sbg.SBG_PREC_FP32}
+    prec_name = "bf16x3" if args.prec == "auto" else args.prec
+    prec = precs[prec_name]
+    ctx = sbg.Context(0)
+    if args.workload == "batch64":
+        members = [synth.batch_member(j) for j in range(64)]
+        fields = [f for f, _ in members]
+        edges = [e for _, e in members]
+        call = lambda: ctx.projected_batch(fields, edges, 10, 10, prec=prec)
+    elif args.workload == "slices256":
+        d = torch.from_numpy(synth.workload_field("full256")).cuda()
+        e = list(synth.edges_log(2.0, 32.0, 10))
+        call = lambda: ctx.projected_slices(d, e, 10, prec=prec)
+    elif args.workload == "full512_3pcf":
+        w = synth.WORKLOADS["full512"]
+        d = torch.from_numpy(synth.workload_field("full512")).cuda()
+        call = lambda: ctx.full(d, w["edges"], lmax3=10)
+    else:
+        w = synth.WORKLOADS["full256"]
+        d = torch.from_numpy(synth.workload_field("full256")).cuda()
+        if args.workload == "full256_odd":
+            call = lambda: ctx.full_odd(d, w["edges"], 4, prec=prec)
+        else:
+            call = lambda: ctx.full(d, w["edges"], lmax4=4, prec=prec)
+    ms = []
+    for _ in range(args.calls):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        call()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    print(json.dumps({"workload": args.workload, "prec": prec_name, "calls": args.calls,
+                      "ms_per_call": [round(x, 3) for x in ms],
+                      "last_call_stage_ms": [round(float(x), 3) for x in np.asarray(ctx.timings())],
+                      "last_call_contraction_ms": round(sbg.sbg_last_contraction_ms(ctx.h), 3)}))
+    ctx.close()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.workload:
+        run_workload(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

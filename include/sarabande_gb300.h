@@ -84,6 +84,20 @@ void sbg_destroy(sbg_context* ctx);
  * own stream.  The caller keeps the stream alive while the context uses it. */
 sbg_status sbg_set_stream(sbg_context* ctx, void* cuda_stream);
 
+/* Bound on every wait inside the tensor-core 4PCF kernel of ctx (SBG_PREC_BF16X3
+ * and SBG_PREC_TF32X3), in nanoseconds of the GPU's global timer; the default is
+ * 1e9 (1 s).  The kernel's roles hand work to each other through barriers in
+ * shared memory; when a wait runs out, every role of the kernel stops, drains the
+ * copies and tensor-core operations it has already issued (each drain bounded
+ * too) and exits, and the measurement call returns SBG_ERR_TIMEOUT.  The context
+ * stays usable.
+ * test_stall = 1 withholds the kernel's MMA issuer in the following calls, so
+ * that the other roles' waits run out: a way to exercise the timeout path from
+ * the host without faulting the GPU (those calls compute nothing and return
+ * SBG_ERR_TIMEOUT).  test_stall = 0 restores normal operation.
+ * Errors: SBG_ERR_INVALID_ARG for a NULL ctx, wait_ns = 0 or test_stall not 0/1. */
+sbg_status sbg_set_wait_limit(sbg_context* ctx, unsigned long long wait_ns, int test_stall);
+
 /* Static string naming a status code. */
 const char* sbg_status_string(sbg_status s);
 
@@ -267,10 +281,13 @@ sbg_status sbg_plan4_info(int dim, int nbins, int lmax, sbg_precision prec, int 
  * Work is queued on `stream`; zeta3 is valid once the stream has completed.
  * Sizes beyond the maxima return SBG_ERR_UNSUPPORTED_SHAPE (n) or
  * SBG_ERR_INVALID_ARG (nbins, mmax, flags).  The first call made with a device
- * current looks up the array's device address for that device; make that
- * first call before any stream capture.  All calls share the one array: calls
- * whose work overlaps on the GPU (other streams, other host threads) race and
- * must be serialised by the caller. */
+ * current looks up the array's device address for that device (set-up, once
+ * per device); make that first call before any stream capture.  The looked-up
+ * address is kept for the life of the process and is not valid across a
+ * cudaDeviceReset.  All calls share the one array, which keeps the previous
+ * call's contents (each call clears what must start at zero): calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller. */
 sbg_status sbg_projected3_noalloc(const void* field, sbg_dtype dtype, int64_t n, const double* edges, int nbins,
                                   int mmax, unsigned flags, double* zeta3, void* stream);
 

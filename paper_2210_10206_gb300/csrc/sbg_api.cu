@@ -141,6 +141,10 @@ struct sbg_context {
   cudaStream_t stream = nullptr;
   size_t budget = 0, used = 0;
   std::string err;
+  // bound of every wait inside the tensor-core kernel, and the test switch that
+  // withholds its MMA issuer (sbg_set_wait_limit)
+  unsigned long long wait_ns = 1000000000ull;
+  int stall = 0;
   double timings[kStages] = {0};
   long long nlaunch = 0;   // kernels launched by the current/last measurement call
   long long last_launches = 0;
@@ -819,6 +823,17 @@ sbg_status ensure_tables4(sbg_context* ctx, int dim, int nb, int L, bool tc, boo
     }
   Tables4* t = new Tables4();
   sbg_status s = build_tables4(ctx, *t, dim, nb, L, tc, odd);
+  if (s == SBG_ERR_OUT_OF_MEMORY && !cache.empty()) {
+    // make room: the cached tables of other geometries are only a speed-up
+    free_tables4(ctx, t);
+    cudaStreamSynchronize(ctx->stream);  // queued work may still read them
+    for (auto& kv : cache) free_tables4(ctx, kv.second);
+    cache.clear();
+    ctx->t4 = nullptr;
+    ctx->err.clear();
+    t = new Tables4();
+    s = build_tables4(ctx, *t, dim, nb, L, tc, odd);
+  }
   if (s != SBG_OK) {
     free_tables4(ctx, t);
     return s;
@@ -1141,7 +1156,7 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
       KL(launch_tc4(d_astore, d_bimg, (const BGroup*)t.d_bgroups.p, (int)t.bgroups.size(), t.chunks_per_kb,
                     t.img_stride, d_delta, ng, (const Tile4*)t.d_tiles[0].p, ntl, (const Row4*)t.d_rows.p,
                     (const int*)t.d_cols.p, (const int*)t.d_uniq.p, nsingle, kmode, best, d_T, d_cnt, d_err,
-                    ctx->nsm, ctx->stream, ctx->kev[0], ctx->kev[1], tf ? 1 : 0));
+                    ctx->nsm, ctx->stream, ctx->kev[0], ctx->kev[1], tf ? 1 : 0, ctx->wait_ns, ctx->stall));
       ctx->kev_used = true;
       if (!ctx->defer) {  // a batch reads the flag once, after its last field
         int* perr;
@@ -1576,6 +1591,14 @@ sbg_status sbg_projected_slices(sbg_context* ctx, const void* cube, sbg_dtype dt
     g.zeta4 = (flags & SBG_4PCF) ? zeta4 + (size_t)i * s4 : nullptr;
   }
   return sbg_projected_batch(ctx, f.data(), (int)shape[0], nbins, mmax, prec, flags);
+}
+
+sbg_status sbg_set_wait_limit(sbg_context* ctx, unsigned long long wait_ns, int test_stall) {
+  if (!ctx) return SBG_ERR_INVALID_ARG;
+  if (wait_ns == 0 || (test_stall != 0 && test_stall != 1)) return fail(ctx, SBG_ERR_INVALID_ARG, "bad wait limit");
+  ctx->wait_ns = wait_ns;
+  ctx->stall = test_stall;
+  return SBG_OK;
 }
 
 sbg_status sbg_last_timings(const sbg_context* ctx, double* ms_per_stage, int* n_stages) {

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace sbg {
 
 struct cplx { float x, y; };
@@ -57,6 +59,46 @@ struct FftPass {
 // parts of neighbouring points are adjacent (packed f32x2 arithmetic).
 __host__ __device__ __forceinline__ long long blocked_re(long long x, int s, int nsingle) {
   return ((x >> 5) * nsingle + s) * 64 + (x & 31);
+}
+
+// Streaming multiprocessors of the current device (queried once per device).
+inline int device_sms() {
+  static std::atomic<int> sms[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (dev >= 64) {
+    int n = 1;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }
+  int n = sms[dev].load(std::memory_order_relaxed);
+  if (n <= 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      return 1;
+    }
+    sms[dev].store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
+
+// Opt kernel K in to `bytes` of dynamic shared memory on the current device.
+// The attribute belongs to the device's context, so it is set once per device
+// (and per kernel), not once per process.
+template <auto K>
+cudaError_t ensure_smem_attr(int bytes) {
+  static std::atomic<unsigned long long> done{0};  // bit d: set on device d
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+  return e;
 }
 
 // Host launcher (sbg_fft.cu).  Returns cudaSuccess or the launch error.

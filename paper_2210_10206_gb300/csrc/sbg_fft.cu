@@ -238,11 +238,9 @@ template <int N, bool CONTIG, int SIGN, int LOAD, int OUTB = 0>
 static cudaError_t launch_t(const FftPass& p, cudaStream_t st) {
   using G = Geo<N, CONTIG>;
   auto kern = fft_axis_kernel<N, CONTIG, SIGN, LOAD, OUTB>;
-  static bool configured = false;  // attribute is per function; set once per process
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+  {
+    cudaError_t e = ensure_smem_attr<fft_axis_kernel<N, CONTIG, SIGN, LOAD, OUTB>>(G::SMEM);
     if (e != cudaSuccess) return e;
-    configured = true;
   }
   // contiguous: outer rows grouped by TL; strided: outer * inner lines grouped by TL
   long long blocks = CONTIG ? p.outer / G::TL : (p.outer * (p.inner / G::TL));

@@ -48,7 +48,8 @@ __global__ void convert_kernel(const void* in, int is_f64, long long n, const do
 
 static int grid_for(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
-  if (b > 152LL * 16) b = 152LL * 16;
+  const long long cap = (long long)device_sms() * 16;
+  if (b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
 }
 
@@ -230,7 +231,8 @@ cudaError_t launch_gram3(const float2* a, long long ng, int nb, const float* del
   // about 4 chunks per CTA on small grids (a CTA's chunks run one after another),
   // at most 8 CTAs per SM of cross-CTA FP64 atomics on large ones
   long long blocks = (ng + 4 * kGramChunk - 1) / (4 * kGramChunk);
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  const long long cap = (long long)device_sms() * 8;
+  if (blocks > cap) blocks = cap;
   gram3_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, ng, nb, delta, S, nsingle, single0);
   return cudaGetLastError();
 }
@@ -416,11 +418,9 @@ static cudaError_t simt4_t(const float2* astore, long long ng, const float* delt
                           int nsm, int imag, cudaStream_t st) {
   const size_t smem = SimtSmem<TCG>::kBytes;
   auto kern = simt4_kernel<TCG, CPLX>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = ensure_smem_attr<simt4_kernel<TCG, CPLX>>((int)smem);
     if (e != cudaSuccess) return e;
-    configured = true;
   }
   if (nsplit <= 0) {
     // x-splits per tile so that the CTAs fill whole waves of the resident

@@ -56,7 +56,10 @@ cudaError_t launch_simt4(const float2* astore, long long ng, const float* delta,
 // K-block's img_stride-byte slab of `bimg` (nkb * img_stride bytes, written by
 // the launcher).  tf32 != 0 selects split TF32 products: every image, offset
 // and stride is twice as large (bimg must hold 2 * nkb * img_stride bytes).
-// *err is set (never cleared) if a bounded wait inside the kernel expired.
+// *err is set (never cleared) if a bounded wait inside the kernel expired:
+// every wait gives up after wait_ns of the GPU's global timer.  stall != 0
+// withholds the kernel's MMA issuer, so that the other roles' waits run out (a
+// host-side test of the timeout path; nothing is computed).
 constexpr int kTcMaxRowSlots = 56;  // row singles staged per K-block
 constexpr int kSimtMaxUniq = 64;    // row singles staged per chunk by the FP32 SIMT kernel
 constexpr int kTcEpoch = 256;       // K-blocks between progress checkpoints of the lag limiter
@@ -74,7 +77,8 @@ cudaError_t launch_tc4(const float2* astore, void* bimg, const BGroup* bgroups, 
                        long long img_stride, const float* delta, long long ng, const Tile4* tiles, int ntiles,
                        const Row4* rows, const int* cols, const int* slots, int nsingle, int complex_out,
                        int nsplit, double* T, int* cnt, int* err, int nsm, cudaStream_t st,
-                       cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr, int tf32 = 0);
+                       cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr, int tf32 = 0,
+                       unsigned long long wait_ns = 1000000000ull, int stall = 0);
 
 // ---- finalisation ----
 // zeta[o] = sum_{e in [ptr[o], ptr[o+1])} coef[e] * T[idx[e]] (idx < 0: conj of T[-idx-1]).

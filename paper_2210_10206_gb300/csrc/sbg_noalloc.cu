@@ -8,9 +8,9 @@
 // one file-scope __device__ array (kScratchBytes per device that loads this
 // library, held until the process exits).  The caller passes the field and the
 // output as device pointers.
+#include <atomic>
 #include <cmath>
 #include <cstring>
-#include <vector>
 
 #include "sarabande_gb300.h"
 #include "sbg_kernels.cuh"
@@ -36,23 +36,43 @@ constexpr size_t kScratchBytes = kOffS + up((size_t)(kMaxM + 1) * kMaxBins * kMa
 
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Device address of g_scratch per device, looked up on the first call made
-// with that device current.
-unsigned char* g_addr[64] = {nullptr};
+// Device address of g_scratch per device, looked up (set-up) on the first call
+// made with that device current.  In host code the name g_scratch is only a
+// host-side stand-in, so kernels are always given this looked-up address.  The
+// slots are atomic so that host threads making their first calls at once are
+// safe (they store the same address).  A cudaDeviceReset unloads the module and
+// may move the array: the cached address is not valid across a reset.
+std::atomic<unsigned char*> g_addr[64];
 
 sbg_status scratch_for_current_device(unsigned char** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SBG_ERR_CUDA;
-  if (!g_addr[dev]) {
+  unsigned char* a = g_addr[dev].load(std::memory_order_acquire);
+  if (!a) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return SBG_ERR_CUDA;
     }
-    g_addr[dev] = (unsigned char*)p;
+    a = (unsigned char*)p;
+    g_addr[dev].store(a, std::memory_order_release);
   }
-  *out = g_addr[dev];
+  *out = a;
   return SBG_OK;
+}
+
+// The small host-computed tables of a call (snapped squared edges, twiddles),
+// passed by value as a kernel parameter and written into the scratch array on
+// the stream, so the call holds no host buffer that the GPU reads later.
+struct HostTables {
+  double e2[kMaxBins + 1];
+  float2 tw[kMaxN];
+  int nbins, n;
+};
+
+__global__ void tables_kernel(const HostTables t, double* e2d, float2* tw) {
+  for (int i = threadIdx.x; i < t.n; i += blockDim.x) tw[i] = t.tw[i];
+  if ((int)threadIdx.x <= t.nbins) e2d[threadIdx.x] = t.e2[threadIdx.x];
 }
 
 #define NA_CU(call)                         \
@@ -96,20 +116,21 @@ extern "C" sbg_status sbg_projected3_noalloc(const void* field, sbg_dtype dtype,
   double* S = (double*)(s + kOffS);
 
   // host tables: squared edges snapped to integers, twiddles
-  std::vector<double> e2(nbins + 1);
+  HostTables ht{};
+  ht.nbins = nbins;
+  ht.n = N;
   for (int i = 0; i <= nbins; ++i) {
     double v = edges[i] * edges[i];
     const double r = std::nearbyint(v);
     if (std::fabs(v - r) <= 1e-9 * (v > 1.0 ? v : 1.0)) v = r;
-    e2[i] = v;
+    ht.e2[i] = v;
   }
-  std::vector<float2> twh(N);
   for (int j = 0; j < N; ++j) {
     const double a = 2.0 * 3.14159265358979323846 * j / N;
-    twh[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+    ht.tw[j] = make_float2((float)std::cos(a), (float)std::sin(a));
   }
-  NA_CU(cudaMemcpyAsync(e2d, e2.data(), (nbins + 1) * sizeof(double), cudaMemcpyHostToDevice, stream));
-  NA_CU(cudaMemcpyAsync(tw, twh.data(), N * sizeof(float2), cudaMemcpyHostToDevice, stream));
+  tables_kernel<<<1, 256, 0, stream>>>(ht, e2d, tw);
+  NA_CU(cudaGetLastError());
   // the array keeps the previous call's contents: clear the accumulators
   NA_CU(cudaMemsetAsync(acc, 0, 8 * sizeof(double), stream));
   NA_CU(cudaMemsetAsync(S, 0, (size_t)(mmax + 1) * nbins * nbins * 16, stream));

@@ -40,8 +40,12 @@
 // CTA per SM; the loaders of all CTAs advance through x together (a CTA may run
 // at most four 256-K-block epochs ahead of the slowest), so that the singles of
 // the current x-window are read from HBM once and then served from L2.
-// Every wait is bounded (1 s of %globaltimer); on expiry the CTA records an
-// error code, drains its own copies, frees TMEM and returns.
+// Every wait is bounded (wait_ns of %globaltimer, 1 s by default); on expiry
+// the CTA records an error code, and before it frees TMEM and returns it drains
+// what it has in flight: the B loader waits for its last bulk copy into each
+// stage, the loaders for their cp.async copies and the MMA issuer for the
+// completion of every MMA it issued (each drain with its own short bound, and
+// whatever the error word says).
 #include <algorithm>
 
 #include "sbg_kernels.cuh"
@@ -106,10 +110,11 @@ constexpr int kTmemCols = 512;
 constexpr int kRawRow = kKX * 8 + 16;
 constexpr int kRawStage = kTcMaxRowSlots * kRawRow;
 constexpr int kLag = 4;                // epochs a loader may run ahead of the slowest CTA
-constexpr int kMeta = 512;             // barriers (2 kRS + 3 * 4 + 1) and the TMEM address
+constexpr int kMeta = 512;             // barriers (2 kRS + 3 * 4 + 2) and the TMEM address
 constexpr int kOpBytes = 4 * 128 * 128;  // B tiles of every operand stage (both precisions)
 constexpr int kSmem = kOpBytes + kRS * kRawStage + kMeta + 1024;
-constexpr unsigned long long kWaitNs = 1000000000ull;
+// bound of a drain wait: copies and MMAs already issued complete in microseconds
+constexpr unsigned long long kDrainNs = 50000000ull;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -153,18 +158,31 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait; false if this or another thread of the grid gave up (after
-// 1 s of %globaltimer, or when the grid's error word is set).
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* err, int code) {
+// `limit` ns of %globaltimer, or when the grid's error word is set).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* err, int code,
+                                          unsigned long long limit) {
   if (mbar_try(b, parity)) return true;
   const unsigned long long t0 = gtime();
   for (;;) {
     if (mbar_try(b, parity)) return true;
     if (*err) return false;
-    if (gtime() - t0 > kWaitNs) {
+    if (gtime() - t0 > limit) {
       atomicCAS((int*)err, 0, code);
       return false;
     }
   }
+}
+// Drain wait before a CTA exits: waits for work this CTA already issued (a
+// bulk copy, its MMAs) whatever the error word says, bounded by kDrainNs.
+__device__ __forceinline__ bool mbar_drain(uint64_t* b, uint32_t parity, volatile int* err, int code) {
+  const unsigned long long t0 = gtime();
+  while (!mbar_try(b, parity)) {
+    if (gtime() - t0 > kDrainNs) {
+      atomicCAS((int*)err, 0, code);
+      return false;
+    }
+  }
+  return true;
 }
 
 __device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
@@ -299,20 +317,22 @@ __device__ __forceinline__ int n_mma(const Tile4& t, int cplx) {
 
 // One lane of the warp polls the barrier; the others wait at __syncwarp, which
 // also orders their later shared-memory reads after the observed phase.
-__device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t parity, volatile int* err, int code) {
+__device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t parity, volatile int* err, int code,
+                                          unsigned long long limit) {
   int good = 1;
-  if ((threadIdx.x & 31) == 0) good = mbar_wait(b, parity, err, code);
+  if ((threadIdx.x & 31) == 0) good = mbar_wait(b, parity, err, code, limit);
   __syncwarp();
   return __shfl_sync(0xffffffffu, good, 0) != 0;
 }
 
 // Bounded wait for a global progress counter written by other CTAs.
-__device__ __forceinline__ bool wait_count(const int* c, int target, volatile int* err, int code) {
+__device__ __forceinline__ bool wait_count(const int* c, int target, volatile int* err, int code,
+                                           unsigned long long limit) {
   if (*(volatile const int*)c >= target) return true;
   const unsigned long long t0 = gtime();
   while (*(volatile const int*)c < target) {
     if (*err) return false;
-    if (gtime() - t0 > kWaitNs) {
+    if (gtime() - t0 > limit) {
       atomicCAS((int*)err, 0, code);
       return false;
     }
@@ -336,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, const BGroup* __restrict__ bgroups,
            long long img_stride, long long ng, const Tile4* __restrict__ tiles, int ntiles,
            const Row4* __restrict__ rows, const int* __restrict__ slots, int nsingle, int cplx, int nsplit,
-           double* __restrict__ T, int* cnt, int* err_flag) {
+           double* __restrict__ T, int* cnt, int* err_flag, unsigned long long wait_ns, int stall) {
   using C = Cfg<TF>;
   constexpr int kGroups = C::kGroups, kOS = C::kOS, kOpStage = C::kOpStage, kRawPer = C::kRawPer;
   constexpr int kFlush = C::kFlush;
@@ -351,7 +371,8 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
   uint64_t* op_empty = bars + 2 * kRS + kOS;
   uint64_t* b_full = bars + 2 * kRS + 2 * kOS;    // B tile landed (transaction bytes)
   uint64_t* acc_full = b_full + kOS;              // a range's MMAs are complete
-  uint32_t* tmem_slot = (uint32_t*)(acc_full + 1);
+  uint64_t* mma_done = acc_full + 1;              // every MMA of this CTA is complete (drain)
+  uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
   volatile int* err = err_flag;
 
   const int tid = threadIdx.x;
@@ -372,6 +393,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
     }
     for (int i = 0; i < kOS; ++i) mbar_init(&b_full[i], 1);  // expect_tx arrival + bytes
     mbar_init(acc_full, 1);
+    mbar_init(mma_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == kMmaWarp) {
@@ -399,7 +421,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
         const uint32_t bytes = (uint32_t)bg.n * 256 * C::kAtoms;
         for (int kb = 0; kb < it.nk; ++kb) {
           const int os = kb % kOS;
-          if (!mbar_wait(&op_empty[os], (issued[os] & 1) ^ 1, err, 41)) {
+          if (!mbar_wait(&op_empty[os], (issued[os] & 1) ^ 1, err, 41, wait_ns)) {
             ok = false;
             break;
           }
@@ -409,9 +431,9 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
                    &b_full[os]);
         }
       }
-      // every copy issued has landed before the CTA may exit
+      // every copy issued has landed before the CTA may exit (also after an error)
       for (int os = 0; os < kOS; ++os)
-        if (issued[os]) mbar_wait(&b_full[os], (issued[os] - 1) & 1, err, 42);
+        if (issued[os]) mbar_drain(&b_full[os], (issued[os] - 1) & 1, err, 42);
     }
   } else if (warp >= kLoad0) {
     // ------------------------------------------------------------ loaders --
@@ -440,7 +462,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
         const long long ce = rd * epochs + e;  // global epoch index
         if (ce >= kLag) {
           int good = 1;
-          if (lane == 0) good = wait_count(&cnt[ce - kLag], (int)gridDim.x * kLoadWarps, err, 13);
+          if (lane == 0) good = wait_count(&cnt[ce - kLag], (int)gridDim.x * kLoadWarps, err, 13, wait_ns);
           if (!__shfl_sync(0xffffffffu, good, 0)) {
             ok = false;
             break;
@@ -451,7 +473,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
           const int gg = kb % kGroups;
           const uint32_t n = gcount[gg]++;
           const int rs = kRawPer * gg + (int)(n % kRawPer);
-          if (!warp_wait(&raw_empty[rs], ((n / kRawPer) & 1) ^ 1, err, 11)) {
+          if (!warp_wait(&raw_empty[rs], ((n / kRawPer) & 1) ^ 1, err, 11, wait_ns)) {
             ok = false;
             break;
           }
@@ -472,7 +494,9 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
     asm volatile("cp.async.wait_all;" ::: "memory");
   } else if (warp == kMmaWarp) {
     // ---------------------------------------------------------------- MMA --
-    if (lane == 0) {
+    // stall != 0 (a test of the timeout path): the issuer takes no work, so
+    // every wait of the other roles runs out
+    if (lane == 0 && !stall) {
       uint32_t uses[kOS] = {};
       bool ok = true;
       for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
@@ -486,7 +510,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
         const uint32_t idesc2 = (idesc & ~(0x3Fu << 17)) | ((uint32_t)((2 * N) >> 3) << 17);
         for (int kb = 0; kb < it.nk; ++kb) {
           const int os = kb % kOS;
-          if (!mbar_wait(&op_full[os], uses[os] & 1, err, 21)) {  // A formed and (checked by a producer) B landed
+          if (!mbar_wait(&op_full[os], uses[os] & 1, err, 21, wait_ns)) {  // A formed and (checked by a producer) B landed
             ok = false;
             break;
           }
@@ -511,6 +535,9 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
           if ((kb + 1) % kFlush == 0 || kb + 1 == it.nk) mma_commit(acc_full);
         }
       }
+      // every MMA issued has completed before TMEM is freed (also after an error)
+      mma_commit(mma_done);
+      mbar_drain(mma_done, 0, err, 22);
     }
   } else {
     // ---------------------------------------------------------- producers --
@@ -538,7 +565,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
       // fold range i of this unit: inner accumulator -> outer (or -> T for the last range)
       auto fold = [&](int i) -> bool {
         const uint32_t Rg = R + i;
-        if (!warp_wait(acc_full, Rg & 1, err, 33)) return false;
+        if (!warp_wait(acc_full, Rg & 1, err, 33, wait_ns)) return false;
         tc_fence_after();
         const bool last = i + 1 == nranges;
         const uint32_t inner = tmem + lane_addr;
@@ -589,8 +616,8 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
           flushed = kb / kFlush;
         }
         const int rs = kRawPer * grp + (int)(uses % kRawPer);
-        if (!warp_wait(&raw_full[rs], (uses / kRawPer) & 1, err, 31) ||
-            !warp_wait(&op_empty[os], (uses & 1) ^ 1, err, 32)) {
+        if (!warp_wait(&raw_full[rs], (uses / kRawPer) & 1, err, 31, wait_ns) ||
+            !warp_wait(&op_empty[os], (uses & 1) ^ 1, err, 32, wait_ns)) {
           ok = false;
           break;
         }
@@ -656,7 +683,7 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
         // the first warp of the group also sees this K-block's B tile land, so
         // the MMA issuer waits on op_full alone (the copy of the stage's next
         // K-block needs this op_full first, so the parity cannot run ahead)
-        if (warp % C::kWarps == 0 && !warp_wait(&b_full[os], (uses - 1) & 1, err, 34)) {
+        if (warp % C::kWarps == 0 && !warp_wait(&b_full[os], (uses - 1) & 1, err, 34, wait_ns)) {
           ok = false;
           break;
         }
@@ -759,7 +786,7 @@ cudaError_t launch_tc4_t(const float2* astore, void* bimg, const BGroup* bgroups
                          long long img_stride, const float* delta, long long ng, const Tile4* tiles, int ntiles,
                          const Row4* rows, const int* cols, const int* slots, int nsingle, int complex_out,
                          int nsplit, double* T, int* cnt, int* err, int nsm, cudaStream_t st, cudaEvent_t ev_begin,
-                         cudaEvent_t ev_end) {
+                         cudaEvent_t ev_end, unsigned long long wait_ns, int stall) {
   constexpr int kAtoms = Cfg<TF>::kAtoms;
   const long long stride = img_stride * kAtoms;  // the tables give BF16 image offsets
   // B images of every K-block, once per field
@@ -773,14 +800,10 @@ cudaError_t launch_tc4_t(const float2* astore, void* bimg, const BGroup* bgroups
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(tc4_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  cudaError_t e = ensure_smem_attr<tc4_kernel<TF>>(kSmem);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc4_kernel<TF>, kThreads, kSmem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc4_kernel<TF>, kThreads, kSmem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const float* af = (const float*)astore;
@@ -789,7 +812,8 @@ cudaError_t launch_tc4_t(const float2* astore, void* bimg, const BGroup* bgroups
   const int grid = nsm;  // every CTA takes part in every round so that the progress counters fill up
   void* args[] = {(void*)&af,    (void*)&bi,      (void*)&bgroups, (void*)&stride,     (void*)&ng,
                   (void*)&tiles, (void*)&ntiles,  (void*)&rows,    (void*)&slots,      (void*)&nsingle,
-                  (void*)&ccols, (void*)&nsplit, (void*)&T,  (void*)&cnt,        (void*)&err};
+                  (void*)&ccols, (void*)&nsplit, (void*)&T,  (void*)&cnt,        (void*)&err,
+                  (void*)&wait_ns, (void*)&stall};
   if (ev_begin && (e = cudaEventRecord(ev_begin, st)) != cudaSuccess) return e;
   e = cudaLaunchCooperativeKernel((const void*)tc4_kernel<TF>, dim3(grid), dim3(kThreads), args, kSmem, st);
   if (e != cudaSuccess) return e;
@@ -803,14 +827,16 @@ cudaError_t launch_tc4(const float2* astore, void* bimg, const BGroup* bgroups, 
                        long long img_stride, const float* delta, long long ng, const Tile4* tiles, int ntiles,
                        const Row4* rows, const int* cols, const int* slots, int nsingle, int complex_out,
                        int nsplit, double* T, int* cnt, int* err, int nsm, cudaStream_t st, cudaEvent_t ev_begin,
-                       cudaEvent_t ev_end, int tf32) {
+                       cudaEvent_t ev_end, int tf32, unsigned long long wait_ns, int stall) {
   if (ntiles <= 0) return cudaSuccess;
   if (ng % kKX || nbgroups <= 0 || chunks_per_kb <= 0 || img_stride % 1024) return cudaErrorInvalidValue;
   if (tf32)
     return launch_tc4_t<true>(astore, bimg, bgroups, chunks_per_kb, img_stride, delta, ng, tiles, ntiles, rows, cols,
-                              slots, nsingle, complex_out, nsplit, T, cnt, err, nsm, st, ev_begin, ev_end);
+                              slots, nsingle, complex_out, nsplit, T, cnt, err, nsm, st, ev_begin, ev_end, wait_ns,
+                              stall);
   return launch_tc4_t<false>(astore, bimg, bgroups, chunks_per_kb, img_stride, delta, ng, tiles, ntiles, rows, cols,
-                             slots, nsingle, complex_out, nsplit, T, cnt, err, nsm, st, ev_begin, ev_end);
+                             slots, nsingle, complex_out, nsplit, T, cnt, err, nsm, st, ev_begin, ev_end, wait_ns,
+                             stall);
 }
 
 }  // namespace sbg

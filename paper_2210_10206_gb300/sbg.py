@@ -19,6 +19,8 @@ SBG_F32, SBG_F64 = 0, 1
 SBG_PREC_FP32, SBG_PREC_BF16X3, SBG_PREC_TF32X3 = 0, 1, 3
 HAS_BF16X3 = True  # the tcgen05 split-BF16 4PCF combination is built in
 SBG_3PCF, SBG_4PCF, SBG_NORMALIZED, SBG_SUBTRACT_MEAN, SBG_FIELD_ON_DEVICE = 1, 2, 4, 8, 16
+(SBG_ERR_INVALID_ARG, SBG_ERR_UNSUPPORTED_SHAPE, SBG_ERR_BIN_RANGE, SBG_ERR_EMPTY_BIN, SBG_ERR_OUT_OF_MEMORY,
+ SBG_ERR_CUDA, SBG_ERR_TIMEOUT, SBG_ERR_INTERNAL) = (-1, -2, -3, -4, -5, -6, -7, -8)
 STATUS = {0: "SBG_OK", -1: "SBG_ERR_INVALID_ARG", -2: "SBG_ERR_UNSUPPORTED_SHAPE", -3: "SBG_ERR_BIN_RANGE",
           -4: "SBG_ERR_EMPTY_BIN", -5: "SBG_ERR_OUT_OF_MEMORY", -6: "SBG_ERR_CUDA", -7: "SBG_ERR_TIMEOUT",
           -8: "SBG_ERR_INTERNAL"}
@@ -85,6 +87,8 @@ def lib():
         L.sbg_plan4_info.restype = st
         L.sbg_projected3_noalloc.argtypes = [vp, i, ctypes.c_int64, vp, i, i, ctypes.c_uint, vp, vp]
         L.sbg_projected3_noalloc.restype = st
+        L.sbg_set_wait_limit.argtypes = [vp, ctypes.c_ulonglong, i]
+        L.sbg_set_wait_limit.restype = st
         _lib = L
     return _lib
 
@@ -104,6 +108,10 @@ def sbg_destroy(h):
 
 def sbg_set_stream(h, stream):
     return lib().sbg_set_stream(h, ctypes.c_void_p(stream))
+
+
+def sbg_set_wait_limit(h, wait_ns, test_stall=0):
+    return lib().sbg_set_wait_limit(h, int(wait_ns), int(test_stall))
 
 
 def sbg_status_string(s):
@@ -362,6 +370,11 @@ class Context:
 
     def set_stream(self, stream):
         return sbg_set_stream(self.h, stream)
+
+    def set_wait_limit(self, wait_ns, test_stall=0):
+        s = sbg_set_wait_limit(self.h, wait_ns, test_stall)
+        if s != SBG_OK:
+            raise SbgError(s, sbg_last_error(self.h))
 
     def full(self, field, edges, lmax3=None, lmax4=None, prec=SBG_PREC_FP32, flags=SBG_SUBTRACT_MEAN):
         if lmax3 is not None:

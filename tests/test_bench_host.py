@@ -19,17 +19,24 @@ def test_convolution_bytes_per_point():
 
 
 def test_profiled_traffic_follows_the_source_hashes(tmp_path, monkeypatch):
+    import hashlib
     import bench
-    t = bench.profiled_traffic(256)
-    assert t is not None and t > 0
-    assert abs(bench.profiled_traffic(128) * 8 - t) < 1e-6 * t  # scaled by grid points
-    # a copy of the tree whose kernel source differs reports no traffic
-    for rel in ("profiles/tc4_kernel_traffic.txt", "paper_2210_10206_gb300/csrc/sbg_api.cu",
-                "paper_2210_10206_gb300/csrc/sbg_tc.cu"):
+    # a tree whose capture file carries the hashes of its current sources
+    srcs = ("paper_2210_10206_gb300/csrc/sbg_api.cu", "paper_2210_10206_gb300/csrc/sbg_tc.cu")
+    for rel in srcs:
         os.makedirs(tmp_path / os.path.dirname(rel), exist_ok=True)
         shutil.copy(os.path.join(ROOT, rel), tmp_path / rel)
+    os.makedirs(tmp_path / "profiles", exist_ok=True)
+    with open(tmp_path / "profiles/tc4_kernel_traffic.txt", "w") as f:
+        f.write("# test capture\n")
+        for rel in srcs:
+            f.write(f"sha256 {rel} {hashlib.sha256(open(tmp_path / rel, 'rb').read()).hexdigest()}\n")
+        f.write("grid 128\ndram_bytes_read 5000000000\ndram_bytes_write 4000000\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.profiled_traffic(256) == t
+    t = bench.profiled_traffic(256)
+    assert t == (5000000000 + 4000000) * 8  # scaled by grid points
+    assert abs(bench.profiled_traffic(128) * 8 - t) < 1e-6 * t
+    # once the kernel source differs the figure is no longer reported
     with open(tmp_path / "paper_2210_10206_gb300/csrc/sbg_tc.cu", "a") as f:
         f.write("\n")
     assert bench.profiled_traffic(256) is None
