@@ -117,48 +117,49 @@ class ClockSampler:
 
 # -------------------------------------------------------------- oracle leg --
 def oracle_sample(field, edges, heavy=True):
-    """Time the FP64 oracle, as it stands, on a bounded sample of one 256^3
-    4PCF field and scale to fields/s.  Per field the oracle runs
-    O.kernel_full for each (l, m in -l..l) (25 at lmax 4), O.a_coefficient for
-    each of those kernels' 10 bins (250), and O.triple_sum for each of the 804
-    (Lambda, M) terms over all grid points.  The sample times six kernel
-    builds, eight convolutions and two triple sums on 1/4 of the grid (about
-    10-30 s of host work), and scales each by its count per field; the light
-    sample (one of each, the triple sum on 1/32 of the grid) is the per-step
-    work of the reference arm."""
-    from oracle import sarabande_oracle as O
+    """Time the FP64 C++ oracle (oracle/sarabande_oracle.cpp, OpenMP on every
+    host core), as it stands, on a bounded sample of one 256^3 4PCF field and
+    scale to fields/s.  Per field the oracle computes delta-hat once, the
+    250 coefficient arrays a^b_lm (l <= 4, every m, 10 bins; each a kernel and
+    two FFTs of the full grid) and the combination of Eq. mu over every grid
+    point.  The sample times a few of those coefficient arrays at full size and
+    the combination over a contiguous slice of the points (its cost per point
+    does not depend on the values, so the slice's arrays are drawn at random),
+    and scales each by its count per field: the value is extrapolated.  The
+    heavy sample (about 10-30 s of host work) is bench.py's cpu_baseline; the
+    light one is the per-step work of the reference arm."""
+    from oracle import cpp as C
     t0 = time.perf_counter()
-    d, _ = O.preprocess(field)
-    lms = [(1, 1), (2, -1), (3, 0), (3, 2), (4, -3), (4, 3)] if heavy else [(1, 1)]
-    tk0 = time.perf_counter()
-    ks = [O.kernel_full(d.shape, edges, l, m) for (l, m) in lms]
-    tk = (time.perf_counter() - tk0) / len(lms)
-    ta0 = time.perf_counter()
-    picks = [(0, 3), (1, 6), (2, 8), (3, 9), (4, 2), (5, 5), (5, 7), (2, 0)] if heavy else [(0, 3)]
-    a = [O.a_coefficient(d, ks[i][b]) for (i, b) in picks]
-    a = a + a if len(a) == 1 else a
-    ta = (time.perf_counter() - ta0) / len(picks)
+    d = field.astype(np.float64)
+    d = d - d.mean()
+    n = d.shape[0]
     ng = d.size
-    frac = 4 if heavy else 32
-    slab = ng // frac
-    dd = d.reshape(1, -1)[:, :slab]
-    A1 = np.stack([a[0].ravel()[:slab]] * NB)
-    A2 = np.stack([a[1].ravel()[:slab]] * NB)
-    tb0 = time.perf_counter()
-    O.triple_sum(dd, A1, A2, A2)
-    if heavy:
-        O.triple_sum(dd, A1, A1, A2)
-    tb = (time.perf_counter() - tb0) / (2 if heavy else 1) * frac
-    n_k = (LMAX4 + 1) ** 2
-    n_a = n_k * NB
-    n_terms = sum(1 for (l1, l2, l3) in O.lambda_list(LMAX4) for m1 in range(-l1, l1 + 1)
-                  for m2 in range(-l2, l2 + 1) if abs(m1 + m2) <= l3)
-    per_field = n_k * tk + n_a * ta + n_terms * tb
-    return {"value": 1.0 / per_field, "unit": "fields/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"one 256^3 lognormal field, lmax 4, 10 bins: {len(lms)} of its {n_k} O.kernel_full, "
-                       f"{len(picks)} of its {n_a} O.a_coefficient and {2 if heavy else 1} of its "
-                       f"{n_terms} O.triple_sum (on 1/{frac} of the grid, scaled x{frac}); per field "
-                       f"{per_field:.0f} s extrapolated from "
+    # one FFT of the grid (delta-hat, once per field)
+    tf0 = time.perf_counter()
+    C.fftn(d, -1)
+    t_fft = time.perf_counter() - tf0
+    picks = [(1, 1, 3), (3, -2, 9), (4, 4, 5)] if heavy else [(2, 1, 4)]
+    ta0 = time.perf_counter()
+    for (l, m, b) in picks:
+        C.coefficient(d, edges, l, m, b)
+    # each call also transforms delta, which the oracle does once per field
+    t_arr = max((time.perf_counter() - ta0) / len(picks) - t_fft, 0.0)
+    frac = 64 if heavy else 512
+    npts = ng // frac
+    rng = np.random.default_rng(5)
+    nlm = (LMAX4 + 1) ** 2
+    a = (rng.standard_normal((nlm, NB, npts)) + 1j * rng.standard_normal((nlm, NB, npts))).astype(np.complex128)
+    tc0 = time.perf_counter()
+    C.zeta4_combine(d.ravel()[:npts], a, LMAX4)
+    t_comb = (time.perf_counter() - tc0) * frac
+    n_a = nlm * NB
+    per_field = t_fft + n_a * t_arr + t_comb
+    return {"value": 1.0 / per_field, "unit": "fields/s", "cores": C.threads(), "kind": "oracle",
+            "extrapolated": True,
+            "sample": (f"FP64 C++ oracle on one {n}^3 lognormal field, lmax 4, 10 bins: delta-hat, {len(picks)} of its "
+                       f"{n_a} coefficient arrays at full size and the 4PCF combination over 1/{frac} of the grid "
+                       f"points (scaled x{frac}); per field {per_field:.0f} s extrapolated "
+                       f"({t_fft:.2f} s FFT + {n_a} x {t_arr:.2f} s arrays + {t_comb:.0f} s combination) from "
                        f"{time.perf_counter() - t0:.1f} s of oracle work"),
             "seconds_per_field": per_field}
 

@@ -45,7 +45,7 @@ __all__ = [
     "a_full", "c_projected", "zeta3_full", "zeta4_full", "zeta3_projected",
     "zeta4_projected", "lambda_list", "wigner3j", "coupling",
     "normalization", "preprocess", "brute_a", "zeta4_full_entries", "kernel_full_bin",
-    "lambda_list_odd", "zeta4_full_odd",
+    "lambda_list_odd", "zeta4_full_odd", "zeta3_full_entries",
 ]
 
 
@@ -356,12 +356,13 @@ def triple_sum(d, a1, a2, a3):
     return (p.reshape(nb * nb, -1) @ a3.T).reshape(nb, nb, nb)
 
 
-def zeta4_full_entries(delta, edges, entries):
-    """The same coefficients as zeta4_full for a list of single entries
+def zeta4_full_entries(delta, edges, entries, odd=False, cache=None):
+    """The same coefficients as zeta4_full (odd=False) or zeta4_full_odd
+    (odd=True: E(Lambda) = -1, imaginary part) for a list of single entries
     ((l1, l2, l3), b1, b2, b3), each computed on its own from only the
     a-arrays it needs (for spot checks at sizes where the full tensor is out
-    of reach)."""
-    cache = {}
+    of reach).  `cache` may pass a dict that keeps a-arrays across calls."""
+    cache = {} if cache is None else cache
     dh = np.fft.fftn(delta)
 
     def a_of(l, m, b):
@@ -383,7 +384,29 @@ def zeta4_full_entries(delta, edges, entries):
                 if c == 0.0:
                     continue
                 s += c * np.sum(d * a_of(l1, m1, b1) * a_of(l2, m2, b2) * a_of(l3, m3, b3))
-        out.append(s.real)
+        out.append(-s.imag if odd else s.real)
+    return np.array(out)
+
+
+def zeta3_full_entries(delta, edges, entries):
+    """zeta_l^{b1 b2} of zeta3_full for a list of single entries (l, b1, b2),
+    each from the a-arrays of its two bins at m = 0..l only: for a real delta
+    a_{l,-m} = (-1)^m conj(a_lm) (Sec. 2.1), so the terms m and -m of
+    Eq. alm_to_zeta_clean are complex conjugates and sum to twice the real part.
+    The arrays of one m are made, used and dropped in turn, so that one entry
+    holds at most two grid-sized arrays (spot checks at 512^3)."""
+    dh = np.fft.fftn(delta)
+    d = delta.ravel()
+    out = []
+    for l, b1, b2 in entries:
+        s = 0.0
+        for m in range(l + 1):
+            a1 = a_coefficient(delta, kernel_full_bin(delta.shape, edges, l, m, b1), dh).ravel()
+            a2 = a1 if b2 == b1 else a_coefficient(delta, kernel_full_bin(delta.shape, edges, l, m, b2), dh).ravel()
+            t = np.sum(d * a1 * np.conj(a2))
+            s += t.real if m == 0 else 2.0 * t.real
+            del a1, a2
+        out.append(s * (-1) ** l / math.sqrt(2 * l + 1))
     return np.array(out)
 
 

@@ -656,3 +656,20 @@ def test_single_entry_oracle_matches_full_tensor():
         assert abs(g - z4[lams.index(lam), b1, b2, b3]) < 1e-12 * np.abs(z4).max()
     k = O.kernel_full(d.shape, edges, 2, -1)
     assert np.array_equal(O.kernel_full_bin(d.shape, edges, 2, -1, 2), k[2])
+
+
+def test_single_entry_oracles_match_full_tensors():
+    # the one-entry paths that write the full-size goldens equal the full
+    # tensors: the odd-parity option, and the 3PCF entries built from m >= 0
+    d = RNG.normal(size=(16, 16, 16))
+    edges = [0.5, 1.5, 2.5, 3.5, 5.0]
+    zo = O.zeta4_full_odd(d, edges, 2)
+    lams = O.lambda_list_odd(2)
+    entries = [((1, 1, 1), 0, 1, 2), ((1, 2, 2), 3, 0, 1), ((2, 1, 2), 2, 2, 3), ((2, 2, 1), 1, 3, 3)]
+    got = O.zeta4_full_entries(d, edges, entries, odd=True)
+    for (lam, b1, b2, b3), g in zip(entries, got):
+        assert abs(g - zo[lams.index(lam), b1, b2, b3]) < 1e-12 * np.abs(zo).max()
+    z3 = O.zeta3_full(d, edges, 4)
+    e3 = [(0, 0, 0), (1, 2, 1), (2, 3, 3), (3, 0, 3), (4, 1, 2)]
+    for (l, b1, b2), g in zip(e3, O.zeta3_full_entries(d, edges, e3)):
+        assert abs(g - z3[l, b1, b2]) < 1e-12 * np.abs(z3).max()
