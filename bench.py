@@ -426,7 +426,7 @@ def run_workload(args):
     elif args.workload == "full512_3pcf":
         w = synth.WORKLOADS["full512"]
         d = torch.from_numpy(synth.workload_field("full512")).cuda()
-        call = lambda: ctx.full(d, w["edges"], lmax3=10)
+        call = lambda: ctx.full(d, w["edges"], lmax3=10, prec=prec)
     else:
         w = synth.WORKLOADS["full256"]
         d = torch.from_numpy(synth.workload_field("full256")).cuda()

@@ -54,13 +54,18 @@ typedef enum {
 
 typedef enum { SBG_F32 = 0, SBG_F64 = 1 } sbg_dtype;
 
-/* Arithmetic of the 4PCF combination (FFTs are FP32, final sums FP64).
+/* Arithmetic of the combination steps: the delta-weighted Gram of the 3PCF
+ * (Algorithms 5, 7) and the pair x single contraction of the 4PCF (Algorithms
+ * 6, 8).  FFTs are FP32, final sums and couplings FP64.
  * FP32: SIMT FP32 products and accumulation.
- * BF16X3: tcgen05 tensor cores, each operand split into bf16 hi + lo, three
- *         products hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM.
+ * BF16X3: tcgen05 tensor cores, each operand split into bf16 hi + lo, products
+ *         hi*hi + hi*lo + lo*hi (the 3PCF Gram also adds lo*lo), FP32
+ *         accumulation in TMEM over ranges of points, FP64 across ranges.
  * TF32X3: the same with tf32 hi + lo (hi rounded to 10 mantissa bits, lo the
  *         exact remainder): more accurate, about twice the MMA work.
- * (2 is reserved.) */
+ * Value 2 is not used: a six-product bf16 split is not built, because the
+ * three-product split already meets its 1e-4 target with margin and split
+ * TF32 serves the 1e-5 target. */
 typedef enum { SBG_PREC_FP32 = 0, SBG_PREC_BF16X3 = 1, SBG_PREC_TF32X3 = 3 } sbg_precision;
 
 enum {
@@ -84,14 +89,14 @@ void sbg_destroy(sbg_context* ctx);
  * own stream.  The caller keeps the stream alive while the context uses it. */
 sbg_status sbg_set_stream(sbg_context* ctx, void* cuda_stream);
 
-/* Bound on every wait inside the tensor-core 4PCF kernel of ctx (SBG_PREC_BF16X3
- * and SBG_PREC_TF32X3), in nanoseconds of the GPU's global timer; the default is
+/* Bound on every wait inside the tensor-core combination kernels of ctx
+ * (SBG_PREC_BF16X3 and SBG_PREC_TF32X3), in nanoseconds of the GPU's global timer; the default is
  * 1e9 (1 s).  The kernel's roles hand work to each other through barriers in
  * shared memory; when a wait runs out, every role of the kernel stops, drains the
  * copies and tensor-core operations it has already issued (each drain bounded
  * too) and exits, and the measurement call returns SBG_ERR_TIMEOUT.  The context
  * stays usable.
- * test_stall = 1 withholds the kernel's MMA issuer in the following calls, so
+ * test_stall = 1 withholds the kernels' MMA issuers in the following calls, so
  * that the other roles' waits run out: a way to exercise the timeout path from
  * the host without faulting the GPU (those calls compute nothing and return
  * SBG_ERR_TIMEOUT).  test_stall = 0 restores normal operation.

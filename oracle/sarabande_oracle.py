@@ -45,7 +45,7 @@ __all__ = [
     "a_full", "c_projected", "zeta3_full", "zeta4_full", "zeta3_projected",
     "zeta4_projected", "lambda_list", "wigner3j", "coupling",
     "normalization", "preprocess", "brute_a", "zeta4_full_entries", "kernel_full_bin",
-    "lambda_list_odd", "zeta4_full_odd", "zeta3_full_entries",
+    "lambda_list_odd", "zeta4_full_odd", "zeta3_full_entries", "zeta_projected_entries",
 ]
 
 
@@ -408,6 +408,24 @@ def zeta3_full_entries(delta, edges, entries):
             del a1, a2
         out.append(s * (-1) ** l / math.sqrt(2 * l + 1))
     return np.array(out)
+
+
+def zeta_projected_entries(delta, edges, entries3, entries4):
+    """Single entries of zeta3_projected, (m, b1, b2), and of zeta4_projected,
+    ((m1, m2), b1, b2, b3) with |m1 + m2| <= mmax, each from the c arrays of the
+    m values it needs (every m from its own kernel, as in c_projected); for spot
+    checks of large batches.  Returns two complex arrays."""
+    cache = {}
+
+    def c_of(m):
+        if m not in cache:
+            cache[m] = c_projected(delta, edges, m).reshape(len(edges) - 1, -1)
+        return cache[m]
+
+    d = delta.ravel()
+    z3 = [np.sum(d * c_of(m)[b1] * np.conj(c_of(m)[b2])) for m, b1, b2 in entries3]
+    z4 = [np.sum(d * c_of(m1)[b1] * c_of(m2)[b2] * c_of(-(m1 + m2))[b3]) for (m1, m2), b1, b2, b3 in entries4]
+    return np.array(z3, dtype=np.complex128), np.array(z4, dtype=np.complex128)
 
 
 def zeta4_projected(delta, edges, mmax):

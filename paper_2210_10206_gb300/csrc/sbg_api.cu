@@ -1083,6 +1083,16 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
     ST(buf(ctx, "S", (size_t)std::max(ngroups3, 1) * nb * nb * 16, (void**)&d_S));
     CU(cudaMemsetAsync(d_S, 0, (size_t)ngroups3 * nb * nb * 16, ctx->stream));
   }
+  // split-BF16 / split-TF32: both combination steps run on the tensor cores,
+  // whose kernels report a wait that ran out in this word (a batch clears it
+  // once and reads it after its last field)
+  const bool tcomb = prec != SBG_PREC_FP32;
+  const int tf32 = prec == SBG_PREC_TF32X3 ? 1 : 0;
+  int* d_err = nullptr;
+  if (tcomb) {
+    ST(buf(ctx, "err", 16, (void**)&d_err));
+    if (!ctx->defer) CU(cudaMemsetAsync(d_err, 0, 16, ctx->stream));
+  }
   for (int g = 0; g < ngroups; ++g) {
     const float2* G;
     if (cached) {
@@ -1109,8 +1119,11 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
     }
     if (do3 && g < ngroups3) {
       double* Sg = d_S + (size_t)g * nb * nb * 2;
-      if (stored) KL(launch_gram3(d_astore, ng, nb, d_delta, Sg, nsingle, g * nb, ctx->stream));
-      else KL(launch_gram3(d_group, ng, nb, d_delta, Sg, 0, 0, ctx->stream));
+      const float2* src = stored ? d_astore : d_group;
+      const int ns = stored ? nsingle : 0, s0 = stored ? g * nb : 0;
+      if (tcomb) KL(launch_gram_tc(src, ng, nb, d_delta, Sg, ns, s0, tf32, d_err, ctx->nsm, ctx->wait_ns, ctx->stall,
+                                   ctx->stream));
+      else KL(launch_gram3(src, ng, nb, d_delta, Sg, ns, s0, ctx->stream));
     }
   }
   rec(ctx, 4);
@@ -1118,8 +1131,8 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
   // ---- 4PCF ----
   double* d_z4 = nullptr;
   if (do4) {
-    const bool tc = prec != SBG_PREC_FP32;         // split BF16 or split TF32 on the tensor cores
-    const bool tf = prec == SBG_PREC_TF32X3;
+    const bool tc = tcomb;                          // split BF16 or split TF32 on the tensor cores
+    const bool tf = tf32 != 0;
     ST(ensure_tables4(ctx, dim, nb, lmax4, tc, odd));
     Tables4& t = *ctx->t4;
     const int cplx = dim == 2 ? 1 : 0;
@@ -1129,9 +1142,6 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
     ST(buf(ctx, "T", (size_t)std::max<long long>(t.tcount, 1) * 8 * (cplx ? 2 : 1), (void**)&d_T));
     CU(cudaMemsetAsync(d_T, 0, (size_t)t.tcount * 8 * (cplx ? 2 : 1), ctx->stream));
     if (tc) {
-      int* d_err;
-      ST(buf(ctx, "err", 16, (void**)&d_err));
-      if (!ctx->defer) CU(cudaMemsetAsync(d_err, 0, 16, ctx->stream));  // a batch clears it once
       const int ntl = (int)t.tiles[0].size();
       const long long kblocks = ng / 32;
       // x-splits per tile: units = ntl * nsplit spread evenly over the CTAs
@@ -1158,15 +1168,6 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
                     (const int*)t.d_cols.p, (const int*)t.d_uniq.p, nsingle, kmode, best, d_T, d_cnt, d_err,
                     ctx->nsm, ctx->stream, ctx->kev[0], ctx->kev[1], tf ? 1 : 0, ctx->wait_ns, ctx->stall));
       ctx->kev_used = true;
-      if (!ctx->defer) {  // a batch reads the flag once, after its last field
-        int* perr;
-        ST(host_staging(ctx, 64, (void**)&perr));
-        CU(cudaMemcpyAsync(perr, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-        CU(cudaStreamSynchronize(ctx->stream));
-        const int herr = *perr;
-        if (herr)
-          return fail(ctx, SBG_ERR_TIMEOUT, "tensor-core 4PCF kernel gave up waiting (code " + std::to_string(herr) + ")");
-      }
     } else {
       const int tcg[3] = {4, 8, 16};
       CU(cudaEventRecord(ctx->kev[0], ctx->stream));
@@ -1187,6 +1188,15 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
       const long long nouter = t.nout / ((long long)nb * nb * nb);
       KL(launch_normalize(d_z4, nouter, nb, 4, cplx ? 2 : 1, d_acc, (double)ng, d_vb, ctx->stream));
     }
+  }
+  if (tcomb && !ctx->defer) {  // a batch reads the flag once, after its last field
+    int* perr;
+    ST(host_staging(ctx, 64, (void**)&perr));
+    CU(cudaMemcpyAsync(perr, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    const int herr = *perr;
+    if (herr)
+      return fail(ctx, SBG_ERR_TIMEOUT, "a tensor-core combination kernel gave up waiting (code " + std::to_string(herr) + ")");
   }
   rec(ctx, 6);
   // ---- 3PCF finish + downloads ----
@@ -1557,7 +1567,7 @@ sbg_status sbg_projected_batch(sbg_context* ctx, const sbg_field2d* fields, int 
   CU(cudaMemcpyAsync(perr, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   finish(SBG_OK);
   if (*perr)
-    return fail(ctx, SBG_ERR_TIMEOUT, "tensor-core 4PCF kernel gave up waiting (code " + std::to_string(*perr) + ")");
+    return fail(ctx, SBG_ERR_TIMEOUT, "a tensor-core combination kernel gave up waiting (code " + std::to_string(*perr) + ")");
   for (int k = 0; k < kStages; ++k) ctx->timings[k] = acc[k];
   ctx->last_launches = nl;
   ctx->contraction_ms = kms;

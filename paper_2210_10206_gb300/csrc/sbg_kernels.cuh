@@ -80,6 +80,17 @@ cudaError_t launch_tc4(const float2* astore, void* bimg, const BGroup* bgroups, 
                        cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr, int tf32 = 0,
                        unsigned long long wait_ns = 1000000000ull, int stall = 0);
 
+// Tensor-core (tcgen05) version of launch_gram3 (sbg_gram_tc.cu): the same
+// S[b1][b2] (b1 <= b2, complex double, accumulated) from split-BF16 (tf32 = 0)
+// or split-TF32 (tf32 = 1) products with FP32 accumulation in tensor memory
+// over ranges of points and FP64 across ranges and CTAs.  nb <= 20, ng a
+// multiple of 64.  *err is set (never cleared) if a bounded wait (wait_ns of
+// the GPU's global timer) expired; stall != 0 withholds its MMA issuer (a
+// host-side test of the timeout path).
+cudaError_t launch_gram_tc(const float2* a, long long ng, int nb, const float* delta, double* S, int nsingle,
+                           int single0, int tf32, int* err, int nsm, unsigned long long wait_ns, int stall,
+                           cudaStream_t st);
+
 // ---- finalisation ----
 // zeta[o] = sum_{e in [ptr[o], ptr[o+1])} coef[e] * T[idx[e]] (idx < 0: conj of T[-idx-1]).
 cudaError_t launch_couple(const double* T, int complex_t, const int* ptr, const int* idx, const double* coef,

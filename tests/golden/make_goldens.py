@@ -7,6 +7,7 @@ paper_2210_10206_gb300.synth; nothing here touches the CUDA path.  Run offline
 
     python tests/golden/make_goldens.py full256      # even and odd 4PCF entries
     python tests/golden/make_goldens.py full512_3pcf # 3PCF entries, l = 1..10
+    python tests/golden/make_goldens.py batch64      # entries of every batch field
 
 Outputs (JSON, one per set) record the workload, the field's fingerprint (sum
 and sum of squares of the float32 field in float64, so a test can tell that it
@@ -17,6 +18,10 @@ regenerated the same input) and the entries with their oracle values:
                       part), bins drawn from {0, 4, 9} of 10 linear bins 2..32
   full512_3pcf.json : zeta_l^{b1 b2} of Eq. alm_to_zeta_clean for l up to 10,
                       20 linear bins 2..62
+  batch64_projected.json : for each of the 64 fields of the projected batch
+                      (128^2 .. 1024^2, mmax 10, 10 log bins 2..N/8) four
+                      zeta_m^{b1 b2} (Eq. proj_3pcf_coeff) and five
+                      zeta_{m1 m2}^{b1 b2 b3} (Eq. proj_4pcf_coeff) entries
 """
 import json
 import os
@@ -79,5 +84,27 @@ def full512_3pcf():
         json.dump(out, fh, indent=1)
 
 
+# batch entries: zeta3 (m, b1, b2) and zeta4 ((m1, m2), b1, b2, b3), |m1 + m2| <= 10
+BATCH_Z3 = [(0, 2, 7), (3, 5, 5), (10, 1, 9), (7, 8, 0)]
+BATCH_Z4 = [((1, 2), 2, 5, 8), ((-3, 5), 4, 4, 9), ((10, -10), 1, 6, 6), ((0, 0), 9, 9, 9), ((7, 3), 0, 3, 9)]
+
+
+def batch64():
+    out = {"workload": "batch64", "mmax": 10, "nbins": 10,
+           "source": "oracle.sarabande_oracle.zeta_projected_entries (FP64, numpy FFT)",
+           "z3_entries": [list(e) for e in BATCH_Z3], "z4_entries": [[list(e[0]), *e[1:]] for e in BATCH_Z4],
+           "fields": []}
+    for j in range(64):
+        f, edges = synth.batch_member(j)
+        delta, _ = O.preprocess(f.astype(np.float64))
+        t = time.time()
+        z3, z4 = O.zeta_projected_entries(delta, edges, BATCH_Z3, BATCH_Z4)
+        out["fields"].append({"index": j, "shape": list(f.shape), "field": fingerprint(f),
+                              "z3": [[v.real, v.imag] for v in z3], "z4": [[v.real, v.imag] for v in z4]})
+        print(j, f.shape, f"{time.time() - t:.1f}s", flush=True)
+    with open(os.path.join(HERE, "batch64_projected.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+
+
 if __name__ == "__main__":
-    {"full256": full256, "full512_3pcf": full512_3pcf}[sys.argv[1]]()
+    {"full256": full256, "full512_3pcf": full512_3pcf, "batch64": batch64}[sys.argv[1]]()

@@ -11,7 +11,13 @@ fields of uneven sizes, against the FP64 oracle.
   recomputed one by one by the oracle; the symmetries zeta3^{b2 b1} =
   conj zeta3^{b1 b2} and zeta4_{-m1,-m2} = conj zeta4_{m1,m2} are checked on
   every tensor.
+- The whole 64-field batch in one call (split BF16 and FP32): every field's
+  stored oracle entries (tests/golden/batch64_projected.json, written by
+  tests/golden/make_goldens.py from the FP64 oracle alone) are compared.
 Tolerance per output tensor: 1e-5 (FP32) / 1e-4 (split-BF16) of max |zeta|."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -129,3 +135,32 @@ def test_workload_batch_symmetries(workload_batch):
         assert np.abs(g4 - flipped).max() <= 1e-4 * s4
         f3 = _cplx(res["fp32"][i][1])
         assert np.abs(g4 - f3).max() <= 1e-4 * np.abs(f3).max(), f.shape
+
+
+def test_whole_64_field_batch_against_goldens(sbgm):
+    sbg = sbgm
+    g = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batch64_projected.json")))
+    members = [synth.batch_member(j) for j in range(64)]
+    fields = [f for f, _ in members]
+    edges = [e for _, e in members]
+    for f, gf in zip(fields, g["fields"]):
+        x = f.astype(np.float64)
+        assert list(f.shape) == gf["shape"]
+        assert abs((x * x).sum() - gf["field"]["sumsq"]) <= 1e-9 * gf["field"]["sumsq"]
+    ctx = sbg.Context(0)
+    for name, p in (("bf16x3", sbg.SBG_PREC_BF16X3), ("fp32", sbg.SBG_PREC_FP32)):
+        outs = ctx.projected_batch(fields, edges, 10, 10, prec=p)
+        worst = 0.0
+        for gf, (z3, z4) in zip(g["fields"], outs):
+            g3, g4 = _cplx(z3), _cplx(z4)
+            s3, s4 = np.abs(g3).max(), np.abs(g4).max()
+            for (m, b1, b2), (re, im) in zip(g["z3_entries"], gf["z3"]):
+                err = abs(g3[m, b1, b2] - complex(re, im)) / s3
+                worst = max(worst, err)
+                assert err <= TOL[name], (gf["index"], name, m, b1, b2)
+            for ((m1, m2), b1, b2, b3), (re, im) in zip(g["z4_entries"], gf["z4"]):
+                err = abs(g4[m1 + 10, m2 + 10, b1, b2, b3] - complex(re, im)) / s4
+                worst = max(worst, err)
+                assert err <= TOL[name], (gf["index"], name, m1, m2, b1, b2, b3)
+        print(f"{name}: 64 fields x 9 golden entries, worst |err|/max|zeta| {worst:.2e}")
+    ctx.close()

@@ -1,9 +1,18 @@
 """Parity at the benchmark's full size, in the launch configuration bench.py
 times (256^3 float32 lognormal field, 10 linear bins 2..32, lmax 4, 4PCF only,
-mean subtracted, field resident on the device; FP32, split BF16 and split TF32):
-sampled zeta_Lambda^{b1 b2 b3}
-entries are recomputed one by one by the FP64 oracle; the whole tensor is
-checked for the symmetries that hold at any size."""
+mean subtracted, field resident on the device; FP32, split BF16 and split TF32).
+
+Expected values are the stored oracle goldens of tests/golden/full256_4pcf.json
+(written by tests/golden/make_goldens.py, which calls only the FP64 oracle):
+one entry for each of the 42 even Lambda (Eq. mu, Sec. 2.3; Algorithm 6) and
+each of the 23 odd Lambda (E(Lambda) = -1), bins drawn from {0, 4, 9}, so every
+l = 3 and l = 4 leg and every m3 column block of the tile plan is touched.  The
+whole tensor is also checked for the symmetries that hold at any size.
+Tolerance per coefficient: 1e-5 (FP32, split TF32) / 1e-4 (split BF16) of
+max |zeta| of the tensor."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -12,8 +21,8 @@ from paper_2210_10206_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-# (Lambda, b1, b2, b3) sampled across l-orders, bin ranges and diagonals
-ENTRIES = [((0, 0, 0), 1, 4, 8), ((1, 1, 0), 0, 2, 9), ((2, 1, 1), 3, 3, 6)]
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "full256_4pcf.json")
+TOLS = (("fp32", 1e-5), ("bf16x3", 1e-4), ("tf32x3", 1e-5))
 
 
 @pytest.fixture(scope="module")
@@ -23,40 +32,50 @@ def full256():
         pytest.skip("no GPU")
     from paper_2210_10206_gb300 import build, sbg
     build.build()
+    g = json.load(open(GOLDEN))
     f = synth.workload_field("full256")
+    x = f.astype(np.float64)
+    # the regenerated input is the one the goldens were computed on
+    assert abs(x.sum() - g["field"]["sum"]) <= 1e-9 * np.sqrt(x.size * g["field"]["sumsq"])
+    assert abs((x * x).sum() - g["field"]["sumsq"]) <= 1e-9 * g["field"]["sumsq"]
     edges = synth.WORKLOADS["full256"]["edges"]
+    assert np.allclose(edges, g["edges"], rtol=0, atol=0)
     ctx = sbg.Context(0)
     d = torch.from_numpy(f).cuda()
     out = {}
     for name, prec in (("fp32", sbg.SBG_PREC_FP32), ("bf16x3", sbg.SBG_PREC_BF16X3),
                        ("tf32x3", sbg.SBG_PREC_TF32X3)):
         _, z4 = ctx.full(d, edges, lmax4=4, prec=prec)
-        out[name] = z4
+        zo = ctx.full_odd(d, edges, 4, prec=prec)
+        out[name] = (z4, zo)
     ctx.close()
-    delta, _ = O.preprocess(f.astype(np.float64))
-    ref = O.zeta4_full_entries(delta, edges, ENTRIES)
-    return out, ref
+    return out, g
 
 
-def test_sampled_entries_match_oracle(full256):
-    out, ref = full256
-    lams = O.lambda_list(4)
-    for name, tol in (("fp32", 1e-5), ("bf16x3", 1e-4), ("tf32x3", 1e-5)):
-        z4 = out[name]
-        scale = np.abs(z4).max()
-        for (lam, b1, b2, b3), r in zip(ENTRIES, ref):
-            got = z4[lams.index(lam), b1, b2, b3]
-            assert abs(got - r) <= tol * scale, (name, lam, b1, b2, b3, got, r, scale)
+def test_every_lambda_matches_oracle_goldens(full256):
+    out, g = full256
+    lams, lams_odd = O.lambda_list(4), O.lambda_list_odd(4)
+    for name, tol in TOLS:
+        z4, zo = out[name]
+        for key, z, ll in (("even", z4, lams), ("odd", zo, lams_odd)):
+            scale = np.abs(z).max()
+            worst = 0.0
+            for e in g[key]:
+                got = z[ll.index(tuple(e["lambda"])), e["bins"][0], e["bins"][1], e["bins"][2]]
+                err = abs(got - e["value"]) / scale
+                worst = max(worst, err)
+                assert err <= tol, (name, key, e, got, scale)
+            print(f"{name} {key}: {len(g[key])} golden entries, worst |err|/max|zeta| {worst:.2e}")
 
 
 def test_permutation_symmetry_at_full_size(full256):
     out, _ = full256
     lams = O.lambda_list(4)
-    for name, tol in (("fp32", 1e-5), ("bf16x3", 1e-4), ("tf32x3", 1e-5)):
-        z4 = out[name]
+    for name, tol in TOLS:
+        z4 = out[name][0]
         scale = np.abs(z4).max()
         for i, (l1, l2, l3) in enumerate(lams):
             j = lams.index((l2, l1, l3))
             assert np.abs(z4[i] - np.transpose(z4[j], (1, 0, 2))).max() <= tol * scale
-        # split-BF16 and FP32 agree within the split-BF16 tolerance
-    assert np.abs(out["bf16x3"] - out["fp32"]).max() <= 1e-4 * np.abs(out["fp32"]).max()
+    # split-BF16 and FP32 agree within the split-BF16 tolerance
+    assert np.abs(out["bf16x3"][0] - out["fp32"][0]).max() <= 1e-4 * np.abs(out["fp32"][0]).max()

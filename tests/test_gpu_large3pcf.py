@@ -7,10 +7,14 @@ FP32 path).
   alm_to_zeta_clean with every m from its own kernel).
 - At the full 512^3 size, the l = 0 entries are checked against the closed
   form zeta_0^{b1 b2} = (1/4 pi) sum_x delta S_b1 S_b2 with S_b(x) =
-  sum_{r in b} delta(x + r) evaluated with a library FFT, and the whole
-  tensor against b1 <-> b2 symmetry.
+  sum_{r in b} delta(x + r) evaluated with a library FFT, entries with l = 1 ..
+  10 against the stored oracle goldens of tests/golden/full512_3pcf.json
+  (written by tests/golden/make_goldens.py from the FP64 oracle alone), and the
+  whole tensor against b1 <-> b2 symmetry.
 Tolerance: 1e-5 of max |zeta| per output tensor."""
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -74,6 +78,13 @@ def test_full_size_512_l0_closed_form_and_symmetry(sbgm):
     ctx.close()
     scale = np.abs(z3).max()
     assert np.abs(z3 - np.transpose(z3, (0, 2, 1))).max() <= TOL * scale
+    # l = 1 .. 10: stored oracle entries of the same field
+    g = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "full512_3pcf.json")))
+    x = f.astype(np.float64)
+    assert abs((x * x).sum() - g["field"]["sumsq"]) <= 1e-9 * g["field"]["sumsq"]
+    for e in g["entries"]:
+        got = z3[e["l"], e["bins"][0], e["bins"][1]]
+        assert abs(got - e["value"]) <= TOL * scale, (e, got, scale)
     # l = 0: S_b = correlation of delta with the 0/1 mask of bin b
     delta = f.astype(np.float64)
     delta -= delta.mean()

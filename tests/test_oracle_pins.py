@@ -673,3 +673,17 @@ def test_single_entry_oracles_match_full_tensors():
     e3 = [(0, 0, 0), (1, 2, 1), (2, 3, 3), (3, 0, 3), (4, 1, 2)]
     for (l, b1, b2), g in zip(e3, O.zeta3_full_entries(d, edges, e3)):
         assert abs(g - z3[l, b1, b2]) < 1e-12 * np.abs(z3).max()
+
+
+def test_projected_entry_oracle_matches_full_tensors():
+    d = RNG.normal(size=(24, 24))
+    edges = [0.5, 2.0, 3.5, 5.0, 7.5]
+    z3 = O.zeta3_projected(d, edges, 3)
+    z4 = O.zeta4_projected(d, edges, 3)
+    e3 = [(0, 1, 2), (3, 3, 0), (2, 2, 2)]
+    e4 = [((1, 2), 0, 1, 3), ((-3, 1), 2, 2, 0), ((3, -3), 1, 0, 1), ((0, 0), 3, 3, 3)]
+    g3, g4 = O.zeta_projected_entries(d, edges, e3, e4)
+    for (m, b1, b2), g in zip(e3, g3):
+        assert abs(g - z3[m, b1, b2]) < 1e-12 * np.abs(z3).max()
+    for ((m1, m2), b1, b2, b3), g in zip(e4, g4):
+        assert abs(g - z4[m1 + 3, m2 + 3, b1, b2, b3]) < 1e-12 * np.abs(z4).max()
