@@ -45,8 +45,10 @@ ALG_BIN_TRIPLES = 220
 #   full256_odd   the odd-parity 4PCF (sbg_full_odd) of the same field
 #   slices256     projected 3PCF + 4PCF of all 256 slices of that field
 #                 (sbg_projected_slices), 10 log bins 2..32, mmax 10
+#   full128_3pcf  128^3 full 3PCF, lmax 2, 20 linear bins 1..31 (a small case of the
+#                 512^3 3PCF's Gram: 20 bins per group, groups larger than L2)
 # The first call of a geometry also builds its plan (kernel spectra, tables).
-WORKLOADS = ("batch64", "full512_3pcf", "full256", "full256_odd", "slices256")
+WORKLOADS = ("batch64", "full512_3pcf", "full256", "full256_odd", "slices256", "full128_3pcf")
 
 
 def parse():
@@ -265,6 +267,46 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def cufft_compare(grid, conv_ms):
+    """cuFFT (through torch.fft), timed only as a comparison: the batched 3D
+    inverse C2C transforms of the convolution stage, one (l, m) group of 10
+    complex64 arrays at a time (125 transforms per field: 100 complex arrays and
+    25 pairs of real m = 0 arrays packed two per transform), with the spectral
+    product delta-hat * G as a separate elementwise pass, against this library's
+    convolution stage of the same field (product fused into the first pass, the
+    last pass writing the blocked coefficient store)."""
+    import torch
+    n = grid
+    x = torch.randn((NB, n, n, n), dtype=torch.complex64, device="cuda")
+    g = torch.randn_like(x)
+    dh = torch.randn((n, n, n), dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+
+    def group():
+        torch.mul(g, dh, out=x)
+        return torch.fft.ifftn(x, dim=(1, 2, 3), norm="forward", out=y)
+
+    for _ in range(3):
+        group()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record()
+    for _ in range(reps):
+        group()
+    e1.record()
+    torch.cuda.synchronize()
+    per_group = e0.elapsed_time(e1) / reps
+    transforms = 125
+    cufft_ms = per_group * transforms / NB
+    del x, g, dh, y
+    torch.cuda.empty_cache()
+    return {"what": "cuFFT batched inverse 3D C2C (torch.fft.ifftn) + separate product pass, 10 arrays per call, "
+                    f"scaled to the field's {transforms} transforms",
+            "cufft_ms_per_field": cufft_ms, "this_library_convolution_ms": conv_ms,
+            "speedup_over_cufft": cufft_ms / conv_ms if conv_ms > 0 else None}
+
+
 def run_gpu(args):
     import torch
     from paper_2210_10206_gb300 import build, sbg
@@ -395,6 +437,7 @@ def run_gpu(args):
                                    "roofline": {"bound": obound, "peak": opeak, "frac": oach / opeak,
                                                 "peak_source": osrc},
                                    "headline_speedup_over_it": oms / step_ms})
+        out["compare_cufft"] = cufft_compare(args.grid, conv_ms)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = oracle_sample(field, edges)
         out["cpu_baseline"].pop("seconds_per_field", None)
@@ -423,6 +466,11 @@ def run_workload(args):
         d = torch.from_numpy(synth.workload_field("full256")).cuda()
         e = list(synth.edges_log(2.0, 32.0, 10))
         call = lambda: ctx.projected_slices(d, e, 10, prec=prec)
+    elif args.workload == "full128_3pcf":
+        w = synth.WORKLOADS["full128"]
+        d = torch.from_numpy(synth.workload_field("full128")).cuda()
+        e = list(np.linspace(1.0, 31.0, 21))
+        call = lambda: ctx.full(d, e, lmax3=2, prec=prec)
     elif args.workload == "full512_3pcf":
         w = synth.WORKLOADS["full512"]
         d = torch.from_numpy(synth.workload_field("full512")).cuda()

@@ -20,23 +20,31 @@
 // the delta values once.
 //
 // Roles of a CTA (one per SM, each on a contiguous range of K-blocks):
-//   warp 0      loader: one thread issues the K-block's bulk copies (one per
-//               bin in the [bin][x] layout of a group buffer, one per 32-point
-//               block in the blocked coefficient store) and the delta copy
-//               into a raw stage, completing on the stage's mbarrier;
+//   warp 0      loader: one thread issues the K-block's copies into a raw
+//               stage, completing on the stage's mbarrier: one 2D TMA tile
+//               (every bin's points of the K-block) from a group buffer in the
+//               [bin][x] layout, or one bulk copy per 32-point block of the
+//               blocked coefficient store, and one bulk copy of delta;
 //   warp 1      MMA issuer: 4 tcgen05.mma (kind::f16 or kind::tf32, both
 //               operands in shared memory) per K-block into one of two TMEM
 //               accumulators (ranges of kFlush K-blocks alternate between them);
-//   warps 2-9   producers: form the bf16 / tf32 hi and lo rows of W and U from
-//               a raw stage into an operand stage (128-byte swizzled K-major
-//               tiles, rows past 2R stay zero);
+//   warps 2-9   producers, in 4 groups of 2 warps: group g forms the K-blocks
+//               k = g (mod 4) of the CTA, the bf16 / tf32 hi and lo rows of W
+//               and U from a raw stage into operand stage g (128-byte swizzled
+//               K-major tiles), so every stage is refilled by one group in
+//               order and four K-blocks are formed at once;
 //   warps 10-13 fold: per finished range, read the accumulator (one TMEM lane
 //               quarter each), sum its quadrants in FP32 and add them to an FP64
 //               accumulator in shared memory; at the end add this CTA's S^{b1 b2}
 //               to the output with FP64 atomics.
 // Every wait is bounded (wait_ns of %globaltimer); on expiry the CTA records an
 // error code, drains the copies and MMAs it issued and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
+#include <atomic>
+#include <cstring>
 
 #include "sbg_kernels.cuh"
 #include "sbg_tcgen05.cuh"
@@ -60,13 +68,19 @@ constexpr int kGLoadWarp = 0;
 constexpr int kGMmaWarp = 1;
 constexpr int kGProd0 = 2;
 constexpr int kGProdWarps = 8;
+constexpr int kGGroups = 4;                    // producer groups = operand stages
+constexpr int kGGroupWarps = kGProdWarps / kGGroups;
 constexpr int kGFold0 = 10;
 constexpr int kGFoldThreads = 128;
 constexpr int kGMaxNb = 20;
 constexpr int kGMaxR = 2 * kGMaxNb;            // real rows per operand half
-constexpr int kGRaw = 6;                       // raw stages
-constexpr int kGOps = 3;                       // operand stages
-constexpr int kGTile = 128 * 128;              // one operand tile: up to 128 rows of 128 bytes
+constexpr int kGRaw = 2 * kGGroups;            // raw stages, two per producer group
+constexpr int kGOps = kGGroups;                // operand stages, one per producer group
+// One operand tile holds 2R <= 80 rows of 128 bytes; A (M = 128) is followed by
+// B, so the MMA's reads of A rows 80..127 fall on B rows (their products land
+// in accumulator rows the fold never reads), and B rows past 2R (read when N
+// is padded to 16) were zeroed at the start and are never written.
+constexpr int kGTile = 2 * kGMaxR * 128;
 constexpr int kGDeltaOff = kGMaxNb * 64 * 8;   // delta within a raw stage
 constexpr int kGRawBytes = kGDeltaOff + 256;
 constexpr int kGScratch = 2 * kGMaxR * 2 * kGMaxR * 4;  // FP32 rows of one folded range [2R][2R]
@@ -131,9 +145,20 @@ __device__ __forceinline__ void store8(uint8_t* tile, int row, int q, const uint
   }
 }
 
+// 2D TMA tile (box of the tensor map) at element coordinates (x, y) into
+// shared memory, completing as transaction bytes on `bar`
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar))
+      : "memory");
+}
+
 template <bool TF>
 __global__ void __launch_bounds__(kGThreads, 1)
-gram_tc_kernel(const float* __restrict__ a, long long ng, int nb, const float* __restrict__ delta,
+gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict__ a, long long ng, int nb,
+               const float* __restrict__ delta,
                double* __restrict__ S, int nsingle, int single0, int* err_flag, unsigned long long wait_ns,
                int stall) {
   using C = GramCfg<TF>;
@@ -171,10 +196,10 @@ gram_tc_kernel(const float* __restrict__ a, long long ng, int nb, const float* _
   if (tid == 0) {
     for (int i = 0; i < kGRaw; ++i) {
       mbar_init(&raw_full[i], 1);
-      mbar_init(&raw_empty[i], kGProdWarps);
+      mbar_init(&raw_empty[i], kGGroupWarps);
     }
     for (int i = 0; i < kGOps; ++i) {
-      mbar_init(&op_full[i], kGProdWarps);
+      mbar_init(&op_full[i], kGGroupWarps);
       mbar_init(&op_empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -201,8 +226,11 @@ gram_tc_kernel(const float* __restrict__ a, long long ng, int nb, const float* _
       uint32_t issued[kGRaw] = {};
       const uint32_t bytes = (uint32_t)(nb * kPts * 8 + kPts * 4);
       for (int k = 0; k < nk; ++k) {
-        const int rs = k % kGRaw;
-        if (!mbar_wait(&raw_empty[rs], ((k / kGRaw) & 1) ^ 1, err, 51, wait_ns)) break;
+        // K-block k belongs to producer group k % 4; its j-th K-block uses raw
+        // stage g + 4 (j mod 2)
+        const int j = k / kGGroups;
+        const int rs = k % kGGroups + kGGroups * (j & 1);
+        if (!mbar_wait(&raw_empty[rs], ((j >> 1) & 1) ^ 1, err, 51, wait_ns)) break;
         ++issued[rs];
         uint8_t* st = raw + rs * kGRawBytes;
         const long long x0 = (kb0 + k) * kPts;
@@ -214,8 +242,8 @@ gram_tc_kernel(const float* __restrict__ a, long long ng, int nb, const float* _
             bulk_g2s(st + j * nb * 256, a + (xb * nsingle + single0) * 64, (uint32_t)nb * 256, &raw_full[rs]);
           }
         } else {
-          for (int b = 0; b < nb; ++b)
-            bulk_g2s(st + b * kPts * 8, a + 2 * ((long long)b * ng + x0), (uint32_t)kPts * 8, &raw_full[rs]);
+          // rows b = 0 .. nb-1, floats 2 x0 .. 2 x0 + 2 kPts - 1 (x0 < 2^30 / 2 for the grids here)
+          tma_load_2d(st, &tmap, (int)(2 * x0), 0, &raw_full[rs]);
         }
         bulk_g2s(st + kGDeltaOff, delta + x0, (uint32_t)kPts * 4, &raw_full[rs]);
       }
@@ -236,7 +264,7 @@ gram_tc_kernel(const float* __restrict__ a, long long ng, int nb, const float* _
         const int os = k % kGOps;
         const int r = k / kFlush, buf = r & 1;
         if (k % kFlush == 0 && r >= 2 && !mbar_wait(&d_free[buf], ((r >> 1) - 1) & 1, err, 53, wait_ns)) break;
-        if (!mbar_wait(&op_full[os], (k / kGOps) & 1, err, 54, wait_ns)) break;
+        if (!mbar_wait(&op_full[os], (k / kGOps) & 1, err, 54, wait_ns)) break;  // stage os = group os
         tc_fence_after();
         const uint64_t ad = sdesc(su32(ops + os * 2 * kGTile));
         const uint64_t bd = sdesc(su32(ops + os * 2 * kGTile + kGTile));
@@ -253,18 +281,20 @@ gram_tc_kernel(const float* __restrict__ a, long long ng, int nb, const float* _
     }
   } else if (warp < kGFold0) {
     // ------------------------------------------------------------- producers --
-    const int ptid = tid - kGProd0 * 32;
+    const int grp = (warp - kGProd0) / kGGroupWarps;         // producer group = operand stage
+    const int ptid = tid - (kGProd0 + grp * kGGroupWarps) * 32;  // thread within the group
     const int items = nb * (kPts / 8);
-    for (int k = 0; k < nk; ++k) {
-      const int rs = k % kGRaw, os = k % kGOps;
-      if (!warp_wait(&raw_full[rs], (k / kGRaw) & 1, err, 56, wait_ns) ||
-          !warp_wait(&op_empty[os], ((k / kGOps) & 1) ^ 1, err, 57, wait_ns))
+    const int os = grp;
+    for (int j = 0; j * kGGroups + grp < nk; ++j) {
+      const int rs = grp + kGGroups * (j & 1);
+      if (!warp_wait(&raw_full[rs], (j >> 1) & 1, err, 56, wait_ns) ||
+          !warp_wait(&op_empty[os], (j & 1) ^ 1, err, 57, wait_ns))
         break;
       tc_fence_after();
       const uint8_t* st = raw + rs * kGRawBytes;
       uint8_t* at = ops + os * 2 * kGTile;  // A = [W_hi; W_lo]
       uint8_t* bt = at + kGTile;            // B = [U_hi | U_lo] (rows of the MMA's N)
-      for (int it = ptid; it < items; it += kGProdWarps * 32) {
+      for (int it = ptid; it < items; it += kGGroupWarps * 32) {
         const int b = it / (kPts / 8), q = it % (kPts / 8);
         float re[8], im[8], dl[8];
         if (nsingle) {
@@ -370,15 +400,50 @@ gram_tc_kernel(const float* __restrict__ a, long long ng, int nb, const float* _
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kGTmemCols));
 }
 
+// cuTensorMapEncodeTiled of the driver, looked up once through the runtime
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::atomic<PFN_cuTensorMapEncodeTiled_v12000> fn{nullptr};
+  PFN_cuTensorMapEncodeTiled_v12000 f = fn.load();
+  if (!f) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    f = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    fn.store(f);
+  }
+  return f;
+}
+
 template <bool TF>
 cudaError_t launch_gram_tc_t(const float2* a, long long ng, int nb, const float* delta, double* S, int nsingle,
                              int single0, int* err, int nsm, unsigned long long wait_ns, int stall,
                              cudaStream_t st) {
   cudaError_t e = ensure_smem_attr<gram_tc_kernel<TF>>(kGSmem);
   if (e != cudaSuccess) return e;
-  const long long nkb = ng / GramCfg<TF>::kPts;
+  constexpr int kPts = GramCfg<TF>::kPts;
+  const long long nkb = ng / kPts;
   const int grid = (int)std::min<long long>(nsm, nkb);
-  gram_tc_kernel<TF><<<grid, kGThreads, kGSmem, st>>>((const float*)a, ng, nb, delta, S, nsingle, single0, err,
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof map);
+  if (!nsingle) {
+    // group buffer [nb][ng] float2 as a 2D float tensor: rows = bins (stride
+    // 8 ng bytes), a box of every row's 2 kPts floats per K-block
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc || 2 * ng >= (1LL << 31)) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 * ng), (cuuint64_t)nb};
+    const cuuint64_t strides[1] = {(cuuint64_t)ng * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * kPts), (cuuint32_t)nb};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)a, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  gram_tc_kernel<TF><<<grid, kGThreads, kGSmem, st>>>(map, (const float*)a, ng, nb, delta, S, nsingle, single0, err,
                                                        wait_ns, stall);
   return cudaGetLastError();
 }
