@@ -15,6 +15,7 @@
 #include <map>
 #include <queue>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <unordered_map>
 #include <vector>
@@ -894,16 +895,26 @@ sbg_status fft3(sbg_context* ctx, int n, int sign, int first_load, const void* i
   return SBG_OK;
 }
 
+// nfld > 1: a slab of fields, batch = nfld x arrays per field; `shared` is per
+// field (stride shared_stride) and the blocked store's points of field f start
+// at f x bstride.
 sbg_status fft2(sbg_context* ctx, int n, int sign, int first_load, const void* in, float2* out, const float2* mul,
                 const float2* shared, int batch, long long bstride, const float2* tw, float2* final_out = nullptr,
-                int nsingle = 0, int single0 = 0, int npack = 0) {
+                int nsingle = 0, int single0 = 0, int npack = 0, int nfld = 1, long long shared_stride = 0) {
   FftPass p{};
   p.twiddle = tw;
   p.batch = batch;
   p.bstride = bstride;
   p.sign = sign;
+  if (nfld > 1) {
+    if (batch % nfld) return fail(ctx, SBG_ERR_INTERNAL, "fft2 slab batch");
+    p.nb_per_field = batch / nfld;
+    p.shared_stride = shared_stride;
+    p.field_points = bstride;
+  }
   if (npack > 0) {  // as in fft3
-    if (first_load != LOAD_MUL || !final_out || batch != (npack + 1) / 2) return fail(ctx, SBG_ERR_INTERNAL, "fft2 packing");
+    if (first_load != LOAD_MUL || !final_out || batch != nfld * ((npack + 1) / 2))
+      return fail(ctx, SBG_ERR_INTERNAL, "fft2 packing");
     first_load = LOAD_MUL2;
     p.npack = npack;
   }
@@ -1240,6 +1251,259 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
   return SBG_OK;
 }
 
+// ------------------------------------------------------------------ slabs --
+// Projected 3PCF / 4PCF of nfld fields of one shape, dtype and bin set, measured
+// together (a slab): their points follow each other in every buffer, and every
+// stage of the path (preprocessing, delta-hat, convolutions, Grams, the 4PCF
+// contraction, couplings, finalisation) is one launch over all of them, the
+// fields being one more batch dimension (Secs. 2.2 and 2.4, Algorithms 2, 4,
+// 7, 8 per field, exactly as measure() computes them one field at a time).
+// Outputs are staged in pinned slot `slot` (layout: z3 of every field, then z4
+// of every field) and copied to the fields' arrays by slab_copy_out once the
+// stream has passed ev_done.
+struct SlabOut {
+  const sbg_field2d* fields = nullptr;
+  int nfld = 0;
+  size_t z3b = 0, z4b = 0;  // bytes per field
+  size_t off4 = 0;          // z4 block within the slot
+  unsigned char* host = nullptr;
+};
+
+sbg_status measure_slab(sbg_context* ctx, const sbg_field2d* fields, int nfld, int n, const double* edges, int nb,
+                        int mmax, sbg_precision prec, unsigned flags, unsigned char* hslot, SlabOut* out) {
+  const bool do3 = flags & SBG_3PCF, do4 = flags & SBG_4PCF;
+  const long long ng = (long long)n * n;
+  const int ngroups = mmax + 1;
+  const int ngroups4 = do4 ? mmax + 1 : 0;
+  const std::vector<double> e2 = snap_e2(edges, nb);
+  const std::vector<double> vb = cell_counts(n, 2, e2, nb);
+  if (flags & SBG_NORMALIZED)
+    for (int b = 0; b < nb; ++b)
+      if (vb[b] == 0.0) return fail(ctx, SBG_ERR_EMPTY_BIN, "bin " + std::to_string(b) + " holds no cell");
+  const sbg_dtype dtype = fields[0].dtype;
+  const size_t esz = dtype == SBG_F64 ? 8 : 4;
+  const bool on_dev = flags & SBG_FIELD_ON_DEVICE;
+  cudaStream_t st = ctx->stream;
+
+  // ---- inputs: the fields one after another (device fields that already are
+  // contiguous, e.g. slices of a cube, are read in place) ----
+  rec(ctx, 0);
+  const void* d_in = nullptr;
+  bool contiguous = on_dev;
+  for (int i = 1; i < nfld && contiguous; ++i)
+    contiguous = (const unsigned char*)fields[i].field == (const unsigned char*)fields[0].field + (size_t)i * ng * esz;
+  if (contiguous) {
+    d_in = fields[0].field;
+  } else {
+    void* stg;
+    ST(buf(ctx, "stage", (size_t)nfld * ng * esz, &stg));
+    for (int i = 0; i < nfld; ++i)
+      CU(cudaMemcpyAsync((unsigned char*)stg + (size_t)i * ng * esz, fields[i].field, ng * esz,
+                         on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    d_in = stg;
+  }
+  float* d_delta;
+  float2 *d_dhat, *d_tw;
+  double *d_acc, *d_e2, *d_vb;
+  ST(buf(ctx, "delta", (size_t)nfld * ng * 4, (void**)&d_delta));
+  ST(buf(ctx, "dhat", (size_t)nfld * ng * 8, (void**)&d_dhat));
+  ST(buf(ctx, "acc", (size_t)std::max(64, 16 * nfld), (void**)&d_acc));
+  ST(buf(ctx, "tw", n * 8, (void**)&d_tw));
+  ST(buf(ctx, "e2", (kMaxBins + 1) * 8, (void**)&d_e2));
+  ST(buf(ctx, "vb", kMaxBins * 8, (void**)&d_vb));
+  {
+    const std::vector<float2> tw = twiddles(n);
+    CU(cudaMemcpyAsync(d_tw, tw.data(), n * 8, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(d_e2, e2.data(), (nb + 1) * 8, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(d_vb, vb.data(), nb * 8, cudaMemcpyHostToDevice, st));
+  }
+  CU(cudaMemsetAsync(d_acc, 0, (size_t)16 * nfld, st));
+  KL(launch_sum(d_in, dtype == SBG_F64, ng, d_acc, st, nfld));
+  KL(launch_convert(d_in, dtype == SBG_F64, ng, d_acc, (flags & SBG_SUBTRACT_MEAN) ? 1 : 0, d_delta, st, nfld));
+  rec(ctx, 1);
+  // ---- delta-hat of every field ----
+  ST(fft2(ctx, n, -1, LOAD_REAL, d_delta, d_dhat, nullptr, nullptr, nfld, ng, d_tw));
+  rec(ctx, 2);
+  // ---- kernel spectra (shared by the fields: one shape, one bin set) ----
+  char keyb[512];
+  snprintf(keyb, sizeof keyb, "%d/%d/%d/%d", 2, n, nb, mmax);
+  std::string key(keyb);
+  for (int i = 0; i <= nb; ++i) key += "/" + std::to_string(e2[i]);
+  const size_t gbytes = (size_t)ngroups * nb * ng * 8;
+  const double inv_ng = 1.0 / (double)ng;
+  auto gen_group = [&](int g, float2* dst) -> sbg_status {
+    CU(cudaMemsetAsync(dst, 0, (size_t)nb * ng * 8, st));
+    KL(launch_kgen2d(n, g, d_e2, nb, inv_ng, dst, st));
+    ST(fft2(ctx, n, +1, LOAD_COMPLEX, dst, dst, nullptr, nullptr, nb, ng, d_tw));
+    return SBG_OK;
+  };
+  bool cached = ctx->gcached && ctx->gkey == key;
+  if (!cached) {
+    ctx->gcached = false;
+    if (dev_alloc(ctx, ctx->gcache, gbytes) == SBG_OK) {
+      for (int g = 0; g < ngroups; ++g) ST(gen_group(g, (float2*)ctx->gcache.p + (size_t)g * nb * ng));
+      ctx->gcached = true;
+      ctx->gkey = key;
+      cached = true;
+    } else {
+      ctx->err.clear();
+    }
+  }
+  rec(ctx, 3);
+  // ---- convolutions + 3PCF Grams of every field ----
+  const int nsingle = ngroups4 * nb;
+  const long long npts = (long long)nfld * ng;  // points of the slab
+  float2* d_astore = nullptr;
+  if (do4) ST(buf(ctx, "astore", (size_t)nsingle * npts * 8, (void**)&d_astore));
+  float2* d_group;
+  ST(buf(ctx, "group", (size_t)nfld * nb * ng * 8, (void**)&d_group));
+  float2* d_gtmp = nullptr;
+  if (!cached) ST(buf(ctx, "gtmp", (size_t)nb * ng * 8, (void**)&d_gtmp));
+  const int ngroups3 = do3 ? mmax + 1 : 0;
+  const long long s_stride = (long long)std::max(ngroups3, 1) * nb * nb * 2;  // doubles of S per field
+  double* d_S = nullptr;
+  if (do3) {
+    ST(buf(ctx, "S", (size_t)nfld * s_stride * 8, (void**)&d_S));
+    CU(cudaMemsetAsync(d_S, 0, (size_t)nfld * s_stride * 8, st));
+  }
+  const bool tcomb = prec != SBG_PREC_FP32;
+  const int tf32 = prec == SBG_PREC_TF32X3 ? 1 : 0;
+  int* d_err = nullptr;
+  if (tcomb) ST(buf(ctx, "err", 16, (void**)&d_err));  // cleared by the caller once per batch
+  for (int g = 0; g < ngroups; ++g) {
+    const float2* G;
+    if (cached) {
+      G = (const float2*)ctx->gcache.p + (size_t)g * nb * ng;
+    } else {
+      ST(gen_group(g, d_gtmp));
+      G = d_gtmp;
+    }
+    const bool stored = g < ngroups4;
+    float2* fin = stored ? d_astore : nullptr;
+    const int npack = stored && g == 0 ? nb : 0;  // m = 0: real coefficients, two bins per transform
+    const int nbatch = npack ? (nb + 1) / 2 : nb;
+    ST(fft2(ctx, n, +1, LOAD_MUL, nullptr, d_group, G, d_dhat, nfld * nbatch, ng, d_tw, fin, nsingle, g * nb, npack,
+            nfld, ng));
+    if (do3 && g < ngroups3) {
+      double* Sg = d_S + (size_t)g * nb * nb * 2;
+      const float2* src = stored ? d_astore : d_group;
+      const int ns = stored ? nsingle : 0, s0 = stored ? g * nb : 0;
+      if (tcomb)
+        KL(launch_gram_tc(src, ng, nb, d_delta, Sg, ns, s0, tf32, d_err, ctx->nsm, ctx->wait_ns, ctx->stall, st, nfld,
+                          s_stride));
+      else
+        KL(launch_gram3(src, ng, nb, d_delta, Sg, ns, s0, st, nfld, s_stride));
+    }
+  }
+  rec(ctx, 4);
+  rec(ctx, 5);
+  // ---- 4PCF of every field ----
+  double* d_z4 = nullptr;
+  Tables4* t4 = nullptr;
+  if (do4) {
+    ST(ensure_tables4(ctx, 2, nb, mmax, tcomb, false));
+    t4 = ctx->t4;
+    Tables4& t = *t4;
+    const long long tstride = std::max<long long>(t.tcount, 1);  // T entries per field (complex)
+    double* d_T;
+    ST(buf(ctx, "T", (size_t)nfld * tstride * 16, (void**)&d_T));
+    CU(cudaMemsetAsync(d_T, 0, (size_t)nfld * tstride * 16, st));
+    if (tcomb) {
+      const int ntl = (int)t.tiles[0].size();
+      const long long fkb = ng / 32;  // K-blocks of one field
+      // x-splits per field: a power of two dividing its K-blocks, for the best
+      // spread of the units over the CTAs
+      int spf = 1;
+      double best_eff = 0.0;
+      for (int k = 1; k <= 16 && k <= fkb; k *= 2) {
+        const long long units = (long long)ntl * nfld * k;
+        const long long rounds = (units + ctx->nsm - 1) / ctx->nsm;
+        const double eff = (double)units / (double)(rounds * ctx->nsm);
+        if (eff > best_eff + 0.02) { best_eff = eff; spf = k; }
+      }
+      const int nsplit = nfld * spf;
+      const long long units = (long long)ntl * nsplit;
+      const long long rounds = (units + ctx->nsm - 1) / ctx->nsm;
+      const long long nk_unit = fkb / spf;
+      const long long epochs = rounds * ((nk_unit + kTcEpoch - 1) / kTcEpoch) + 4;
+      int* d_cnt;
+      ST(buf(ctx, "tccnt", (size_t)epochs * 4, (void**)&d_cnt));
+      CU(cudaMemsetAsync(d_cnt, 0, (size_t)epochs * 4, st));
+      void* d_bimg;
+      ST(buf(ctx, "bimg", (size_t)(npts / 32) * (size_t)t.img_stride * (tf32 ? 2 : 1), &d_bimg));
+      ctx->nlaunch += 1;  // bimage_kernel
+      KL(launch_tc4(d_astore, d_bimg, (const BGroup*)t.d_bgroups.p, (int)t.bgroups.size(), t.chunks_per_kb,
+                    t.img_stride, d_delta, npts, (const Tile4*)t.d_tiles[0].p, ntl, (const Row4*)t.d_rows.p,
+                    (const int*)t.d_cols.p, (const int*)t.d_uniq.p, nsingle, 1, nsplit, d_T, d_cnt, d_err, ctx->nsm,
+                    st, ctx->kev[0], ctx->kev[1], tf32, ctx->wait_ns, ctx->stall, spf, tstride * 2));
+      ctx->kev_used = true;
+    } else {
+      const int tcg[3] = {4, 8, 16};
+      CU(cudaEventRecord(ctx->kev[0], st));
+      ctx->kev_used = true;
+      for (int k = 0; k < 3; ++k) {
+        const int ntl = (int)t.tiles[k].size();
+        if (!ntl) continue;
+        KL(launch_simt4(d_astore, npts, d_delta, (const Tile4*)t.d_tiles[k].p, ntl, (const Row4*)t.d_rows.p,
+                        (const int*)t.d_cols.p, (const int*)t.d_uniq.p, 1, tcg[k], 0, nsingle, d_T, ctx->nsm, st,
+                        nfld, tstride * 2));
+      }
+      CU(cudaEventRecord(ctx->kev[1], st));
+    }
+    ST(buf(ctx, "z4", (size_t)nfld * t.nout * 16, (void**)&d_z4));
+    KL(launch_couple(d_T, 1, (const int*)t.d_ptr.p, (const int*)t.d_idx.p, (const double*)t.d_coef.p, t.nout, d_z4, st,
+                     nfld, tstride));
+    if (flags & SBG_NORMALIZED) {
+      const long long nouter = t.nout / ((long long)nb * nb * nb);
+      KL(launch_normalize(d_z4, nouter, nb, 4, 2, d_acc, (double)ng, d_vb, st, nfld));
+    }
+  }
+  rec(ctx, 6);
+  // ---- 3PCF finish + downloads into the pinned slot ----
+  const size_t z3b = do3 ? (size_t)(mmax + 1) * nb * nb * 16 : 0;
+  const size_t z4b = do4 ? (size_t)t4->nout * 16 : 0;
+  const size_t off4 = ((size_t)nfld * z3b + 255) / 256 * 256;
+  if (do3) {
+    double* d_z3;
+    ST(buf(ctx, "z3", (size_t)nfld * z3b, (void**)&d_z3));
+    KL(launch_finish3(d_S, 0, mmax, nb, d_z3, st, nfld, s_stride));
+    if (flags & SBG_NORMALIZED) KL(launch_normalize(d_z3, mmax + 1, nb, 3, 2, d_acc, (double)ng, d_vb, st, nfld));
+    CU(cudaMemcpyAsync(hslot, d_z3, (size_t)nfld * z3b, cudaMemcpyDeviceToHost, st));
+  }
+  if (do4) CU(cudaMemcpyAsync(hslot + off4, d_z4, (size_t)nfld * z4b, cudaMemcpyDeviceToHost, st));
+  rec(ctx, 7);
+  out->fields = fields;
+  out->nfld = nfld;
+  out->z3b = z3b;
+  out->z4b = z4b;
+  out->off4 = off4;
+  out->host = hslot;
+  return SBG_OK;
+}
+
+// Copies a slab's results from the pinned slot to the fields' arrays, with
+// several host threads when there is much to copy (the dense 4PCF outputs of a
+// slab of slices reach hundreds of MB).
+void slab_copy_out(const SlabOut& o) {
+  auto part = [&o](int f0, int f1) {
+    for (int i = f0; i < f1; ++i) {
+      if (o.z3b && o.fields[i].zeta3) std::memcpy(o.fields[i].zeta3, o.host + (size_t)i * o.z3b, o.z3b);
+      if (o.z4b && o.fields[i].zeta4) std::memcpy(o.fields[i].zeta4, o.host + o.off4 + (size_t)i * o.z4b, o.z4b);
+    }
+  };
+  const size_t total = (size_t)o.nfld * (o.z3b + o.z4b);
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nt = (int)std::min<size_t>({(size_t)8, (size_t)hw, (size_t)o.nfld, total / (16u << 20) + 1});
+  if (nt <= 1) {
+    part(0, o.nfld);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) th.emplace_back(part, o.nfld * t / nt, o.nfld * (t + 1) / nt);
+  part(0, o.nfld / nt);
+  for (auto& x : th) x.join();
+}
+
 }  // namespace
 
 // =================================================================== C ABI ==
@@ -1487,6 +1751,7 @@ sbg_status sbg_projected(sbg_context* ctx, const void* field, sbg_dtype dtype, c
   const int n = (int)shape[0];
   ST(check_edges(ctx, edges, nbins, n));
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SBG_ERR_CUDA, "cudaSetDevice");
+  if (ctx->defer) return SBG_OK;  // checks only (a batch validates its fields first)
   return measure(ctx, 2, field, dtype, n, edges, nbins, mmax, mmax, prec, flags, zeta3, zeta4);
 }
 
@@ -1496,78 +1761,138 @@ sbg_status sbg_projected_batch(sbg_context* ctx, const sbg_field2d* fields, int 
   ctx->err.clear();
   if (!fields || nfields < 1) return fail(ctx, SBG_ERR_INVALID_ARG, "fields/nfields");
   if (nbins < 1 || nbins > kMaxBins || mmax < 0) return fail(ctx, SBG_ERR_INVALID_ARG, "nbins/mmax");
-  // Fields are queued back to back: field i + 1 is queued before field i's
-  // results are waited for and copied out of their pinned staging slot, so
-  // the GPU runs while the host prepares the next field.
-  const size_t w = 2 * (size_t)mmax + 1;
-  const size_t b3 = (flags & SBG_3PCF) ? (size_t)(mmax + 1) * nbins * nbins * 16 : 0;
-  const size_t b4 = (flags & SBG_4PCF) ? w * w * nbins * nbins * nbins * 16 : 0;
-  ctx->slot_bytes = (b3 + 255) / 256 * 256 + b4 + 256;
-  void* hs;
-  ST(host_staging(ctx, 64 + 2 * ctx->slot_bytes, &hs));
-  int* d_err;
-  ST(buf(ctx, "err", 16, (void**)&d_err));
-  CU(cudaMemsetAsync(d_err, 0, 16, ctx->stream));
+  // every field is checked before any work is queued
+  ctx->defer = true;
+  for (int i = 0; i < nfields; ++i) {
+    sbg_status s = sbg_projected(ctx, fields[i].field, fields[i].dtype, fields[i].shape, fields[i].edges, nbins, mmax,
+                                 prec, flags, fields[i].zeta3, fields[i].zeta4);
+    if (s != SBG_OK) {
+      ctx->defer = false;
+      ctx->err = "field " + std::to_string(i) + ": " + ctx->err;
+      return s;
+    }
+  }
+  ctx->defer = false;
+  const bool do3 = flags & SBG_3PCF, do4 = flags & SBG_4PCF;
+  const bool tcomb = prec != SBG_PREC_FP32;
+  const int tf32 = prec == SBG_PREC_TF32X3 ? 1 : 0;
+  // the 4PCF plan is shared by every field (one bin count, one order)
+  if (do4) ST(ensure_tables4(ctx, 2, nbins, mmax, tcomb, false));
+  const Tables4* t4 = do4 ? ctx->t4 : nullptr;
+  const int nsingle = do4 ? (mmax + 1) * nbins : 0;
+  const size_t z3b = do3 ? (size_t)(mmax + 1) * nbins * nbins * 16 : 0;
+  const size_t z4b = do4 ? (size_t)t4->nout * 16 : 0;
+  // Slabs: runs of consecutive fields with one shape, dtype and bin set, cut
+  // so that a slab's buffers fit the device (or the context's budget), its
+  // results a pinned staging slot of kSlotMax bytes, and its FFT batches the
+  // grid's 65535 rows.
+  constexpr size_t kSlotMax = 512ull << 20;
+  size_t freeb = 0, totb = 0;
+  cudaMemGetInfo(&freeb, &totb);
+  size_t avail = (freeb > (4ull << 30) ? freeb - (4ull << 30) : freeb / 2) + ctx->used;
+  if (ctx->budget) avail = std::min(avail, ctx->budget);
+  avail = avail / 10 * 7;
+  struct Slab {
+    int i0, nf, n;
+  };
+  std::vector<Slab> slabs;
+  auto same = [&](const sbg_field2d& a, const sbg_field2d& b) {
+    if (a.dtype != b.dtype || a.shape[0] != b.shape[0]) return false;
+    for (int k = 0; k <= nbins; ++k)
+      if (a.edges[k] != b.edges[k]) return false;
+    return true;
+  };
+  for (int i = 0; i < nfields;) {
+    int j = i + 1;
+    while (j < nfields && same(fields[i], fields[j])) ++j;
+    const int n = (int)fields[i].shape[0];
+    const size_t ng = (size_t)n * n;
+    const size_t esz = fields[i].dtype == SBG_F64 ? 8 : 4;
+    size_t per = ng * (esz + 4 + 8 + (size_t)nbins * 8) + 2 * z3b;
+    if (do4) per += ng * ((size_t)nsingle * 8 + (size_t)(t4->img_stride + 31) / 32 * (tf32 ? 2 : 1)) +
+                    (size_t)std::max<long long>(t4->tcount, 1) * 16 + 2 * z4b;
+    int cap = (int)std::max<size_t>(1, avail / std::max<size_t>(per, 1));
+    cap = std::min(cap, (int)std::max<size_t>(1, kSlotMax / std::max<size_t>(z3b + z4b, 1)));
+    cap = std::min(cap, 65535 / nbins);
+    for (int k = i; k < j; k += cap) slabs.push_back({k, std::min(cap, j - k), n});
+    i = j;
+  }
+  size_t slot = 0;
+  for (const Slab& sl : slabs) slot = std::max(slot, ((size_t)sl.nf * z3b + 255) / 256 * 256 + (size_t)sl.nf * z4b);
+  slot = (slot + 255) / 256 * 256;
+  unsigned char* hs;
+  ST(host_staging(ctx, 64 + 2 * slot, (void**)&hs));
+  int* d_err = nullptr;
+  if (tcomb) {
+    ST(buf(ctx, "err", 16, (void**)&d_err));
+    CU(cudaMemsetAsync(d_err, 0, 16, ctx->stream));
+  }
+  // Slab c is queued in pinned slot c % 2 with event set c % 2; slab c - 1 is
+  // completed (waited for, timed and copied out) after slab c is queued, so
+  // the host's copies overlap the GPU's next slab.
   double acc[kStages] = {0};
-  long long nl = 0;
   double kms = 0.0;
-  auto complete = [&](int slot) -> sbg_status {
-    sbg_context::Pending& pd = ctx->pend[slot];
-    if (!pd.live) return SBG_OK;
-    pd.live = false;
-    CU(cudaEventSynchronize(ctx->evs[slot][kStages]));
+  long long nl = 0;
+  SlabOut pend[2];
+  bool live[2] = {false, false};
+  bool kev_live[2] = {false, false};
+  auto complete = [&](int sl) -> sbg_status {
+    if (!live[sl]) return SBG_OK;
+    live[sl] = false;
+    CU(cudaEventSynchronize(ctx->evs[sl][kStages]));
     for (int k = 0; k < kStages; ++k) {
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, ctx->evs[slot][k], ctx->evs[slot][k + 1]) != cudaSuccess) {
+      if (cudaEventElapsedTime(&ms, ctx->evs[sl][k], ctx->evs[sl][k + 1]) != cudaSuccess) {
         cudaGetLastError();
         ms = 0.f;
       }
       acc[k] += ms;
     }
-    if (pd.kev_used) {
+    if (kev_live[sl]) {
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, ctx->kevs[slot][0], ctx->kevs[slot][1]) == cudaSuccess) kms += ms;
+      if (cudaEventElapsedTime(&ms, ctx->kevs[sl][0], ctx->kevs[sl][1]) == cudaSuccess) kms += ms;
       else cudaGetLastError();
     }
-    nl += pd.launches;
-    const unsigned char* hst = (const unsigned char*)ctx->hpin + 64 + (size_t)slot * ctx->slot_bytes;
-    if (pd.zeta3) std::memcpy(pd.zeta3, hst + pd.off3, pd.b3);
-    if (pd.zeta4) std::memcpy(pd.zeta4, hst + pd.off4, pd.b4);
+    slab_copy_out(pend[sl]);
     return SBG_OK;
   };
-  auto finish = [&](sbg_status s) -> sbg_status {
+  auto done = [&](sbg_status s) -> sbg_status {
     cudaStreamSynchronize(ctx->stream);
-    ctx->pend[0].live = ctx->pend[1].live = false;
-    ctx->defer = false;
-    ctx->cur = 0;
     ctx->ev = ctx->evs[0];
     ctx->kev = ctx->kevs[0];
     return s;
   };
-  ctx->defer = true;
-  for (int i = 0; i < nfields; ++i) {
-    const int slot = i & 1;
-    ctx->cur = slot;
-    ctx->ev = ctx->evs[slot];
-    ctx->kev = ctx->kevs[slot];
-    sbg_status s = sbg_projected(ctx, fields[i].field, fields[i].dtype, fields[i].shape, fields[i].edges, nbins, mmax,
-                                 prec, flags, fields[i].zeta3, fields[i].zeta4);
+  ctx->nlaunch = 0;
+  for (size_t c = 0; c < slabs.size(); ++c) {
+    const int sl = (int)(c & 1);
+    ctx->ev = ctx->evs[sl];
+    ctx->kev = ctx->kevs[sl];
+    ctx->kev_used = false;
+    const Slab& b = slabs[c];
+    sbg_status s = measure_slab(ctx, fields + b.i0, b.nf, b.n, fields[b.i0].edges, nbins, mmax, prec, flags,
+                                hs + 64 + (size_t)sl * slot, &pend[sl]);
     if (s != SBG_OK) {
-      ctx->err = "field " + std::to_string(i) + ": " + ctx->err;
-      return finish(s);
+      ctx->err = "fields " + std::to_string(b.i0) + ".." + std::to_string(b.i0 + b.nf - 1) + ": " + ctx->err;
+      return done(s);
     }
-    if (i > 0) {
-      s = complete(slot ^ 1);
-      if (s != SBG_OK) return finish(s);
-    }
+    live[sl] = true;
+    kev_live[sl] = ctx->kev_used;
+    if (c > 0 && (s = complete(sl ^ 1)) != SBG_OK) return done(s);
   }
-  sbg_status s = complete((nfields - 1) & 1);
-  if (s != SBG_OK) return finish(s);
-  int* perr = (int*)ctx->hpin;
-  CU(cudaMemcpyAsync(perr, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  finish(SBG_OK);
-  if (*perr)
-    return fail(ctx, SBG_ERR_TIMEOUT, "a tensor-core combination kernel gave up waiting (code " + std::to_string(*perr) + ")");
+  sbg_status s = complete((int)((slabs.size() - 1) & 1));
+  if (s != SBG_OK) return done(s);
+  int herr = 0;
+  if (tcomb) {
+    int* perr = (int*)ctx->hpin;
+    CU(cudaMemcpyAsync(perr, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    done(SBG_OK);
+    herr = *perr;
+  } else {
+    done(SBG_OK);
+  }
+  if (herr)
+    return fail(ctx, SBG_ERR_TIMEOUT, "a tensor-core combination kernel gave up waiting (code " + std::to_string(herr) + ")");
+  nl = ctx->nlaunch;
   for (int k = 0; k < kStages; ++k) ctx->timings[k] = acc[k];
   ctx->last_launches = nl;
   ctx->contraction_ms = kms;

@@ -51,6 +51,14 @@ struct FftPass {
   //   prune_mode 2: inner index = x (second pass).
   int prune_mode;
   int prune_r;
+  // A slab of fields (0: one field): batch b is array b % nb_per_field of
+  // field b / nb_per_field; the factor array of LOAD_MUL / LOAD_MUL2 is taken
+  // per array of a field (offset (b % nb_per_field) bstride), `shared` per
+  // field (offset (b / nb_per_field) shared_stride), and a blocked-store
+  // output puts field f's points at f field_points onwards.
+  int nb_per_field;
+  long long shared_stride;
+  long long field_points;
 };
 
 // Blocked coefficient store (float view): for each 32-point K-block xb and

@@ -143,6 +143,13 @@ fft_axis_kernel(FftPass p) {
   const int j = CONTIG ? (t % T) : (t / TL);
   const int l = CONTIG ? (t / T) : (t % TL);
   const long long boff = (long long)blockIdx.y * p.bstride;
+  // batch index = field bf x nb_per_field + array bj of that field (a slab of
+  // fields); without nb_per_field every batch is array bj of one field
+  const int bj = p.nb_per_field ? (int)blockIdx.y % p.nb_per_field : (int)blockIdx.y;
+  const long long bf = p.nb_per_field ? (long long)blockIdx.y / p.nb_per_field : 0;
+  const long long moff = (long long)bj * p.bstride;      // factor array of the batch
+  const long long soff = bf * p.shared_stride;            // shared array of its field
+  const long long fpts = bf * p.field_points;             // its first point in the blocked store
 
   long long base;    // element index of point n = 0 of this thread's line
   long long estride; // element stride along the line
@@ -178,16 +185,16 @@ fft_axis_kernel(FftPass p) {
       if (LOAD == LOAD_REAL) {
         v[n2] = make_float2(__ldg(reinterpret_cast<const float*>(p.in) + boff + e), 0.0f);
       } else if (LOAD == LOAD_MUL) {
-        v[n2] = cmul(__ldg(p.shared + e), __ldg(p.mul + boff + e));
+        v[n2] = cmul(__ldg(p.shared + soff + e), __ldg(p.mul + moff + e));
       } else if (LOAD == LOAD_MUL2) {
-        const long long ia = 2 * boff + e;
+        const long long ia = 2 * moff + e;
         float2 f = __ldg(p.mul + ia);
-        if (2 * (int)blockIdx.y + 1 < p.npack) {
+        if (2 * bj + 1 < p.npack) {
           const float2 g = __ldg(p.mul + ia + p.bstride);
           f.x -= g.y;
           f.y += g.x;
         }
-        v[n2] = cmul(__ldg(p.shared + e), f);
+        v[n2] = cmul(__ldg(p.shared + soff + e), f);
       } else {
         v[n2] = __ldg(reinterpret_cast<const float2*>(p.in) + boff + e);
       }
@@ -214,16 +221,16 @@ fft_axis_kernel(FftPass p) {
     for (int k1 = 0; k1 < R1; ++k1) {
       const long long e = base + (long long)(k2 + R2 * k1) * estride;
       if (OUTB == 1) {
-        float* o = reinterpret_cast<float*>(p.out) + blocked_re(e, p.single0 + (int)blockIdx.y, p.nsingle);
+        float* o = reinterpret_cast<float*>(p.out) + blocked_re(fpts + e, p.single0 + bj, p.nsingle);
         o[0] = u[k1].x;
         o[32] = u[k1].y;
       } else if (OUTB == 2) {
-        const int s = p.single0 + 2 * (int)blockIdx.y;
-        float* o = reinterpret_cast<float*>(p.out) + blocked_re(e, s, p.nsingle);
+        const int s = p.single0 + 2 * bj;
+        float* o = reinterpret_cast<float*>(p.out) + blocked_re(fpts + e, s, p.nsingle);
         o[0] = u[k1].x;
         o[32] = 0.0f;
-        if (2 * (int)blockIdx.y + 1 < p.npack) {
-          o = reinterpret_cast<float*>(p.out) + blocked_re(e, s + 1, p.nsingle);
+        if (2 * bj + 1 < p.npack) {
+          o = reinterpret_cast<float*>(p.out) + blocked_re(fpts + e, s + 1, p.nsingle);
           o[0] = u[k1].y;
           o[32] = 0.0f;
         }
@@ -245,6 +252,7 @@ static cudaError_t launch_t(const FftPass& p, cudaStream_t st) {
   // contiguous: outer rows grouped by TL; strided: outer * inner lines grouped by TL
   long long blocks = CONTIG ? p.outer / G::TL : (p.outer * (p.inner / G::TL));
   if (blocks <= 0 || blocks > 0x7fffffffLL || p.batch <= 0 || p.batch > 65535) return cudaErrorInvalidValue;
+  if (p.nb_per_field < 0 || (p.nb_per_field && p.batch % p.nb_per_field)) return cudaErrorInvalidValue;
   if (CONTIG ? (p.outer % G::TL) : (p.inner % G::TL)) return cudaErrorInvalidValue;
   dim3 grid((unsigned)blocks, (unsigned)p.batch);
   kern<<<grid, G::THREADS, G::SMEM, st>>>(p);

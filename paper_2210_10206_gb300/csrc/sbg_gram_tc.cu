@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict__ a, long long ng, int nb,
                const float* __restrict__ delta,
                double* __restrict__ S, int nsingle, int single0, int* err_flag, unsigned long long wait_ns,
-               int stall) {
+               int stall, long long s_stride) {
   using C = GramCfg<TF>;
   constexpr int kPts = C::kPts, kFlush = C::kFlush;
   extern __shared__ uint8_t smem_raw[];
@@ -184,6 +184,11 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int R = 2 * nb;                                // real rows of W and of U
   const int N = (2 * R + 15) & ~15;                    // MMA N: [U_hi | U_lo] padded
+  // field f = blockIdx.y of a slab of fields: its points follow field f - 1's
+  // in the blocked store and delta, its bins in the [field][bin][x] buffer
+  // (rows f nb .. f nb + nb - 1 of the tensor map), its S after field f - 1's
+  const int fld = blockIdx.y;
+  S += (long long)fld * s_stride;
   const long long nkb_all = ng / kPts;
   const long long per = (nkb_all + gridDim.x - 1) / gridDim.x;
   const long long kb0 = blockIdx.x * per;
@@ -238,14 +243,14 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict
         if (nsingle) {
           // blocked store: one contiguous run of nb singles per 32-point block
           for (int j = 0; j < kPts / 32; ++j) {
-            const long long xb = (x0 >> 5) + j;
+            const long long xb = (((long long)fld * ng + x0) >> 5) + j;
             bulk_g2s(st + j * nb * 256, a + (xb * nsingle + single0) * 64, (uint32_t)nb * 256, &raw_full[rs]);
           }
         } else {
           // rows b = 0 .. nb-1, floats 2 x0 .. 2 x0 + 2 kPts - 1 (x0 < 2^30 / 2 for the grids here)
-          tma_load_2d(st, &tmap, (int)(2 * x0), 0, &raw_full[rs]);
+          tma_load_2d(st, &tmap, (int)(2 * x0), fld * nb, &raw_full[rs]);
         }
-        bulk_g2s(st + kGDeltaOff, delta + x0, (uint32_t)kPts * 4, &raw_full[rs]);
+        bulk_g2s(st + kGDeltaOff, delta + (long long)fld * ng + x0, (uint32_t)kPts * 4, &raw_full[rs]);
       }
       // every copy issued has landed before the CTA may exit (also after an error)
       for (int rs = 0; rs < kGRaw; ++rs)
@@ -420,13 +425,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 template <bool TF>
 cudaError_t launch_gram_tc_t(const float2* a, long long ng, int nb, const float* delta, double* S, int nsingle,
-                             int single0, int* err, int nsm, unsigned long long wait_ns, int stall,
-                             cudaStream_t st) {
+                             int single0, int* err, int nsm, unsigned long long wait_ns, int stall, int nfld,
+                             long long s_stride, cudaStream_t st) {
   cudaError_t e = ensure_smem_attr<gram_tc_kernel<TF>>(kGSmem);
   if (e != cudaSuccess) return e;
   constexpr int kPts = GramCfg<TF>::kPts;
   const long long nkb = ng / kPts;
-  const int grid = (int)std::min<long long>(nsm, nkb);
+  // CTAs per field: the SMs shared out over the fields
+  const int grid = (int)std::max<long long>(1, std::min<long long>((nsm + nfld - 1) / nfld, nkb));
   CUtensorMap map;
   std::memset(&map, 0, sizeof map);
   if (!nsingle) {
@@ -434,7 +440,7 @@ cudaError_t launch_gram_tc_t(const float2* a, long long ng, int nb, const float*
     // 8 ng bytes), a box of every row's 2 kPts floats per K-block
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc || 2 * ng >= (1LL << 31)) return cudaErrorNotSupported;
-    const cuuint64_t dims[2] = {(cuuint64_t)(2 * ng), (cuuint64_t)nb};
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 * ng), (cuuint64_t)nb * nfld};
     const cuuint64_t strides[1] = {(cuuint64_t)ng * 8};
     const cuuint32_t box[2] = {(cuuint32_t)(2 * kPts), (cuuint32_t)nb};
     const cuuint32_t estr[2] = {1, 1};
@@ -443,8 +449,8 @@ cudaError_t launch_gram_tc_t(const float2* a, long long ng, int nb, const float*
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
-  gram_tc_kernel<TF><<<grid, kGThreads, kGSmem, st>>>(map, (const float*)a, ng, nb, delta, S, nsingle, single0, err,
-                                                       wait_ns, stall);
+  gram_tc_kernel<TF><<<dim3(grid, nfld), kGThreads, kGSmem, st>>>(map, (const float*)a, ng, nb, delta, S, nsingle,
+                                                                   single0, err, wait_ns, stall, s_stride);
   return cudaGetLastError();
 }
 
@@ -452,10 +458,11 @@ cudaError_t launch_gram_tc_t(const float2* a, long long ng, int nb, const float*
 
 cudaError_t launch_gram_tc(const float2* a, long long ng, int nb, const float* delta, double* S, int nsingle,
                            int single0, int tf32, int* err, int nsm, unsigned long long wait_ns, int stall,
-                           cudaStream_t st) {
-  if (nb < 1 || nb > kGMaxNb || ng % 64 || !err) return cudaErrorInvalidValue;
-  if (tf32) return launch_gram_tc_t<true>(a, ng, nb, delta, S, nsingle, single0, err, nsm, wait_ns, stall, st);
-  return launch_gram_tc_t<false>(a, ng, nb, delta, S, nsingle, single0, err, nsm, wait_ns, stall, st);
+                           cudaStream_t st, int nfld, long long s_stride) {
+  if (nb < 1 || nb > kGMaxNb || ng % 64 || !err || nfld < 1 || nfld > 65535) return cudaErrorInvalidValue;
+  if (tf32)
+    return launch_gram_tc_t<true>(a, ng, nb, delta, S, nsingle, single0, err, nsm, wait_ns, stall, nfld, s_stride, st);
+  return launch_gram_tc_t<false>(a, ng, nb, delta, S, nsingle, single0, err, nsm, wait_ns, stall, nfld, s_stride, st);
 }
 
 }  // namespace sbg

@@ -26,24 +26,28 @@ __device__ __forceinline__ void block_add_d(double v, double* dst) {
   }
 }
 
+// field f = blockIdx.y of a slab: its n values start at f * n; acc[2f] collects
+// the sum and acc[2f + 1] N_gal
 __global__ void sum_kernel(const void* in, int is_f64, long long n, double* acc) {
+  const long long f0 = (long long)blockIdx.y * n;
   double s = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    s += is_f64 ? reinterpret_cast<const double*>(in)[i] : (double)reinterpret_cast<const float*>(in)[i];
-  block_add_d(s, acc);
+    s += is_f64 ? reinterpret_cast<const double*>(in)[f0 + i] : (double)reinterpret_cast<const float*>(in)[f0 + i];
+  block_add_d(s, acc + 2 * blockIdx.y);
 }
 
 __global__ void convert_kernel(const void* in, int is_f64, long long n, const double* acc, int subtract,
                                float* out, double* ngal) {
-  const double mean = subtract ? acc[0] / (double)n : 0.0;
+  const long long f0 = (long long)blockIdx.y * n;
+  const double mean = subtract ? acc[2 * blockIdx.y] / (double)n : 0.0;
   double s = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double v = is_f64 ? reinterpret_cast<const double*>(in)[i] : (double)reinterpret_cast<const float*>(in)[i];
+    double v = is_f64 ? reinterpret_cast<const double*>(in)[f0 + i] : (double)reinterpret_cast<const float*>(in)[f0 + i];
     v -= mean;
-    out[i] = (float)v;
+    out[f0 + i] = (float)v;
     s += v + 1.0;
   }
-  block_add_d(s, ngal);
+  block_add_d(s, ngal + 2 * blockIdx.y);
 }
 
 static int grid_for(long long n, int threads) {
@@ -53,15 +57,24 @@ static int grid_for(long long n, int threads) {
   return (int)(b < 1 ? 1 : b);
 }
 
-cudaError_t launch_sum(const void* in, int is_f64, long long n, double* acc, cudaStream_t st) {
-  sum_kernel<<<grid_for(n, 256), 256, 0, st>>>(in, is_f64, n, acc);
+// CTAs per field of a slab of nfld fields: the single-field grid, shared out
+static dim3 grid_fields(long long n, int nfld) {
+  long long b = grid_for(n, 256);
+  if (nfld > 1) b = std::max<long long>(1, std::min<long long>(b, ((long long)device_sms() * 16 + nfld - 1) / nfld));
+  return dim3((unsigned)b, (unsigned)nfld);
+}
+
+cudaError_t launch_sum(const void* in, int is_f64, long long n, double* acc, cudaStream_t st, int nfld) {
+  if (nfld < 1 || nfld > 65535) return cudaErrorInvalidValue;
+  sum_kernel<<<grid_fields(n, nfld), 256, 0, st>>>(in, is_f64, n, acc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_convert(const void* in, int is_f64, long long n, const double* acc, int subtract, float* out,
-                           cudaStream_t st) {
-  convert_kernel<<<grid_for(n, 256), 256, 0, st>>>(in, is_f64, n, acc, subtract, out,
-                                                    const_cast<double*>(acc) + 1);
+                           cudaStream_t st, int nfld) {
+  if (nfld < 1 || nfld > 65535) return cudaErrorInvalidValue;
+  convert_kernel<<<grid_fields(n, nfld), 256, 0, st>>>(in, is_f64, n, acc, subtract, out,
+                                                        const_cast<double*>(acc) + 1);
   return cudaGetLastError();
 }
 
@@ -155,7 +168,13 @@ constexpr int kGramMaxNb = 32;
 
 __global__ void __launch_bounds__(256) gram3_kernel(const float2* __restrict__ a, long long ng, int nb,
                                                     const float* __restrict__ delta, double* __restrict__ S,
-                                                    int nsingle, int single0) {
+                                                    int nsingle, int single0, long long s_stride) {
+  // field f = blockIdx.y of a slab: its bins follow field f - 1's (group
+  // buffer) or its points do (blocked store); its delta and S likewise
+  const long long fx = (long long)blockIdx.y * ng;
+  if (!nsingle) a += (long long)blockIdx.y * nb * ng;
+  delta += fx;
+  S += (long long)blockIdx.y * s_stride;
   // rows padded by one element: the threads of a warp read the same point of
   // up to 20 different bins, which a 512-byte row stride would put in one bank
   __shared__ float2 sa[kGramMaxNb][kGramChunk + 1];
@@ -184,7 +203,7 @@ __global__ void __launch_bounds__(256) gram3_kernel(const float2* __restrict__ a
       if (b < nb && xx < cnt) {
         const long long x = xc + xx;
         if (nsingle) {
-          const float* f = reinterpret_cast<const float*>(a) + blocked_re(x, single0 + b, nsingle);
+          const float* f = reinterpret_cast<const float*>(a) + blocked_re(fx + x, single0 + b, nsingle);
           v = make_float2(f[0], f[32]);
         } else {
           v = a[(long long)b * ng + x];
@@ -226,14 +245,14 @@ __global__ void __launch_bounds__(256) gram3_kernel(const float2* __restrict__ a
 }
 
 cudaError_t launch_gram3(const float2* a, long long ng, int nb, const float* delta, double* S, int nsingle,
-                         int single0, cudaStream_t st) {
-  if (nb > kGramMaxNb || nb * (nb + 1) / 2 > 256) return cudaErrorInvalidValue;
+                         int single0, cudaStream_t st, int nfld, long long s_stride) {
+  if (nb > kGramMaxNb || nb * (nb + 1) / 2 > 256 || nfld < 1 || nfld > 65535) return cudaErrorInvalidValue;
   // about 4 chunks per CTA on small grids (a CTA's chunks run one after another),
   // at most 8 CTAs per SM of cross-CTA FP64 atomics on large ones
   long long blocks = (ng + 4 * kGramChunk - 1) / (4 * kGramChunk);
-  const long long cap = (long long)device_sms() * 8;
+  const long long cap = std::max<long long>(1, ((long long)device_sms() * 8 + nfld - 1) / nfld);
   if (blocks > cap) blocks = cap;
-  gram3_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, ng, nb, delta, S, nsingle, single0);
+  gram3_kernel<<<dim3((unsigned)blocks, nfld), 256, 0, st>>>(a, ng, nb, delta, S, nsingle, single0, s_stride);
   return cudaGetLastError();
 }
 
@@ -269,7 +288,10 @@ __global__ void __launch_bounds__(256) simt4_kernel(const float2* __restrict__ a
                                                     const float* __restrict__ delta, const Tile4* __restrict__ tiles,
                                                     const Row4* __restrict__ rows, const int* __restrict__ cols,
                                                     const int* __restrict__ uniq, int nsplit, int nsingle,
-                                                    double* __restrict__ T, int imag) {
+                                                    double* __restrict__ T, int imag, int splits_per_field,
+                                                    long long t_field_stride) {
+  // a slab of fields: x-split blockIdx.y belongs to field blockIdx.y / splits_per_field
+  if (splits_per_field) T += (long long)(blockIdx.y / splits_per_field) * t_field_stride;
   using SM = SimtSmem<TCG>;
   constexpr int TR = SM::TR, TC = SM::TC;
   extern __shared__ float4 smem4[];
@@ -415,14 +437,35 @@ __global__ void __launch_bounds__(256) simt4_kernel(const float2* __restrict__ a
 template <int TCG, bool CPLX>
 static cudaError_t simt4_t(const float2* astore, long long ng, const float* delta, const Tile4* tiles, int ntiles,
                           const Row4* rows, const int* cols, const int* uniq, int nsplit, int nsingle, double* T,
-                          int nsm, int imag, cudaStream_t st) {
+                          int nsm, int imag, cudaStream_t st, int nfld, long long t_field_stride) {
   const size_t smem = SimtSmem<TCG>::kBytes;
   auto kern = simt4_kernel<TCG, CPLX>;
   {
     cudaError_t e = ensure_smem_attr<simt4_kernel<TCG, CPLX>>((int)smem);
     if (e != cudaSuccess) return e;
   }
-  if (nsplit <= 0) {
+  int spf = 0;  // x-splits per field of a slab
+  if (nfld > 1) {
+    // a slab: every field is split alike (a power of two dividing its
+    // K-blocks), the split count chosen for the best fill of the resident slots
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    if (e != cudaSuccess) return e;
+    const long long slots = (long long)nsm * (per_sm > 0 ? per_sm : 1), fchunks = ng / nfld / kX;
+    double best = -1.0;
+    spf = 1;
+    for (long long k = 1; k <= fchunks && k <= 64; k *= 2) {
+      const long long units = (long long)ntiles * nfld * k;
+      if (units > 65535LL * ntiles) break;
+      const double fill = (double)units / (double)(slots * ((units + slots - 1) / slots));
+      if (fill > best + 1e-3) {
+        best = fill;
+        spf = (int)k;
+      }
+      if (units >= 4 * slots) break;
+    }
+    nsplit = nfld * spf;
+  } else if (nsplit <= 0) {
     // x-splits per tile so that the CTAs fill whole waves of the resident
     // slots (SMs x CTAs per SM): the best fill over 2..8 waves, fewer on ties
     int per_sm = 0;
@@ -441,25 +484,27 @@ static cudaError_t simt4_t(const float2* astore, long long ng, const float* delt
       }
     }
   }
+  if (nsplit > 65535) return cudaErrorInvalidValue;
   dim3 grid((unsigned)ntiles, (unsigned)nsplit);
-  kern<<<grid, 256, smem, st>>>(astore, ng, delta, tiles, rows, cols, uniq, nsplit, nsingle, T, imag);
+  kern<<<grid, 256, smem, st>>>(astore, ng, delta, tiles, rows, cols, uniq, nsplit, nsingle, T, imag, spf,
+                                t_field_stride);
   return cudaGetLastError();
 }
 
 cudaError_t launch_simt4(const float2* astore, long long ng, const float* delta, const Tile4* tiles, int ntiles,
                          const Row4* rows, const int* cols, const int* uniq, int complex_out, int tcg, int nsplit,
-                         int nsingle, double* T, int nsm, cudaStream_t st) {
+                         int nsingle, double* T, int nsm, cudaStream_t st, int nfld, long long t_field_stride) {
   if (ntiles <= 0) return cudaSuccess;
-  if (ng % kX || complex_out < 0 || complex_out > 2) return cudaErrorInvalidValue;
+  if (ng % kX || complex_out < 0 || complex_out > 2 || nfld < 1 || (ng / nfld) % kX) return cudaErrorInvalidValue;
   const int imag = complex_out == 2 ? 1 : 0;  // real T holding Im(P a)
   if (complex_out == 1) {
-    if (tcg == 4) return simt4_t<4, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st);
-    if (tcg == 8) return simt4_t<8, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st);
-    if (tcg == 16) return simt4_t<16, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st);
+    if (tcg == 4) return simt4_t<4, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st, nfld, t_field_stride);
+    if (tcg == 8) return simt4_t<8, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st, nfld, t_field_stride);
+    if (tcg == 16) return simt4_t<16, true>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st, nfld, t_field_stride);
   } else {
-    if (tcg == 4) return simt4_t<4, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st);
-    if (tcg == 8) return simt4_t<8, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st);
-    if (tcg == 16) return simt4_t<16, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st);
+    if (tcg == 4) return simt4_t<4, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st, nfld, t_field_stride);
+    if (tcg == 8) return simt4_t<8, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st, nfld, t_field_stride);
+    if (tcg == 16) return simt4_t<16, false>(astore, ng, delta, tiles, ntiles, rows, cols, uniq, nsplit, nsingle, T, nsm, imag, st, nfld, t_field_stride);
   }
   return cudaErrorInvalidValue;
 }
@@ -467,9 +512,12 @@ cudaError_t launch_simt4(const float2* astore, long long ng, const float* delta,
 // ------------------------------------------------------------- finalisation --
 __global__ void couple_kernel(const double* __restrict__ T, int complex_t, const int* __restrict__ ptr,
                               const int* __restrict__ idx, const double* __restrict__ coef, int nout,
-                              double* __restrict__ zeta) {
+                              double* __restrict__ zeta, long long t_stride) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= nout) return;
+  // field blockIdx.y of a slab: its T and zeta follow the previous field's
+  T += (long long)blockIdx.y * t_stride * (complex_t ? 2 : 1);
+  zeta += (long long)blockIdx.y * nout * (complex_t ? 2 : 1);
   double re = 0.0, im = 0.0;
   for (int e = ptr[o]; e < ptr[o + 1]; ++e) {
     int i = idx[e];
@@ -492,16 +540,21 @@ __global__ void couple_kernel(const double* __restrict__ T, int complex_t, const
 }
 
 cudaError_t launch_couple(const double* T, int complex_t, const int* ptr, const int* idx, const double* coef, int nout,
-                          double* zeta, cudaStream_t st) {
+                          double* zeta, cudaStream_t st, int nfld, long long t_stride) {
   if (nout <= 0) return cudaSuccess;
-  couple_kernel<<<(nout + 255) / 256, 256, 0, st>>>(T, complex_t, ptr, idx, coef, nout, zeta);
+  if (nfld < 1 || nfld > 65535) return cudaErrorInvalidValue;
+  couple_kernel<<<dim3((nout + 255) / 256, nfld), 256, 0, st>>>(T, complex_t, ptr, idx, coef, nout, zeta, t_stride);
   return cudaGetLastError();
 }
 
-__global__ void finish3_kernel(const double* __restrict__ S, int full, int lmax, int nb, double* __restrict__ zeta) {
+__global__ void finish3_kernel(const double* __restrict__ S, int full, int lmax, int nb, double* __restrict__ zeta,
+                               long long s_stride) {
   const int nl = lmax + 1;
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= nl * nb * nb) return;
+  // field blockIdx.y of a slab
+  S += (long long)blockIdx.y * s_stride;
+  zeta += (long long)blockIdx.y * nl * nb * nb * (full ? 1 : 2);
   const int l = o / (nb * nb), b1 = (o / nb) % nb, b2 = o % nb;
   // S stored for b1 <= b2; S[b2][b1] = conj(S[b1][b2])
   const int lo = min(b1, b2), hi = max(b1, b2);
@@ -521,9 +574,11 @@ __global__ void finish3_kernel(const double* __restrict__ S, int full, int lmax,
   }
 }
 
-cudaError_t launch_finish3(const double* S, int full, int lmax, int nb, double* zeta, cudaStream_t st) {
+cudaError_t launch_finish3(const double* S, int full, int lmax, int nb, double* zeta, cudaStream_t st, int nfld,
+                           long long s_stride) {
+  if (nfld < 1 || nfld > 65535) return cudaErrorInvalidValue;
   const int n = (lmax + 1) * nb * nb;
-  finish3_kernel<<<(n + 255) / 256, 256, 0, st>>>(S, full, lmax, nb, zeta);
+  finish3_kernel<<<dim3((n + 255) / 256, nfld), 256, 0, st>>>(S, full, lmax, nb, zeta, s_stride);
   return cudaGetLastError();
 }
 
@@ -532,7 +587,9 @@ __global__ void normalize_kernel(double* zeta, long long nouter, int nb, int ord
   const long long per = (order == 4 ? (long long)nb * nb * nb : (long long)nb * nb);
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= nouter * per) return;
-  const double ngal = acc[1];
+  // field blockIdx.y of a slab: its outputs and N_gal
+  zeta += (long long)blockIdx.y * nouter * per * ncomp;
+  const double ngal = acc[2 * blockIdx.y + 1];
   const double nbar = ngal / ng;
   const long long w = i % per;
   double norm = ngal;
@@ -545,11 +602,13 @@ __global__ void normalize_kernel(double* zeta, long long nouter, int nb, int ord
 }
 
 cudaError_t launch_normalize(double* zeta, long long nouter, int nb, int order, int ncomp, const double* acc, double ng,
-                             const double* vbin_dev, cudaStream_t st) {
+                             const double* vbin_dev, cudaStream_t st, int nfld) {
   const long long per = (order == 4 ? (long long)nb * nb * nb : (long long)nb * nb);
   const long long n = nouter * per;
   if (n <= 0) return cudaSuccess;
-  normalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(zeta, nouter, nb, order, ncomp, acc, ng, vbin_dev);
+  if (nfld < 1 || nfld > 65535) return cudaErrorInvalidValue;
+  normalize_kernel<<<dim3((unsigned)((n + 255) / 256), nfld), 256, 0, st>>>(zeta, nouter, nb, order, ncomp, acc, ng,
+                                                                            vbin_dev);
   return cudaGetLastError();
 }
 

@@ -6,9 +6,11 @@ namespace sbg {
 
 // ---- preprocessing (Sec. 4.1 mean subtraction; Eq. num_gals) ----
 // acc[0] += sum(x); then out = float(x - mean) and acc[1] += sum(x - mean + 1).
-cudaError_t launch_sum(const void* in, int is_f64, long long n, double* acc, cudaStream_t st);
+// A slab of nfld fields of n values each (field f at in + f n, out + f n) uses
+// acc[2f] and acc[2f + 1].
+cudaError_t launch_sum(const void* in, int is_f64, long long n, double* acc, cudaStream_t st, int nfld = 1);
 cudaError_t launch_convert(const void* in, int is_f64, long long n, const double* acc, int subtract,
-                           float* out, cudaStream_t st);
+                           float* out, cudaStream_t st, int nfld = 1);
 
 // ---- kernel generation (Algorithms 1-2) ----
 // 3D: out[b][cell] = conj(Y_lm(r_hat)) Theta_b(|r|) * scale for b < nb (buffer pre-zeroed).
@@ -22,8 +24,11 @@ cudaError_t launch_kgen2d(int n, int m, const double* e2_dev, int nb, double sca
 // S[b1][b2] += sum_x delta(x) a_b1(x) conj(a_b2(x)) for b1 <= b2, complex double.
 // nsingle > 0: `a` is the blocked coefficient store and bin b is single single0 + b;
 // nsingle = 0: `a` is [nb][ng].
+// A slab of nfld fields of ng points: field f's bins follow field f - 1's in
+// the [field][bin][x] buffer (nsingle = 0) or its points follow in the blocked
+// store; delta + f ng; S + f s_stride (doubles).
 cudaError_t launch_gram3(const float2* a, long long ng, int nb, const float* delta, double* S, int nsingle,
-                         int single0, cudaStream_t st);
+                         int single0, cudaStream_t st, int nfld = 1, long long s_stride = 0);
 
 // ---- 4PCF pair x single contraction tables (Algorithms 6 and 8) ----
 struct Tile4 {
@@ -43,9 +48,12 @@ struct Row4 {
 // T[tile][r][c] (+)= sum_x delta * f1 * f2 * a_col: its real part
 // (complex_out 0), complex value (1, two doubles per entry) or imaginary part
 // (2).  nsplit <= 0: x-splits per tile chosen to fill whole waves of nsm SMs.
+// A slab of nfld fields (ng = nfld x the points of one field): each field is
+// split alike and adds into T + f t_field_stride (doubles).
 cudaError_t launch_simt4(const float2* astore, long long ng, const float* delta, const Tile4* tiles,
                          int ntiles, const Row4* rows, const int* cols, const int* uniq, int complex_out,
-                         int tcg, int nsplit, int nsingle, double* T, int nsm, cudaStream_t st);
+                         int tcg, int nsplit, int nsingle, double* T, int nsm, cudaStream_t st, int nfld = 1,
+                         long long t_field_stride = 0);
 
 // Tensor-core (tcgen05) split-BF16 version of the same contraction (sbg_tc.cu).
 // Tiles of <= 128 rows whose row singles (<= kTcMaxRowSlots, in the slot order
@@ -69,6 +77,9 @@ struct BGroup {
   int pad;
   long long off;       // byte offset of the image in a K-block's slab
 };
+// A slab of fields (splits_per_field > 0): the points of the fields follow each
+// other, each field is splits_per_field consecutive x-splits, and field f adds
+// into T + f t_field_stride (doubles).
 // Units (tile, x-split) are spread over a cooperative grid of one CTA per SM;
 // cnt holds one progress counter per (round, epoch), zeroed by the caller.
 // chunks_per_kb = 8 * sum of the groups' n.  complex_out as for launch_simt4:
@@ -78,7 +89,8 @@ cudaError_t launch_tc4(const float2* astore, void* bimg, const BGroup* bgroups, 
                        const Row4* rows, const int* cols, const int* slots, int nsingle, int complex_out,
                        int nsplit, double* T, int* cnt, int* err, int nsm, cudaStream_t st,
                        cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr, int tf32 = 0,
-                       unsigned long long wait_ns = 1000000000ull, int stall = 0);
+                       unsigned long long wait_ns = 1000000000ull, int stall = 0, int splits_per_field = 0,
+                       long long t_field_stride = 0);
 
 // Tensor-core (tcgen05) version of launch_gram3 (sbg_gram_tc.cu): the same
 // S[b1][b2] (b1 <= b2, complex double, accumulated) from split-BF16 (tf32 = 0)
@@ -87,20 +99,25 @@ cudaError_t launch_tc4(const float2* astore, void* bimg, const BGroup* bgroups, 
 // multiple of 64.  *err is set (never cleared) if a bounded wait (wait_ns of
 // the GPU's global timer) expired; stall != 0 withholds its MMA issuer (a
 // host-side test of the timeout path).
+// Slabs of nfld fields as for launch_gram3.
 cudaError_t launch_gram_tc(const float2* a, long long ng, int nb, const float* delta, double* S, int nsingle,
                            int single0, int tf32, int* err, int nsm, unsigned long long wait_ns, int stall,
-                           cudaStream_t st);
+                           cudaStream_t st, int nfld = 1, long long s_stride = 0);
 
 // ---- finalisation ----
 // zeta[o] = sum_{e in [ptr[o], ptr[o+1])} coef[e] * T[idx[e]] (idx < 0: conj of T[-idx-1]).
+// A slab of nfld fields: field f reads T + f t_stride (entries) and writes zeta + f nout.
 cudaError_t launch_couple(const double* T, int complex_t, const int* ptr, const int* idx, const double* coef,
-                          int nout, double* zeta, cudaStream_t st);
+                          int nout, double* zeta, cudaStream_t st, int nfld = 1, long long t_stride = 0);
 // 3PCF from Grams: full: zeta[l][b1][b2] = (-1)^l/sqrt(2l+1) (Re S_l0 + 2 sum_{m>0} Re S_lm);
 // projected: zeta[m][b1][b2] = S_m (complex).  S is [npair][nb][nb][2] with b1 <= b2 filled.
-cudaError_t launch_finish3(const double* S, int full, int lmax, int nb, double* zeta, cudaStream_t st);
+// A slab of nfld fields: field f reads S + f s_stride (doubles) and writes its own zeta block.
+cudaError_t launch_finish3(const double* S, int full, int lmax, int nb, double* zeta, cudaStream_t st, int nfld = 1,
+                           long long s_stride = 0);
 // zeta[i] /= N_gal * prod nbar V_b over the bin indices of output i (Eq. for the normalisation
 // coefficient, Sec. 2.5).  order = 3 or 4; outputs laid out [..][b1][b2]([b3])[ncomp].
+// A slab of nfld fields: field f's outputs follow field f - 1's, its N_gal is acc[2f + 1].
 cudaError_t launch_normalize(double* zeta, long long nouter, int nb, int order, int ncomp, const double* acc,
-                             double ng, const double* vbin_dev, cudaStream_t st);
+                             double ng, const double* vbin_dev, cudaStream_t st, int nfld = 1);
 
 }  // namespace sbg

@@ -168,7 +168,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, const BGroup* __restrict__ bgroups,
            long long img_stride, long long ng, const Tile4* __restrict__ tiles, int ntiles,
            const Row4* __restrict__ rows, const int* __restrict__ slots, int nsingle, int cplx, int nsplit,
-           double* __restrict__ T, int* cnt, int* err_flag, unsigned long long wait_ns, int stall) {
+           double* __restrict__ T, int* cnt, int* err_flag, unsigned long long wait_ns, int stall,
+           int splits_per_field, long long t_field_stride) {
   using C = Cfg<TF>;
   constexpr int kGroups = C::kGroups, kOS = C::kOS, kOpStage = C::kOpStage, kRawPer = C::kRawPer;
   constexpr int kFlush = C::kFlush;
@@ -367,6 +368,8 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
       const Tile4 tl = tiles[it.tile];
       const int N = n_mma(tl, cplx);
       const int nranges = (it.nk + kFlush - 1) / kFlush;
+      // a slab of fields: the x-splits of a field are consecutive, its T follows the previous field's
+      double* Tu = T + (splits_per_field ? (long long)(u / ntiles) / splits_per_field * t_field_stride : 0LL);
       const bool aval = row < tl.nrows;
       // a padding row repeats row 0: its accumulator row is never read out
       const Row4 rw = rows[tl.row0 + (aval ? row : 0)];
@@ -406,9 +409,9 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
               const int c = c0 + e;
               if (cplx) {
                 if ((c >> 1) < tl.ncols)
-                  atomicAdd(&T[(tl.tout + (long long)row * tl.ncols + (c >> 1)) * 2 + (c & 1)], (double)out[e]);
+                  atomicAdd(&Tu[(tl.tout + (long long)row * tl.ncols + (c >> 1)) * 2 + (c & 1)], (double)out[e]);
               } else if (c < tl.ncols) {
-                atomicAdd(&T[tl.tout + (long long)row * tl.ncols + c], (double)out[e]);
+                atomicAdd(&Tu[tl.tout + (long long)row * tl.ncols + c], (double)out[e]);
               }
             }
           }
@@ -598,7 +601,8 @@ cudaError_t launch_tc4_t(const float2* astore, void* bimg, const BGroup* bgroups
                          long long img_stride, const float* delta, long long ng, const Tile4* tiles, int ntiles,
                          const Row4* rows, const int* cols, const int* slots, int nsingle, int complex_out,
                          int nsplit, double* T, int* cnt, int* err, int nsm, cudaStream_t st, cudaEvent_t ev_begin,
-                         cudaEvent_t ev_end, unsigned long long wait_ns, int stall) {
+                         cudaEvent_t ev_end, unsigned long long wait_ns, int stall, int splits_per_field,
+                         long long t_field_stride) {
   constexpr int kAtoms = Cfg<TF>::kAtoms;
   const long long stride = img_stride * kAtoms;  // the tables give BF16 image offsets
   // B images of every K-block, once per field
@@ -625,7 +629,7 @@ cudaError_t launch_tc4_t(const float2* astore, void* bimg, const BGroup* bgroups
   void* args[] = {(void*)&af,    (void*)&bi,      (void*)&bgroups, (void*)&stride,     (void*)&ng,
                   (void*)&tiles, (void*)&ntiles,  (void*)&rows,    (void*)&slots,      (void*)&nsingle,
                   (void*)&ccols, (void*)&nsplit, (void*)&T,  (void*)&cnt,        (void*)&err,
-                  (void*)&wait_ns, (void*)&stall};
+                  (void*)&wait_ns, (void*)&stall, (void*)&splits_per_field, (void*)&t_field_stride};
   if (ev_begin && (e = cudaEventRecord(ev_begin, st)) != cudaSuccess) return e;
   e = cudaLaunchCooperativeKernel((const void*)tc4_kernel<TF>, dim3(grid), dim3(kThreads), args, kSmem, st);
   if (e != cudaSuccess) return e;
@@ -639,16 +643,18 @@ cudaError_t launch_tc4(const float2* astore, void* bimg, const BGroup* bgroups, 
                        long long img_stride, const float* delta, long long ng, const Tile4* tiles, int ntiles,
                        const Row4* rows, const int* cols, const int* slots, int nsingle, int complex_out,
                        int nsplit, double* T, int* cnt, int* err, int nsm, cudaStream_t st, cudaEvent_t ev_begin,
-                       cudaEvent_t ev_end, int tf32, unsigned long long wait_ns, int stall) {
+                       cudaEvent_t ev_end, int tf32, unsigned long long wait_ns, int stall, int splits_per_field,
+                       long long t_field_stride) {
+  if (splits_per_field < 0 || (splits_per_field && nsplit % splits_per_field)) return cudaErrorInvalidValue;
   if (ntiles <= 0) return cudaSuccess;
   if (ng % kKX || nbgroups <= 0 || chunks_per_kb <= 0 || img_stride % 1024) return cudaErrorInvalidValue;
   if (tf32)
     return launch_tc4_t<true>(astore, bimg, bgroups, chunks_per_kb, img_stride, delta, ng, tiles, ntiles, rows, cols,
                               slots, nsingle, complex_out, nsplit, T, cnt, err, nsm, st, ev_begin, ev_end, wait_ns,
-                              stall);
+                              stall, splits_per_field, t_field_stride);
   return launch_tc4_t<false>(astore, bimg, bgroups, chunks_per_kb, img_stride, delta, ng, tiles, ntiles, rows, cols,
                              slots, nsingle, complex_out, nsplit, T, cnt, err, nsm, st, ev_begin, ev_end, wait_ns,
-                             stall);
+                             stall, splits_per_field, t_field_stride);
 }
 
 }  // namespace sbg
