@@ -438,6 +438,7 @@ def run_gpu(args):
                                                 "peak_source": osrc},
                                    "headline_speedup_over_it": oms / step_ms})
         out["compare_cufft"] = cufft_compare(args.grid, conv_ms)
+    out["autotune"] = sbg.sbg_autotune_report(ctx.h)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = oracle_sample(field, edges)
         out["cpu_baseline"].pop("seconds_per_field", None)

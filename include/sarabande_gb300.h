@@ -230,6 +230,25 @@ sbg_status sbg_projected_slices(sbg_context* ctx, const void* cube, sbg_dtype dt
                                 const double* edges, int nbins, int mmax, sbg_precision prec, unsigned flags,
                                 double* zeta3, double* zeta4);
 
+/* The launch choices the context's autotuner has made so far, one
+ * "key=choice" line each.  The first call of a geometry measures, with CUDA
+ * events on the context's stream, the candidates of each choice and keeps the
+ * fastest for the life of the context:
+ *   fft/N/sign/load/axis : lines per CTA of a strided FFT pass (0 the default,
+ *                          1 half of it, 2 twice it);
+ *   tc4/..., tc4slab/... : x-splits per tile (per field of a slab) of the
+ *                          tensor-core 4PCF contraction, among the three that
+ *                          fill the SMs' waves best.
+ * text: out, up to len bytes including a NUL (may be NULL); *needed (may be
+ * NULL) receives the length of the whole report plus one.
+ * Errors: SBG_ERR_INVALID_ARG for a NULL ctx. */
+sbg_status sbg_autotune_report(const sbg_context* ctx, char* text, size_t len, size_t* needed);
+
+/* Turn the autotuner of ctx on (enable = 1, the default) or off (0: every
+ * launch takes its default shape, and the choices made so far are dropped).
+ * Errors: SBG_ERR_INVALID_ARG for a NULL ctx or enable not 0 / 1. */
+sbg_status sbg_set_autotune(sbg_context* ctx, int enable);
+
 /* Device times (ms, CUDA events) of the stages of the last measurement call:
  * [0] upload+preprocess, [1] forward FFT of delta, [2] kernel spectra (plan),
  * [3] convolutions (inverse FFTs), [4] 3PCF Gram, [5] 4PCF combination,

@@ -185,6 +185,10 @@ struct sbg_context {
   };
   bool defer = false;
   int cur = 0;
+  // autotuner: launch choices measured on their first use, by key
+  std::map<std::string, int> tune;
+  cudaEvent_t tev[2] = {};
+  bool autotune_on = true;
   size_t slot_bytes = 0;
   Pending pend[2];
 };
@@ -852,6 +856,78 @@ sbg_status ensure_tables4(sbg_context* ctx, int dim, int nb, int L, bool tc, boo
 
 void rec(sbg_context* ctx, int i) { cudaEventRecord(ctx->ev[i], ctx->stream); }
 
+// ---------------------------------------------------------------- autotuner --
+// The choice under `key` among `cands`: measured on its first use by running
+// run(c) for every candidate (one warm-up run each, then three rounds in which
+// every candidate runs once, each run timed with CUDA events on the context's
+// stream, so that drifts of clock or memory state fall on all of them), kept
+// for the life of the context.  The first candidate is the default: another
+// must be more than 3% faster in total to be taken.  run(c) must leave the
+// caller's data as it found it (it writes scratch).
+template <class F>
+sbg_status autotune(sbg_context* ctx, const std::string& key, const std::vector<int>& cands, F run, int* choice) {
+  auto it = ctx->tune.find(key);
+  if (it != ctx->tune.end()) {
+    *choice = it->second;
+    return SBG_OK;
+  }
+  if (cands.size() == 1 || !ctx->autotune_on) {
+    *choice = cands[0];  // the default (not recorded: a later enabled call measures)
+    return SBG_OK;
+  }
+  if (!ctx->tev[0]) {
+    CU(cudaEventCreate(&ctx->tev[0]));
+    CU(cudaEventCreate(&ctx->tev[1]));
+  }
+  std::vector<float> total(cands.size(), 0.f);
+  for (size_t i = 0; i < cands.size(); ++i) CU(run(cands[i]));
+  for (int r = 0; r < 3; ++r)
+    for (size_t i = 0; i < cands.size(); ++i) {
+      CU(cudaEventRecord(ctx->tev[0], ctx->stream));
+      CU(run(cands[i]));
+      CU(cudaEventRecord(ctx->tev[1], ctx->stream));
+      CU(cudaEventSynchronize(ctx->tev[1]));
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, ctx->tev[0], ctx->tev[1]));
+      total[i] += ms;
+    }
+  size_t best = 0;
+  for (size_t i = 1; i < cands.size(); ++i)
+    if (total[i] < 0.97f * total[0] && total[i] < total[best]) best = i;
+  ctx->tune[key] = *choice = cands[best];
+  return SBG_OK;
+}
+
+// Lines per CTA of a strided FFT pass (N >= 128): the default, half or twice
+// it, timed on the pass's own input (its whole batch, up to 4 GB of output),
+// writing a scratch buffer; one choice per (N, direction, load, axis).
+sbg_status tune_fft(sbg_context* ctx, int n, FftPass& p) {
+  if (p.inner == 1 || n < 128) return SBG_OK;
+  char key[96];
+  snprintf(key, sizeof key, "fft/%d/%d/%d/%s", n, p.sign, p.load, p.inner == (long long)n * n ? "z" : "y");
+  if (ctx->tune.count(key)) {
+    p.tl = ctx->tune[key];
+    return SBG_OK;
+  }
+  if (!ctx->autotune_on) return SBG_OK;
+  FftPass q = p;
+  q.batch = (int)std::max<long long>(
+      1, std::min<long long>(p.nb_per_field ? p.nb_per_field : p.batch, (4ll << 30) / (q.bstride * 8)));
+  q.nb_per_field = 0;
+  q.shared_stride = 0;
+  q.field_points = 0;
+  if (q.npack) q.npack = std::min(q.npack, 2 * q.batch);
+  void* scratch;
+  ST(buf(ctx, "tune", (size_t)q.batch * (size_t)q.bstride * 8, &scratch));
+  q.out = (float2*)scratch;
+  std::vector<int> cands = {0, 1};
+  if (n <= 512) cands.push_back(2);
+  int tl = 0;
+  ST(autotune(ctx, key, cands, [&](int c) { q.tl = c; return fft_axis_pass(n, q, ctx->stream); }, &tl));
+  p.tl = tl;
+  return SBG_OK;
+}
+
 // -------------------------------------------------------- FFT helpers ----
 // 3D transform in three axis passes; with final_out the last pass writes the
 // blocked coefficient store (singles single0 .. single0 + batch - 1 of nsingle).
@@ -879,12 +955,16 @@ sbg_status fft3(sbg_context* ctx, int n, int sign, int first_load, const void* i
   // every axis, so z-lines outside the (y, x) support and, after that pass,
   // y-lines outside the x support stay zero and are skipped
   if (prune_r >= 0) { p.prune_mode = 1; p.prune_r = prune_r; }
+  ST(tune_fft(ctx, n, p));
   KL(fft_axis_pass(n, p, ctx->stream));
   // y axis
   p.in = out; p.load = LOAD_COMPLEX; p.mul = nullptr; p.shared = nullptr;
   p.outer = n; p.inner = n;
   if (prune_r >= 0) p.prune_mode = 2;
+  p.tl = 0;
+  ST(tune_fft(ctx, n, p));
   KL(fft_axis_pass(n, p, ctx->stream));
+  p.tl = 0;
   // x axis (contiguous)
   p.prune_mode = 0;
   p.outer = (long long)n * n; p.inner = 1;
@@ -920,7 +1000,9 @@ sbg_status fft2(sbg_context* ctx, int n, int sign, int first_load, const void* i
   }
   p.in = in; p.out = out; p.mul = mul; p.shared = shared; p.load = first_load;
   p.outer = 1; p.inner = n;  // y axis
+  ST(tune_fft(ctx, n, p));
   KL(fft_axis_pass(n, p, ctx->stream));
+  p.tl = 0;
   p.in = out; p.load = LOAD_COMPLEX; p.mul = nullptr; p.shared = nullptr;
   p.outer = n; p.inner = 1;  // x axis
   if (final_out) {
@@ -1155,29 +1237,48 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
     if (tc) {
       const int ntl = (int)t.tiles[0].size();
       const long long kblocks = ng / 32;
-      // x-splits per tile: units = ntl * nsplit spread evenly over the CTAs
-      int best = 1;
-      double best_eff = 0.0;
+      // x-splits per tile: units = ntl * nsplit spread over the CTAs; the three
+      // best by their wave fill are timed by the autotuner on the first call
+      std::vector<std::pair<double, int>> fill;
       for (int k = 1; k <= 16 && k <= kblocks; ++k) {
         const long long units = (long long)ntl * k;
         const long long rounds = (units + ctx->nsm - 1) / ctx->nsm;
-        const double eff = (double)units / (double)(rounds * ctx->nsm);
-        if (eff > best_eff + 0.02) { best_eff = eff; best = k; }
+        fill.push_back({(double)units / (double)(rounds * ctx->nsm), k});
+      }
+      std::stable_sort(fill.begin(), fill.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+        return x.first > y.first + 0.02;
+      });
+      std::vector<int> cands;
+      for (size_t i = 0; i < fill.size() && cands.size() < 3; ++i) cands.push_back(fill[i].second);
+      long long epochs = 4;
+      for (int k : cands) {
+        const long long units = (long long)ntl * k;
+        const long long rounds = (units + ctx->nsm - 1) / ctx->nsm;
+        const long long nk_unit = (kblocks + k - 1) / k;
+        epochs = std::max(epochs, rounds * ((nk_unit + kTcEpoch - 1) / kTcEpoch) + 4);
       }
       int* d_cnt;
-      const long long units = (long long)ntl * best;
-      const long long rounds = (units + ctx->nsm - 1) / ctx->nsm;
-      const long long nk_unit = (kblocks + best - 1) / best;
-      const long long epochs = rounds * ((nk_unit + kTcEpoch - 1) / kTcEpoch) + 4;
       ST(buf(ctx, "tccnt", (size_t)epochs * 4, (void**)&d_cnt));
-      CU(cudaMemsetAsync(d_cnt, 0, (size_t)epochs * 4, ctx->stream));
       void* d_bimg;
       ST(buf(ctx, "bimg", (size_t)(ng / 32) * (size_t)t.img_stride * (tf ? 2 : 1), &d_bimg));
+      auto tc4_run = [&](int nsplit, double* T, cudaEvent_t e0, cudaEvent_t e1) -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(d_cnt, 0, (size_t)epochs * 4, ctx->stream);
+        if (e != cudaSuccess) return e;
+        return launch_tc4(d_astore, d_bimg, (const BGroup*)t.d_bgroups.p, (int)t.bgroups.size(), t.chunks_per_kb,
+                          t.img_stride, d_delta, ng, (const Tile4*)t.d_tiles[0].p, ntl, (const Row4*)t.d_rows.p,
+                          (const int*)t.d_cols.p, (const int*)t.d_uniq.p, nsingle, kmode, nsplit, T, d_cnt, d_err,
+                          ctx->nsm, ctx->stream, e0, e1, tf ? 1 : 0, ctx->wait_ns, ctx->stall);
+      };
+      int best = cands[0];
+      if (cands.size() > 1 && !ctx->stall) {
+        char key[160];
+        snprintf(key, sizeof key, "tc4/%d/%d/%d/%d/%d/%d/%d", dim, n, nb, lmax4, (int)prec, odd ? 1 : 0, ntl);
+        double* d_Ts;
+        ST(buf(ctx, "tuneT", (size_t)std::max<long long>(t.tcount, 1) * 8 * (cplx ? 2 : 1), (void**)&d_Ts));
+        ST(autotune(ctx, key, cands, [&](int c) { return tc4_run(c, d_Ts, nullptr, nullptr); }, &best));
+      }
       ctx->nlaunch += 1;  // bimage_kernel
-      KL(launch_tc4(d_astore, d_bimg, (const BGroup*)t.d_bgroups.p, (int)t.bgroups.size(), t.chunks_per_kb,
-                    t.img_stride, d_delta, ng, (const Tile4*)t.d_tiles[0].p, ntl, (const Row4*)t.d_rows.p,
-                    (const int*)t.d_cols.p, (const int*)t.d_uniq.p, nsingle, kmode, best, d_T, d_cnt, d_err,
-                    ctx->nsm, ctx->stream, ctx->kev[0], ctx->kev[1], tf ? 1 : 0, ctx->wait_ns, ctx->stall));
+      KL(tc4_run(best, d_T, ctx->kev[0], ctx->kev[1]));
       ctx->kev_used = true;
     } else {
       const int tcg[3] = {4, 8, 16};
@@ -1413,29 +1514,47 @@ sbg_status measure_slab(sbg_context* ctx, const sbg_field2d* fields, int nfld, i
       const long long fkb = ng / 32;  // K-blocks of one field
       // x-splits per field: a power of two dividing its K-blocks, for the best
       // spread of the units over the CTAs
-      int spf = 1;
-      double best_eff = 0.0;
+      // (the three best by their wave fill are timed by the autotuner on the
+      // first slab of this size)
+      std::vector<std::pair<double, int>> fill;
       for (int k = 1; k <= 16 && k <= fkb; k *= 2) {
         const long long units = (long long)ntl * nfld * k;
         const long long rounds = (units + ctx->nsm - 1) / ctx->nsm;
-        const double eff = (double)units / (double)(rounds * ctx->nsm);
-        if (eff > best_eff + 0.02) { best_eff = eff; spf = k; }
+        fill.push_back({(double)units / (double)(rounds * ctx->nsm), k});
       }
-      const int nsplit = nfld * spf;
-      const long long units = (long long)ntl * nsplit;
-      const long long rounds = (units + ctx->nsm - 1) / ctx->nsm;
-      const long long nk_unit = fkb / spf;
-      const long long epochs = rounds * ((nk_unit + kTcEpoch - 1) / kTcEpoch) + 4;
+      std::stable_sort(fill.begin(), fill.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+        return x.first > y.first + 0.02;
+      });
+      std::vector<int> cands;
+      for (size_t i = 0; i < fill.size() && cands.size() < 3; ++i) cands.push_back(fill[i].second);
+      long long epochs = 4;
+      for (int k : cands) {
+        const long long units = (long long)ntl * nfld * k;
+        const long long rounds = (units + ctx->nsm - 1) / ctx->nsm;
+        epochs = std::max(epochs, rounds * ((fkb / k + kTcEpoch - 1) / kTcEpoch) + 4);
+      }
       int* d_cnt;
       ST(buf(ctx, "tccnt", (size_t)epochs * 4, (void**)&d_cnt));
-      CU(cudaMemsetAsync(d_cnt, 0, (size_t)epochs * 4, st));
       void* d_bimg;
       ST(buf(ctx, "bimg", (size_t)(npts / 32) * (size_t)t.img_stride * (tf32 ? 2 : 1), &d_bimg));
+      auto tc4_run = [&](int spf, double* T, cudaEvent_t e0, cudaEvent_t e1) -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(d_cnt, 0, (size_t)epochs * 4, st);
+        if (e != cudaSuccess) return e;
+        return launch_tc4(d_astore, d_bimg, (const BGroup*)t.d_bgroups.p, (int)t.bgroups.size(), t.chunks_per_kb,
+                          t.img_stride, d_delta, npts, (const Tile4*)t.d_tiles[0].p, ntl, (const Row4*)t.d_rows.p,
+                          (const int*)t.d_cols.p, (const int*)t.d_uniq.p, nsingle, 1, nfld * spf, T, d_cnt, d_err,
+                          ctx->nsm, st, e0, e1, tf32, ctx->wait_ns, ctx->stall, spf, tstride * 2);
+      };
+      int spf = cands[0];
+      if (cands.size() > 1 && !ctx->stall) {
+        char key[160];
+        snprintf(key, sizeof key, "tc4slab/%d/%d/%d/%d/%d/%d", n, nb, mmax, (int)prec, ntl, nfld);
+        double* d_Ts;
+        ST(buf(ctx, "tuneT", (size_t)nfld * tstride * 16, (void**)&d_Ts));
+        ST(autotune(ctx, key, cands, [&](int c) { return tc4_run(c, d_Ts, nullptr, nullptr); }, &spf));
+      }
       ctx->nlaunch += 1;  // bimage_kernel
-      KL(launch_tc4(d_astore, d_bimg, (const BGroup*)t.d_bgroups.p, (int)t.bgroups.size(), t.chunks_per_kb,
-                    t.img_stride, d_delta, npts, (const Tile4*)t.d_tiles[0].p, ntl, (const Row4*)t.d_rows.p,
-                    (const int*)t.d_cols.p, (const int*)t.d_uniq.p, nsingle, 1, nsplit, d_T, d_cnt, d_err, ctx->nsm,
-                    st, ctx->kev[0], ctx->kev[1], tf32, ctx->wait_ns, ctx->stall, spf, tstride * 2));
+      KL(tc4_run(spf, d_T, ctx->kev[0], ctx->kev[1]));
       ctx->kev_used = true;
     } else {
       const int tcg[3] = {4, 8, 16};
@@ -1562,6 +1681,8 @@ void sbg_destroy(sbg_context* ctx) {
     for (int i = 0; i < 2; ++i)
       if (ctx->kevs[k][i]) cudaEventDestroy(ctx->kevs[k][i]);
   }
+  for (int i = 0; i < 2; ++i)
+    if (ctx->tev[i]) cudaEventDestroy(ctx->tev[i]);
   if (ctx->own) cudaStreamDestroy(ctx->own);
   delete ctx;
 }
@@ -1933,6 +2054,27 @@ sbg_status sbg_set_wait_limit(sbg_context* ctx, unsigned long long wait_ns, int 
   if (wait_ns == 0 || (test_stall != 0 && test_stall != 1)) return fail(ctx, SBG_ERR_INVALID_ARG, "bad wait limit");
   ctx->wait_ns = wait_ns;
   ctx->stall = test_stall;
+  return SBG_OK;
+}
+
+sbg_status sbg_set_autotune(sbg_context* ctx, int enable) {
+  if (!ctx) return SBG_ERR_INVALID_ARG;
+  if (enable != 0 && enable != 1) return fail(ctx, SBG_ERR_INVALID_ARG, "enable must be 0 or 1");
+  ctx->autotune_on = enable != 0;
+  if (!ctx->autotune_on) ctx->tune.clear();
+  return SBG_OK;
+}
+
+sbg_status sbg_autotune_report(const sbg_context* ctx, char* text, size_t len, size_t* needed) {
+  if (!ctx) return SBG_ERR_INVALID_ARG;
+  std::string r;
+  for (const auto& kv : ctx->tune) r += kv.first + "=" + std::to_string(kv.second) + "\n";
+  if (needed) *needed = r.size() + 1;
+  if (text && len) {
+    const size_t k = std::min(len - 1, r.size());
+    std::memcpy(text, r.data(), k);
+    text[k] = '\0';
+  }
   return SBG_OK;
 }
 

@@ -59,6 +59,9 @@ struct FftPass {
   int nb_per_field;
   long long shared_stride;
   long long field_points;
+  // Strided passes of N >= 128: lines per CTA, 0 the default, 1 half of it,
+  // 2 twice it (chosen by measurement, see the context's autotuner).
+  int tl;
 };
 
 // Blocked coefficient store (float view): for each 32-point K-block xb and

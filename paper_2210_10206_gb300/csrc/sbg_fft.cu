@@ -117,13 +117,20 @@ template <> struct Plan<256>  { static constexpr int R1 = 16, R2 = 16; };
 template <> struct Plan<512>  { static constexpr int R1 = 16, R2 = 32; };
 template <> struct Plan<1024> { static constexpr int R1 = 32, R2 = 32; };
 
-template <int N, bool CONTIG> struct Geo {
+// Lines per CTA of a strided pass: the default, or (variants 1 and 2, chosen
+// by the context's autotuner) half or twice it.
+template <int N> constexpr int tl_strided_default() { return N >= 1024 ? 8 : (N >= 16 ? 16 : N); }
+template <int N> constexpr int tl_strided(int variant) {
+  return variant == 1 ? tl_strided_default<N>() / 2 : variant == 2 ? 2 * tl_strided_default<N>() : tl_strided_default<N>();
+}
+
+template <int N, bool CONTIG, int TLV = 0> struct Geo {
   static constexpr int R1 = Plan<N>::R1, R2 = Plan<N>::R2;
   static constexpr int T = R1 < R2 ? R1 : R2;            // threads per line
   // lines per CTA; strided passes of N = 1024 take 8 lines (64 B runs) so that a
   // CTA stages 64 KB rather than 128 KB and two CTAs per SM overlap their loads
-  // and stores (at N = 512, 16 lines measured faster)
-  static constexpr int TL = CONTIG ? (N <= 32 ? 8 : 256 / T) : (N >= 1024 ? 8 : (N >= 16 ? 16 : N));
+  // and stores (at N = 512, 16 lines measured faster); TLV selects a variant
+  static constexpr int TL = CONTIG ? (N <= 32 ? 8 : 256 / T) : tl_strided<N>(TLV);
   static constexpr int THREADS = TL * T;
   static constexpr int R2S = CONTIG ? R2 + 1 : R2;       // padded row of Y (contiguous layout)
   static constexpr int LS = CONTIG ? R1 * R2S + 1 : 0;
@@ -133,10 +140,10 @@ template <int N, bool CONTIG> struct Geo {
   }
 };
 
-template <int N, bool CONTIG, int SIGN, int LOAD, int OUTB>
-__global__ void __launch_bounds__(Geo<N, CONTIG>::THREADS)
+template <int N, bool CONTIG, int SIGN, int LOAD, int OUTB, int TLV, bool SLAB>
+__global__ void __launch_bounds__(Geo<N, CONTIG, TLV>::THREADS)
 fft_axis_kernel(FftPass p) {
-  using G = Geo<N, CONTIG>;
+  using G = Geo<N, CONTIG, TLV>;
   constexpr int R1 = G::R1, R2 = G::R2, T = G::T, TL = G::TL;
   extern __shared__ float2 sm[];
   const int t = threadIdx.x;
@@ -144,9 +151,9 @@ fft_axis_kernel(FftPass p) {
   const int l = CONTIG ? (t / T) : (t % TL);
   const long long boff = (long long)blockIdx.y * p.bstride;
   // batch index = field bf x nb_per_field + array bj of that field (a slab of
-  // fields); without nb_per_field every batch is array bj of one field
-  const int bj = p.nb_per_field ? (int)blockIdx.y % p.nb_per_field : (int)blockIdx.y;
-  const long long bf = p.nb_per_field ? (long long)blockIdx.y / p.nb_per_field : 0;
+  // fields, SLAB variants); otherwise every batch is array bj of one field
+  const int bj = SLAB ? (int)blockIdx.y % p.nb_per_field : (int)blockIdx.y;
+  const long long bf = SLAB ? (long long)blockIdx.y / p.nb_per_field : 0;
   const long long moff = (long long)bj * p.bstride;      // factor array of the batch
   const long long soff = bf * p.shared_stride;            // shared array of its field
   const long long fpts = bf * p.field_points;             // its first point in the blocked store
@@ -241,12 +248,12 @@ fft_axis_kernel(FftPass p) {
   }
 }
 
-template <int N, bool CONTIG, int SIGN, int LOAD, int OUTB = 0>
-static cudaError_t launch_t(const FftPass& p, cudaStream_t st) {
-  using G = Geo<N, CONTIG>;
-  auto kern = fft_axis_kernel<N, CONTIG, SIGN, LOAD, OUTB>;
+template <int N, bool CONTIG, int SIGN, int LOAD, int OUTB, int TLV, bool SLAB>
+static cudaError_t launch_s(const FftPass& p, cudaStream_t st) {
+  using G = Geo<N, CONTIG, TLV>;
+  auto kern = fft_axis_kernel<N, CONTIG, SIGN, LOAD, OUTB, TLV, SLAB>;
   {
-    cudaError_t e = ensure_smem_attr<fft_axis_kernel<N, CONTIG, SIGN, LOAD, OUTB>>(G::SMEM);
+    cudaError_t e = ensure_smem_attr<fft_axis_kernel<N, CONTIG, SIGN, LOAD, OUTB, TLV, SLAB>>(G::SMEM);
     if (e != cudaSuccess) return e;
   }
   // contiguous: outer rows grouped by TL; strided: outer * inner lines grouped by TL
@@ -257,6 +264,30 @@ static cudaError_t launch_t(const FftPass& p, cudaStream_t st) {
   dim3 grid((unsigned)blocks, (unsigned)p.batch);
   kern<<<grid, G::THREADS, G::SMEM, st>>>(p);
   return cudaGetLastError();
+}
+
+// Strided passes of N >= 128 take the lines-per-CTA variant p.tl (0 default,
+// 1 half, 2 twice; N = 1024: 0 and 1); the other passes have one variant.
+// Passes that index by field (the product's factors, the blocked-store output)
+// have a slab variant, taken when p.nb_per_field is set; single fields keep
+// the plain index arithmetic (and its registers).
+template <int N, bool CONTIG, int SIGN, int LOAD, int OUTB, int TLV>
+static cudaError_t launch_v(const FftPass& p, cudaStream_t st) {
+  if constexpr (LOAD == LOAD_MUL || LOAD == LOAD_MUL2 || OUTB != 0)
+    if (p.nb_per_field) return launch_s<N, CONTIG, SIGN, LOAD, OUTB, TLV, true>(p, st);
+  return launch_s<N, CONTIG, SIGN, LOAD, OUTB, TLV, false>(p, st);
+}
+
+template <int N, bool CONTIG, int SIGN, int LOAD, int OUTB = 0>
+static cudaError_t launch_t(const FftPass& p, cudaStream_t st) {
+  if constexpr (!CONTIG && N >= 128) {
+    if (p.tl == 1) return launch_v<N, CONTIG, SIGN, LOAD, OUTB, 1>(p, st);
+    // twice the lines at N = 1024 would stage 128 KB per CTA and spill registers
+    if constexpr (N <= 512)
+      if (p.tl == 2) return launch_v<N, CONTIG, SIGN, LOAD, OUTB, 2>(p, st);
+  }
+  if (p.tl < 0 || p.tl > 2) return cudaErrorInvalidValue;
+  return launch_v<N, CONTIG, SIGN, LOAD, OUTB, 0>(p, st);
 }
 
 template <int N>

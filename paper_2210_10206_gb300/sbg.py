@@ -89,6 +89,10 @@ def lib():
         L.sbg_projected3_noalloc.restype = st
         L.sbg_set_wait_limit.argtypes = [vp, ctypes.c_ulonglong, i]
         L.sbg_set_wait_limit.restype = st
+        L.sbg_autotune_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+        L.sbg_autotune_report.restype = st
+        L.sbg_set_autotune.argtypes = [vp, i]
+        L.sbg_set_autotune.restype = st
         _lib = L
     return _lib
 
@@ -112,6 +116,23 @@ def sbg_set_stream(h, stream):
 
 def sbg_set_wait_limit(h, wait_ns, test_stall=0):
     return lib().sbg_set_wait_limit(h, int(wait_ns), int(test_stall))
+
+
+def sbg_set_autotune(h, enable):
+    return lib().sbg_set_autotune(h, int(enable))
+
+
+def sbg_autotune_report(h):
+    """The autotuner's choices so far as a dict key -> choice."""
+    need = ctypes.c_size_t()
+    lib().sbg_autotune_report(h, None, 0, ctypes.byref(need))
+    buf = ctypes.create_string_buffer(need.value)
+    lib().sbg_autotune_report(h, buf, need.value, None)
+    out = {}
+    for line in buf.value.decode().splitlines():
+        k, v = line.rsplit("=", 1)
+        out[k] = int(v)
+    return out
 
 
 def sbg_status_string(s):

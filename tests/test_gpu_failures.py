@@ -69,3 +69,19 @@ def test_budget_exceeded_is_out_of_memory(sbg):
     z3b, _ = ok.full(f, EDGES, lmax3=2)
     assert np.array_equal(z3, z3b) or np.abs(z3b - z3).max() < 1e-12 * np.abs(z3).max()
     ok.close()
+
+
+def test_autotuner_records_its_choices(sbg):
+    # the first call of a geometry measures the launch choices and keeps them
+    f = _field()
+    ctx = sbg.Context(0)
+    ctx.full(f, EDGES, lmax4=2, prec=sbg.SBG_PREC_BF16X3)
+    rep = sbg.sbg_autotune_report(ctx.h)
+    assert any(k.startswith("tc4/") for k in rep), rep
+    assert all(v in (0, 1, 2) for k, v in rep.items() if k.startswith("fft/")), rep
+    g = synth.lognormal_field(3, (128, 128, 128), 1.0, -2.0, dtype=np.float32)
+    ctx.full(g, [2.0, 5.0, 9.0], lmax3=1)
+    rep2 = sbg.sbg_autotune_report(ctx.h)
+    assert any(k.startswith("fft/128/") for k in rep2), rep2   # strided passes of N >= 128
+    assert all(rep2[k] == v for k, v in rep.items())          # earlier choices are kept
+    ctx.close()
