@@ -1186,11 +1186,30 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
     ST(buf(ctx, "err", 16, (void**)&d_err));
     if (!ctx->defer) CU(cudaMemsetAsync(d_err, 0, 16, ctx->stream));
   }
+  // 3D groups without cached spectra: kernel generation fused with the forward
+  // FFT and the spectral product fused between the forward and inverse z
+  // transforms (sbg_fft_fused.cu); the lines of the kernel support are listed
+  // once per call
+  const bool fused = dim == 3 && !cached;
+  int* d_lines = nullptr;
+  int nlines = 0, Rsup = 0;
+  if (fused) {
+    std::vector<int> lines;
+    for (int zi = 0; zi < n; ++zi)
+      for (int yi = 0; yi < n; ++yi) {
+        const double z = zi < n - zi ? zi : zi - n, y = yi < n - yi ? yi : yi - n;
+        if (y * y + z * z <= e2[nb]) lines.push_back(zi * n + yi);
+      }
+    while ((double)(Rsup + 1) * (Rsup + 1) <= e2[nb]) ++Rsup;
+    nlines = (int)lines.size();
+    ST(buf(ctx, "klines", std::max<size_t>(lines.size(), 1) * 4, (void**)&d_lines));
+    if (nlines) CU(cudaMemcpyAsync(d_lines, lines.data(), lines.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+  }
   for (int g = 0; g < ngroups; ++g) {
-    const float2* G;
+    const float2* G = nullptr;
     if (cached) {
       G = (const float2*)ctx->gcache.p + (size_t)g * nb * ng;
-    } else {
+    } else if (!fused) {
       ST(gen_group(g, d_gtmp));
       G = d_gtmp;
     }
@@ -1205,7 +1224,52 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
     const bool m0 = dim == 3 ? g == l0 * (l0 + 1) / 2 : g == 0;
     const int npack = stored && m0 ? nb : 0;
     const int nbatch = npack ? (nb + 1) / 2 : nb;
-    if (dim == 3) {
+    if (fused) {
+      int l = 0;
+      while ((l + 1) * (l + 2) / 2 <= g) ++l;
+      const int m = g - l * (l + 1) / 2;
+      FusedGroup fg{};
+      fg.l = l;
+      fg.m = m;
+      fg.nb = nb;
+      fg.norm_scale = ylm_norm(l, m) * inv_ng;
+      fg.e2 = d_e2;
+      fg.e2nb = e2[nb];
+      fg.lines = d_lines;
+      fg.nlines = nlines;
+      fg.R = Rsup;
+      fg.npack = npack;
+      fg.tw = d_tw;
+      fg.kbuf = d_gtmp;
+      fg.dhat = d_dhat;
+      fg.out = d_group;
+      ctx->nlaunch += 2;  // passes A and B (pass C counted by KL)
+      KL(launch_fused_group(n, fg, ctx->stream));
+      // inverse y and x passes
+      FftPass p{};
+      p.twiddle = d_tw;
+      p.batch = nbatch;
+      p.bstride = ng;
+      p.sign = +1;
+      p.in = d_group;
+      p.out = d_group;
+      p.load = LOAD_COMPLEX;
+      p.outer = n;
+      p.inner = n;
+      ST(tune_fft(ctx, n, p));
+      KL(fft_axis_pass(n, p, ctx->stream));
+      p.tl = 0;
+      p.outer = (long long)n * n;
+      p.inner = 1;
+      if (fin) {
+        p.out = fin;
+        p.out_blocked = npack > 0 ? 2 : 1;
+        p.nsingle = nsingle;
+        p.single0 = g * nb;
+        p.npack = npack;
+      }
+      KL(fft_axis_pass(n, p, ctx->stream));
+    } else if (dim == 3) {
       ST(fft3(ctx, n, +1, LOAD_MUL, nullptr, d_group, G, d_dhat, nbatch, d_tw, fin, nsingle, g * nb, -1, npack));
     } else {
       ST(fft2(ctx, n, +1, LOAD_MUL, nullptr, d_group, G, d_dhat, nbatch, ng, d_tw, fin, nsingle, g * nb, npack));

@@ -1,0 +1,245 @@
+// Kernel generation fused with the forward FFT, and the spectral product fused
+// between the last forward and the first inverse pass, for 3D groups whose
+// kernel spectra are not cached (the kernel spectra of every (l, m) do not fit
+// in HBM, e.g. the 512^3 l <= 10 3PCF): per (l, m) group of nb bins,
+//
+//   pass A (x, contiguous): K^b_lm = conj(Y_lm) Theta_b (Algorithm 1) is
+//       evaluated in FP64 on the fly for the x-lines (z, y) that meet the
+//       kernel support (y^2 + z^2 <= e_nb^2) and transformed along x; no other
+//       line is touched (they are zero);
+//   pass B (y, strided): the planes |z| <= e_nb, reading only the entries of
+//       lines that pass A wrote;
+//   pass C (z, strided): per column, the forward transform along z of every
+//       bin's kernel (reading only the planes pass B wrote), the product with
+//       delta-hat (one read of delta-hat per group, kept in shared memory for
+//       all bins), and the inverse transform along z (Algorithms 3-4: the
+//       convolution a = IFFT(delta-hat x FFT(K)), in the correlation convention
+//       of Eq. almconv: G(k) = sum_r K(r) e^{+i k.r} / N_g);
+//   then the inverse y and x passes of sbg_fft.cu.
+//
+// Compared with generating every spectrum in HBM (memset, kgen3d, three
+// forward passes, three inverse passes) this moves no zero lines and never
+// writes or reads the kernel spectra G.  Real m = 0 arrays are packed two per
+// inverse transform as in the other path (delta-hat (G_2j + i G_2j+1)).
+#include "sbg_fft_core.cuh"
+#include "sbg_kernels.cuh"
+
+namespace sbg {
+
+namespace {
+
+__device__ __forceinline__ int min_img(int i, int n) { return i < n - i ? i : i - n; }
+
+// conj(Y_lm(r_hat)) norm scale at the integer offset (x, y, z), r2 = |r|^2 > 0,
+// in FP64: the reduced associated Legendre recurrence times ((x + i y)/r)^m
+__device__ __noinline__ float2 kernel_value(int l, int m, double norm_scale, int x, int y, int z, double r2) {
+  const double r = sqrt(r2);
+  const double t = z / r;
+  double pmm = (m & 1) ? -1.0 : 1.0;
+  for (int k = 1; k < 2 * m; k += 2) pmm *= k;
+  double p = pmm;
+  if (l > m) {
+    double a = pmm, bb = (2 * m + 1) * t * pmm;
+    for (int ll = m + 2; ll <= l; ++ll) {
+      const double c = ((2 * ll - 1) * t * bb - (ll + m - 1) * a) / (ll - m);
+      a = bb;
+      bb = c;
+    }
+    p = bb;
+  }
+  const double ur = x / r, ui = y / r;
+  double er = 1.0, ei = 0.0;
+  for (int k = 0; k < m; ++k) {
+    const double tr = er * ur - ei * ui;
+    ei = er * ui + ei * ur;
+    er = tr;
+  }
+  const double s = norm_scale * p;
+  return make_float2((float)(s * er), (float)(-s * ei));
+}
+
+// One transform (sign +1) of TL lines of N points, T = min(R1, R2) threads per
+// line, in the two steps of sbg_fft.cu: thread (line l, index j) loads points
+// n = n1 + R1 n2 through ld(n), exchanges through `ex`, and stores k = k2 + R2 k1
+// through st(k, value).  STRIDED: lines adjacent in the thread index (j = t / TL),
+// otherwise points adjacent (j = t % T).  Every thread of the CTA calls it.
+template <int N, int TL, bool STRIDED, class LD, class ST>
+__device__ __forceinline__ void line_fft(float2* ex, const float2* __restrict__ tw, int l, int j, LD ld, ST st) {
+  constexpr int R1 = Plan<N>::R1, R2 = Plan<N>::R2, T = R1 < R2 ? R1 : R2;
+  constexpr int R2S = STRIDED ? R2 : R2 + 1, LS = R1 * R2S + 1;
+  auto sidx = [&](int n1, int k2) { return STRIDED ? (n1 * R2 + k2) * TL + l : l * LS + n1 * R2S + k2; };
+#pragma unroll
+  for (int q = 0; q < R1 / T; ++q) {
+    const int n1 = j + T * q;
+    float2 v[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) v[n2] = ld(n1 + R1 * n2);
+    Dft<R2, 1>::run(v);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) ex[sidx(n1, k2)] = k2 ? cmul(v[k2], __ldg(tw + ((n1 * k2) & (N - 1)))) : v[k2];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < R2 / T; ++q) {
+    const int k2 = j + T * q;
+    float2 u[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) u[n1] = ex[sidx(n1, k2)];
+    Dft<R1, 1>::run(u);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) st(k2 + R2 * k1, u[k1]);
+  }
+}
+
+template <int N> struct FusedGeo {
+  static constexpr int T = Plan<N>::R1 < Plan<N>::R2 ? Plan<N>::R1 : Plan<N>::R2;
+  static constexpr int TLA = N <= 32 ? 8 : 256 / T;  // pass A: x-lines per CTA
+  static constexpr int TLS = 8;                      // passes B and C: lines per CTA (adjacent x)
+  static constexpr int LSA = Plan<N>::R1 * (Plan<N>::R2 + 1) + 1;
+  static constexpr int SMEM_A = TLA * LSA * 8;
+  static constexpr int SMEM_B = TLS * N * 8;
+  static constexpr int SMEM_C = 3 * TLS * N * 8;     // exchange, kernel column, delta-hat column
+};
+
+// Pass A: the x-lines (z, y) of `lines` (row index z N + y), bin b = blockIdx.y:
+// generate K^b_lm along x and transform; out[b][z][y][:] for those lines only.
+template <int N>
+__global__ void __launch_bounds__(FusedGeo<N>::TLA * FusedGeo<N>::T)
+kgen_fft_x_kernel(int l, int m, double norm_scale, const double* __restrict__ e2, const int* __restrict__ lines,
+                  int nlines, const float2* __restrict__ tw, float2* __restrict__ out, long long ng) {
+  using G = FusedGeo<N>;
+  extern __shared__ float2 ex[];
+  const int t = threadIdx.x, j = t % G::T, li = t / G::T;
+  const int L = blockIdx.x * G::TLA + li;
+  const bool valid = L < nlines;
+  const int row = valid ? lines[L] : 0;
+  const int z = min_img(row / N, N), y = min_img(row % N, N);
+  const double yz2 = (double)y * y + (double)z * z;
+  const int b = blockIdx.y;
+  const double lo = e2[b], hi = e2[b + 1];
+  float2* o = out + (long long)b * ng + (long long)row * N;
+  line_fft<N, G::TLA, false>(
+      ex, tw, li, j,
+      [&](int n) {
+        const int x = min_img(n, N);
+        const double r2 = yz2 + (double)x * x;
+        return (valid && r2 > lo && r2 <= hi) ? kernel_value(l, m, norm_scale, x, y, z, r2) : make_float2(0.f, 0.f);
+      },
+      [&](int k, float2 v) {
+        if (valid) o[k] = v;
+      });
+}
+
+// Pass B: y-lines of the planes |z| <= R (plane p = blockIdx.x / (N / TL), z = p - R),
+// TL adjacent x per CTA, bin blockIdx.y, in place; entry (z, y) is read only if
+// y^2 + z^2 <= e2nb (pass A wrote that x-line).
+template <int N>
+__global__ void __launch_bounds__(FusedGeo<N>::TLS * FusedGeo<N>::T)
+disk_fft_y_kernel(double e2nb, int R, const float2* __restrict__ tw, float2* __restrict__ buf, long long ng) {
+  using G = FusedGeo<N>;
+  extern __shared__ float2 ex[];
+  const int t = threadIdx.x, j = t / G::TLS, li = t % G::TLS;
+  const int xg = blockIdx.x % (N / G::TLS), p = blockIdx.x / (N / G::TLS);
+  const int z = p - R, zi = z < 0 ? z + N : z;
+  const int x = xg * G::TLS + li;
+  float2* col = buf + (long long)blockIdx.y * ng + (long long)zi * N * N + x;
+  const double z2 = (double)z * z;
+  line_fft<N, G::TLS, true>(
+      ex, tw, li, j,
+      [&](int n) {
+        const int y = min_img(n, N);
+        return ((double)y * y + z2 <= e2nb) ? col[(long long)n * N] : make_float2(0.f, 0.f);
+      },
+      [&](int k, float2 v) { col[(long long)k * N] = v; });
+}
+
+// Pass C: columns (y, x0 .. x0 + TL - 1) along z, every bin of the group: forward
+// transform of the kernel column (planes z^2 <= e2nb only), times delta-hat, inverse
+// transform, to out.  npack > 0: real arrays packed two per transform, output j
+// holding delta-hat (G_2j + i G_2j+1) (G_2j+1 taken as 0 past npack).
+template <int N>
+__global__ void __launch_bounds__(FusedGeo<N>::TLS * FusedGeo<N>::T)
+fused_fft_z_kernel(double e2nb, int nb, int npack, const float2* __restrict__ tw, const float2* __restrict__ kin,
+                   const float2* __restrict__ dhat, float2* __restrict__ out, long long ng) {
+  using G = FusedGeo<N>;
+  constexpr int TL = G::TLS;
+  extern __shared__ float2 smem[];
+  float2* ex = smem;
+  float2* C = smem + TL * N;   // the kernel column's spectrum, [k][line]
+  float2* D = C + TL * N;      // delta-hat, [k][line]
+  const int t = threadIdx.x, j = t / TL, li = t % TL;
+  const int xg = blockIdx.x % (N / TL), yy = blockIdx.x / (N / TL);
+  const long long cbase = (long long)yy * N + (long long)xg * TL;  // (0, y, x0)
+  for (int i = t; i < N * TL; i += blockDim.x) {
+    const int k = i / TL, c = i % TL;
+    D[i] = __ldg(dhat + (long long)k * N * N + cbase + c);
+  }
+  const int nout = npack ? (npack + 1) / 2 : nb;
+  for (int o = 0; o < nout; ++o) {
+    const int nsrc = npack ? (2 * o + 1 < npack ? 2 : 1) : 1;
+    for (int s = 0; s < nsrc; ++s) {
+      const int b = npack ? 2 * o + s : o;
+      const float2* col = kin + (long long)b * ng + cbase + li;
+      __syncthreads();  // the exchange buffer and C are free
+      line_fft<N, TL, true>(
+          ex, tw, li, j,
+          [&](int n) {
+            const int z = min_img(n, N);
+            return ((double)z * z <= e2nb) ? col[(long long)n * N * N] : make_float2(0.f, 0.f);
+          },
+          [&](int k, float2 v) {
+            if (s == 0) {
+              C[k * TL + li] = v;
+            } else {  // C += i v
+              const float2 c = C[k * TL + li];
+              C[k * TL + li] = make_float2(c.x - v.y, c.y + v.x);
+            }
+          });
+    }
+    __syncthreads();
+    float2* oc = out + (long long)o * ng + cbase + li;
+    line_fft<N, TL, true>(
+        ex, tw, li, j, [&](int n) { return cmul(C[n * TL + li], D[n * TL + li]); },
+        [&](int k, float2 v) { oc[(long long)k * N * N] = v; });
+  }
+}
+
+template <int N>
+cudaError_t launch_n(const FusedGroup& g, cudaStream_t st) {
+  using G = FusedGeo<N>;
+  cudaError_t e;
+  if ((e = ensure_smem_attr<kgen_fft_x_kernel<N>>(G::SMEM_A)) != cudaSuccess) return e;
+  if ((e = ensure_smem_attr<disk_fft_y_kernel<N>>(G::SMEM_B)) != cudaSuccess) return e;
+  if ((e = ensure_smem_attr<fused_fft_z_kernel<N>>(G::SMEM_C)) != cudaSuccess) return e;
+  const long long ng = (long long)N * N * N;
+  if (g.nlines > 0) {
+    dim3 ga((unsigned)((g.nlines + G::TLA - 1) / G::TLA), (unsigned)g.nb);
+    kgen_fft_x_kernel<N><<<ga, G::TLA * G::T, G::SMEM_A, st>>>(g.l, g.m, g.norm_scale, g.e2, g.lines, g.nlines, g.tw,
+                                                               g.kbuf, ng);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    dim3 gb((unsigned)((2 * g.R + 1) * (N / G::TLS)), (unsigned)g.nb);
+    disk_fft_y_kernel<N><<<gb, G::TLS * G::T, G::SMEM_B, st>>>(g.e2nb, g.R, g.tw, g.kbuf, ng);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  fused_fft_z_kernel<N><<<(unsigned)(N * (N / G::TLS)), G::TLS * G::T, G::SMEM_C, st>>>(
+      g.e2nb, g.nb, g.npack, g.tw, g.kbuf, g.dhat, g.out, ng);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_fused_group(int n, const FusedGroup& g, cudaStream_t st) {
+  if (g.nb < 1 || g.R < 0 || 2 * g.R + 1 > n || (g.npack && (g.npack > g.nb))) return cudaErrorInvalidValue;
+  switch (n) {
+    case 8: return launch_n<8>(g, st);
+    case 16: return launch_n<16>(g, st);
+    case 32: return launch_n<32>(g, st);
+    case 64: return launch_n<64>(g, st);
+    case 128: return launch_n<128>(g, st);
+    case 256: return launch_n<256>(g, st);
+    case 512: return launch_n<512>(g, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sbg

@@ -104,6 +104,29 @@ cudaError_t launch_gram_tc(const float2* a, long long ng, int nb, const float* d
                            int single0, int tf32, int* err, int nsm, unsigned long long wait_ns, int stall,
                            cudaStream_t st, int nfld = 1, long long s_stride = 0);
 
+// ---- kernel generation fused with the FFT (sbg_fft_fused.cu) ----
+// One (l, m) group of nb bins of a 3D grid of side n whose kernel spectra are
+// not cached: pass A generates conj(Y_lm) Theta_b * norm_scale on the `lines`
+// (z n + y rows whose y^2 + z^2 <= e2nb) and transforms them along x into kbuf
+// ([nb][n^3]); pass B transforms the planes |z| <= R along y in place; pass C
+// transforms every column along z, multiplies by dhat and transforms back
+// along z into out ([nb or (npack + 1) / 2][n^3]).  The inverse y and x passes
+// follow (fft_axis_pass).
+struct FusedGroup {
+  int l, m, nb;
+  double norm_scale;     // sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) / N_g
+  const double* e2;      // device, nb + 1 snapped squared edges
+  double e2nb;           // e2[nb] on the host
+  const int* lines;      // device
+  int nlines, R;         // R = max |z| of the support
+  int npack;             // > 0: real arrays packed two per transform
+  const float2* tw;
+  float2* kbuf;
+  const float2* dhat;
+  float2* out;
+};
+cudaError_t launch_fused_group(int n, const FusedGroup& g, cudaStream_t st);
+
 // ---- finalisation ----
 // zeta[o] = sum_{e in [ptr[o], ptr[o+1])} coef[e] * T[idx[e]] (idx < 0: conj of T[-idx-1]).
 // A slab of nfld fields: field f reads T + f t_stride (entries) and writes zeta + f nout.
