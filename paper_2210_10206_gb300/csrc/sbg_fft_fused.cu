@@ -94,10 +94,11 @@ __device__ __forceinline__ void line_fft(float2* ex, const float2* __restrict__ 
 template <int N> struct FusedGeo {
   static constexpr int T = Plan<N>::R1 < Plan<N>::R2 ? Plan<N>::R1 : Plan<N>::R2;
   static constexpr int TLA = N <= 32 ? 8 : 256 / T;  // pass A: x-lines per CTA
-  static constexpr int TLS = 8;                      // passes B and C: lines per CTA (adjacent x)
+  static constexpr int TLB = N >= 16 ? 16 : 8;       // pass B: lines per CTA (adjacent x; 128-byte runs)
+  static constexpr int TLS = 8;                      // pass C: lines per CTA (adjacent x)
   static constexpr int LSA = Plan<N>::R1 * (Plan<N>::R2 + 1) + 1;
   static constexpr int SMEM_A = TLA * LSA * 8;
-  static constexpr int SMEM_B = TLS * N * 8;
+  static constexpr int SMEM_B = TLB * N * 8;
   static constexpr int SMEM_C = 3 * TLS * N * 8;     // exchange, kernel column, delta-hat column
 };
 
@@ -130,21 +131,21 @@ kgen_fft_x_kernel(int l, int m, double norm_scale, const double* __restrict__ e2
       });
 }
 
-// Pass B: y-lines of the planes |z| <= R (plane p = blockIdx.x / (N / TL), z = p - R),
-// TL adjacent x per CTA, bin blockIdx.y, in place; entry (z, y) is read only if
+// Pass B: y-lines of the planes |z| <= R (plane p = blockIdx.x / (N / TLB), z = p - R),
+// TLB adjacent x per CTA, bin blockIdx.y, in place; entry (z, y) is read only if
 // y^2 + z^2 <= e2nb (pass A wrote that x-line).
 template <int N>
-__global__ void __launch_bounds__(FusedGeo<N>::TLS * FusedGeo<N>::T)
+__global__ void __launch_bounds__(FusedGeo<N>::TLB * FusedGeo<N>::T)
 disk_fft_y_kernel(double e2nb, int R, const float2* __restrict__ tw, float2* __restrict__ buf, long long ng) {
   using G = FusedGeo<N>;
   extern __shared__ float2 ex[];
-  const int t = threadIdx.x, j = t / G::TLS, li = t % G::TLS;
-  const int xg = blockIdx.x % (N / G::TLS), p = blockIdx.x / (N / G::TLS);
+  const int t = threadIdx.x, j = t / G::TLB, li = t % G::TLB;
+  const int xg = blockIdx.x % (N / G::TLB), p = blockIdx.x / (N / G::TLB);
   const int z = p - R, zi = z < 0 ? z + N : z;
-  const int x = xg * G::TLS + li;
+  const int x = xg * G::TLB + li;
   float2* col = buf + (long long)blockIdx.y * ng + (long long)zi * N * N + x;
   const double z2 = (double)z * z;
-  line_fft<N, G::TLS, true>(
+  line_fft<N, G::TLB, true>(
       ex, tw, li, j,
       [&](int n) {
         const int y = min_img(n, N);
@@ -153,13 +154,22 @@ disk_fft_y_kernel(double e2nb, int R, const float2* __restrict__ tw, float2* __r
       [&](int k, float2 v) { col[(long long)k * N] = v; });
 }
 
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 // Pass C: columns (y, x0 .. x0 + TL - 1) along z, every bin of the group: forward
-// transform of the kernel column (planes z^2 <= e2nb only), times delta-hat, inverse
+// transform of the kernel column (planes |z| <= R only), times delta-hat, inverse
 // transform, to out.  npack > 0: real arrays packed two per transform, output j
-// holding delta-hat (G_2j + i G_2j+1) (G_2j+1 taken as 0 past npack).
+// holding delta-hat (G_2j + i G_2j+1) (G_2j+1 taken as 0 past npack).  The 2R + 1
+// support rows of bin b + 1 are copied (cp.async) into one of two staging buffers
+// while bin b is transformed.
 template <int N>
 __global__ void __launch_bounds__(FusedGeo<N>::TLS * FusedGeo<N>::T)
-fused_fft_z_kernel(double e2nb, int nb, int npack, const float2* __restrict__ tw, const float2* __restrict__ kin,
+fused_fft_z_kernel(int R, int nb, int npack, const float2* __restrict__ tw, const float2* __restrict__ kin,
                    const float2* __restrict__ dhat, float2* __restrict__ out, long long ng) {
   using G = FusedGeo<N>;
   constexpr int TL = G::TLS;
@@ -167,35 +177,51 @@ fused_fft_z_kernel(double e2nb, int nb, int npack, const float2* __restrict__ tw
   float2* ex = smem;
   float2* C = smem + TL * N;   // the kernel column's spectrum, [k][line]
   float2* D = C + TL * N;      // delta-hat, [k][line]
+  float2* stg = D + TL * N;    // two staging buffers of the support rows, [2][2R + 1][line]
+  const int rows = 2 * R + 1;
   const int t = threadIdx.x, j = t / TL, li = t % TL;
   const int xg = blockIdx.x % (N / TL), yy = blockIdx.x / (N / TL);
   const long long cbase = (long long)yy * N + (long long)xg * TL;  // (0, y, x0)
+  // rows z = -R .. R of bin b into staging buffer b & 1 (TL x 8 bytes = TL / 2 chunks per row)
+  auto prefetch = [&](int b) {
+    float2* dst = stg + (b & 1) * rows * TL;
+    const float2* src = kin + (long long)b * ng + cbase;
+    for (int c = t; c < rows * (TL / 2); c += blockDim.x) {
+      const int r = c / (TL / 2), q = c % (TL / 2);
+      const int z = r - R, zi = z < 0 ? z + N : z;
+      cp_async16(dst + r * TL + 2 * q, src + (long long)zi * N * N + 2 * q);
+    }
+    cp_async_commit();
+  };
+  prefetch(0);
   for (int i = t; i < N * TL; i += blockDim.x) {
     const int k = i / TL, c = i % TL;
     D[i] = __ldg(dhat + (long long)k * N * N + cbase + c);
   }
-  const int nout = npack ? (npack + 1) / 2 : nb;
-  for (int o = 0; o < nout; ++o) {
-    const int nsrc = npack ? (2 * o + 1 < npack ? 2 : 1) : 1;
-    for (int s = 0; s < nsrc; ++s) {
-      const int b = npack ? 2 * o + s : o;
-      const float2* col = kin + (long long)b * ng + cbase + li;
-      __syncthreads();  // the exchange buffer and C are free
-      line_fft<N, TL, true>(
-          ex, tw, li, j,
-          [&](int n) {
-            const int z = min_img(n, N);
-            return ((double)z * z <= e2nb) ? col[(long long)n * N * N] : make_float2(0.f, 0.f);
-          },
-          [&](int k, float2 v) {
-            if (s == 0) {
-              C[k * TL + li] = v;
-            } else {  // C += i v
-              const float2 c = C[k * TL + li];
-              C[k * TL + li] = make_float2(c.x - v.y, c.y + v.x);
-            }
-          });
-    }
+  for (int b = 0; b < nb; ++b) {
+    const int o = npack ? b / 2 : b;
+    const int s = npack ? b % 2 : 0;
+    if (b + 1 < nb) prefetch(b + 1);
+    else cp_async_commit();  // an empty group keeps the wait count uniform
+    cp_async_wait1();         // bin b's rows have landed (this thread's copies)
+    __syncthreads();          // ... everyone's; the exchange buffer and C are free
+    const float2* sb = stg + (b & 1) * rows * TL;
+    line_fft<N, TL, true>(
+        ex, tw, li, j,
+        [&](int n) {
+          const int z = min_img(n, N);
+          return (z >= -R && z <= R) ? sb[(z + R) * TL + li] : make_float2(0.f, 0.f);
+        },
+        [&](int k, float2 v) {
+          if (s == 0) {
+            C[k * TL + li] = v;
+          } else {  // C += i v
+            const float2 c = C[k * TL + li];
+            C[k * TL + li] = make_float2(c.x - v.y, c.y + v.x);
+          }
+        });
+    const bool last = !npack || s == 1 || b == nb - 1;
+    if (!last) continue;
     __syncthreads();
     float2* oc = out + (long long)o * ng + cbase + li;
     line_fft<N, TL, true>(
@@ -210,19 +236,20 @@ cudaError_t launch_n(const FusedGroup& g, cudaStream_t st) {
   cudaError_t e;
   if ((e = ensure_smem_attr<kgen_fft_x_kernel<N>>(G::SMEM_A)) != cudaSuccess) return e;
   if ((e = ensure_smem_attr<disk_fft_y_kernel<N>>(G::SMEM_B)) != cudaSuccess) return e;
-  if ((e = ensure_smem_attr<fused_fft_z_kernel<N>>(G::SMEM_C)) != cudaSuccess) return e;
+  if ((e = ensure_smem_attr<fused_fft_z_kernel<N>>(G::SMEM_C + 2 * N * G::TLS * 8)) != cudaSuccess) return e;
   const long long ng = (long long)N * N * N;
   if (g.nlines > 0) {
     dim3 ga((unsigned)((g.nlines + G::TLA - 1) / G::TLA), (unsigned)g.nb);
     kgen_fft_x_kernel<N><<<ga, G::TLA * G::T, G::SMEM_A, st>>>(g.l, g.m, g.norm_scale, g.e2, g.lines, g.nlines, g.tw,
                                                                g.kbuf, ng);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    dim3 gb((unsigned)((2 * g.R + 1) * (N / G::TLS)), (unsigned)g.nb);
-    disk_fft_y_kernel<N><<<gb, G::TLS * G::T, G::SMEM_B, st>>>(g.e2nb, g.R, g.tw, g.kbuf, ng);
+    dim3 gb((unsigned)((2 * g.R + 1) * (N / G::TLB)), (unsigned)g.nb);
+    disk_fft_y_kernel<N><<<gb, G::TLB * G::T, G::SMEM_B, st>>>(g.e2nb, g.R, g.tw, g.kbuf, ng);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  fused_fft_z_kernel<N><<<(unsigned)(N * (N / G::TLS)), G::TLS * G::T, G::SMEM_C, st>>>(
-      g.e2nb, g.nb, g.npack, g.tw, g.kbuf, g.dhat, g.out, ng);
+  const int smem_c = G::SMEM_C + 2 * (2 * g.R + 1) * G::TLS * 8;
+  fused_fft_z_kernel<N><<<(unsigned)(N * (N / G::TLS)), G::TLS * G::T, smem_c, st>>>(
+      g.R, g.nb, g.npack, g.tw, g.kbuf, g.dhat, g.out, ng);
   return cudaGetLastError();
 }
 
