@@ -52,11 +52,26 @@ fft_axis_kernel(FftPass p) {
   const int t = threadIdx.x;
   const int j = CONTIG ? (t % T) : (t / TL);
   const int l = CONTIG ? (t / T) : (t % TL);
-  const long long boff = (long long)blockIdx.y * p.bstride;
+  // Passes with the spectral product take the arrays of one field in the
+  // fastest grid index: the CTAs of one line group run together, so the
+  // field's delta-hat lines come from HBM once and then from L2 for the other
+  // arrays (delta-hat of a 256^3 field is larger than L2).  Other passes: line
+  // group blockIdx.x of batch blockIdx.y.
+  constexpr bool kInter = LOAD == LOAD_MUL || LOAD == LOAD_MUL2;
+  unsigned tile = blockIdx.x;
+  int bat = (int)blockIdx.y;
+  if (kInter) {
+    const unsigned nbpf = SLAB ? (unsigned)p.nb_per_field : (unsigned)p.batch;
+    const unsigned ntile = (unsigned)(p.outer * (p.inner / TL));
+    const unsigned r = blockIdx.x / nbpf;
+    tile = r % ntile;
+    bat = (int)((r / ntile) * nbpf + blockIdx.x % nbpf);
+  }
+  const long long boff = (long long)bat * p.bstride;
   // batch index = field bf x nb_per_field + array bj of that field (a slab of
   // fields, SLAB variants); otherwise every batch is array bj of one field
-  const int bj = SLAB ? (int)blockIdx.y % p.nb_per_field : (int)blockIdx.y;
-  const long long bf = SLAB ? (long long)blockIdx.y / p.nb_per_field : 0;
+  const int bj = SLAB ? bat % p.nb_per_field : bat;
+  const long long bf = SLAB ? (long long)bat / p.nb_per_field : 0;
   const long long moff = (long long)bj * p.bstride;      // factor array of the batch
   const long long soff = bf * p.shared_stride;            // shared array of its field
   const long long fpts = bf * p.field_points;             // its first point in the blocked store
@@ -64,12 +79,12 @@ fft_axis_kernel(FftPass p) {
   long long base;    // element index of point n = 0 of this thread's line
   long long estride; // element stride along the line
   if (CONTIG) {
-    base = ((long long)blockIdx.x * TL + l) * N;
+    base = ((long long)tile * TL + l) * N;
     estride = 1;
   } else {
     const long long tiles = p.inner / TL;
-    const long long o = blockIdx.x / tiles;
-    const long long i0 = (blockIdx.x % tiles) * TL;
+    const long long o = tile / tiles;
+    const long long i0 = (tile % tiles) * TL;
     if (p.prune_mode) {
       // the whole CTA leaves together: the test depends on blockIdx only
       const long long x0 = p.prune_mode == 1 ? i0 % N : i0;
@@ -165,6 +180,11 @@ static cudaError_t launch_s(const FftPass& p, cudaStream_t st) {
   if (p.nb_per_field < 0 || (p.nb_per_field && p.batch % p.nb_per_field)) return cudaErrorInvalidValue;
   if (CONTIG ? (p.outer % G::TL) : (p.inner % G::TL)) return cudaErrorInvalidValue;
   dim3 grid((unsigned)blocks, (unsigned)p.batch);
+  if constexpr (LOAD == LOAD_MUL || LOAD == LOAD_MUL2) {
+    // one grid index over (field, line group, array of the field)
+    if (blocks * p.batch > 0x7fffffffLL) return cudaErrorInvalidValue;
+    grid = dim3((unsigned)(blocks * p.batch), 1u);
+  }
   kern<<<grid, G::THREADS, G::SMEM, st>>>(p);
   return cudaGetLastError();
 }

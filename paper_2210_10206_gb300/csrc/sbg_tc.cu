@@ -4,8 +4,9 @@
 //     D[r][c] = sum_x Re( P_r(x) * delta(x) a_c(x) ),   P_r = f1 f2
 // (Eq. mu of Sec. 2.3 / Eq. proj_4pcf_coeff of Sec. 2.4 before the coupling
 // contraction).  As a real GEMM over K = 64 per 32-point K-block:
-// A[r] = (Re P(x0..x31), Im P(x0..x31)), B[c] = (Re(delta a), -Im(delta a)); 2D adds
-// the column (Im(delta a), Re(delta a)) for Im.  Each operand is split into
+// A[r] = (Re P, Im P), B[c] = (Re(delta a), -Im(delta a)) over the block's 32
+// points (split BF16: Re and Im of points 8q..8q+7 in turn; split TF32: all
+// Re, then all Im); 2D adds the column (Im(delta a), Re(delta a)) for Im.  Each operand is split into
 // bf16 hi + lo and D += Ahi Bhi + Ahi Blo + Alo Bhi (three products summed in
 // TMEM).  The row signs (-1)^m of a_{l,-m} are applied in the FP64
 // coupling step, not here.
@@ -481,16 +482,18 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
             tmem_st8_nw(acol + 64 + 8 * cq, lr);   // lo, real parts
             tmem_st8_nw(acol + 96 + 8 * cq, li);   // lo, imaginary parts
           } else {
-            uint32_t hr[4], lr[4], hi[4], li[4];
+            // A K order: per 8 points (Re x0..x7, Im x0..x7), two bf16 per
+            // column: hi in columns [8 cq, 8 cq + 8), lo 32 columns further,
+            // one 8-column store each (half the store instructions of four
+            // 4-column stores, which contend less with the MMAs' reads)
+            uint32_t h[8], lw[8];
 #pragma unroll
             for (int p2 = 0; p2 < 4; ++p2) {
-              split_pair(prs[p2], hr[p2], lr[p2]);
-              split_pair(pis[p2], hi[p2], li[p2]);
+              split_pair(prs[p2], h[p2], lw[p2]);
+              split_pair(pis[p2], h[4 + p2], lw[4 + p2]);
             }
-            tmem_st4_nw(acol + 4 * cq, hr[0], hr[1], hr[2], hr[3]);        // hi, real parts
-            tmem_st4_nw(acol + 16 + 4 * cq, hi[0], hi[1], hi[2], hi[3]);   // hi, imaginary parts
-            tmem_st4_nw(acol + 32 + 4 * cq, lr[0], lr[1], lr[2], lr[3]);   // lo, real parts
-            tmem_st4_nw(acol + 48 + 4 * cq, li[0], li[1], li[2], li[3]);   // lo, imaginary parts
+            tmem_st8u_nw(acol + 8 * cq, h);
+            tmem_st8u_nw(acol + 32 + 8 * cq, lw);
           }
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -551,8 +554,11 @@ __global__ void bimage_kernel(const float* __restrict__ astore, const float* __r
     const BGroup bg = groups[g];
     const int c = r / (8 * kAtoms), j = r % (8 * kAtoms);
     const int atom = j >> 3, jj = j & 7;
-    const int k0 = TF ? 32 * atom + 4 * jj : 8 * jj;  // first K value of the chunk
-    const int second = k0 >> 5, p0 = k0 & 31;          // K 32..63: the second half of the row
+    // the chunk's 8 (BF16) or 4 (TF32) K values: points p0.. of the real
+    // (second = 0) or imaginary (second = 1) form.  BF16 K order: per 8 points
+    // (Re, then Im), as the producers lay out A; TF32: Re x0..x31, Im x0..x31.
+    const int second = TF ? atom : (jj & 1);
+    const int p0 = TF ? 4 * jj : 8 * (jj >> 1);
     // columns of the (Im v, Re v) form: the odd ones of a complex group, and
     // every one of an imaginary-only group (cplx = 2)
     const bool imcol = cplx == 2 || (cplx == 1 && (c & 1));
