@@ -921,7 +921,10 @@ sbg_status tune_fft(sbg_context* ctx, int n, FftPass& p) {
   ST(buf(ctx, "tune", (size_t)q.batch * (size_t)q.bstride * 8, &scratch));
   q.out = (float2*)scratch;
   std::vector<int> cands = {0, 1};
-  if (n <= 512) cands.push_back(2);
+  // twice the lines: up to N = 512, and N = 256 for the product passes (which
+  // also stage delta-hat in shared memory)
+  const bool product = p.load == LOAD_MUL || p.load == LOAD_MUL2;
+  if (n <= (product ? 256 : 512)) cands.push_back(2);
   int tl = 0;
   ST(autotune(ctx, key, cands, [&](int c) { q.tl = c; return fft_axis_pass(n, q, ctx->stream); }, &tl));
   p.tl = tl;

@@ -52,30 +52,20 @@ fft_axis_kernel(FftPass p) {
   const int t = threadIdx.x;
   const int j = CONTIG ? (t % T) : (t / TL);
   const int l = CONTIG ? (t / T) : (t % TL);
-  // Passes with the spectral product take the arrays of one field in the
-  // fastest grid index: the CTAs of one line group run together, so the
-  // field's delta-hat lines come from HBM once and then from L2 for the other
-  // arrays (delta-hat of a 256^3 field is larger than L2).  Other passes: line
-  // group blockIdx.x of batch blockIdx.y.
-  constexpr bool kInter = LOAD == LOAD_MUL || LOAD == LOAD_MUL2;
+  // Passes with the spectral product run every array of a field in one CTA:
+  // the field's delta-hat values of the CTA's lines are read from HBM once
+  // (into a thread-private shared-memory slot) and reused for each array.
+  // Other passes: line group blockIdx.x of batch blockIdx.y.
+  constexpr bool kBins = LOAD == LOAD_MUL || LOAD == LOAD_MUL2;
+  const int nbpf = kBins ? (SLAB ? p.nb_per_field : p.batch) : 1;
   unsigned tile = blockIdx.x;
-  int bat = (int)blockIdx.y;
-  if (kInter) {
-    const unsigned nbpf = SLAB ? (unsigned)p.nb_per_field : (unsigned)p.batch;
+  long long bf0 = 0;  // field of the CTA (kBins)
+  if (kBins) {
     const unsigned ntile = (unsigned)(p.outer * (p.inner / TL));
-    const unsigned r = blockIdx.x / nbpf;
-    tile = r % ntile;
-    bat = (int)((r / ntile) * nbpf + blockIdx.x % nbpf);
+    tile = blockIdx.x % ntile;
+    bf0 = blockIdx.x / ntile;
   }
-  const long long boff = (long long)bat * p.bstride;
-  // batch index = field bf x nb_per_field + array bj of that field (a slab of
-  // fields, SLAB variants); otherwise every batch is array bj of one field
-  const int bj = SLAB ? bat % p.nb_per_field : bat;
-  const long long bf = SLAB ? (long long)bat / p.nb_per_field : 0;
-  const long long moff = (long long)bj * p.bstride;      // factor array of the batch
-  const long long soff = bf * p.shared_stride;            // shared array of its field
-  const long long fpts = bf * p.field_points;             // its first point in the blocked store
-
+  float2* sdh = sm + G::SMEM / 8;  // kBins: delta-hat slots, R1 / T x R2 per thread
   long long base;    // element index of point n = 0 of this thread's line
   long long estride; // element stride along the line
   if (CONTIG) {
@@ -99,6 +89,33 @@ fft_axis_kernel(FftPass p) {
     estride = p.inner;
   }
 
+  if (kBins) {
+    // this thread's delta-hat values (the points it loads in step 1), once
+    const long long soff = (SLAB ? bf0 : 0LL) * p.shared_stride;
+#pragma unroll
+    for (int q = 0; q < R1 / T; ++q)
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2)
+        sdh[(q * R2 + n2) * G::THREADS + t] = __ldg(p.shared + soff + base + (long long)(j + T * q + R1 * n2) * estride);
+  }
+#pragma unroll 1
+  for (int it = 0; it < nbpf; ++it) {
+  const int bat = kBins ? (int)(bf0 * nbpf + it) : (int)blockIdx.y;
+  const long long boff = (long long)bat * p.bstride;
+  // batch index = field bf x nb_per_field + array bj of that field (a slab of
+  // fields, SLAB variants); otherwise every batch is array bj of one field
+  const int bj = SLAB ? bat % p.nb_per_field : bat;
+  const long long bf = SLAB ? (long long)bat / p.nb_per_field : 0;
+  const long long moff = (long long)bj * p.bstride;      // factor array of the batch
+  const long long soff = bf * p.shared_stride;            // shared array of its field
+  const long long fpts = bf * p.field_points;             // its first point in the blocked store
+  if (it > 0) __syncthreads();  // the previous array's step 2 has read the exchange buffer
+  // opaque per array: the compiler would otherwise keep every point's address
+  // and twiddle in registers across the loop (over 160 per thread)
+  const float2* twid = p.twiddle;
+  long long lbase = base;
+  if (kBins) asm volatile("" : "+l"(twid), "+l"(lbase));
+
   // ---- step 1: R1/T DFTs of length R2 per thread ----
 #pragma unroll
   for (int q = 0; q < R1 / T; ++q) {
@@ -106,20 +123,23 @@ fft_axis_kernel(FftPass p) {
     float2 v[R2];
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) {
-      const long long e = base + (long long)(n1 + R1 * n2) * estride;
+      const long long e = lbase + (long long)(n1 + R1 * n2) * estride;
       if (LOAD == LOAD_REAL) {
         v[n2] = make_float2(__ldg(reinterpret_cast<const float*>(p.in) + boff + e), 0.0f);
-      } else if (LOAD == LOAD_MUL) {
-        v[n2] = cmul(__ldg(p.shared + soff + e), __ldg(p.mul + moff + e));
-      } else if (LOAD == LOAD_MUL2) {
-        const long long ia = 2 * moff + e;
-        float2 f = __ldg(p.mul + ia);
-        if (2 * bj + 1 < p.npack) {
-          const float2 g = __ldg(p.mul + ia + p.bstride);
-          f.x -= g.y;
-          f.y += g.x;
+      } else if (LOAD == LOAD_MUL || LOAD == LOAD_MUL2) {
+        const float2 dh = sdh[(q * R2 + n2) * G::THREADS + t];
+        if (LOAD == LOAD_MUL) {
+          v[n2] = cmul(dh, __ldg(p.mul + moff + e));
+        } else {
+          const long long ia = 2 * moff + e;
+          float2 f = __ldg(p.mul + ia);
+          if (2 * bj + 1 < p.npack) {
+            const float2 g = __ldg(p.mul + ia + p.bstride);
+            f.x -= g.y;
+            f.y += g.x;
+          }
+          v[n2] = cmul(dh, f);
         }
-        v[n2] = cmul(__ldg(p.shared + soff + e), f);
       } else {
         v[n2] = __ldg(reinterpret_cast<const float2*>(p.in) + boff + e);
       }
@@ -127,7 +147,7 @@ fft_axis_kernel(FftPass p) {
     Dft<R2, SIGN>::run(v);
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) {
-      float2 w = __ldg(p.twiddle + ((n1 * k2) & (N - 1)));
+      float2 w = __ldg(twid + ((n1 * k2) & (N - 1)));
       if (SIGN < 0) w.y = -w.y;
       sm[G::sidx(l, n1, k2)] = (k2 == 0) ? v[k2] : cmul(v[k2], w);
     }
@@ -144,7 +164,7 @@ fft_axis_kernel(FftPass p) {
     Dft<R1, SIGN>::run(u);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
-      const long long e = base + (long long)(k2 + R2 * k1) * estride;
+      const long long e = lbase + (long long)(k2 + R2 * k1) * estride;
       if (OUTB == 1) {
         float* o = reinterpret_cast<float*>(p.out) + blocked_re(fpts + e, p.single0 + bj, p.nsingle);
         o[0] = u[k1].x;
@@ -164,14 +184,17 @@ fft_axis_kernel(FftPass p) {
       }
     }
   }
+  }  // arrays of the CTA
 }
 
 template <int N, bool CONTIG, int SIGN, int LOAD, int OUTB, int TLV, bool SLAB>
 static cudaError_t launch_s(const FftPass& p, cudaStream_t st) {
   using G = Geo<N, CONTIG, TLV>;
   auto kern = fft_axis_kernel<N, CONTIG, SIGN, LOAD, OUTB, TLV, SLAB>;
+  constexpr bool kBins = LOAD == LOAD_MUL || LOAD == LOAD_MUL2;
+  constexpr int smem = kBins ? 2 * G::SMEM : G::SMEM;  // + the delta-hat slots
   {
-    cudaError_t e = ensure_smem_attr<fft_axis_kernel<N, CONTIG, SIGN, LOAD, OUTB, TLV, SLAB>>(G::SMEM);
+    cudaError_t e = ensure_smem_attr<fft_axis_kernel<N, CONTIG, SIGN, LOAD, OUTB, TLV, SLAB>>(smem);
     if (e != cudaSuccess) return e;
   }
   // contiguous: outer rows grouped by TL; strided: outer * inner lines grouped by TL
@@ -180,12 +203,13 @@ static cudaError_t launch_s(const FftPass& p, cudaStream_t st) {
   if (p.nb_per_field < 0 || (p.nb_per_field && p.batch % p.nb_per_field)) return cudaErrorInvalidValue;
   if (CONTIG ? (p.outer % G::TL) : (p.inner % G::TL)) return cudaErrorInvalidValue;
   dim3 grid((unsigned)blocks, (unsigned)p.batch);
-  if constexpr (LOAD == LOAD_MUL || LOAD == LOAD_MUL2) {
-    // one grid index over (field, line group, array of the field)
-    if (blocks * p.batch > 0x7fffffffLL) return cudaErrorInvalidValue;
-    grid = dim3((unsigned)(blocks * p.batch), 1u);
+  if constexpr (kBins) {
+    // one CTA per (field, line group), looping over the field's arrays
+    const long long nfld = SLAB ? p.batch / p.nb_per_field : 1;
+    if (blocks * nfld > 0x7fffffffLL) return cudaErrorInvalidValue;
+    grid = dim3((unsigned)(blocks * nfld), 1u);
   }
-  kern<<<grid, G::THREADS, G::SMEM, st>>>(p);
+  kern<<<grid, G::THREADS, smem, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -205,8 +229,10 @@ template <int N, bool CONTIG, int SIGN, int LOAD, int OUTB = 0>
 static cudaError_t launch_t(const FftPass& p, cudaStream_t st) {
   if constexpr (!CONTIG && N >= 128) {
     if (p.tl == 1) return launch_v<N, CONTIG, SIGN, LOAD, OUTB, 1>(p, st);
-    // twice the lines at N = 1024 would stage 128 KB per CTA and spill registers
-    if constexpr (N <= 512)
+    // twice the lines at N = 1024 would stage 128 KB per CTA and spill registers;
+    // product passes stage their delta-hat values as well (256 KB at N = 512)
+    constexpr bool kBins = LOAD == LOAD_MUL || LOAD == LOAD_MUL2;
+    if constexpr (N <= 512 && !(kBins && N >= 512))
       if (p.tl == 2) return launch_v<N, CONTIG, SIGN, LOAD, OUTB, 2>(p, st);
   }
   if (p.tl < 0 || p.tl > 2) return cudaErrorInvalidValue;
