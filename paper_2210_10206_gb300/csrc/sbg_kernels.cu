@@ -3,6 +3,7 @@
 #include <algorithm>
 
 #include "sbg_kernels.cuh"
+#include "sbg_tcgen05.cuh"
 
 namespace sbg {
 
@@ -159,14 +160,35 @@ cudaError_t launch_kgen2d(int n, int m, const double* e2_dev, int nb, double sca
 }
 
 // ------------------------------------------------------------------ gram3 --
-// One CTA sweeps a contiguous x-range in chunks of 64 points staged in shared
-// memory (the next chunk is fetched into registers while the current one is
-// summed); thread p owns bin pair p (b1 <= b2), accumulating FP32 over each
-// chunk and FP64 across chunks.
-constexpr int kGramChunk = 64;
+// S[b1][b2] += sum_x delta(x) a_b1(x) conj(a_b2(x)) for b1 <= b2 (Algorithm 5's
+// delta-weighted products of the coefficients, Eq. zeta3 of Sec. 2.2).  One CTA
+// sweeps a contiguous x-range in chunks of 128 points, staged in shared memory
+// by cp.async through a ring of kGramStages chunks (three in flight while one
+// is summed).  The bins form blocks of 4; warp w owns the block pairs (I <= J)
+// w, w + warps, ... and its lanes take every 32nd point, so each lane holds a
+// 4 x 4 tile of pair sums (16 complex, FP32 with packed f32x2 FMAs: 8 operand
+// loads per 16 products).  Every kGramFlush chunks a warp reduce-scatter hands
+// lane k the warp's total of tile element k, which it adds to an FP64
+// register; at the end each lane adds its element to S (FP64 atomics).
+constexpr int kGramChunk = 128;
 constexpr int kGramMaxNb = 32;
+constexpr int kGramFlush = 4;   // chunks (16 points per lane) between FP64 flushes
+constexpr int kGramStages = 4;  // ring of staged chunks
 
-__global__ void __launch_bounds__(256) gram3_kernel(const float2* __restrict__ a, long long ng, int nb,
+__device__ __forceinline__ void gram_cp(void* dst, const void* src, bool ok, int bytes) {
+  // bytes 4 / 8 / 16; a copy outside the range reads nothing and writes zeros
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  const int n = ok ? bytes : 0;
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+
+template <int KP>  // block pairs per warp
+__global__ void __launch_bounds__(512, KP == 1 ? 2 : 1) gram3_kernel(const float2* __restrict__ a, long long ng, int nb,
                                                     const float* __restrict__ delta, double* __restrict__ S,
                                                     int nsingle, int single0, long long s_stride) {
   // field f = blockIdx.y of a slab: its bins follow field f - 1's (group
@@ -175,85 +197,195 @@ __global__ void __launch_bounds__(256) gram3_kernel(const float2* __restrict__ a
   if (!nsingle) a += (long long)blockIdx.y * nb * ng;
   delta += fx;
   S += (long long)blockIdx.y * s_stride;
-  // rows padded by one element: the threads of a warp read the same point of
-  // up to 20 different bins, which a 512-byte row stride would put in one bank
-  __shared__ float2 sa[kGramMaxNb][kGramChunk + 1];
-  __shared__ float sd[kGramChunk];
-  const int npairs = nb * (nb + 1) / 2;
-  // pair index -> (b1, b2)
-  int b1 = -1, b2 = -1;
-  for (int p = threadIdx.x, c = 0, i = 0; i < nb && b1 < 0; ++i) {
-    if (p < c + (nb - i)) { b1 = i; b2 = i + (p - c); }
-    c += nb - i;
-  }
-  const long long per = (ng + gridDim.x - 1) / gridDim.x;
+  const int nbb = (nb + 3) / 4, nrow = 4 * nbb;
+  // stage: nrow rows of kGramChunk (re, im), then kGramChunk deltas; rows nb ..
+  // of the last block stay zero
+  extern __shared__ __align__(16) uint8_t gsm[];
+  const int stage_bytes = nrow * kGramChunk * 8 + kGramChunk * 4;
+  auto srow = [&](int st, int b) { return reinterpret_cast<float2*>(gsm + st * stage_bytes) + b * kGramChunk; };
+  auto sdel = [&](int st) { return reinterpret_cast<float*>(gsm + st * stage_bytes + nrow * kGramChunk * 8); };
+  const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // x-ranges of whole chunks: x0 and x1 are multiples of 4 (ng is), so the
+  // 16-byte copies below never straddle x1
+  const long long per = ((ng + gridDim.x - 1) / gridDim.x + kGramChunk - 1) / kGramChunk * kGramChunk;
   const long long x0 = blockIdx.x * per, x1 = min(ng, x0 + per);
-  double accr = 0.0, acci = 0.0;
-  // the next chunk is fetched into registers while the current one is summed
-  constexpr int kPer = kGramMaxNb * kGramChunk / 256;
-  float2 pre[kPer];
-  float pd = 0.f;
-  auto fetch = [&](long long xc) {
-    const int cnt = (int)min((long long)kGramChunk, x1 - xc);
+  const int nch = x0 < x1 ? (int)((x1 - x0 + kGramChunk - 1) / kGramChunk) : 0;
+  for (int i = threadIdx.x; i < kGramStages * (nrow - nb) * kGramChunk; i += blockDim.x) {
+    const int st = i / ((nrow - nb) * kGramChunk), r = i % ((nrow - nb) * kGramChunk);
+    srow(st, nb + r / kGramChunk)[r % kGramChunk] = make_float2(0.f, 0.f);
+  }
+  // this warp's block pairs
+  int bI[KP], bJ[KP];
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const int i = threadIdx.x + 256 * k;
-      const int b = i / kGramChunk, xx = i % kGramChunk;
-      float2 v = make_float2(0.f, 0.f);
-      if (b < nb && xx < cnt) {
-        const long long x = xc + xx;
-        if (nsingle) {
-          const float* f = reinterpret_cast<const float*>(a) + blocked_re(fx + x, single0 + b, nsingle);
-          v = make_float2(f[0], f[32]);
-        } else {
-          v = a[(long long)b * ng + x];
+  for (int k = 0; k < KP; ++k) {
+    int q = warp + warps * k;
+    bI[k] = -1;
+    bJ[k] = -1;
+    for (int i = 0; i < nbb && q >= 0; ++i) {
+      if (q < nbb - i) {
+        bI[k] = i;
+        bJ[k] = i + q;
+      }
+      q -= nbb - i;
+    }
+  }
+  // copies of chunk c into stage c % kGramStages, one commit group per chunk
+  auto issue = [&](int c) {
+    if (c < nch) {
+      const int st = c % kGramStages;
+      const long long xc = x0 + (long long)c * kGramChunk;
+      if (nsingle) {
+        // blocked store: per 32-point block 32 Re then 32 Im floats of a single
+        for (int i = threadIdx.x; i < nb * kGramChunk; i += blockDim.x) {
+          const int b = i / kGramChunk, xx = i % kGramChunk;
+          const long long x = xc + xx;
+          const bool ok = x < x1;
+          const float* f = reinterpret_cast<const float*>(a) + blocked_re(fx + (ok ? x : x0), single0 + b, nsingle);
+          float2* dst = srow(st, b) + xx;
+          gram_cp(&dst->x, f, ok, 4);
+          gram_cp(&dst->y, f + 32, ok, 4);
+        }
+      } else {
+        // group buffer: bins of ng complex, two points per 16-byte copy
+        for (int i = threadIdx.x; i < nb * kGramChunk / 2; i += blockDim.x) {
+          const int b = i / (kGramChunk / 2), xx = 2 * (i % (kGramChunk / 2));
+          const long long x = xc + xx;  // even, and x1 is a multiple of 4
+          const bool ok = x < x1;
+          gram_cp(srow(st, b) + xx, a + (long long)b * ng + (ok ? x : x0), ok, 16);
         }
       }
-      pre[k] = v;
-    }
-    pd = threadIdx.x < cnt ? delta[xc + threadIdx.x] : 0.f;
-  };
-  if (x0 < x1) fetch(x0);
-  for (long long xc = x0; xc < x1; xc += kGramChunk) {
-    __syncthreads();  // the previous chunk has been summed
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const int i = threadIdx.x + 256 * k;
-      if (i < nb * kGramChunk) sa[i / kGramChunk][i % kGramChunk] = pre[k];
-    }
-    if (threadIdx.x < kGramChunk) sd[threadIdx.x] = pd;
-    __syncthreads();
-    if (xc + kGramChunk < x1) fetch(xc + kGramChunk);
-    if (threadIdx.x < npairs) {
-      float sr = 0.f, si = 0.f;
-#pragma unroll 8
-      for (int xx = 0; xx < kGramChunk; ++xx) {
-        const float2 u = sa[b1][xx], v = sa[b2][xx];
-        const float d = sd[xx];
-        // delta * u * conj(v)
-        sr += d * (u.x * v.x + u.y * v.y);
-        si += d * (u.y * v.x - u.x * v.y);
+      for (int i = threadIdx.x; i < kGramChunk / 4; i += blockDim.x) {
+        const long long x = xc + 4 * i;
+        const bool ok = x < x1;
+        gram_cp(sdel(st) + 4 * i, delta + (ok ? x : x0), ok, 16);
       }
-      accr += sr;
-      acci += si;
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  uint64_t acc[KP][16];
+  double dacc[KP];
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    dacc[k] = 0.0;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc[k][e] = 0ull;
+  }
+  // lane k of the warp gets the warp's total of element k of the 32 floats
+  auto flush = [&]() {
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      float v[32];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        upk(acc[k][e], v[2 * e], v[2 * e + 1]);
+        acc[k][e] = 0ull;
+      }
+#pragma unroll
+      for (int lv = 0; lv < 5; ++lv) {
+        const int o = 16 >> lv;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int e = 0; e < o; ++e) {
+          const float send = up ? v[e] : v[e + o];
+          const float keep = up ? v[e + o] : v[e];
+          v[e] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+      }
+      dacc[k] += (double)v[0];
+    }
+  };
+  __syncthreads();  // zero rows written
+#pragma unroll
+  for (int c = 0; c < kGramStages - 1; ++c) issue(c);
+  int nflush = 0;
+  for (int c = 0; c < nch; ++c) {
+    asm volatile("cp.async.wait_group %0;" ::"n"(kGramStages - 2) : "memory");
+    __syncthreads();  // chunk c landed for every thread; chunk c - 1 has been summed
+    issue(c + kGramStages - 1);
+    const int st = c % kGramStages;
+    const float* sd = sdel(st);
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      if (bI[k] < 0) continue;
+      const float2* s1 = srow(st, 4 * bI[k]);
+      const float2* s2 = srow(st, 4 * bJ[k]);
+#pragma unroll 2
+      for (int m = 0; m < kGramChunk / 32; ++m) {
+        const int xx = lane + 32 * m;
+        const float d = sd[xx];
+        const uint64_t dd = pk(d, d);
+        uint64_t w[4], wr[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float2 u = s1[i * kGramChunk + xx];
+          w[i] = mul2(pk(u.x, u.y), dd);    // delta u
+          wr[i] = mul2(pk(u.y, -u.x), dd);  // delta (Im u, -Re u)
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float2 v = s2[j * kGramChunk + xx];
+          const uint64_t vr = pk(v.x, v.x), vi = pk(v.y, v.y);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            // (Re, Im) of delta u conj(v) = w Re v + (Im w, -Re w) Im v
+            acc[k][4 * i + j] = fma2(w[i], vr, acc[k][4 * i + j]);
+            acc[k][4 * i + j] = fma2(wr[i], vi, acc[k][4 * i + j]);
+          }
+        }
+      }
+    }
+    if (++nflush == kGramFlush) {
+      flush();
+      nflush = 0;
     }
   }
-  if (threadIdx.x < npairs) {
-    atomicAdd(&S[((long long)b1 * nb + b2) * 2 + 0], accr);
-    atomicAdd(&S[((long long)b1 * nb + b2) * 2 + 1], acci);
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  if (nflush) flush();
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    if (bI[k] < 0) continue;
+    // lane = 2 (4 i + j) + component
+    const int e = lane >> 1, c = lane & 1, i = e >> 2, j = e & 3;
+    const int b1 = 4 * bI[k] + i, b2 = 4 * bJ[k] + j;
+    if (b1 <= b2 && b2 < nb) atomicAdd(&S[((long long)b1 * nb + b2) * 2 + c], dacc[k]);
   }
+}
+
+template <int KP>
+static cudaError_t gram3_launch(dim3 grid, int threads, int smem, cudaStream_t st, const float2* a, long long ng,
+                                int nb, const float* delta, double* S, int nsingle, int single0, long long s_stride) {
+  // the attribute is set once per device: to the largest stage ring (32 bins)
+  constexpr int kMaxSmem = kGramStages * (kGramMaxNb * kGramChunk * 8 + kGramChunk * 4);
+  if (smem > kMaxSmem) return cudaErrorInvalidValue;
+  cudaError_t e = ensure_smem_attr<gram3_kernel<KP>>(kMaxSmem);
+  if (e != cudaSuccess) return e;
+  gram3_kernel<KP><<<grid, threads, smem, st>>>(a, ng, nb, delta, S, nsingle, single0, s_stride);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gram3(const float2* a, long long ng, int nb, const float* delta, double* S, int nsingle,
                          int single0, cudaStream_t st, int nfld, long long s_stride) {
-  if (nb > kGramMaxNb || nb * (nb + 1) / 2 > 256 || nfld < 1 || nfld > 65535) return cudaErrorInvalidValue;
-  // about 4 chunks per CTA on small grids (a CTA's chunks run one after another),
-  // at most 8 CTAs per SM of cross-CTA FP64 atomics on large ones
+  if (nb < 1 || nb > kGramMaxNb || nfld < 1 || nfld > 65535) return cudaErrorInvalidValue;
+  // 16-byte copies of the group buffer and of delta
+  if (!nsingle && (((uintptr_t)a & 15) || (ng & 1))) return cudaErrorInvalidValue;
+  if (((uintptr_t)delta & 15) || (ng & 3)) return cudaErrorInvalidValue;
+  const int nbb = (nb + 3) / 4, nbp = nbb * (nbb + 1) / 2;
+  const int kp = (nbp + 15) / 16;  // block pairs per warp, at most 16 warps
+  const int threads = std::max(32 * ((nbp + kp - 1) / kp), 128);
+  const int smem = kGramStages * (4 * nbb * kGramChunk * 8 + kGramChunk * 4);
+  // chunks per CTA: about 4 on small grids; on large ones as many CTAs as fit
   long long blocks = (ng + 4 * kGramChunk - 1) / (4 * kGramChunk);
-  const long long cap = std::max<long long>(1, ((long long)device_sms() * 8 + nfld - 1) / nfld);
+  int per_sm = 1;
+  cudaError_t e = kp == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gram3_kernel<1>, threads, smem)
+                : kp == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gram3_kernel<2>, threads, smem)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gram3_kernel<3>, threads, smem);
+  if (e != cudaSuccess) return e;
+  const long long cap = std::max<long long>(1, ((long long)device_sms() * std::max(per_sm, 1) + nfld - 1) / nfld);
   if (blocks > cap) blocks = cap;
-  gram3_kernel<<<dim3((unsigned)blocks, nfld), 256, 0, st>>>(a, ng, nb, delta, S, nsingle, single0, s_stride);
-  return cudaGetLastError();
+  const dim3 grid((unsigned)blocks, nfld);
+  if (kp == 1) return gram3_launch<1>(grid, threads, smem, st, a, ng, nb, delta, S, nsingle, single0, s_stride);
+  if (kp == 2) return gram3_launch<2>(grid, threads, smem, st, a, ng, nb, delta, S, nsingle, single0, s_stride);
+  return gram3_launch<3>(grid, threads, smem, st, a, ng, nb, delta, S, nsingle, single0, s_stride);
 }
 
 // ------------------------------------------------------------------ simt4 --
