@@ -164,14 +164,14 @@ cudaError_t launch_kgen2d(int n, int m, const double* e2_dev, int nb, double sca
 // delta-weighted products of the coefficients, Eq. zeta3 of Sec. 2.2).  One CTA
 // sweeps a contiguous x-range in chunks of 128 points, staged in shared memory
 // by cp.async through a ring of kGramStages chunks (three in flight while one
-// is summed).  The bins form blocks of 4; warp w owns the block pairs (I <= J)
-// w, w + warps, ... and its lanes take every 32nd point, so each lane holds a
-// 4 x 4 tile of pair sums (16 complex, FP32 with packed f32x2 FMAs: 8 operand
-// loads per 16 products).  Every kGramFlush chunks a warp reduce-scatter hands
+// is summed).  The bins (at most 20) form blocks of 4; warp w owns block pair
+// w (I <= J; at most 15) and its lanes take every 32nd point, so each lane
+// holds a 4 x 4 tile of pair sums (16 complex, FP32 with packed f32x2 FMAs: 8
+// operand loads per 16 products).  Every kGramFlush chunks a warp reduce-scatter hands
 // lane k the warp's total of tile element k, which it adds to an FP64
 // register; at the end each lane adds its element to S (FP64 atomics).
 constexpr int kGramChunk = 128;
-constexpr int kGramMaxNb = 32;
+constexpr int kGramMaxNb = 20;
 constexpr int kGramFlush = 4;   // chunks (16 points per lane) between FP64 flushes
 constexpr int kGramStages = 4;  // ring of staged chunks
 
@@ -187,8 +187,7 @@ __device__ __forceinline__ void gram_cp(void* dst, const void* src, bool ok, int
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
 
-template <int KP>  // block pairs per warp
-__global__ void __launch_bounds__(512, KP == 1 ? 2 : 1) gram3_kernel(const float2* __restrict__ a, long long ng, int nb,
+__global__ void __launch_bounds__(512, 2) gram3_kernel(const float2* __restrict__ a, long long ng, int nb,
                                                     const float* __restrict__ delta, double* __restrict__ S,
                                                     int nsingle, int single0, long long s_stride) {
   // field f = blockIdx.y of a slab: its bins follow field f - 1's (group
@@ -204,7 +203,7 @@ __global__ void __launch_bounds__(512, KP == 1 ? 2 : 1) gram3_kernel(const float
   const int stage_bytes = nrow * kGramChunk * 8 + kGramChunk * 4;
   auto srow = [&](int st, int b) { return reinterpret_cast<float2*>(gsm + st * stage_bytes) + b * kGramChunk; };
   auto sdel = [&](int st) { return reinterpret_cast<float*>(gsm + st * stage_bytes + nrow * kGramChunk * 8); };
-  const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // x-ranges of whole chunks: x0 and x1 are multiples of 4 (ng is), so the
   // 16-byte copies below never straddle x1
   const long long per = ((ng + gridDim.x - 1) / gridDim.x + kGramChunk - 1) / kGramChunk * kGramChunk;
@@ -214,20 +213,14 @@ __global__ void __launch_bounds__(512, KP == 1 ? 2 : 1) gram3_kernel(const float
     const int st = i / ((nrow - nb) * kGramChunk), r = i % ((nrow - nb) * kGramChunk);
     srow(st, nb + r / kGramChunk)[r % kGramChunk] = make_float2(0.f, 0.f);
   }
-  // this warp's block pairs
-  int bI[KP], bJ[KP];
-#pragma unroll
-  for (int k = 0; k < KP; ++k) {
-    int q = warp + warps * k;
-    bI[k] = -1;
-    bJ[k] = -1;
-    for (int i = 0; i < nbb && q >= 0; ++i) {
-      if (q < nbb - i) {
-        bI[k] = i;
-        bJ[k] = i + q;
-      }
-      q -= nbb - i;
+  // this warp's block pair (none for warps past the last one)
+  int bI = -1, bJ = -1;
+  for (int i = 0, q = warp; i < nbb && q >= 0; ++i) {
+    if (q < nbb - i) {
+      bI = i;
+      bJ = i + q;
     }
+    q -= nbb - i;
   }
   // copies of chunk c into stage c % kGramStages, one commit group per chunk
   auto issue = [&](int c) {
@@ -262,37 +255,30 @@ __global__ void __launch_bounds__(512, KP == 1 ? 2 : 1) gram3_kernel(const float
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  uint64_t acc[KP][16];
-  double dacc[KP];
+  uint64_t acc[16];
+  double dacc = 0.0;
 #pragma unroll
-  for (int k = 0; k < KP; ++k) {
-    dacc[k] = 0.0;
-#pragma unroll
-    for (int e = 0; e < 16; ++e) acc[k][e] = 0ull;
-  }
+  for (int e = 0; e < 16; ++e) acc[e] = 0ull;
   // lane k of the warp gets the warp's total of element k of the 32 floats
   auto flush = [&]() {
+    float v[32];
 #pragma unroll
-    for (int k = 0; k < KP; ++k) {
-      float v[32];
-#pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        upk(acc[k][e], v[2 * e], v[2 * e + 1]);
-        acc[k][e] = 0ull;
-      }
-#pragma unroll
-      for (int lv = 0; lv < 5; ++lv) {
-        const int o = 16 >> lv;
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int e = 0; e < o; ++e) {
-          const float send = up ? v[e] : v[e + o];
-          const float keep = up ? v[e + o] : v[e];
-          v[e] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
-      }
-      dacc[k] += (double)v[0];
+    for (int e = 0; e < 16; ++e) {
+      upk(acc[e], v[2 * e], v[2 * e + 1]);
+      acc[e] = 0ull;
     }
+#pragma unroll
+    for (int lv = 0; lv < 5; ++lv) {
+      const int o = 16 >> lv;
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int e = 0; e < o; ++e) {
+        const float send = up ? v[e] : v[e + o];
+        const float keep = up ? v[e + o] : v[e];
+        v[e] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    }
+    dacc += (double)v[0];
   };
   __syncthreads();  // zero rows written
 #pragma unroll
@@ -304,11 +290,9 @@ __global__ void __launch_bounds__(512, KP == 1 ? 2 : 1) gram3_kernel(const float
     issue(c + kGramStages - 1);
     const int st = c % kGramStages;
     const float* sd = sdel(st);
-#pragma unroll
-    for (int k = 0; k < KP; ++k) {
-      if (bI[k] < 0) continue;
-      const float2* s1 = srow(st, 4 * bI[k]);
-      const float2* s2 = srow(st, 4 * bJ[k]);
+    if (bI >= 0) {
+      const float2* s1 = srow(st, 4 * bI);
+      const float2* s2 = srow(st, 4 * bJ);
 #pragma unroll 2
       for (int m = 0; m < kGramChunk / 32; ++m) {
         const int xx = lane + 32 * m;
@@ -328,8 +312,8 @@ __global__ void __launch_bounds__(512, KP == 1 ? 2 : 1) gram3_kernel(const float
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             // (Re, Im) of delta u conj(v) = w Re v + (Im w, -Re w) Im v
-            acc[k][4 * i + j] = fma2(w[i], vr, acc[k][4 * i + j]);
-            acc[k][4 * i + j] = fma2(wr[i], vi, acc[k][4 * i + j]);
+            acc[4 * i + j] = fma2(w[i], vr, acc[4 * i + j]);
+            acc[4 * i + j] = fma2(wr[i], vi, acc[4 * i + j]);
           }
         }
       }
@@ -341,26 +325,12 @@ __global__ void __launch_bounds__(512, KP == 1 ? 2 : 1) gram3_kernel(const float
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
   if (nflush) flush();
-#pragma unroll
-  for (int k = 0; k < KP; ++k) {
-    if (bI[k] < 0) continue;
+  if (bI >= 0) {
     // lane = 2 (4 i + j) + component
     const int e = lane >> 1, c = lane & 1, i = e >> 2, j = e & 3;
-    const int b1 = 4 * bI[k] + i, b2 = 4 * bJ[k] + j;
-    if (b1 <= b2 && b2 < nb) atomicAdd(&S[((long long)b1 * nb + b2) * 2 + c], dacc[k]);
+    const int b1 = 4 * bI + i, b2 = 4 * bJ + j;
+    if (b1 <= b2 && b2 < nb) atomicAdd(&S[((long long)b1 * nb + b2) * 2 + c], dacc);
   }
-}
-
-template <int KP>
-static cudaError_t gram3_launch(dim3 grid, int threads, int smem, cudaStream_t st, const float2* a, long long ng,
-                                int nb, const float* delta, double* S, int nsingle, int single0, long long s_stride) {
-  // the attribute is set once per device: to the largest stage ring (32 bins)
-  constexpr int kMaxSmem = kGramStages * (kGramMaxNb * kGramChunk * 8 + kGramChunk * 4);
-  if (smem > kMaxSmem) return cudaErrorInvalidValue;
-  cudaError_t e = ensure_smem_attr<gram3_kernel<KP>>(kMaxSmem);
-  if (e != cudaSuccess) return e;
-  gram3_kernel<KP><<<grid, threads, smem, st>>>(a, ng, nb, delta, S, nsingle, single0, s_stride);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_gram3(const float2* a, long long ng, int nb, const float* delta, double* S, int nsingle,
@@ -370,22 +340,20 @@ cudaError_t launch_gram3(const float2* a, long long ng, int nb, const float* del
   if (!nsingle && (((uintptr_t)a & 15) || (ng & 1))) return cudaErrorInvalidValue;
   if (((uintptr_t)delta & 15) || (ng & 3)) return cudaErrorInvalidValue;
   const int nbb = (nb + 3) / 4, nbp = nbb * (nbb + 1) / 2;
-  const int kp = (nbp + 15) / 16;  // block pairs per warp, at most 16 warps
-  const int threads = std::max(32 * ((nbp + kp - 1) / kp), 128);
+  const int threads = std::max(32 * nbp, 128);  // a warp per block pair, at least 4 to stage
   const int smem = kGramStages * (4 * nbb * kGramChunk * 8 + kGramChunk * 4);
+  // the attribute is set once per device: to the largest stage ring
+  constexpr int kMaxSmem = kGramStages * (4 * ((kGramMaxNb + 3) / 4) * kGramChunk * 8 + kGramChunk * 4);
+  cudaError_t e = ensure_smem_attr<gram3_kernel>(kMaxSmem);
+  if (e != cudaSuccess) return e;
   // chunks per CTA: about 4 on small grids; on large ones as many CTAs as fit
   long long blocks = (ng + 4 * kGramChunk - 1) / (4 * kGramChunk);
   int per_sm = 1;
-  cudaError_t e = kp == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gram3_kernel<1>, threads, smem)
-                : kp == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gram3_kernel<2>, threads, smem)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gram3_kernel<3>, threads, smem);
-  if (e != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gram3_kernel, threads, smem)) != cudaSuccess) return e;
   const long long cap = std::max<long long>(1, ((long long)device_sms() * std::max(per_sm, 1) + nfld - 1) / nfld);
   if (blocks > cap) blocks = cap;
-  const dim3 grid((unsigned)blocks, nfld);
-  if (kp == 1) return gram3_launch<1>(grid, threads, smem, st, a, ng, nb, delta, S, nsingle, single0, s_stride);
-  if (kp == 2) return gram3_launch<2>(grid, threads, smem, st, a, ng, nb, delta, S, nsingle, single0, s_stride);
-  return gram3_launch<3>(grid, threads, smem, st, a, ng, nb, delta, S, nsingle, single0, s_stride);
+  gram3_kernel<<<dim3((unsigned)blocks, nfld), threads, smem, st>>>(a, ng, nb, delta, S, nsingle, single0, s_stride);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ simt4 --
