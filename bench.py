@@ -458,15 +458,19 @@ def run_workload(args):
     prec_name = "bf16x3" if args.prec == "auto" else args.prec
     prec = precs[prec_name]
     ctx = sbg.Context(0)
+    # the batch and slice workloads write into the previous call's result
+    # arrays (out=), as a caller measuring field after field would; their
+    # results are large (the slices' zeta4 is 1.8 GB)
+    prev = [None]
     if args.workload == "batch64":
         members = [synth.batch_member(j) for j in range(64)]
         fields = [f for f, _ in members]
         edges = [e for _, e in members]
-        call = lambda: ctx.projected_batch(fields, edges, 10, 10, prec=prec)
+        call = lambda: ctx.projected_batch(fields, edges, 10, 10, prec=prec, out=prev[0])
     elif args.workload == "slices256":
         d = torch.from_numpy(synth.workload_field("full256")).cuda()
         e = list(synth.edges_log(2.0, 32.0, 10))
-        call = lambda: ctx.projected_slices(d, e, 10, prec=prec)
+        call = lambda: ctx.projected_slices(d, e, 10, prec=prec, out=prev[0])
     elif args.workload == "full128_3pcf":
         w = synth.WORKLOADS["full128"]
         d = torch.from_numpy(synth.workload_field("full128")).cuda()
@@ -488,10 +492,11 @@ def run_workload(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
-        call()
+        res = call()
         e1.record()
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
+        prev[0] = res
     print(json.dumps({"workload": args.workload, "prec": prec_name, "calls": args.calls,
                       "ms_per_call": [round(x, 3) for x in ms],
                       "last_call_stage_ms": [round(float(x), 3) for x in np.asarray(ctx.timings())],

@@ -169,10 +169,8 @@ def sbg_projected_slices(h, cube, edges, mmax, prec, flags, zeta3=None, zeta4=No
     if on_dev:
         flags |= SBG_FIELD_ON_DEVICE
     w = 2 * mmax + 1
-    if (flags & SBG_3PCF) and zeta3 is None:
-        zeta3 = np.zeros((shape[0], mmax + 1, nb, nb, 2))
-    if (flags & SBG_4PCF) and zeta4 is None:
-        zeta4 = np.zeros((shape[0], w, w, nb, nb, nb, 2))
+    zeta3 = _out(zeta3, (shape[0], mmax + 1, nb, nb, 2), "zeta3") if flags & SBG_3PCF else None
+    zeta4 = _out(zeta4, (shape[0], w, w, nb, nb, nb, 2), "zeta4") if flags & SBG_4PCF else None
     shp = (ctypes.c_int64 * 3)(*shape)
     s = lib().sbg_projected_slices(h, ptr, dt, shp, e.ctypes.data, nb, mmax, prec, flags,
                                    zeta3.ctypes.data if zeta3 is not None else None,
@@ -250,16 +248,27 @@ def _edges(edges):
     return np.ascontiguousarray(np.asarray(edges, dtype=np.float64))
 
 
+def _out(a, shape, name):
+    """A result array: a new zeroed one, or the caller's (reused across calls),
+    which must be a writable C-contiguous float64 array of exactly this shape
+    (the library writes every element through its pointer)."""
+    shape = tuple(int(x) for x in shape)
+    if a is None:
+        return np.zeros(shape)
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or a.shape != shape \
+            or not a.flags.c_contiguous or not a.flags.writeable:
+        raise ValueError(f"{name} must be a writable C-contiguous float64 array of shape {shape}")
+    return a
+
+
 def sbg_full(h, field, edges, lmax3, lmax4, prec, flags, zeta3=None, zeta4=None):
     ptr, dt, shape, on_dev, keep = _field_ptr(field)
     e = _edges(edges)
     nb = len(e) - 1
     if on_dev:
         flags |= SBG_FIELD_ON_DEVICE
-    if (flags & SBG_3PCF) and zeta3 is None:
-        zeta3 = np.zeros((lmax3 + 1, nb, nb))
-    if (flags & SBG_4PCF) and zeta4 is None:
-        zeta4 = np.zeros((sbg_lambda_count(lmax4), nb, nb, nb))
+    zeta3 = _out(zeta3, (lmax3 + 1, nb, nb), "zeta3") if flags & SBG_3PCF else None
+    zeta4 = _out(zeta4, (sbg_lambda_count(lmax4), nb, nb, nb), "zeta4") if flags & SBG_4PCF else None
     shp = (ctypes.c_int64 * 3)(*shape) if len(shape) == 3 else (ctypes.c_int64 * 3)(*(list(shape) + [0, 0, 0])[:3])
     s = lib().sbg_full(h, ptr, dt, shp, e.ctypes.data, nb, int(lmax3 or 0), int(lmax4 or 0), prec, flags,
                        zeta3.ctypes.data if zeta3 is not None else None,
@@ -276,8 +285,7 @@ def sbg_full_odd(h, field, edges, lmax4, prec, flags, zeta4_odd=None):
     nb = len(e) - 1
     if on_dev:
         flags |= SBG_FIELD_ON_DEVICE
-    if zeta4_odd is None:
-        zeta4_odd = np.zeros((sbg_lambda_odd_count(lmax4), nb, nb, nb))
+    zeta4_odd = _out(zeta4_odd, (sbg_lambda_odd_count(lmax4), nb, nb, nb), "zeta4_odd")
     shp = (ctypes.c_int64 * 3)(*shape) if len(shape) == 3 else (ctypes.c_int64 * 3)(*(list(shape) + [0, 0, 0])[:3])
     s = lib().sbg_full_odd(h, ptr, dt, shp, e.ctypes.data, nb, int(lmax4), prec, flags, zeta4_odd.ctypes.data)
     del keep
@@ -293,10 +301,8 @@ def sbg_projected(h, field, edges, mmax, prec, flags, zeta3=None, zeta4=None):
     if on_dev:
         flags |= SBG_FIELD_ON_DEVICE
     w = 2 * mmax + 1
-    if (flags & SBG_3PCF) and zeta3 is None:
-        zeta3 = np.zeros((mmax + 1, nb, nb, 2))
-    if (flags & SBG_4PCF) and zeta4 is None:
-        zeta4 = np.zeros((w, w, nb, nb, nb, 2))
+    zeta3 = _out(zeta3, (mmax + 1, nb, nb, 2), "zeta3") if flags & SBG_3PCF else None
+    zeta4 = _out(zeta4, (w, w, nb, nb, nb, 2), "zeta4") if flags & SBG_4PCF else None
     shp = (ctypes.c_int64 * 2)(*(list(shape) + [0, 0])[:2])
     s = lib().sbg_projected(h, ptr, dt, shp, e.ctypes.data, nb, mmax, prec, flags,
                             zeta3.ctypes.data if zeta3 is not None else None,
@@ -307,18 +313,22 @@ def sbg_projected(h, field, edges, mmax, prec, flags, zeta3=None, zeta4=None):
     return zeta3, zeta4
 
 
-def sbg_projected_batch(h, fields, edges_list, nbins, mmax, prec, flags):
+def sbg_projected_batch(h, fields, edges_list, nbins, mmax, prec, flags, outs=None):
+    """outs: None, or one (zeta3, zeta4) pair per field to write into."""
     n = len(fields)
+    if outs is not None and len(outs) != n:
+        raise ValueError("outs must hold one (zeta3, zeta4) pair per field")
     arr = (Field2D * n)()
-    keep, outs = [], []
+    keep, res = [], []
     w = 2 * mmax + 1
     for i, (f, e) in enumerate(zip(fields, edges_list)):
         ptr, dt, shape, on_dev, k = _field_ptr(f)
         ee = _edges(e)
-        z3 = np.zeros((mmax + 1, nbins, nbins, 2)) if flags & SBG_3PCF else None
-        z4 = np.zeros((w, w, nbins, nbins, nbins, 2)) if flags & SBG_4PCF else None
+        o3, o4 = outs[i] if outs is not None else (None, None)
+        z3 = _out(o3, (mmax + 1, nbins, nbins, 2), "zeta3") if flags & SBG_3PCF else None
+        z4 = _out(o4, (w, w, nbins, nbins, nbins, 2), "zeta4") if flags & SBG_4PCF else None
         keep += [k, ee]
-        outs.append((z3, z4))
+        res.append((z3, z4))
         arr[i].field = ptr
         arr[i].dtype = dt
         arr[i].shape[0], arr[i].shape[1] = shape[0], shape[1]
@@ -331,7 +341,7 @@ def sbg_projected_batch(h, fields, edges_list, nbins, mmax, prec, flags):
     del keep
     if s != SBG_OK:
         raise SbgError(s, sbg_last_error(h))
-    return outs
+    return res
 
 
 def sbg_last_timings(h):
@@ -397,37 +407,43 @@ class Context:
         if s != SBG_OK:
             raise SbgError(s, sbg_last_error(self.h))
 
-    def full(self, field, edges, lmax3=None, lmax4=None, prec=SBG_PREC_FP32, flags=SBG_SUBTRACT_MEAN):
+    # out: arrays from an earlier call of the same shapes, written again in
+    # place (no allocation or first-touch page faults per call)
+    def full(self, field, edges, lmax3=None, lmax4=None, prec=SBG_PREC_FP32, flags=SBG_SUBTRACT_MEAN, out=None):
         if lmax3 is not None:
             flags |= SBG_3PCF
         if lmax4 is not None:
             flags |= SBG_4PCF
-        return sbg_full(self.h, field, edges, lmax3, lmax4, prec, flags)
+        z3, z4 = out if out is not None else (None, None)
+        return sbg_full(self.h, field, edges, lmax3, lmax4, prec, flags, z3, z4)
 
     def full_odd(self, field, edges, lmax4, prec=SBG_PREC_FP32, flags=SBG_SUBTRACT_MEAN):
         return sbg_full_odd(self.h, field, edges, lmax4, prec, flags)
 
-    def projected(self, field, edges, mmax, npcf=(3, 4), prec=SBG_PREC_FP32, flags=SBG_SUBTRACT_MEAN):
+    def projected(self, field, edges, mmax, npcf=(3, 4), prec=SBG_PREC_FP32, flags=SBG_SUBTRACT_MEAN, out=None):
         if 3 in npcf:
             flags |= SBG_3PCF
         if 4 in npcf:
             flags |= SBG_4PCF
-        return sbg_projected(self.h, field, edges, mmax, prec, flags)
+        z3, z4 = out if out is not None else (None, None)
+        return sbg_projected(self.h, field, edges, mmax, prec, flags, z3, z4)
 
     def projected_batch(self, fields, edges_list, nbins, mmax, npcf=(3, 4), prec=SBG_PREC_FP32,
-                        flags=SBG_SUBTRACT_MEAN):
+                        flags=SBG_SUBTRACT_MEAN, out=None):
         if 3 in npcf:
             flags |= SBG_3PCF
         if 4 in npcf:
             flags |= SBG_4PCF
-        return sbg_projected_batch(self.h, fields, edges_list, nbins, mmax, prec, flags)
+        return sbg_projected_batch(self.h, fields, edges_list, nbins, mmax, prec, flags, out)
 
-    def projected_slices(self, cube, edges, mmax, npcf=(3, 4), prec=SBG_PREC_FP32, flags=SBG_SUBTRACT_MEAN):
+    def projected_slices(self, cube, edges, mmax, npcf=(3, 4), prec=SBG_PREC_FP32, flags=SBG_SUBTRACT_MEAN,
+                         out=None):
         if 3 in npcf:
             flags |= SBG_3PCF
         if 4 in npcf:
             flags |= SBG_4PCF
-        return sbg_projected_slices(self.h, cube, edges, mmax, prec, flags)
+        z3, z4 = out if out is not None else (None, None)
+        return sbg_projected_slices(self.h, cube, edges, mmax, prec, flags, z3, z4)
 
     def timings(self):
         return sbg_last_timings(self.h)
