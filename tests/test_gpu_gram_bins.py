@@ -62,3 +62,18 @@ def test_projected_gram_bins(ctx, nb):
     assert _err(_cplx(z3), r3) < TOL_FP32
     z3b, _ = ctx.projected(f, edges, 3, npcf=(3, 4))
     assert _err(_cplx(z3b), r3) < TOL_FP32
+
+
+@pytest.mark.parametrize("n,nb", [(128, 20), (256, 10)])
+def test_gram_large_grids(ctx, n, nb):
+    # 3PCF without 4PCF at N = 128 / 256 (groups read from the group buffer at
+    # sizes larger than L2); single entries against the FP64 oracle
+    f = synth.lognormal_field(500 + n, (n, n, n), 1.2, -3.0, cutoff=np.pi / 2, dtype=np.float32)
+    edges = list(np.linspace(2.0, n / 4, nb + 1))
+    z3, _ = ctx.full(f, edges, lmax3=2)
+    d, _ = O.preprocess(f.astype(np.float64))
+    entries = [(0, 0, nb - 1), (1, 2, 3), (2, nb - 1, nb - 1), (2, 1, nb // 2)]
+    want = O.zeta3_full_entries(d, edges, entries)
+    scale = np.abs(z3).max()
+    for (l, b1, b2), w in zip(entries, want):
+        assert abs(z3[l, b1, b2] - w) <= TOL_FP32 * scale, (n, l, b1, b2, z3[l, b1, b2], w)
