@@ -557,6 +557,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
     std::priority_queue<std::pair<double, int>> heap;
     for (int i = 0; i < (int)cands.size(); ++i) heap.push({value(cands[i], cands[i].n), -i});
     std::vector<std::vector<RowKey>> grows(L + 1);
+    std::vector<char> chosen(cands.size(), 0);
     while (left > 0 && !heap.empty()) {
       const auto top = heap.top();
       heap.pop();
@@ -570,14 +571,135 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
       }
       for (int k = c.off; k < c.off + c.n; ++k) done[cov[k]] = 1;
       left -= fresh;
-      grows[c.m3].push_back(c.rk);
+      chosen[-top.second] = 1;
     }
     if (left > 0) return fail(ctx, SBG_ERR_INTERNAL, "4PCF greedy covering left triples uncovered");
-    // rows sharing singles sit together: sorted by the stored index of each single
-    for (auto& g : grows)
+    auto sort_rows = [&](std::vector<RowKey>& g) {
+      // rows sharing singles sit together: sorted by the stored index of each single
       std::sort(g.begin(), g.end(), [&](const RowKey& p, const RowKey& q) {
         return std::make_pair(sidx(p.a1, p.b1), sidx(p.a2, p.b2)) < std::make_pair(sidx(q.a1, q.b1), sidx(q.a2, q.b2));
       });
+    };
+    auto block_rows = [&](int m3) {
+      std::vector<RowKey> g;
+      for (size_t i = 0; i < cands.size(); ++i)
+        if (chosen[i] && cands[i].m3 == m3) g.push_back(cands[i].rk);
+      sort_rows(g);
+      return g;
+    };
+    if (tc) {
+      // Tile trimming: the tensor-core kernel pays per 128-row tile, so a block
+      // whose last tile holds few rows is worth emptying.  Rows of that block
+      // are dropped while every triple that only they cover can be re-covered
+      // by unchosen candidates of other blocks that stay within their tile
+      // counts (the last triple of a row may go to any single as the column,
+      // so coverage moves between blocks); the moves of one attempt are kept
+      // only if the plan's tile count (with the staged-singles limit) drops.
+      std::vector<int> tstart(tid.size() + 1, 0), tcand;
+      for (const Cand& c : cands)
+        for (int k = c.off; k < c.off + c.n; ++k) ++tstart[cov[k] + 1];
+      for (size_t t = 0; t < tid.size(); ++t) tstart[t + 1] += tstart[t];
+      tcand.resize(tstart.back());
+      {
+        std::vector<int> fill(tstart.begin(), tstart.end() - 1);
+        for (int i = 0; i < (int)cands.size(); ++i)
+          for (int k = cands[i].off; k < cands[i].off + cands[i].n; ++k) tcand[fill[cov[k]]++] = i;
+      }
+      std::vector<int> cnt(tid.size(), 0);  // chosen rows covering each triple
+      std::vector<long long> nrow(L + 1, 0), tb(L + 1, 0);
+      for (size_t i = 0; i < cands.size(); ++i)
+        if (chosen[i]) {
+          ++nrow[cands[i].m3];
+          for (int k = cands[i].off; k < cands[i].off + cands[i].n; ++k) ++cnt[cov[k]];
+        }
+      for (int m3 = 0; m3 <= L; ++m3) tb[m3] = count_tiles(block_rows(m3));
+      auto total = [&](const std::vector<long long>& v) {
+        long long x = 0;
+        for (long long y : v) x += y;
+        return x;
+      };
+      for (int round = 0; round < 8; ++round) {
+        bool improved = false;
+        std::vector<int> order;
+        for (int m3 = 0; m3 <= L; ++m3)
+          if (tb[m3] > 0) order.push_back(m3);
+        std::sort(order.begin(), order.end(), [&](int x, int y) {
+          return nrow[x] - 128 * (tb[x] - 1) < nrow[y] - 128 * (tb[y] - 1);
+        });
+        for (int B : order) {
+          const std::vector<char> chosen0 = chosen;
+          const std::vector<int> cnt0 = cnt;
+          const std::vector<long long> nrow0 = nrow;
+          // rows of B, those covering the fewest triples alone first
+          std::vector<std::pair<int, int>> inB;
+          for (int i = 0; i < (int)cands.size(); ++i)
+            if (chosen[i] && cands[i].m3 == B) {
+              int alone = 0;
+              for (int k = cands[i].off; k < cands[i].off + cands[i].n; ++k) alone += cnt[cov[k]] == 1;
+              inB.push_back({alone, i});
+            }
+          std::sort(inB.begin(), inB.end());
+          for (const auto& e : inB) {
+            if (nrow[B] <= 128 * (tb[B] - 1)) break;
+            const int c = e.second;
+            const Cand& cc = cands[c];
+            chosen[c] = 0;
+            --nrow[B];
+            for (int k = cc.off; k < cc.off + cc.n; ++k) --cnt[cov[k]];
+            std::vector<int> added;
+            bool ok = true;
+            for (int k = cc.off; k < cc.off + cc.n && ok; ++k) {
+              const int t0 = cov[k];
+              if (cnt[t0] > 0) continue;
+              // the unchosen candidate outside B (with room) covering the most
+              // of c's still uncovered triples
+              int best = -1, bestv = 0;
+              for (int q = tstart[t0]; q < tstart[t0 + 1]; ++q) {
+                const int c2 = tcand[q];
+                const Cand& d = cands[c2];
+                if (chosen[c2] || d.m3 == B || nrow[d.m3] >= 128 * std::max(tb[d.m3], 1LL)) continue;
+                int v = 0;
+                for (int k2 = d.off; k2 < d.off + d.n; ++k2) v += cnt[cov[k2]] == 0;
+                if (v > bestv) {
+                  bestv = v;
+                  best = c2;
+                }
+              }
+              if (best < 0) {
+                ok = false;
+                break;
+              }
+              chosen[best] = 1;
+              ++nrow[cands[best].m3];
+              for (int k2 = cands[best].off; k2 < cands[best].off + cands[best].n; ++k2) ++cnt[cov[k2]];
+              added.push_back(best);
+            }
+            if (!ok) {  // undo this row's move
+              for (int c2 : added) {
+                chosen[c2] = 0;
+                --nrow[cands[c2].m3];
+                for (int k2 = cands[c2].off; k2 < cands[c2].off + cands[c2].n; ++k2) --cnt[cov[k2]];
+              }
+              chosen[c] = 1;
+              ++nrow[B];
+              for (int k = cc.off; k < cc.off + cc.n; ++k) ++cnt[cov[k]];
+            }
+          }
+          std::vector<long long> tb2(L + 1, 0);
+          for (int m3 = 0; m3 <= L; ++m3) tb2[m3] = count_tiles(block_rows(m3));
+          if (total(tb2) < total(tb)) {
+            tb = tb2;
+            improved = true;
+          } else {
+            chosen = chosen0;
+            cnt = cnt0;
+            nrow = nrow0;
+          }
+        }
+        if (!improved) break;
+      }
+    }
+    for (int m3 = 0; m3 <= L; ++m3) grows[m3] = block_rows(m3);
     if (tc) {
       long long t_half = 0, t_greedy = 0;
       for (int m3 = 0; m3 <= L; ++m3) {
@@ -1307,7 +1429,7 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
       // x-splits per tile: units = ntl * nsplit spread over the CTAs; the three
       // best by their wave fill are timed by the autotuner on the first call
       std::vector<std::pair<double, int>> fill;
-      for (int k = 1; k <= 16 && k <= kblocks; ++k) {
+      for (int k = 1; k <= 32 && k <= kblocks; ++k) {
         const long long units = (long long)ntl * k;
         const long long rounds = (units + ctx->nsm - 1) / ctx->nsm;
         fill.push_back({(double)units / (double)(rounds * ctx->nsm), k});

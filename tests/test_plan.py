@@ -55,10 +55,12 @@ def _needed_triples(lmax, nb):
 
 
 def test_greedy_cover_at_the_benchmark_geometry(sbg):
-    # 3D, lmax 4, 10 bins: the greedy cover halves the bin-half rows
+    # 3D, lmax 4, 10 bins: the greedy cover halves the bin-half rows (65
+    # tiles); trimming then empties the last tile of block m3 = 2 (445 rows,
+    # 4 tiles) by moving the triples its rows cover alone to other blocks
     nt, nr, cov = sbg.sbg_plan4_info(3, 10, 4, sbg.SBG_PREC_BF16X3)
     assert cov == 1
-    assert nt <= 30 and nr <= 3700
+    assert nt <= 29 and nr <= 3700
     # a row of block m3 meets at most nb (lmax - m3 + 1) columns, of which the
     # parity and triangle rules leave at most 3 l3 values at lmax 4: the rows
     # cannot reach every needed triple with fewer than needed / (3 nb) of them
@@ -83,3 +85,10 @@ def test_plan_argument_errors(sbg):
         sbg.sbg_plan4_info(3, 10, 4, 2)  # precision 2 is not built
     with pytest.raises(sbg.SbgError):
         sbg.sbg_plan4_info(2, 10, 4, sbg.SBG_PREC_BF16X3, 1)  # odd parity is a 3D output
+
+
+def test_trimmed_projected_plan(sbg):
+    # 2D, mmax 10, 10 bins: the greedy cover's 27 tiles trim to 25 (block
+    # m3 = 1 was 4 rows over 7 tiles, block m3 = 2 60 rows over 5)
+    nt, nr, cov = sbg.sbg_plan4_info(2, 10, 10, sbg.SBG_PREC_BF16X3)
+    assert cov == 1 and nt <= 25
