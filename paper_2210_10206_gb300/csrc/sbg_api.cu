@@ -750,7 +750,7 @@ sbg_status build_tables4(sbg_context* ctx, Tables4& t, int dim, int nb, int L, b
         BGroup g{};
         g.col0 = col0;
         g.ncols = nc;
-        g.n = ((cplx ? 2 * nc : nc) + 15) & ~15;
+        g.n = ((cplx ? 2 * nc : nc) + 7) & ~7;  // the MMAs take 2n and n rounded up to 16
         // the kernel's B stage holds 2n rows of 128 bytes and its inner
         // accumulator 3n TMEM columns: n <= 64
         if (g.n > 64) return fail(ctx, SBG_ERR_INTERNAL, "tensor-core column group wider than 64");

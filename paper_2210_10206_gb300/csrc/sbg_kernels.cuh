@@ -73,7 +73,7 @@ constexpr int kSimtMaxUniq = 64;    // row singles staged per chunk by the FP32 
 constexpr int kTcEpoch = 256;       // K-blocks between progress checkpoints of the lag limiter
 struct BGroup {
   int col0, ncols;     // columns (global col table)
-  int n;               // B rows of the MMA (multiple of 16, <= 64)
+  int n;               // B rows of each half (hi, lo) of the image (multiple of 8, <= 64)
   int pad;
   long long off;       // byte offset of the image in a K-block's slab
 };

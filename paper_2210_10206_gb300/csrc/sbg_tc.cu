@@ -98,7 +98,8 @@ struct Cfg {
   static_assert(kFlush % kGroups == 0, "ranges must start on group 0's K-blocks");
 };
 // TMEM columns: the inner accumulator [0, 192) of the current range (columns
-// [0, n) collect Ahi Bhi, [n, 2n) Ahi Blo, [2n, 3n) Alo Bhi), the outer
+// [0, n) collect Ahi Bhi, [n, 2n) Ahi Blo, [2n, 3n) Alo Bhi, whose MMA writes
+// up to column 2n + 64 <= 192 when n is rounded up to 16 there), the outer
 // accumulator [192, 256), then the A stages in [256, 512) (per operand stage
 // 64 columns for split BF16, 128 for split TF32).  Alo Bhi has columns of its
 // own so that its MMAs do not wait for the Ahi MMAs before them: the two
@@ -133,9 +134,12 @@ __device__ __forceinline__ Unit unit_of(long long u, int ntiles, int nsplit, lon
   return it;
 }
 
+// n: B rows of each half of the tile's B image (its columns rounded up to 8);
+// the Ahi MMA takes N = 2n (a multiple of 16), the Alo MMA N = n rounded up to
+// 16 (its extra columns meet lo rows of B and are never read)
 __device__ __forceinline__ int n_mma(const Tile4& t, int cplx) {
   const int nb = cplx ? 2 * t.ncols : t.ncols;
-  return (nb + 15) & ~15;
+  return (nb + 7) & ~7;
 }
 
 // Bounded wait for a global progress counter written by other CTAs.
@@ -316,10 +320,10 @@ tc4_kernel(const float* __restrict__ astore, const uint8_t* __restrict__ bimg, c
       for (long long u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
         const Unit it = unit_of(u, ntiles, nsplit, ng);
         const Tile4 tl = tiles[it.tile];
-        const int N = n_mma(tl, cplx);
-        // BF16 inputs, FP32 accumulator, K-major A and B, M = 128; N = n for
-        // Alo Bhi and N = 2n for Ahi [Bhi | Blo]
-        const uint32_t idesc = (1u << 4) | (C::kFmt << 7) | (C::kFmt << 10) | ((uint32_t)(N >> 3) << 17) |
+        const int N = n_mma(tl, cplx), Nlo = (N + 15) & ~15;
+        // BF16 inputs, FP32 accumulator, K-major A and B, M = 128; N = n
+        // rounded up to 16 for Alo Bhi and N = 2n for Ahi [Bhi | Blo]
+        const uint32_t idesc = (1u << 4) | (C::kFmt << 7) | (C::kFmt << 10) | ((uint32_t)(Nlo >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
         const uint32_t idesc2 = (idesc & ~(0x3Fu << 17)) | ((uint32_t)((2 * N) >> 3) << 17);
         for (int kb = 0; kb < it.nk; ++kb) {
@@ -596,7 +600,7 @@ __global__ void bimage_kernel(const float* __restrict__ astore, const float* __r
       (void)kPer;
     }
     uint8_t* img = bimg + xb * img_stride + bg.off * kAtoms + atom * (2 * bg.n * 128);
-    const int pos = (jj ^ (c & 7)) << 4;  // rows c and n + c share c & 7 (n is a multiple of 16)
+    const int pos = (jj ^ (c & 7)) << 4;  // rows c and n + c share c & 7 (n is a multiple of 8)
     *(uint4*)(img + c * 128 + pos) = hi;
     *(uint4*)(img + (bg.n + c) * 128 + pos) = lo;
   }
