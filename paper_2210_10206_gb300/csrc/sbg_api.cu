@@ -162,6 +162,10 @@ struct sbg_context {
   std::string gkey;
   DevBuf gcache;
   bool gcached = false;
+  // projected kernel spectra of the last few slab geometries, most recently
+  // used first (a batch of uneven sizes alternates between them)
+  static constexpr int kG2Cache = 4;
+  std::vector<std::pair<std::string, DevBuf>> g2cache;
   // 4PCF tables of the last few geometries (dim, bins, order, kernel, parity),
   // so that calls alternating between them (e.g. sbg_full and sbg_full_odd on
   // each field) do not rebuild a plan per call; t4 is the current one
@@ -1627,18 +1631,38 @@ sbg_status measure_slab(sbg_context* ctx, const sbg_field2d* fields, int nfld, i
     ST(fft2(ctx, n, +1, LOAD_COMPLEX, dst, dst, nullptr, nullptr, nb, ng, d_tw));
     return SBG_OK;
   };
-  bool cached = ctx->gcached && ctx->gkey == key;
-  if (!cached) {
-    ctx->gcached = false;
-    if (dev_alloc(ctx, ctx->gcache, gbytes) == SBG_OK) {
-      for (int g = 0; g < ngroups; ++g) ST(gen_group(g, (float2*)ctx->gcache.p + (size_t)g * nb * ng));
-      ctx->gcached = true;
-      ctx->gkey = key;
-      cached = true;
+  const float2* gbase = nullptr;
+  {
+    auto& gc = ctx->g2cache;
+    auto it = std::find_if(gc.begin(), gc.end(), [&](const std::pair<std::string, DevBuf>& e) { return e.first == key; });
+    if (it != gc.end()) {
+      std::rotate(gc.begin(), it, it + 1);
+      gbase = (const float2*)gc.front().second.p;
     } else {
-      ctx->err.clear();
+      // a new geometry: make room by evicting the least recently used ones if
+      // the allocation fails (cudaFree waits for the work that reads them)
+      DevBuf b;
+      sbg_status sa = dev_alloc(ctx, b, gbytes);
+      while (sa != SBG_OK && !gc.empty()) {
+        ctx->err.clear();
+        dev_free(ctx, gc.back().second);
+        gc.pop_back();
+        sa = dev_alloc(ctx, b, gbytes);
+      }
+      if (sa == SBG_OK) {
+        for (int g = 0; g < ngroups; ++g) ST(gen_group(g, (float2*)b.p + (size_t)g * nb * ng));
+        gc.insert(gc.begin(), {key, b});
+        if ((int)gc.size() > sbg_context::kG2Cache) {
+          dev_free(ctx, gc.back().second);
+          gc.pop_back();
+        }
+        gbase = (const float2*)gc.front().second.p;
+      } else {
+        ctx->err.clear();  // regenerated per group below
+      }
     }
   }
+  const bool cached = gbase != nullptr;
   rec(ctx, 3);
   // ---- convolutions + 3PCF Grams of every field ----
   const int nsingle = ngroups4 * nb;
@@ -1663,7 +1687,7 @@ sbg_status measure_slab(sbg_context* ctx, const sbg_field2d* fields, int nfld, i
   for (int g = 0; g < ngroups; ++g) {
     const float2* G;
     if (cached) {
-      G = (const float2*)ctx->gcache.p + (size_t)g * nb * ng;
+      G = (const float2*)gbase + (size_t)g * nb * ng;
     } else {
       ST(gen_group(g, d_gtmp));
       G = d_gtmp;
@@ -1860,6 +1884,8 @@ void sbg_destroy(sbg_context* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (auto& kv : ctx->bufs) dev_free(ctx, kv.second);
   dev_free(ctx, ctx->gcache);
+  for (auto& kv : ctx->g2cache) dev_free(ctx, kv.second);
+  ctx->g2cache.clear();
   for (auto& kv : ctx->t4cache) free_tables4(ctx, kv.second);
   ctx->t4cache.clear();
   ctx->t4 = nullptr;
