@@ -230,6 +230,112 @@ fused_fft_z_kernel(int R, int nb, int npack, const float2* __restrict__ tw, cons
   }
 }
 
+// Pass C without packed pairs, in place: the forward transform's outputs,
+// times delta-hat, go back into the exchange buffer in natural order, and the
+// inverse transform starts from there, so no kernel-column buffer is kept
+// (exchange + delta-hat + staging: 72 KB per CTA at N = 512, three CTAs per SM
+// where pass C with the column buffer fits two).  Each thread gathers its
+// points in registers before the buffer is rewritten (six barriers per bin).
+template <int N>
+__global__ void __launch_bounds__(FusedGeo<N>::TLS * FusedGeo<N>::T)
+fused_fft_z_ip_kernel(int R, int nb, const float2* __restrict__ tw, const float2* __restrict__ kin,
+                      const float2* __restrict__ dhat, float2* __restrict__ out, long long ng) {
+  using G = FusedGeo<N>;
+  constexpr int TL = G::TLS, R1 = Plan<N>::R1, R2 = Plan<N>::R2, T = G::T;
+  extern __shared__ float2 smem[];
+  float2* ex = smem;          // exchange layout (n1 R2 + k2) TL + line, or natural k TL + line
+  float2* D = ex + TL * N;    // delta-hat, [k][line]
+  float2* stg = D + TL * N;   // two staging buffers of the support rows, [2][2R + 1][line]
+  const int rows = 2 * R + 1;
+  const int t = threadIdx.x, j = t / TL, li = t % TL;
+  const int xg = blockIdx.x % (N / TL), yy = blockIdx.x / (N / TL);
+  const long long cbase = (long long)yy * N + (long long)xg * TL;  // (0, y, x0)
+  auto sidx = [&](int n1, int k2) { return (n1 * R2 + k2) * TL + li; };
+  auto prefetch = [&](int b) {
+    float2* dst = stg + (b & 1) * rows * TL;
+    const float2* src = kin + (long long)b * ng + cbase;
+    for (int c = t; c < rows * (TL / 2); c += blockDim.x) {
+      const int r = c / (TL / 2), q = c % (TL / 2);
+      const int z = r - R, zi = z < 0 ? z + N : z;
+      cp_async16(dst + r * TL + 2 * q, src + (long long)zi * N * N + 2 * q);
+    }
+    cp_async_commit();
+  };
+  prefetch(0);
+  for (int i = t; i < N * TL; i += blockDim.x) {
+    const int k = i / TL, c = i % TL;
+    D[i] = __ldg(dhat + (long long)k * N * N + cbase + c);
+  }
+  float2 v[R1 / T][R2];
+  float2 u[R2 / T][R1];
+  for (int b = 0; b < nb; ++b) {
+    if (b + 1 < nb) prefetch(b + 1);
+    else cp_async_commit();  // an empty group keeps the wait count uniform
+    cp_async_wait1();         // bin b's rows have landed (this thread's copies)
+    __syncthreads();          // ... everyone's; the previous bin has read the exchange buffer
+    const float2* sb = stg + (b & 1) * rows * TL;
+    // forward, step 1 (from the staged support rows; zero outside |z| <= R)
+#pragma unroll
+    for (int q = 0; q < R1 / T; ++q) {
+      const int n1 = j + T * q;
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) {
+        const int z = min_img(n1 + R1 * n2, N);
+        v[q][n2] = (z >= -R && z <= R) ? sb[(z + R) * TL + li] : make_float2(0.f, 0.f);
+      }
+      Dft<R2, 1>::run(v[q]);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) ex[sidx(n1, k2)] = k2 ? cmul(v[q][k2], __ldg(tw + ((n1 * k2) & (N - 1)))) : v[q][k2];
+    }
+    __syncthreads();
+    // forward, step 2, into registers
+#pragma unroll
+    for (int q = 0; q < R2 / T; ++q) {
+      const int k2 = j + T * q;
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) u[q][n1] = ex[sidx(n1, k2)];
+      Dft<R1, 1>::run(u[q]);
+    }
+    __syncthreads();  // every exchange value read
+    // the product with delta-hat, natural order k = k2 + R2 k1
+#pragma unroll
+    for (int q = 0; q < R2 / T; ++q)
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) {
+        const int k = j + T * q + R2 * k1;
+        ex[k * TL + li] = cmul(u[q][k1], D[k * TL + li]);
+      }
+    __syncthreads();
+    // inverse, step 1, gathered into registers
+#pragma unroll
+    for (int q = 0; q < R1 / T; ++q) {
+      const int n1 = j + T * q;
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) v[q][n2] = ex[(n1 + R1 * n2) * TL + li];
+      Dft<R2, 1>::run(v[q]);
+    }
+    __syncthreads();  // every product read
+#pragma unroll
+    for (int q = 0; q < R1 / T; ++q) {
+      const int n1 = j + T * q;
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) ex[sidx(n1, k2)] = k2 ? cmul(v[q][k2], __ldg(tw + ((n1 * k2) & (N - 1)))) : v[q][k2];
+    }
+    __syncthreads();
+    // inverse, step 2, to the coefficient array
+    float2* oc = out + (long long)b * ng + cbase + li;
+#pragma unroll
+    for (int q = 0; q < R2 / T; ++q) {
+      const int k2 = j + T * q;
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) u[q][n1] = ex[sidx(n1, k2)];
+      Dft<R1, 1>::run(u[q]);
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) oc[(long long)(k2 + R2 * k1) * N * N] = u[q][k1];
+    }
+  }
+}
+
 template <int N>
 cudaError_t launch_n(const FusedGroup& g, cudaStream_t st) {
   using G = FusedGeo<N>;
@@ -246,6 +352,15 @@ cudaError_t launch_n(const FusedGroup& g, cudaStream_t st) {
     dim3 gb((unsigned)((2 * g.R + 1) * (N / G::TLB)), (unsigned)g.nb);
     disk_fft_y_kernel<N><<<gb, G::TLB * G::T, G::SMEM_B, st>>>(g.e2nb, g.R, g.tw, g.kbuf, ng);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (g.npack == 0) {
+    // 2 TLS N exchange / delta-hat values and the staging of at most N rows
+    if ((e = ensure_smem_attr<fused_fft_z_ip_kernel<N>>(2 * G::TLS * N * 8 + 2 * N * G::TLS * 8)) != cudaSuccess)
+      return e;
+    const int smem_ip = 2 * G::TLS * N * 8 + 2 * (2 * g.R + 1) * G::TLS * 8;
+    fused_fft_z_ip_kernel<N><<<(unsigned)(N * (N / G::TLS)), G::TLS * G::T, smem_ip, st>>>(g.R, g.nb, g.tw, g.kbuf,
+                                                                                             g.dhat, g.out, ng);
+    return cudaGetLastError();
   }
   const int smem_c = G::SMEM_C + 2 * (2 * g.R + 1) * G::TLS * 8;
   fused_fft_z_kernel<N><<<(unsigned)(N * (N / G::TLS)), G::TLS * G::T, smem_c, st>>>(
