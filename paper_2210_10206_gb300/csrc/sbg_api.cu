@@ -1334,6 +1334,7 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
     ST(buf(ctx, "klines", std::max<size_t>(lines.size(), 1) * 4, (void**)&d_lines));
     if (nlines) CU(cudaMemcpyAsync(d_lines, lines.data(), lines.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
   }
+  int gpend = -1;  // a stored group whose Gram waits for the next one's
   for (int g = 0; g < ngroups; ++g) {
     const float2* G = nullptr;
     if (cached) {
@@ -1404,12 +1405,21 @@ sbg_status measure(sbg_context* ctx, int dim, const void* field, sbg_dtype dtype
       ST(fft2(ctx, n, +1, LOAD_MUL, nullptr, d_group, G, d_dhat, nbatch, ng, d_tw, fin, nsingle, g * nb, npack));
     }
     if (do3 && g < ngroups3) {
-      double* Sg = d_S + (size_t)g * nb * nb * 2;
-      const float2* src = stored ? d_astore : d_group;
-      const int ns = stored ? nsingle : 0, s0 = stored ? g * nb : 0;
-      if (tcomb) KL(launch_gram_tc(src, ng, nb, d_delta, Sg, ns, s0, tf32, d_err, ctx->nsm, ctx->wait_ns, ctx->stall,
-                                   ctx->stream));
-      else KL(launch_gram3(src, ng, nb, d_delta, Sg, ns, s0, ctx->stream));
+      // two adjacent stored groups are one launch of the tensor-core Gram
+      // (their singles sit side by side in the blocked store)
+      const bool pair = tcomb && stored && 2 * nb <= kGramTcMaxNb;
+      if (pair && gpend < 0 && g + 1 < std::min(ngroups3, ngroups4)) {
+        gpend = g;
+      } else {
+        const int g0 = gpend >= 0 ? gpend : g, k = g - g0 + 1;
+        gpend = -1;
+        double* Sg = d_S + (size_t)g0 * nb * nb * 2;
+        const float2* src = stored ? d_astore : d_group;
+        const int ns = stored ? nsingle : 0, s0 = stored ? g0 * nb : 0;
+        if (tcomb) KL(launch_gram_tc(src, ng, k * nb, d_delta, Sg, ns, s0, tf32, d_err, ctx->nsm, ctx->wait_ns,
+                                     ctx->stall, ctx->stream, 1, 0, k, (long long)nb * nb * 2));
+        else KL(launch_gram3(src, ng, nb, d_delta, Sg, ns, s0, ctx->stream));
+      }
     }
   }
   rec(ctx, 4);
@@ -1684,6 +1694,7 @@ sbg_status measure_slab(sbg_context* ctx, const sbg_field2d* fields, int nfld, i
   const int tf32 = prec == SBG_PREC_TF32X3 ? 1 : 0;
   int* d_err = nullptr;
   if (tcomb) ST(buf(ctx, "err", 16, (void**)&d_err));  // cleared by the caller once per batch
+  int gpend = -1;  // a stored group whose Gram waits for the next one's
   for (int g = 0; g < ngroups; ++g) {
     const float2* G;
     if (cached) {
@@ -1699,14 +1710,22 @@ sbg_status measure_slab(sbg_context* ctx, const sbg_field2d* fields, int nfld, i
     ST(fft2(ctx, n, +1, LOAD_MUL, nullptr, d_group, G, d_dhat, nfld * nbatch, ng, d_tw, fin, nsingle, g * nb, npack,
             nfld, ng));
     if (do3 && g < ngroups3) {
-      double* Sg = d_S + (size_t)g * nb * nb * 2;
-      const float2* src = stored ? d_astore : d_group;
-      const int ns = stored ? nsingle : 0, s0 = stored ? g * nb : 0;
-      if (tcomb)
-        KL(launch_gram_tc(src, ng, nb, d_delta, Sg, ns, s0, tf32, d_err, ctx->nsm, ctx->wait_ns, ctx->stall, st, nfld,
-                          s_stride));
-      else
-        KL(launch_gram3(src, ng, nb, d_delta, Sg, ns, s0, st, nfld, s_stride));
+      // two adjacent stored groups are one launch of the tensor-core Gram
+      const bool pair = tcomb && stored && 2 * nb <= kGramTcMaxNb;
+      if (pair && gpend < 0 && g + 1 < std::min(ngroups3, ngroups4)) {
+        gpend = g;
+      } else {
+        const int g0 = gpend >= 0 ? gpend : g, k = g - g0 + 1;
+        gpend = -1;
+        double* Sg = d_S + (size_t)g0 * nb * nb * 2;
+        const float2* src = stored ? d_astore : d_group;
+        const int ns = stored ? nsingle : 0, s0 = stored ? g0 * nb : 0;
+        if (tcomb)
+          KL(launch_gram_tc(src, ng, k * nb, d_delta, Sg, ns, s0, tf32, d_err, ctx->nsm, ctx->wait_ns, ctx->stall, st,
+                            nfld, s_stride, k, (long long)nb * nb * 2));
+        else
+          KL(launch_gram3(src, ng, nb, d_delta, Sg, ns, s0, st, nfld, s_stride));
+      }
     }
   }
   rec(ctx, 4);

@@ -72,7 +72,7 @@ constexpr int kGGroups = 4;                    // producer groups = operand stag
 constexpr int kGGroupWarps = kGProdWarps / kGGroups;
 constexpr int kGFold0 = 10;
 constexpr int kGFoldThreads = 128;
-constexpr int kGMaxNb = 20;
+constexpr int kGMaxNb = kGramTcMaxNb;
 constexpr int kGMaxR = 2 * kGMaxNb;            // real rows per operand half
 constexpr int kGRaw = 2 * kGGroups;            // raw stages, two per producer group
 constexpr int kGOps = kGGroups;                // operand stages, one per producer group
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict__ a, long long ng, int nb,
                const float* __restrict__ delta,
                double* __restrict__ S, int nsingle, int single0, int* err_flag, unsigned long long wait_ns,
-               int stall, long long s_stride) {
+               int stall, long long s_stride, int gnb, long long g_stride) {
   using C = GramCfg<TF>;
   constexpr int kPts = C::kPts, kFlush = C::kFlush;
   extern __shared__ uint8_t smem_raw[];
@@ -386,15 +386,18 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict
       }
       asm volatile("bar.sync 1, %0;" ::"n"(kGFoldThreads) : "memory");
     }
-    // this CTA's S^{b1 b2} (b1 <= b2) into the output
+    // this CTA's S^{b1 b2} (b1 <= b2) into the output; with groups of gnb bins
+    // stacked into one launch, only pairs within a group, each group's S
+    // g_stride doubles after the previous one's
     if (ok && nranges > 0) {
       for (int p = ft; p < nb * nb; p += kGFoldThreads) {
         const int b1 = p / nb, b2 = p % nb;
-        if (b1 > b2) continue;
+        if (b1 > b2 || b1 / gnb != b2 / gnb) continue;
         const double sre = gacc[(2 * b1) * R + 2 * b2] + gacc[(2 * b1 + 1) * R + 2 * b2 + 1];
         const double sim = gacc[(2 * b1 + 1) * R + 2 * b2] - gacc[(2 * b1) * R + 2 * b2 + 1];
-        atomicAdd(&S[((long long)b1 * nb + b2) * 2 + 0], sre);
-        atomicAdd(&S[((long long)b1 * nb + b2) * 2 + 1], sim);
+        double* Sg = S + (long long)(b1 / gnb) * g_stride + ((long long)(b1 % gnb) * gnb + b2 % gnb) * 2;
+        atomicAdd(&Sg[0], sre);
+        atomicAdd(&Sg[1], sim);
       }
     }
   }
@@ -426,7 +429,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 template <bool TF>
 cudaError_t launch_gram_tc_t(const float2* a, long long ng, int nb, const float* delta, double* S, int nsingle,
                              int single0, int* err, int nsm, unsigned long long wait_ns, int stall, int nfld,
-                             long long s_stride, cudaStream_t st) {
+                             long long s_stride, int gnb, long long g_stride, cudaStream_t st) {
   cudaError_t e = ensure_smem_attr<gram_tc_kernel<TF>>(kGSmem);
   if (e != cudaSuccess) return e;
   constexpr int kPts = GramCfg<TF>::kPts;
@@ -450,7 +453,8 @@ cudaError_t launch_gram_tc_t(const float2* a, long long ng, int nb, const float*
       return cudaErrorInvalidValue;
   }
   gram_tc_kernel<TF><<<dim3(grid, nfld), kGThreads, kGSmem, st>>>(map, (const float*)a, ng, nb, delta, S, nsingle,
-                                                                   single0, err, wait_ns, stall, s_stride);
+                                                                   single0, err, wait_ns, stall, s_stride, gnb,
+                                                                   g_stride);
   return cudaGetLastError();
 }
 
@@ -458,11 +462,15 @@ cudaError_t launch_gram_tc_t(const float2* a, long long ng, int nb, const float*
 
 cudaError_t launch_gram_tc(const float2* a, long long ng, int nb, const float* delta, double* S, int nsingle,
                            int single0, int tf32, int* err, int nsm, unsigned long long wait_ns, int stall,
-                           cudaStream_t st, int nfld, long long s_stride) {
+                           cudaStream_t st, int nfld, long long s_stride, int ngroups, long long g_stride) {
   if (nb < 1 || nb > kGMaxNb || ng % 64 || !err || nfld < 1 || nfld > 65535) return cudaErrorInvalidValue;
+  if (ngroups < 1 || nb % ngroups || (ngroups > 1 && !nsingle)) return cudaErrorInvalidValue;
+  const int gnb = nb / ngroups;
   if (tf32)
-    return launch_gram_tc_t<true>(a, ng, nb, delta, S, nsingle, single0, err, nsm, wait_ns, stall, nfld, s_stride, st);
-  return launch_gram_tc_t<false>(a, ng, nb, delta, S, nsingle, single0, err, nsm, wait_ns, stall, nfld, s_stride, st);
+    return launch_gram_tc_t<true>(a, ng, nb, delta, S, nsingle, single0, err, nsm, wait_ns, stall, nfld, s_stride, gnb,
+                                  g_stride, st);
+  return launch_gram_tc_t<false>(a, ng, nb, delta, S, nsingle, single0, err, nsm, wait_ns, stall, nfld, s_stride, gnb,
+                                 g_stride, st);
 }
 
 }  // namespace sbg

@@ -99,10 +99,14 @@ cudaError_t launch_tc4(const float2* astore, void* bimg, const BGroup* bgroups, 
 // multiple of 64.  *err is set (never cleared) if a bounded wait (wait_ns of
 // the GPU's global timer) expired; stall != 0 withholds its MMA issuer (a
 // host-side test of the timeout path).
-// Slabs of nfld fields as for launch_gram3.
+// Slabs of nfld fields as for launch_gram3.  With ngroups > 1 (blocked store
+// only) the nb singles from single0 are ngroups adjacent groups of nb / ngroups
+// bins: only pairs within one group are kept, group k's S at S + k * g_stride.
+constexpr int kGramTcMaxNb = 20;
 cudaError_t launch_gram_tc(const float2* a, long long ng, int nb, const float* delta, double* S, int nsingle,
                            int single0, int tf32, int* err, int nsm, unsigned long long wait_ns, int stall,
-                           cudaStream_t st, int nfld = 1, long long s_stride = 0);
+                           cudaStream_t st, int nfld = 1, long long s_stride = 0, int ngroups = 1,
+                           long long g_stride = 0);
 
 // ---- kernel generation fused with the FFT (sbg_fft_fused.cu) ----
 // One (l, m) group of nb bins of a 3D grid of side n whose kernel spectra are
