@@ -30,9 +30,10 @@
 //               accumulators (ranges of kFlush K-blocks alternate between them);
 //   warps 2-9   producers, in 4 groups of 2 warps: group g forms the K-blocks
 //               k = g (mod 4) of the CTA, the bf16 / tf32 hi and lo rows of W
-//               and U from a raw stage into operand stage g (128-byte swizzled
-//               K-major tiles), so every stage is refilled by one group in
-//               order and four K-blocks are formed at once;
+//               and U (128-byte swizzled K-major tiles); it reads raw stage
+//               k mod 6 into registers and frees it, then waits for operand
+//               stage k mod 6, so four K-blocks are formed at once while the
+//               MMAs of up to six drain;
 //   warps 10-13 fold: per finished range, read the accumulator (one TMEM lane
 //               quarter each), sum its quadrants in FP32 and add them to an FP64
 //               accumulator in shared memory; at the end add this CTA's S^{b1 b2}
@@ -74,8 +75,11 @@ constexpr int kGFold0 = 10;
 constexpr int kGFoldThreads = 128;
 constexpr int kGMaxNb = kGramTcMaxNb;
 constexpr int kGMaxR = 2 * kGMaxNb;            // real rows per operand half
-constexpr int kGRaw = 2 * kGGroups;            // raw stages, two per producer group
-constexpr int kGOps = kGGroups;                // operand stages, one per producer group
+// K-block k goes through raw stage k % kGRaw and operand stage k % kGOps,
+// formed by producer group k % kGGroups: a stage's next user is another group,
+// so a group never waits for the MMAs of its own previous K-block
+constexpr int kGRaw = 6;                       // raw stages
+constexpr int kGOps = 6;                       // operand stages
 // One operand tile holds 2R <= 80 rows of 128 bytes; A (M = 128) is followed by
 // B, so the MMA's reads of A rows 80..127 fall on B rows (their products land
 // in accumulator rows the fold never reads), and B rows past 2R (read when N
@@ -231,11 +235,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict
       uint32_t issued[kGRaw] = {};
       const uint32_t bytes = (uint32_t)(nb * kPts * 8 + kPts * 4);
       for (int k = 0; k < nk; ++k) {
-        // K-block k belongs to producer group k % 4; its j-th K-block uses raw
-        // stage g + 4 (j mod 2)
-        const int j = k / kGGroups;
-        const int rs = k % kGGroups + kGGroups * (j & 1);
-        if (!mbar_wait(&raw_empty[rs], ((j >> 1) & 1) ^ 1, err, 51, wait_ns)) break;
+        const int rs = k % kGRaw;
+        if (!mbar_wait(&raw_empty[rs], ((k / kGRaw) & 1) ^ 1, err, 51, wait_ns)) break;
         ++issued[rs];
         uint8_t* st = raw + rs * kGRawBytes;
         const long long x0 = (kb0 + k) * kPts;
@@ -269,7 +270,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict
         const int os = k % kGOps;
         const int r = k / kFlush, buf = r & 1;
         if (k % kFlush == 0 && r >= 2 && !mbar_wait(&d_free[buf], ((r >> 1) - 1) & 1, err, 53, wait_ns)) break;
-        if (!mbar_wait(&op_full[os], (k / kGOps) & 1, err, 54, wait_ns)) break;  // stage os = group os
+        if (!mbar_wait(&op_full[os], (k / kGOps) & 1, err, 54, wait_ns)) break;
         tc_fence_after();
         const uint64_t ad = sdesc(su32(ops + os * 2 * kGTile));
         const uint64_t bd = sdesc(su32(ops + os * 2 * kGTile + kGTile));
@@ -286,48 +287,65 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict
     }
   } else if (warp < kGFold0) {
     // ------------------------------------------------------------- producers --
-    const int grp = (warp - kGProd0) / kGGroupWarps;         // producer group = operand stage
+    // A thread's items (bin b, 8-point chunk q) of a K-block are it = ptid +
+    // 64 u; they share q, hence delta.  The raw stage is read into registers
+    // and released before the wait for the operand stage, so the loader can
+    // refill it while the previous MMAs drain.
+    constexpr int kGU = (kGMaxNb * (kPts / 8) + kGGroupWarps * 32 - 1) / (kGGroupWarps * 32);
+    const int grp = (warp - kGProd0) / kGGroupWarps;         // producer group
     const int ptid = tid - (kGProd0 + grp * kGGroupWarps) * 32;  // thread within the group
     const int items = nb * (kPts / 8);
-    const int os = grp;
-    for (int j = 0; j * kGGroups + grp < nk; ++j) {
-      const int rs = grp + kGGroups * (j & 1);
-      if (!warp_wait(&raw_full[rs], (j >> 1) & 1, err, 56, wait_ns) ||
-          !warp_wait(&op_empty[os], (j & 1) ^ 1, err, 57, wait_ns))
-        break;
-      tc_fence_after();
+    const int q = ptid % (kPts / 8);
+    for (int k = grp; k < nk; k += kGGroups) {
+      const int rs = k % kGRaw, os = k % kGOps;
+      if (!warp_wait(&raw_full[rs], (k / kGRaw) & 1, err, 56, wait_ns)) break;
       const uint8_t* st = raw + rs * kGRawBytes;
-      uint8_t* at = ops + os * 2 * kGTile;  // A = [W_hi; W_lo]
-      uint8_t* bt = at + kGTile;            // B = [U_hi | U_lo] (rows of the MMA's N)
-      for (int it = ptid; it < items; it += kGGroupWarps * 32) {
-        const int b = it / (kPts / 8), q = it % (kPts / 8);
-        float re[8], im[8], dl[8];
+      float re[kGU][8], im[kGU][8], dl[8];
+      {
+        const float4 d0 = *(const float4*)(st + kGDeltaOff + q * 32);
+        const float4 d1 = *(const float4*)(st + kGDeltaOff + q * 32 + 16);
+        dl[0] = d0.x; dl[1] = d0.y; dl[2] = d0.z; dl[3] = d0.w; dl[4] = d1.x; dl[5] = d1.y; dl[6] = d1.z; dl[7] = d1.w;
+      }
+#pragma unroll
+      for (int u = 0; u < kGU; ++u) {
+        const int it = ptid + u * kGGroupWarps * 32;
+        if (it >= items) break;
+        const int b = it / (kPts / 8);
         if (nsingle) {
           const float* p = (const float*)(st + (q / 4) * nb * 256 + b * 256) + (q % 4) * 8;
           const float4 r0 = *(const float4*)p, r1 = *(const float4*)(p + 4);
           const float4 i0 = *(const float4*)(p + 32), i1 = *(const float4*)(p + 36);
-          re[0] = r0.x; re[1] = r0.y; re[2] = r0.z; re[3] = r0.w; re[4] = r1.x; re[5] = r1.y; re[6] = r1.z; re[7] = r1.w;
-          im[0] = i0.x; im[1] = i0.y; im[2] = i0.z; im[3] = i0.w; im[4] = i1.x; im[5] = i1.y; im[6] = i1.z; im[7] = i1.w;
+          re[u][0] = r0.x; re[u][1] = r0.y; re[u][2] = r0.z; re[u][3] = r0.w;
+          re[u][4] = r1.x; re[u][5] = r1.y; re[u][6] = r1.z; re[u][7] = r1.w;
+          im[u][0] = i0.x; im[u][1] = i0.y; im[u][2] = i0.z; im[u][3] = i0.w;
+          im[u][4] = i1.x; im[u][5] = i1.y; im[u][6] = i1.z; im[u][7] = i1.w;
         } else {
           const float4* p = (const float4*)(st + (b * kPts + q * 8) * 8);
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const float4 v = p[e];
-            re[2 * e] = v.x; im[2 * e] = v.y; re[2 * e + 1] = v.z; im[2 * e + 1] = v.w;
+            re[u][2 * e] = v.x; im[u][2 * e] = v.y; re[u][2 * e + 1] = v.z; im[u][2 * e + 1] = v.w;
           }
         }
-        {
-          const float4 d0 = *(const float4*)(st + kGDeltaOff + q * 32);
-          const float4 d1 = *(const float4*)(st + kGDeltaOff + q * 32 + 16);
-          dl[0] = d0.x; dl[1] = d0.y; dl[2] = d0.z; dl[3] = d0.w; dl[4] = d1.x; dl[5] = d1.y; dl[6] = d1.z; dl[7] = d1.w;
-        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&raw_empty[rs]);  // its values are in registers
+      if (!warp_wait(&op_empty[os], ((k / kGOps) & 1) ^ 1, err, 57, wait_ns)) break;
+      tc_fence_after();
+      uint8_t* at = ops + os * 2 * kGTile;  // A = [W_hi; W_lo]
+      uint8_t* bt = at + kGTile;            // B = [U_hi | U_lo] (rows of the MMA's N)
+#pragma unroll
+      for (int u = 0; u < kGU; ++u) {
+        const int it = ptid + u * kGGroupWarps * 32;
+        if (it >= items) break;
+        const int b = it / (kPts / 8);
         float wr[8], wi[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          wr[e] = dl[e] * re[e];
-          wi[e] = dl[e] * im[e];
+          wr[e] = dl[e] * re[u][e];
+          wi[e] = dl[e] * im[u][e];
         }
-        const Split8<TF> ur = split8<TF>(re), ui = split8<TF>(im), vr = split8<TF>(wr), vi = split8<TF>(wi);
+        const Split8<TF> ur = split8<TF>(re[u]), ui = split8<TF>(im[u]), vr = split8<TF>(wr), vi = split8<TF>(wi);
         store8<TF>(bt, 2 * b, q, ur.hi);
         store8<TF>(bt, 2 * b + 1, q, ui.hi);
         store8<TF>(bt, R + 2 * b, q, ur.lo);
@@ -340,10 +358,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict
       // generic-proxy stores -> visible to the tensor core, then publish
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&op_full[os]);
-        mbar_arrive(&raw_empty[rs]);
-      }
+      if (lane == 0) mbar_arrive(&op_full[os]);
     }
   } else {
     // ------------------------------------------------------------------ fold --
