@@ -85,12 +85,16 @@ constexpr int kGOps = 6;                       // operand stages
 // in accumulator rows the fold never reads), and B rows past 2R (read when N
 // is padded to 16) were zeroed at the start and are never written.
 constexpr int kGTile = 2 * kGMaxR * 128;
-constexpr int kGDeltaOff = kGMaxNb * 64 * 8;   // delta within a raw stage
-constexpr int kGRawBytes = kGDeltaOff + 256;
+// A raw stage holds every bin's points of a K-block (1024-byte aligned, as the
+// 128-byte swizzle of the tiled copy needs); the stages' delta values follow
+// all of them, 256 bytes each.
+constexpr int kGRawBytes = kGMaxNb * 64 * 8;
+constexpr int kGDeltaBytes = 256;
 constexpr int kGScratch = 2 * kGMaxR * 2 * kGMaxR * 4;  // FP32 rows of one folded range [2R][2R]
 constexpr int kGAcc = kGMaxR * kGMaxR * 8;               // FP64 G [R][R]
 constexpr int kGMeta = 256;                    // barriers, TMEM address, fold flag
-constexpr int kGSmem = kGOps * 2 * kGTile + kGRaw * kGRawBytes + kGScratch + kGAcc + kGMeta + 1024;
+constexpr int kGSmem = kGOps * 2 * kGTile + kGRaw * (kGRawBytes + kGDeltaBytes) + kGScratch + kGAcc + kGMeta + 1024;
+static_assert(kGTile % 1024 == 0 && kGRawBytes % 1024 == 0, "raw stages must stay 1024-byte aligned");
 constexpr int kGTmemCols = 256;                // two accumulators of <= 128 columns
 
 template <bool TF>
@@ -149,13 +153,13 @@ __device__ __forceinline__ void store8(uint8_t* tile, int row, int q, const uint
   }
 }
 
-// 2D TMA tile (box of the tensor map) at element coordinates (x, y) into
+// 3D TMA tile (box of the tensor map) at element coordinates (x, y, z) into
 // shared memory, completing as transaction bytes on `bar`
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-          "r"(su32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar))
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(su32(bar))
       : "memory");
 }
 
@@ -171,7 +175,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* ops = sm;                                   // kGOps x (A tile, B tile)
   uint8_t* raw = ops + kGOps * 2 * kGTile;             // kGRaw raw stages
-  float* scratch = (float*)(raw + kGRaw * kGRawBytes); // [2R][2R] FP32
+  uint8_t* draw = raw + kGRaw * kGRawBytes;             // kGRaw x delta of the stage's points
+  float* scratch = (float*)(draw + kGRaw * kGDeltaBytes); // [2R][2R] FP32
   double* gacc = (double*)((uint8_t*)scratch + kGScratch);  // [R][R] FP64
   uint64_t* bars = (uint64_t*)((uint8_t*)gacc + kGAcc);
   uint64_t* raw_full = bars;                 // kGRaw
@@ -248,10 +253,12 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict
             bulk_g2s(st + j * nb * 256, a + (xb * nsingle + single0) * 64, (uint32_t)nb * 256, &raw_full[rs]);
           }
         } else {
-          // rows b = 0 .. nb-1, floats 2 x0 .. 2 x0 + 2 kPts - 1 (x0 < 2^30 / 2 for the grids here)
-          tma_load_2d(st, &tmap, (int)(2 * x0), fld * nb, &raw_full[rs]);
+          // rows b = 0 .. nb-1, 128-byte lines x0 / 16 .. x0 / 16 + kPts / 16 - 1
+          // (floats 2 x0 .. 2 x0 + 2 kPts - 1), each line's 16-byte chunks
+          // swizzled by its line index within the stage
+          tma_load_3d(st, &tmap, 0, (int)(x0 / 16), fld * nb, &raw_full[rs]);
         }
-        bulk_g2s(st + kGDeltaOff, delta + (long long)fld * ng + x0, (uint32_t)kPts * 4, &raw_full[rs]);
+        bulk_g2s(draw + rs * kGDeltaBytes, delta + (long long)fld * ng + x0, (uint32_t)kPts * 4, &raw_full[rs]);
       }
       // every copy issued has landed before the CTA may exit (also after an error)
       for (int rs = 0; rs < kGRaw; ++rs)
@@ -302,8 +309,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict
       const uint8_t* st = raw + rs * kGRawBytes;
       float re[kGU][8], im[kGU][8], dl[8];
       {
-        const float4 d0 = *(const float4*)(st + kGDeltaOff + q * 32);
-        const float4 d1 = *(const float4*)(st + kGDeltaOff + q * 32 + 16);
+        const uint8_t* dp = draw + rs * kGDeltaBytes + q * 32;
+        const float4 d0 = *(const float4*)dp;
+        const float4 d1 = *(const float4*)(dp + 16);
         dl[0] = d0.x; dl[1] = d0.y; dl[2] = d0.z; dl[3] = d0.w; dl[4] = d1.x; dl[5] = d1.y; dl[6] = d1.z; dl[7] = d1.w;
       }
 #pragma unroll
@@ -320,10 +328,14 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict
           im[u][0] = i0.x; im[u][1] = i0.y; im[u][2] = i0.z; im[u][3] = i0.w;
           im[u][4] = i1.x; im[u][5] = i1.y; im[u][6] = i1.z; im[u][7] = i1.w;
         } else {
-          const float4* p = (const float4*)(st + (b * kPts + q * 8) * 8);
+          // 64 bytes from byte (b kPts + 8 q) 8 of the unswizzled tile: line
+          // L = that / 128, chunks 4 (q & 1) + e, stored at chunk ^ (L & 7);
+          // the 8 threads of a quarter warp hit 8 distinct bank groups
+          const int line = (b * kPts + q * 8) >> 4;
+          const uint8_t* lp = st + line * 128;
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const float4 v = p[e];
+            const float4 v = *(const float4*)(lp + ((((q & 1) * 4 + e) ^ (line & 7)) << 4));
             re[u][2 * e] = v.x; im[u][2 * e] = v.y; re[u][2 * e + 1] = v.z; im[u][2 * e + 1] = v.w;
           }
         }
@@ -454,16 +466,17 @@ cudaError_t launch_gram_tc_t(const float2* a, long long ng, int nb, const float*
   CUtensorMap map;
   std::memset(&map, 0, sizeof map);
   if (!nsingle) {
-    // group buffer [nb][ng] float2 as a 2D float tensor: rows = bins (stride
-    // 8 ng bytes), a box of every row's 2 kPts floats per K-block
+    // group buffer [nb][ng] float2 as a 3D float tensor: 128-byte lines of 32
+    // floats, ng / 16 lines per row, rows = bins (stride 8 ng bytes); a box of
+    // every row's 2 kPts / 32 lines per K-block, 128-byte swizzled
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-    if (!enc || 2 * ng >= (1LL << 31)) return cudaErrorNotSupported;
-    const cuuint64_t dims[2] = {(cuuint64_t)(2 * ng), (cuuint64_t)nb * nfld};
-    const cuuint64_t strides[1] = {(cuuint64_t)ng * 8};
-    const cuuint32_t box[2] = {(cuuint32_t)(2 * kPts), (cuuint32_t)nb};
-    const cuuint32_t estr[2] = {1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)a, dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    if (!enc || ng / 16 >= (1LL << 31)) return cudaErrorNotSupported;
+    const cuuint64_t dims[3] = {32, (cuuint64_t)(ng / 16), (cuuint64_t)nb * nfld};
+    const cuuint64_t strides[2] = {128, (cuuint64_t)ng * 8};
+    const cuuint32_t box[3] = {32, (cuuint32_t)(2 * kPts / 32), (cuuint32_t)nb};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)a, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
