@@ -47,8 +47,12 @@ ALG_BIN_TRIPLES = 220
 #                 (sbg_projected_slices), 10 log bins 2..32, mmax 10
 #   full128_3pcf  128^3 full 3PCF, lmax 2, 20 linear bins 1..31 (a small case of the
 #                 512^3 3PCF's Gram: 20 bins per group, groups larger than L2)
+#   fused512_small  512^3 full 3PCF, lmax 1, 2 bins 2..32..62, in a context with an
+#                 8 GB budget, so that the kernels are generated per group on chip
+#                 (a small case of the 512^3 3PCF's fused FFT passes: same support
+#                 radius, a few GB on the device)
 # The first call of a geometry also builds its plan (kernel spectra, tables).
-WORKLOADS = ("batch64", "full512_3pcf", "full256", "full256_odd", "slices256", "full128_3pcf")
+WORKLOADS = ("batch64", "full512_3pcf", "full256", "full256_odd", "slices256", "full128_3pcf", "fused512_small")
 
 
 def parse():
@@ -457,7 +461,7 @@ def run_workload(args):
     precs = {"bf16x3": sbg.SBG_PREC_BF16X3, "tf32x3": sbg.SBG_PREC_TF32X3, "fp32": sbg.SBG_PREC_FP32}
     prec_name = "bf16x3" if args.prec == "auto" else args.prec
     prec = precs[prec_name]
-    ctx = sbg.Context(0)
+    ctx = sbg.Context(0, budget=(8 << 30) if args.workload == "fused512_small" else 0)
     # the batch and slice workloads write into the previous call's result
     # arrays (out=), as a caller measuring field after field would; their
     # results are large (the slices' zeta4 is 1.8 GB)
@@ -476,6 +480,9 @@ def run_workload(args):
         d = torch.from_numpy(synth.workload_field("full128")).cuda()
         e = list(np.linspace(1.0, 31.0, 21))
         call = lambda: ctx.full(d, e, lmax3=2, prec=prec)
+    elif args.workload == "fused512_small":
+        d = torch.from_numpy(synth.workload_field("full512")).cuda()
+        call = lambda: ctx.full(d, [2.0, 32.0, 62.0], lmax3=1, prec=prec)
     elif args.workload == "full512_3pcf":
         w = synth.WORKLOADS["full512"]
         d = torch.from_numpy(synth.workload_field("full512")).cuda()

@@ -160,6 +160,7 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Pass C: columns (y, x0 .. x0 + TL - 1) along z, every bin of the group: forward
 // transform of the kernel column (planes |z| <= R only), times delta-hat, inverse
@@ -232,10 +233,12 @@ fused_fft_z_kernel(int R, int nb, int npack, const float2* __restrict__ tw, cons
 
 // Pass C without packed pairs, in place: the forward transform's outputs,
 // times delta-hat, go back into the exchange buffer in natural order, and the
-// inverse transform starts from there, so no kernel-column buffer is kept
-// (exchange + delta-hat + staging: 72 KB per CTA at N = 512, three CTAs per SM
-// where pass C with the column buffer fits two).  Each thread gathers its
-// points in registers before the buffer is rewritten (six barriers per bin).
+// inverse transform starts from there, so no kernel-column buffer is kept.
+// One staging buffer of the support rows, refilled for the next bin once the
+// first forward step has read it: exchange + delta-hat + staging is 72 KB per
+// CTA at N = 512 with |z| <= 62, three CTAs per SM (pass C with the column
+// buffer fits two).  Each thread gathers its points in registers before the
+// buffer is rewritten (six barriers per bin).
 template <int N>
 __global__ void __launch_bounds__(FusedGeo<N>::TLS * FusedGeo<N>::T)
 fused_fft_z_ip_kernel(int R, int nb, const float2* __restrict__ tw, const float2* __restrict__ kin,
@@ -245,14 +248,14 @@ fused_fft_z_ip_kernel(int R, int nb, const float2* __restrict__ tw, const float2
   extern __shared__ float2 smem[];
   float2* ex = smem;          // exchange layout (n1 R2 + k2) TL + line, or natural k TL + line
   float2* D = ex + TL * N;    // delta-hat, [k][line]
-  float2* stg = D + TL * N;   // two staging buffers of the support rows, [2][2R + 1][line]
+  float2* stg = D + TL * N;   // staging of the support rows, [2R + 1][line]
   const int rows = 2 * R + 1;
   const int t = threadIdx.x, j = t / TL, li = t % TL;
   const int xg = blockIdx.x % (N / TL), yy = blockIdx.x / (N / TL);
   const long long cbase = (long long)yy * N + (long long)xg * TL;  // (0, y, x0)
   auto sidx = [&](int n1, int k2) { return (n1 * R2 + k2) * TL + li; };
   auto prefetch = [&](int b) {
-    float2* dst = stg + (b & 1) * rows * TL;
+    float2* dst = stg;
     const float2* src = kin + (long long)b * ng + cbase;
     for (int c = t; c < rows * (TL / 2); c += blockDim.x) {
       const int r = c / (TL / 2), q = c % (TL / 2);
@@ -261,19 +264,18 @@ fused_fft_z_ip_kernel(int R, int nb, const float2* __restrict__ tw, const float2
     }
     cp_async_commit();
   };
-  prefetch(0);
-  for (int i = t; i < N * TL; i += blockDim.x) {
-    const int k = i / TL, c = i % TL;
-    D[i] = __ldg(dhat + (long long)k * N * N + cbase + c);
+  // delta-hat of the CTA's lines (16-byte copies, in bin 0's copy group)
+  for (int c = t; c < N * (TL / 2); c += blockDim.x) {
+    const int k = c / (TL / 2), q = c % (TL / 2);
+    cp_async16(D + k * TL + 2 * q, dhat + (long long)k * N * N + cbase + 2 * q);
   }
+  prefetch(0);
   float2 v[R1 / T][R2];
   float2 u[R2 / T][R1];
   for (int b = 0; b < nb; ++b) {
-    if (b + 1 < nb) prefetch(b + 1);
-    else cp_async_commit();  // an empty group keeps the wait count uniform
-    cp_async_wait1();         // bin b's rows have landed (this thread's copies)
+    cp_async_wait0();         // bin b's rows have landed (this thread's copies)
     __syncthreads();          // ... everyone's; the previous bin has read the exchange buffer
-    const float2* sb = stg + (b & 1) * rows * TL;
+    const float2* sb = stg;
     // forward, step 1 (from the staged support rows; zero outside |z| <= R)
 #pragma unroll
     for (int q = 0; q < R1 / T; ++q) {
@@ -288,6 +290,8 @@ fused_fft_z_ip_kernel(int R, int nb, const float2* __restrict__ tw, const float2
       for (int k2 = 0; k2 < R2; ++k2) ex[sidx(n1, k2)] = k2 ? cmul(v[q][k2], __ldg(tw + ((n1 * k2) & (N - 1)))) : v[q][k2];
     }
     __syncthreads();
+    // the staging buffer is read: the next bin's rows land while this one is transformed
+    if (b + 1 < nb) prefetch(b + 1);
     // forward, step 2, into registers
 #pragma unroll
     for (int q = 0; q < R2 / T; ++q) {
@@ -354,11 +358,13 @@ cudaError_t launch_n(const FusedGroup& g, cudaStream_t st) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (g.npack == 0) {
-    // 2 TLS N exchange / delta-hat values and the staging of at most N rows
-    if ((e = ensure_smem_attr<fused_fft_z_ip_kernel<N>>(2 * G::TLS * N * 8 + 2 * N * G::TLS * 8)) != cudaSuccess)
+    // 2 TLS N exchange / delta-hat values and the staging of at most N + 1 rows
+    if ((e = ensure_smem_attr<fused_fft_z_ip_kernel<N>>(2 * G::TLS * N * 8 + (N + 1) * G::TLS * 8)) != cudaSuccess)
       return e;
-    const int smem_ip = 2 * G::TLS * N * 8 + 2 * (2 * g.R + 1) * G::TLS * 8;
-    fused_fft_z_ip_kernel<N><<<(unsigned)(N * (N / G::TLS)), G::TLS * G::T, smem_ip, st>>>(g.R, g.nb, g.tw, g.kbuf,
+    // |z| <= N / 2 covers every plane (z = +-N/2 is the same plane, staged twice)
+    const int rz = g.R < N / 2 ? g.R : N / 2;
+    const int smem_ip = 2 * G::TLS * N * 8 + (2 * rz + 1) * G::TLS * 8;
+    fused_fft_z_ip_kernel<N><<<(unsigned)(N * (N / G::TLS)), G::TLS * G::T, smem_ip, st>>>(rz, g.nb, g.tw, g.kbuf,
                                                                                              g.dhat, g.out, ng);
     return cudaGetLastError();
   }
