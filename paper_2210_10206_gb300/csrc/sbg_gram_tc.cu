@@ -305,6 +305,12 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict
     const int q = ptid % (kPts / 8);
     for (int k = grp; k < nk; k += kGGroups) {
       const int rs = k % kGRaw, os = k % kGOps;
+      // Raw stage rs alternates between two groups (6 stages, 4 groups), and
+      // copies into different stages may land out of order.  So before the
+      // parity wait for K-block k's copy, wait until the stage's previous
+      // K-block (k - kGRaw, the other group's) has been read and released:
+      // its copy has then landed, and raw_full cannot be two phases behind.
+      if (k >= kGRaw && !warp_wait(&raw_empty[rs], ((k / kGRaw) - 1) & 1, err, 59, wait_ns)) break;
       if (!warp_wait(&raw_full[rs], (k / kGRaw) & 1, err, 56, wait_ns)) break;
       const uint8_t* st = raw + rs * kGRawBytes;
       float re[kGU][8], im[kGU][8], dl[8];
