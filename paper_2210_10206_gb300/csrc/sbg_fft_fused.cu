@@ -115,16 +115,21 @@ kgen_fft_x_kernel(int l, int m, double norm_scale, const double* __restrict__ e2
   const bool valid = L < nlines;
   const int row = valid ? lines[L] : 0;
   const int z = min_img(row / N, N), y = min_img(row % N, N);
-  const double yz2 = (double)y * y + (double)z * z;
+  const int yz2 = y * y + z * z;
   const int b = blockIdx.y;
-  const double lo = e2[b], hi = e2[b + 1];
+  // Bin membership e2[b] < |r|^2 <= e2[b+1] in integer arithmetic: for an
+  // integer |r|^2 it holds exactly when floor(e2[b]) < |r|^2 <= floor(e2[b+1])
+  // (|r|^2 <= 3 (N/2)^2 fits an int).  Only the kernel values take FP64, whose
+  // rate on this part is a small fraction of the FP32 rate.
+  const int lo = (int)floor(e2[b]), hi = (int)floor(e2[b + 1]);
   float2* o = out + (long long)b * ng + (long long)row * N;
   line_fft<N, G::TLA, false>(
       ex, tw, li, j,
       [&](int n) {
         const int x = min_img(n, N);
-        const double r2 = yz2 + (double)x * x;
-        return (valid && r2 > lo && r2 <= hi) ? kernel_value(l, m, norm_scale, x, y, z, r2) : make_float2(0.f, 0.f);
+        const int r2 = yz2 + x * x;
+        return (valid && r2 > lo && r2 <= hi) ? kernel_value(l, m, norm_scale, x, y, z, (double)r2)
+                                               : make_float2(0.f, 0.f);
       },
       [&](int k, float2 v) {
         if (valid) o[k] = v;
@@ -144,12 +149,13 @@ disk_fft_y_kernel(double e2nb, int R, const float2* __restrict__ tw, float2* __r
   const int z = p - R, zi = z < 0 ? z + N : z;
   const int x = xg * G::TLB + li;
   float2* col = buf + (long long)blockIdx.y * ng + (long long)zi * N * N + x;
-  const double z2 = (double)z * z;
+  // y^2 + z^2 <= e2nb for integers, in integer arithmetic (as in pass A)
+  const int z2 = z * z, r2max = (int)floor(e2nb);
   line_fft<N, G::TLB, true>(
       ex, tw, li, j,
       [&](int n) {
         const int y = min_img(n, N);
-        return ((double)y * y + z2 <= e2nb) ? col[(long long)n * N] : make_float2(0.f, 0.f);
+        return (y * y + z2 <= r2max) ? col[(long long)n * N] : make_float2(0.f, 0.f);
       },
       [&](int k, float2 v) { col[(long long)k * N] = v; });
 }
