@@ -100,6 +100,9 @@ template <int N> struct FusedGeo {
   static constexpr int SMEM_A = TLA * LSA * 8;
   static constexpr int SMEM_B = TLB * N * 8;
   static constexpr int SMEM_C = 3 * TLS * N * 8;     // exchange, kernel column, delta-hat column
+  // pass C in place: each n1 row of the exchange layout is padded by 8 float2
+  // (16 banks), so the warp's four n1 rows fall on distinct bank halves
+  static constexpr int EXPAD = Plan<N>::R1 * 8;
 };
 
 // Pass A: the x-lines (z, y) of `lines` (row index z N + y), bin b = blockIdx.y:
@@ -241,7 +244,7 @@ fused_fft_z_kernel(int R, int nb, int npack, const float2* __restrict__ tw, cons
 // times delta-hat, go back into the exchange buffer in natural order, and the
 // inverse transform starts from there, so no kernel-column buffer is kept.
 // One staging buffer of the support rows, refilled for the next bin once the
-// first forward step has read it: exchange + delta-hat + staging is 72 KB per
+// first forward step has read it: exchange + delta-hat + staging is 73 KB per
 // CTA at N = 512 with |z| <= 62, three CTAs per SM (pass C with the column
 // buffer fits two).  Each thread gathers its points in registers before the
 // buffer is rewritten (six barriers per bin).
@@ -252,14 +255,14 @@ fused_fft_z_ip_kernel(int R, int nb, const float2* __restrict__ tw, const float2
   using G = FusedGeo<N>;
   constexpr int TL = G::TLS, R1 = Plan<N>::R1, R2 = Plan<N>::R2, T = G::T;
   extern __shared__ float2 smem[];
-  float2* ex = smem;          // exchange layout (n1 R2 + k2) TL + line, or natural k TL + line
-  float2* D = ex + TL * N;    // delta-hat, [k][line]
-  float2* stg = D + TL * N;   // staging of the support rows, [2R + 1][line]
+  float2* ex = smem;                   // exchange layout n1 (R2 TL + 8) + k2 TL + line, or natural k TL + line
+  float2* D = ex + TL * N + G::EXPAD;  // delta-hat, [k][line]
+  float2* stg = D + TL * N;            // staging of the support rows, [2R + 1][line]
   const int rows = 2 * R + 1;
   const int t = threadIdx.x, j = t / TL, li = t % TL;
   const int xg = blockIdx.x % (N / TL), yy = blockIdx.x / (N / TL);
   const long long cbase = (long long)yy * N + (long long)xg * TL;  // (0, y, x0)
-  auto sidx = [&](int n1, int k2) { return (n1 * R2 + k2) * TL + li; };
+  auto sidx = [&](int n1, int k2) { return n1 * (R2 * TL + 8) + k2 * TL + li; };
   auto prefetch = [&](int b) {
     float2* dst = stg;
     const float2* src = kin + (long long)b * ng + cbase;
@@ -364,12 +367,14 @@ cudaError_t launch_n(const FusedGroup& g, cudaStream_t st) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (g.npack == 0) {
-    // 2 TLS N exchange / delta-hat values and the staging of at most N + 1 rows
-    if ((e = ensure_smem_attr<fused_fft_z_ip_kernel<N>>(2 * G::TLS * N * 8 + (N + 1) * G::TLS * 8)) != cudaSuccess)
+    // 2 TLS N exchange / delta-hat values (+ the exchange padding) and the
+    // staging of at most N + 1 rows
+    if ((e = ensure_smem_attr<fused_fft_z_ip_kernel<N>>(2 * G::TLS * N * 8 + G::EXPAD * 8 + (N + 1) * G::TLS * 8)) !=
+        cudaSuccess)
       return e;
     // |z| <= N / 2 covers every plane (z = +-N/2 is the same plane, staged twice)
     const int rz = g.R < N / 2 ? g.R : N / 2;
-    const int smem_ip = 2 * G::TLS * N * 8 + (2 * rz + 1) * G::TLS * 8;
+    const int smem_ip = 2 * G::TLS * N * 8 + G::EXPAD * 8 + (2 * rz + 1) * G::TLS * 8;
     fused_fft_z_ip_kernel<N><<<(unsigned)(N * (N / G::TLS)), G::TLS * G::T, smem_ip, st>>>(rz, g.nb, g.tw, g.kbuf,
                                                                                              g.dhat, g.out, ng);
     return cudaGetLastError();
