@@ -156,6 +156,18 @@ sbg_status sbg_unique_bins(int nbins, int order, int* n_index, int* bins);
  * arguments outside the ranges above. */
 sbg_status sbg_unique_gather(const double* zeta, long long nouter, int nbins, int order, int ncomp, double* out);
 
+/* Zero, in place, the coefficients whose bin combination has two coincident
+ * bins: b1 = b2 for order 3; b1 = b2, b2 = b3 or b1 = b3 for order 4.  These
+ * hold the grid estimator's self-overlap terms, which the paper's application
+ * figure ignores by showing those diagonals as zero (Sec. 4, caption of
+ * Fig. Full_path).  Every other entry is left as it is.
+ *   zeta    : host pointer, nouter blocks of [nbins]^(order - 1) entries of
+ *             ncomp doubles (1: real, 2: re, im), the layout of sbg_unique_gather;
+ *             owned by the caller, modified in place.
+ * Host only.  Errors: SBG_ERR_INVALID_ARG for a NULL pointer, nouter < 0,
+ * nbins outside 1..20, order not 3 or 4, or ncomp not 1 or 2 (zeta untouched). */
+sbg_status sbg_zero_overlap(double* zeta, long long nouter, int nbins, int order, int ncomp);
+
 /* Number of odd-parity Lambda (l1 + l2 + l3 odd, triangle rule, each l <=
  * lmax) for lmax in 0..10: 1 at lmax 1, 4 at lmax 2, 23 at lmax 4. */
 sbg_status sbg_lambda_odd_count(int lmax, int* n_lambda);

@@ -78,6 +78,8 @@ def lib():
         L.sbg_unique_bins.restype = st
         L.sbg_unique_gather.argtypes = [vp, ctypes.c_longlong, i, i, i, vp]
         L.sbg_unique_gather.restype = st
+        L.sbg_zero_overlap.argtypes = [vp, ctypes.c_longlong, i, i, i]
+        L.sbg_zero_overlap.restype = st
         L.sbg_lambda_odd_count.argtypes = [i, ctypes.POINTER(i)]
         L.sbg_lambda_odd_count.restype = st
         L.sbg_lambda_odd_list.argtypes = [i, vp]
@@ -208,6 +210,24 @@ def sbg_unique_gather(zeta, order, ncomp=1):
     if s != SBG_OK:
         raise SbgError(s, "sbg_unique_gather")
     return out
+
+
+def sbg_zero_overlap(zeta, order, ncomp=1):
+    """Zero, in place, the entries of a dense output (the layout of
+    sbg_unique_gather: float64, C-contiguous, writable) whose bins coincide;
+    returns the array."""
+    if not (isinstance(zeta, np.ndarray) and zeta.dtype == np.float64 and zeta.flags.c_contiguous
+            and zeta.flags.writeable):
+        raise ValueError("sbg_zero_overlap needs a writable C-contiguous float64 array")
+    nlead = zeta.ndim - (order - 1) - (1 if ncomp == 2 else 0)
+    if nlead < 0 or len(set(zeta.shape[nlead:nlead + order - 1])) != 1 or (ncomp == 2 and zeta.shape[-1] != 2):
+        raise ValueError("sbg_zero_overlap: trailing axes must be [nbins]^(order - 1) (then 2 when ncomp = 2)")
+    nbins = zeta.shape[nlead]
+    nouter = int(np.prod(zeta.shape[:nlead])) if nlead else 1
+    s = lib().sbg_zero_overlap(zeta.ctypes.data, nouter, nbins, order, ncomp)
+    if s != SBG_OK:
+        raise SbgError(s, "sbg_zero_overlap")
+    return zeta
 
 
 def sbg_lambda_odd_count(lmax):

@@ -84,6 +84,34 @@ def test_unique_gather_picks_the_off_diagonal_entries(sbg):
     assert np.array_equal(u3, np.stack([[z3c[i][t] for t in idx2] for i in range(4)]))
 
 
+def test_zero_overlap_zeroes_exactly_the_coincident_bins(sbg):
+    # the diagonals of the application figure (Sec. 4): b1 = b2 (3PCF), any two
+    # bins equal (4PCF); everything else is left bit for bit
+    rng = np.random.default_rng(5)
+    z4 = rng.normal(size=(3, 6, 6, 6))
+    ref = z4.copy()
+    assert sbg.sbg_zero_overlap(z4, 4) is z4
+    b1, b2, b3 = np.meshgrid(np.arange(6), np.arange(6), np.arange(6), indexing="ij")
+    overlap = (b1 == b2) | (b2 == b3) | (b1 == b3)
+    assert np.all(z4[:, overlap] == 0.0)
+    assert np.array_equal(z4[:, ~overlap], ref[:, ~overlap])
+    assert int((~overlap).sum()) == 6 * 5 * 4  # ordered triples of distinct bins
+    z3c = rng.normal(size=(4, 5, 5, 2))  # complex projected 3PCF layout
+    ref3 = z3c.copy()
+    sbg.sbg_zero_overlap(z3c, 3, ncomp=2)
+    eye = np.eye(5, dtype=bool)
+    assert np.all(z3c[:, eye] == 0.0) and np.array_equal(z3c[:, ~eye], ref3[:, ~eye])
+    # the unique gather never reads the zeroed entries
+    assert np.array_equal(sbg.sbg_unique_gather(z3c, 3, ncomp=2), sbg.sbg_unique_gather(ref3, 3, ncomp=2))
+    L = sbg.lib()
+    assert L.sbg_zero_overlap(None, 1, 5, 3, 1) == -1
+    bad = np.zeros((2, 2))
+    assert L.sbg_zero_overlap(bad.ctypes.data, 1, 2, 5, 1) == -1
+    assert L.sbg_zero_overlap(bad.ctypes.data, 1, 21, 3, 1) == -1
+    with pytest.raises(ValueError):
+        sbg.sbg_zero_overlap(np.zeros((3, 4, 5)), 3)
+
+
 def test_status_strings_and_argument_errors(sbg):
     assert sbg.sbg_status_string(-3) == "SBG_ERR_BIN_RANGE"
     assert sbg.sbg_status_string(0) == "SBG_OK"
