@@ -251,11 +251,13 @@ def run_reference(args):
     if rank != 0:
         return
     field, edges = field_for(0, args.grid)
-    times = []
+    times, walls = [], []
     for _ in range(args.warmup):
         oracle_sample(field, edges, heavy=False)
     for _ in range(args.steps):
+        t0 = time.perf_counter()
         times.append(oracle_sample(field, edges, heavy=False))
+        walls.append(time.perf_counter() - t0)
     per = statistics.mean(t["seconds_per_field"] for t in times)
     v = 1.0 / per
     cb = dict(times[-1])
@@ -267,7 +269,10 @@ def run_reference(args):
            "config": {"workload": f"full 3D 4PCF, {args.grid}^3 float32 lognormal (sigma_G 1.5, P~k^-11/3), "
                                   "lmax 4, 10 linear bins 2..32", "grid": args.grid, "nbins": NB, "lmax4": LMAX4},
            "cpu_baseline": cb, "e2e": {"value": v, "unit": "fields/s", "h2d_bytes_per_step": 0,
-                                       "d2h_bytes_per_step": 0}}
+                                       "d2h_bytes_per_step": 0},
+           # each step times a bounded sample of the field and scales it to one
+           # field: ms_per_step is that per-field figure, this the sample's wall time
+           "extrapolated": True, "sample_wall_ms_per_step": statistics.mean(walls) * 1e3}
     print(json.dumps(out))
 
 
