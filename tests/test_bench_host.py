@@ -40,3 +40,22 @@ def test_profiled_traffic_follows_the_source_hashes(tmp_path, monkeypatch):
     with open(tmp_path / "paper_2210_10206_gb300/csrc/sbg_tc.cu", "a") as f:
         f.write("\n")
     assert bench.profiled_traffic(256) is None
+
+
+def test_algorithmic_flops_of_the_roofline_are_counted_from_the_definition():
+    # the roofline's numerator: the (Lambda, M) terms of the 4PCF sum of Eq. mu
+    # with m3 >= 0 (even Lambda at lmax 4, every M, as Algorithm 6 loops them)
+    # times the bin triples b1 <= b2 <= b3, 4 flops per term and grid point
+    import itertools
+
+    from oracle import sarabande_oracle as O
+    terms = 0
+    for l1, l2, l3 in O.lambda_list(bench.LMAX4):
+        for m1 in range(-l1, l1 + 1):
+            for m2 in range(-l2, l2 + 1):
+                m3 = -(m1 + m2)
+                if 0 <= m3 <= l3:
+                    terms += 1
+    triples = sum(1 for _ in itertools.combinations_with_replacement(range(bench.NB), 3))
+    assert (terms, triples) == (bench.ALG_TERMS_LM, bench.ALG_BIN_TRIPLES) == (490, 220)
+    assert abs(terms * triples * 256 ** 3 * 4 - 7.2343e12) < 1e9
