@@ -48,6 +48,7 @@ def test_algorithmic_flops_of_the_roofline_are_counted_from_the_definition():
     # times the bin triples b1 <= b2 <= b3, 4 flops per term and grid point
     import itertools
 
+    import bench
     from oracle import sarabande_oracle as O
     terms = 0
     for l1, l2, l3 in O.lambda_list(bench.LMAX4):
